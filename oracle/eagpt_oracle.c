@@ -1,0 +1,896 @@
+/* FP64 brute-force oracle for emission-aware 2D Gaussian surfel path tracing.
+ *
+ * TEST INFRASTRUCTURE ONLY: the tests, the smoke check and the CPU baseline
+ * leg of the benchmark are the only users.  It shares no code with the CUDA
+ * path and is deliberately plain: every segment tests every surfel, hits are
+ * collected and sorted, then blended front to back exactly as written in the
+ * paper (Sec. 3.1, Eq. 1-3), the bounce follows Sec. 3.1 "Light Bouncing",
+ * the single-bounce estimator is Eq. 6 and the path tracer is Eq. 8.
+ *
+ * Readings of points the paper leaves open (each also listed in the design
+ * notes): hits are ordered by (t, surfel index); the blend stops after the
+ * hit that takes the transmittance below T_min; Gaussian support is
+ * support_sigma standard deviations; alpha = min(sigma*g, alpha_max) and hits
+ * with alpha < alpha_min are skipped; the blended normal faces the ray origin;
+ * the primary ray goes through the pixel centre and is shared by all samples;
+ * the new origin is offset by bounce_offset along the blended normal; the
+ * cosine sample uses Duff et al.'s orthonormal basis; Russian roulette (not in
+ * the paper) survives with probability min(1, max(beta)); random numbers are
+ * Philox4x32-10 with counter (pixel, sample, bounce, 0) and key = seed.
+ *
+ * Near-boundary flags: every discrete decision records whether its FP64
+ * margin is within an estimate of the error an FP32 evaluation could make
+ * (scaled by fp32_eps); a flagged sample may legitimately differ.
+ */
+#include "eagpt_oracle.h"
+
+#include <math.h>
+#include <pthread.h>
+#include <stdatomic.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define FLAG_K 16.0 /* slack factor on the FP32 error estimates */
+#define ORA_PI 3.14159265358979323846
+
+/* ------------------------------------------------------------------------ */
+/* Philox4x32-10 (Salmon, Moraes, Dror, Shaw: "Parallel random numbers: as    */
+/* easy as 1, 2, 3", SC'11): 10 rounds of the 4x32 S-box with multipliers     */
+/* 0xD2511F53 / 0xCD9E8D57 and Weyl key increments 0x9E3779B9 / 0xBB67AE85.   */
+/* ------------------------------------------------------------------------ */
+void ora_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
+  uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+  uint32_t k0 = key[0], k1 = key[1];
+  for (int round = 0; round < 10; ++round) {
+    if (round > 0) {
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+    uint64_t p0 = (uint64_t)0xD2511F53u * (uint64_t)c0;
+    uint64_t p1 = (uint64_t)0xCD9E8D57u * (uint64_t)c2;
+    uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+    uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+    uint32_t n0 = hi1 ^ c1 ^ k0;
+    uint32_t n2 = hi0 ^ c3 ^ k1;
+    c0 = n0;
+    c1 = lo1;
+    c2 = n2;
+    c3 = lo0;
+  }
+  out[0] = c0;
+  out[1] = c1;
+  out[2] = c2;
+  out[3] = c3;
+}
+
+/* Uniform in [0,1) from the top 24 bits (exactly representable in FP32). */
+static double u24(uint32_t x) { return (double)(x >> 8) * (1.0 / 16777216.0); }
+
+static void draws(uint64_t seed, int64_t pixel, int32_t sample, int32_t bounce, double u[4]) {
+  uint32_t ctr[4] = {(uint32_t)pixel, (uint32_t)sample, (uint32_t)bounce, 0u};
+  uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+  uint32_t o[4];
+  ora_philox4x32_10(ctr, key, o);
+  for (int i = 0; i < 4; ++i) u[i] = u24(o[i]);
+}
+
+/* ------------------------------------------------------------------------ */
+/* small vector helpers                                                      */
+/* ------------------------------------------------------------------------ */
+static double dot3(const double* a, const double* b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+static double norm3(const double* a) { return sqrt(dot3(a, a)); }
+static double amax3(const double* a) {
+  double m = fabs(a[0]);
+  if (fabs(a[1]) > m) m = fabs(a[1]);
+  if (fabs(a[2]) > m) m = fabs(a[2]);
+  return m;
+}
+
+/* Duff, Burgess, Christensen, Hery, Kensler, Liani, Villemin:
+ * "Building an Orthonormal Basis, Revisited" (JCGT 2017). */
+static void onb(const double n[3], double b1[3], double b2[3]) {
+  double sgn = copysign(1.0, n[2]);
+  double a = -1.0 / (sgn + n[2]);
+  double b = n[0] * n[1] * a;
+  b1[0] = 1.0 + sgn * n[0] * n[0] * a;
+  b1[1] = sgn * b;
+  b1[2] = -sgn * n[0];
+  b2[0] = b;
+  b2[1] = sgn + n[1] * n[1] * a;
+  b2[2] = -n[1];
+}
+
+/* Local cosine-weighted direction: radius sqrt(u0), angle 2*pi*u1, height
+ * sqrt(1-u0) (Malley's method; pdf cos(theta)/pi). */
+static void cosine_local(double u0, double u1, double l[3]) {
+  double r = sqrt(u0), phi = 2.0 * ORA_PI * u1;
+  l[0] = r * cos(phi);
+  l[1] = r * sin(phi);
+  l[2] = sqrt(fmax(0.0, 1.0 - u0));
+}
+
+void ora_cosine_direction(const double n[3], double u0, double u1, double out[3]) {
+  double b1[3], b2[3], l[3];
+  onb(n, b1, b2);
+  cosine_local(u0, u1, l);
+  for (int i = 0; i < 3; ++i) out[i] = l[0] * b1[i] + l[1] * b2[i] + l[2] * n[i];
+}
+
+/* ------------------------------------------------------------------------ */
+/* surfel frame (Eq. 1): rotation of the normalised quaternion; t_u, t_v are   */
+/* its first two columns and n = t_u x t_v its third.                         */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+  double p[3], tu[3], tv[3], n[3];
+  double su, sv, sigma;
+  double rho[3], r[3], e;
+} surfel64;
+
+static void quat_frame(const double* q_raw, double tu[3], double tv[3], double n[3]) {
+  double qn = sqrt(q_raw[0] * q_raw[0] + q_raw[1] * q_raw[1] + q_raw[2] * q_raw[2] + q_raw[3] * q_raw[3]);
+  double w = q_raw[0] / qn, x = q_raw[1] / qn, y = q_raw[2] / qn, z = q_raw[3] / qn;
+  tu[0] = 1 - 2 * (y * y + z * z);
+  tu[1] = 2 * (x * y + w * z);
+  tu[2] = 2 * (x * z - w * y);
+  tv[0] = 2 * (x * y - w * z);
+  tv[1] = 1 - 2 * (x * x + z * z);
+  tv[2] = 2 * (y * z + w * x);
+  /* n = t_u x t_v */
+  n[0] = tu[1] * tv[2] - tu[2] * tv[1];
+  n[1] = tu[2] * tv[0] - tu[0] * tv[2];
+  n[2] = tu[0] * tv[1] - tu[1] * tv[0];
+}
+
+static surfel64* load_surfels(const ora_scene* sc) {
+  surfel64* s = (surfel64*)malloc(sizeof(surfel64) * (size_t)(sc->n > 0 ? sc->n : 1));
+  if (!s) return NULL;
+  for (int64_t i = 0; i < sc->n; ++i) {
+    surfel64* g = &s[i];
+    for (int k = 0; k < 3; ++k) {
+      g->p[k] = sc->pos[3 * i + k];
+      g->rho[k] = sc->albedo[3 * i + k];
+      g->r[k] = sc->radiance[3 * i + k];
+    }
+    quat_frame(&sc->quat[4 * i], g->tu, g->tv, g->n);
+    g->su = sc->scale[2 * i];
+    g->sv = sc->scale[2 * i + 1];
+    g->sigma = sc->opacity[i];
+    g->e = sc->emissive[i];
+  }
+  return s;
+}
+
+/* ------------------------------------------------------------------------ */
+/* one segment: brute force over all surfels, sort, blend (Eq. 1-3)           */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+  double t, alpha, g, sg, u, v, d, q, rel_alpha;
+  int64_t idx;
+  int clamped;
+} hit64;
+
+typedef struct {
+  hit64* h;
+  int64_t n, cap;
+} hitbuf;
+
+static int hb_push(hitbuf* b, const hit64* x) {
+  if (b->n == b->cap) {
+    int64_t nc = b->cap ? 2 * b->cap : 256;
+    hit64* nh = (hit64*)realloc(b->h, sizeof(hit64) * (size_t)nc);
+    if (!nh) return -1;
+    b->h = nh;
+    b->cap = nc;
+  }
+  b->h[b->n++] = *x;
+  return 0;
+}
+
+static int hit_cmp(const void* a, const void* b) {
+  const hit64* x = (const hit64*)a;
+  const hit64* y = (const hit64*)b;
+  if (x->t < y->t) return -1;
+  if (x->t > y->t) return 1;
+  return (x->idx < y->idx) ? -1 : (x->idx > y->idx);
+}
+
+typedef struct {
+  const surfel64* s;
+  int64_t n;
+  const ora_params* prm;
+} world;
+
+/* Collects every blended hit of the segment in order (after the stop) into
+ * b, fills seg, returns 0.  mode 1 masks the radiance of non-emitters. */
+static int segment(const world* W, const double O[3], const double w[3], double t_lo, int mode,
+                   hitbuf* b, ora_segment* seg) {
+  const ora_params* prm = W->prm;
+  const double eps = prm->fp32_eps;
+  const double S2 = prm->support_sigma * prm->support_sigma;
+  uint32_t flags = 0;
+  b->n = 0;
+  double Omax = amax3(O);
+  for (int64_t i = 0; i < W->n; ++i) {
+    const surfel64* g = &W->s[i];
+    double d = dot3(w, g->n);
+    if (fabs(d) < 1e-12) continue;
+    double pO[3] = {g->p[0] - O[0], g->p[1] - O[1], g->p[2] - O[2]};
+    double t = dot3(pO, g->n) / d;
+    /* x - p = (O - p) + t w */
+    double dx[3] = {-pO[0] + t * w[0], -pO[1] + t * w[1], -pO[2] + t * w[2]};
+    double u = dot3(dx, g->tu) / g->su;
+    double v = dot3(dx, g->tv) / g->sv;
+    double q = u * u + v * v;
+    /* FP32 error model: coordinates of magnitude L carry ~eps*L absolute
+     * error, amplified by 1/|d| through t and divided by the scale in u, v. */
+    double L = Omax + amax3(g->p) + fabs(t);
+    double dt = FLAG_K * eps * L / fabs(d);
+    double smin = g->su < g->sv ? g->su : g->sv;
+    double du = FLAG_K * eps * L / (fabs(d) * smin);
+    double dq = 2.0 * sqrt(2.0 * (q > S2 ? q : S2)) * du + FLAG_K * eps * S2;
+    double sg = g->sigma * exp(-0.5 * q);
+    double rel_a = sqrt(2.0 * q) * du + FLAG_K * eps;
+    int in_support = q <= S2;
+    int near_support = eps > 0 && fabs(q - S2) <= dq;
+    int ahead = t > t_lo;
+    int near_tlo = eps > 0 && fabs(t - t_lo) <= dt;
+    double alpha = sg < prm->alpha_max ? sg : prm->alpha_max;
+    int big = alpha >= prm->alpha_min;
+    int near_amin = eps > 0 && fabs(sg - prm->alpha_min) <= sg * rel_a + FLAG_K * eps * prm->alpha_min;
+    /* flags only matter for surfels that are, or could be, accepted */
+    if ((in_support || near_support) && (ahead || near_tlo) && (big || near_amin)) {
+      if (near_support) flags |= ORA_FLAG_SUPPORT;
+      if (near_tlo) flags |= ORA_FLAG_TLO;
+      if (near_amin) flags |= ORA_FLAG_AMIN;
+      if (eps > 0 && fabs(sg - prm->alpha_max) <= sg * rel_a + FLAG_K * eps) flags |= ORA_FLAG_AMAX;
+      if (eps > 0 && fabs(d) < FLAG_K * eps) flags |= ORA_FLAG_GRAZE;
+    }
+    if (!(in_support && ahead && big)) continue;
+    hit64 h;
+    h.t = t;
+    h.alpha = alpha;
+    h.g = exp(-0.5 * q);
+    h.sg = sg;
+    h.u = u;
+    h.v = v;
+    h.d = d;
+    h.q = q;
+    h.rel_alpha = rel_a;
+    h.idx = i;
+    h.clamped = sg >= prm->alpha_max;
+    if (hb_push(b, &h)) return -1;
+  }
+  qsort(b->h, (size_t)b->n, sizeof(hit64), hit_cmp);
+
+  memset(seg, 0, sizeof(*seg));
+  double T = 1.0, relT = 0.0;
+  int64_t used = 0;
+  for (int64_t k = 0; k < b->n; ++k) {
+    const hit64* h = &b->h[k];
+    const surfel64* g = &W->s[h->idx];
+    double wgt = T * h->alpha;
+    double sgn = h->d > 0 ? -1.0 : 1.0; /* normal facing the ray origin */
+    double remit = (mode == 1 && !(g->e > prm->tau_E)) ? 0.0 : 1.0;
+    for (int c = 0; c < 3; ++c) {
+      seg->N[c] += wgt * sgn * g->n[c];
+      seg->R[c] += wgt * remit * g->r[c];
+      seg->P[c] += wgt * g->rho[c];
+    }
+    seg->D += wgt * h->t;
+    seg->E += wgt * g->e;
+    T *= (1.0 - h->alpha);
+    relT += h->alpha / (1.0 - h->alpha) * h->rel_alpha;
+    used = k + 1;
+    if (eps > 0) {
+      if (fabs(T - prm->T_min) <= 2.0 * relT * T + FLAG_K * eps * prm->T_min) flags |= ORA_FLAG_TSTOP;
+      if (k + 1 < b->n) {
+        const hit64* h2 = &b->h[k + 1];
+        double L1 = Omax + amax3(g->p) + fabs(h->t);
+        double L2 = Omax + amax3(W->s[h2->idx].p) + fabs(h2->t);
+        if (fabs(h2->t - h->t) <= FLAG_K * eps * (L1 / fabs(h->d) + L2 / fabs(h2->d))) flags |= ORA_FLAG_ORDER;
+      }
+    }
+    if (T < prm->T_min) break;
+  }
+  b->n = used;
+  seg->A = 1.0 - T;
+  seg->n_hits = (int32_t)used;
+  if (used > 0) {
+    double nn = norm3(seg->N);
+    for (int c = 0; c < 3; ++c) seg->Nn[c] = seg->N[c] / nn;
+    seg->Dn = seg->D / seg->A;
+  }
+  if (eps > 0 && fabs(seg->E - prm->tau_E) <= 2.0 * (relT + 4 * FLAG_K * eps) * fabs(seg->E) + FLAG_K * eps)
+    flags |= ORA_FLAG_EMIT;
+  seg->flags = flags;
+  return 0;
+}
+
+int ora_trace_segment(const ora_scene* sc, const ora_params* prm, const double O[3], const double w[3],
+                      double t_lo, int32_t mode, ora_segment* out, int32_t* hit_idx, int32_t max_hits) {
+  surfel64* s = load_surfels(sc);
+  if (!s) return -1;
+  world W = {s, sc->n, prm};
+  hitbuf b = {0, 0, 0};
+  int rc = segment(&W, O, w, t_lo, mode, &b, out);
+  if (hit_idx)
+    for (int32_t k = 0; k < max_hits; ++k) hit_idx[k] = k < b.n ? (int32_t)b.h[k].idx : -1;
+  free(b.h);
+  free(s);
+  return rc;
+}
+
+static void write_rec(const ora_segment* g, double* rec) {
+  rec[0] = g->Nn[0];
+  rec[1] = g->Nn[1];
+  rec[2] = g->Nn[2];
+  rec[3] = g->Dn;
+  rec[4] = g->R[0];
+  rec[5] = g->R[1];
+  rec[6] = g->R[2];
+  rec[7] = g->E;
+  rec[8] = g->P[0];
+  rec[9] = g->P[1];
+  rec[10] = g->P[2];
+  rec[11] = g->A;
+}
+
+/* ------------------------------------------------------------------------ */
+/* camera: OpenCV pinhole ray through the pixel centre                        */
+/* ------------------------------------------------------------------------ */
+static void primary_ray(const ora_camera* cam, int64_t pixel, double O[3], double w[3]) {
+  int64_t x = pixel % cam->width, y = pixel / cam->width;
+  double dc[3] = {((double)x + 0.5 - cam->cx) / cam->fx, ((double)y + 0.5 - cam->cy) / cam->fy, 1.0};
+  for (int r = 0; r < 3; ++r) {
+    O[r] = cam->c2w[4 * r + 3];
+    w[r] = cam->c2w[4 * r + 0] * dc[0] + cam->c2w[4 * r + 1] * dc[1] + cam->c2w[4 * r + 2] * dc[2];
+  }
+  double l = norm3(w);
+  for (int r = 0; r < 3; ++r) w[r] /= l;
+}
+
+/* ------------------------------------------------------------------------ */
+/* threading: a shared atomic work counter over items                        */
+/* ------------------------------------------------------------------------ */
+typedef struct job job;
+typedef int (*item_fn)(job* jb, int64_t item, hitbuf* b);
+struct job {
+  world W;
+  item_fn fn;
+  int64_t n_items;
+  atomic_llong next;
+  atomic_int err;
+  void* ctx;
+};
+
+static void* worker(void* arg) {
+  job* jb = (job*)arg;
+  hitbuf b = {0, 0, 0};
+  for (;;) {
+    int64_t i = atomic_fetch_add(&jb->next, 1);
+    if (i >= jb->n_items) break;
+    if (jb->fn(jb, i, &b)) atomic_store(&jb->err, 1);
+  }
+  free(b.h);
+  return NULL;
+}
+
+static int run_job(job* jb, int32_t n_threads) {
+  if (n_threads < 1) n_threads = 1;
+  if (n_threads > 256) n_threads = 256;
+  atomic_store(&jb->next, 0);
+  atomic_store(&jb->err, 0);
+  pthread_t th[256];
+  int started = 0;
+  for (int i = 1; i < n_threads; ++i) {
+    if (pthread_create(&th[i], NULL, worker, jb) == 0) started = i;
+    else break;
+  }
+  worker(jb);
+  for (int i = 1; i <= started; ++i) pthread_join(th[i], NULL);
+  return atomic_load(&jb->err) ? -1 : 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* batch of rays                                                             */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+  const double* rays;
+  int32_t mode, max_hits;
+  double* out_rec;
+  int32_t* out_nhits;
+  uint32_t* out_flags;
+  int32_t* hit_idx;
+} rays_ctx;
+
+static int rays_item(job* jb, int64_t i, hitbuf* b) {
+  rays_ctx* c = (rays_ctx*)jb->ctx;
+  const double* r = &c->rays[6 * i];
+  ora_segment g;
+  if (segment(&jb->W, r, r + 3, 0.0, c->mode, b, &g)) return -1;
+  write_rec(&g, &c->out_rec[12 * i]);
+  if (c->out_nhits) c->out_nhits[i] = g.n_hits;
+  if (c->out_flags) c->out_flags[i] = g.flags;
+  if (c->hit_idx)
+    for (int32_t k = 0; k < c->max_hits; ++k) c->hit_idx[i * c->max_hits + k] = k < b->n ? (int32_t)b->h[k].idx : -1;
+  return 0;
+}
+
+int ora_trace_rays(const ora_scene* sc, const ora_params* prm, const double* rays, int64_t n_rays,
+                   int32_t mode, double* out_rec, int32_t* out_nhits, uint32_t* out_flags, int32_t* hit_idx,
+                   int32_t max_hits, int32_t n_threads) {
+  surfel64* s = load_surfels(sc);
+  if (!s) return -1;
+  rays_ctx c = {rays, mode, max_hits, out_rec, out_nhits, out_flags, hit_idx};
+  job jb;
+  jb.W.s = s;
+  jb.W.n = sc->n;
+  jb.W.prm = prm;
+  jb.fn = rays_item;
+  jb.n_items = n_rays;
+  jb.ctx = &c;
+  int rc = run_job(&jb, n_threads);
+  free(s);
+  return rc;
+}
+
+/* ------------------------------------------------------------------------ */
+/* primary records                                                           */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+  const ora_camera* cam;
+  int32_t mode;
+  const int32_t* pixels;
+  double* out_rec;
+  uint32_t* out_flags;
+} prim_ctx;
+
+static int prim_item(job* jb, int64_t i, hitbuf* b) {
+  prim_ctx* c = (prim_ctx*)jb->ctx;
+  double O[3], w[3];
+  primary_ray(c->cam, c->pixels[i], O, w);
+  ora_segment g;
+  if (segment(&jb->W, O, w, 0.0, c->mode, b, &g)) return -1;
+  write_rec(&g, &c->out_rec[12 * i]);
+  if (c->out_flags) c->out_flags[i] = g.flags;
+  return 0;
+}
+
+int ora_primary(const ora_scene* sc, const ora_camera* cam, const ora_params* prm, int32_t mode,
+                const int32_t* pixels, int64_t n_pix, double* out_rec, uint32_t* out_flags, int32_t n_threads) {
+  surfel64* s = load_surfels(sc);
+  if (!s) return -1;
+  prim_ctx c = {cam, mode, pixels, out_rec, out_flags};
+  job jb;
+  jb.W.s = s;
+  jb.W.n = sc->n;
+  jb.W.prm = prm;
+  jb.fn = prim_item;
+  jb.n_items = n_pix;
+  jb.ctx = &c;
+  int rc = run_job(&jb, n_threads);
+  free(s);
+  return rc;
+}
+
+/* ------------------------------------------------------------------------ */
+/* rendering (Eq. 6 and Eq. 8)                                               */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+  const ora_camera* cam;
+  int32_t kind, spp, max_bounces, rr_start;
+  uint64_t seed;
+  const int32_t* pixels;
+  double* out_rgb;
+  double* out_samples;
+  uint32_t* out_sample_flags;
+  int64_t* out_segments;
+} render_ctx;
+
+/* relative-error estimate of a segment's blended values for path-level flags */
+static double seg_rel(const ora_segment* g, double eps) { return g->n_hits * FLAG_K * eps * 8.0; }
+
+static int render_item(job* jb, int64_t i, hitbuf* b) {
+  render_ctx* c = (render_ctx*)jb->ctx;
+  const ora_params* prm = jb->W.prm;
+  const double eps = prm->fp32_eps;
+  const int64_t pix = c->pixels[i];
+  const int pt = c->kind == 1;
+  const int seg_mode = pt ? 1 : 0;
+  double O[3], w[3];
+  primary_ray(c->cam, pix, O, w);
+  ora_segment g1;
+  if (segment(&jb->W, O, w, 0.0, seg_mode, b, &g1)) return -1;
+  int64_t segments = 1;
+  double acc[3] = {0, 0, 0};
+  const int emitter1 = g1.E > prm->tau_E;
+  const int reflect_all = prm->emitters_reflect != 0;
+  for (int32_t s = 0; s < c->spp; ++s) {
+    uint32_t sflags = g1.flags;
+    double contrib[3] = {0, 0, 0};
+    if (g1.n_hits == 0) {
+      /* primary miss: no light (no environment) */
+    } else if (emitter1 && !reflect_all) {
+      for (int k = 0; k < 3; ++k) contrib[k] = g1.R[k]; /* Eq. 4: L_o = L_e = R */
+    } else {
+      double beta[3], X[3], Nn[3], rel = seg_rel(&g1, eps);
+      if (reflect_all)
+        for (int k = 0; k < 3; ++k) contrib[k] = g1.R[k];
+      for (int k = 0; k < 3; ++k) {
+        beta[k] = g1.P[k]; /* f cos / p = (P/pi) cos / (cos/pi) = P */
+        X[k] = O[k] + g1.Dn * w[k];
+        Nn[k] = g1.Nn[k];
+      }
+      const int B = pt ? c->max_bounces : 1;
+      for (int32_t k = 1; k <= B; ++k) {
+        double u[4];
+        draws(c->seed, pix, s, k, u);
+        if (pt && !reflect_all && k >= c->rr_start) {
+          double q = beta[0];
+          if (beta[1] > q) q = beta[1];
+          if (beta[2] > q) q = beta[2];
+          if (q > 1.0) q = 1.0;
+          if (eps > 0 && fabs(u[2] - q) <= 2.0 * rel * q + FLAG_K * eps) sflags |= ORA_FLAG_RR;
+          if (!(u[2] < q)) break; /* terminated, contributes 0 */
+          for (int j = 0; j < 3; ++j) beta[j] /= q;
+        }
+        if (eps > 0 && fabs(Nn[2]) <= 8.0 * rel + FLAG_K * eps) sflags |= ORA_FLAG_ONB;
+        double w2[3], O2[3];
+        ora_cosine_direction(Nn, u[0], u[1], w2);
+        for (int j = 0; j < 3; ++j) O2[j] = X[j] + prm->bounce_offset * Nn[j];
+        ora_segment g2;
+        if (segment(&jb->W, O2, w2, 0.0, seg_mode, b, &g2)) return -1;
+        ++segments;
+        sflags |= g2.flags;
+        rel += seg_rel(&g2, eps);
+        if (g2.n_hits == 0) break; /* miss: no light */
+        if (reflect_all) {
+          for (int j = 0; j < 3; ++j) contrib[j] += beta[j] * g2.R[j];
+        } else if (!pt) {
+          /* Eq. 6: the secondary's accumulated radiance is the cache */
+          for (int j = 0; j < 3; ++j) contrib[j] = beta[j] * g2.R[j];
+          break;
+        } else if (g2.E > prm->tau_E) {
+          /* Eq. 8: first emissive vertex within the bounce limit */
+          for (int j = 0; j < 3; ++j) contrib[j] = beta[j] * g2.R[j];
+          break;
+        }
+        if (k == B) break; /* bounce limit exceeded: discarded (or done) */
+        for (int j = 0; j < 3; ++j) {
+          beta[j] *= g2.P[j];
+          X[j] = O2[j] + g2.Dn * w2[j];
+          Nn[j] = g2.Nn[j];
+        }
+      }
+    }
+    for (int k = 0; k < 3; ++k) acc[k] += contrib[k];
+    if (c->out_samples)
+      for (int k = 0; k < 3; ++k) c->out_samples[(i * c->spp + s) * 3 + k] = contrib[k];
+    if (c->out_sample_flags) c->out_sample_flags[i * c->spp + s] = sflags;
+  }
+  for (int k = 0; k < 3; ++k) c->out_rgb[3 * i + k] = c->spp > 0 ? acc[k] / c->spp : 0.0;
+  if (c->out_segments) c->out_segments[i] = segments;
+  return 0;
+}
+
+int ora_render(const ora_scene* sc, const ora_camera* cam, const ora_params* prm, int32_t kind, int32_t spp,
+               int32_t max_bounces, int32_t rr_start, uint64_t seed, const int32_t* pixels, int64_t n_pix,
+               double* out_rgb, double* out_samples, uint32_t* out_sample_flags, int64_t* out_segments,
+               int32_t n_threads) {
+  surfel64* s = load_surfels(sc);
+  if (!s) return -1;
+  render_ctx c = {cam, kind, spp, max_bounces, rr_start, seed, pixels, out_rgb, out_samples, out_sample_flags,
+                  out_segments};
+  job jb;
+  jb.W.s = s;
+  jb.W.n = sc->n;
+  jb.W.prm = prm;
+  jb.fn = render_item;
+  jb.n_items = n_pix;
+  jb.ctx = &c;
+  int rc = run_job(&jb, n_threads);
+  free(s);
+  return rc;
+}
+
+/* ------------------------------------------------------------------------ */
+/* adjoint of the single-bounce render                                       */
+/* ------------------------------------------------------------------------ */
+
+/* dL/d(q_raw) from dL/d(t_u, t_v, n) for the normalised-quaternion frame. */
+static void quat_frame_adjoint(const double* q_raw, const double a[3], const double bb[3], const double c[3],
+                               double dq[4]) {
+  double qn = sqrt(q_raw[0] * q_raw[0] + q_raw[1] * q_raw[1] + q_raw[2] * q_raw[2] + q_raw[3] * q_raw[3]);
+  double w = q_raw[0] / qn, x = q_raw[1] / qn, y = q_raw[2] / qn, z = q_raw[3] / qn;
+  /* n is written as t_u x t_v in the forward pass; for a unit quaternion it
+   * equals the third rotation column, whose partials are used here. */
+  double gw = a[1] * 2 * z - a[2] * 2 * y - bb[0] * 2 * z + bb[2] * 2 * x + c[0] * 2 * y - c[1] * 2 * x;
+  double gx = a[1] * 2 * y + a[2] * 2 * z + bb[0] * 2 * y - bb[1] * 4 * x + bb[2] * 2 * w + c[0] * 2 * z -
+              c[1] * 2 * w - c[2] * 4 * x;
+  double gy = -a[0] * 4 * y + a[1] * 2 * x - a[2] * 2 * w + bb[0] * 2 * x + bb[2] * 2 * z + c[0] * 2 * w +
+              c[1] * 2 * z - c[2] * 4 * y;
+  double gz = -a[0] * 4 * z + a[1] * 2 * w + a[2] * 2 * x - bb[0] * 2 * w - bb[1] * 4 * z + bb[2] * 2 * y +
+              c[0] * 2 * x + c[1] * 2 * y;
+  double qh[4] = {w, x, y, z}, g[4] = {gw, gx, gy, gz};
+  double proj = qh[0] * g[0] + qh[1] * g[1] + qh[2] * g[2] + qh[3] * g[3];
+  for (int k = 0; k < 4; ++k) dq[k] = (g[k] - qh[k] * proj) / qn;
+}
+
+/* gradient record of one surfel touched by a sample */
+typedef struct {
+  int64_t idx;
+  double g[16];
+} grad_entry;
+
+typedef struct {
+  grad_entry* e;
+  int64_t n, cap;
+} gradbuf;
+
+static int gb_push(gradbuf* b, const grad_entry* x) {
+  if (b->n == b->cap) {
+    int64_t nc = b->cap ? 2 * b->cap : 1024;
+    grad_entry* ne = (grad_entry*)realloc(b->e, sizeof(grad_entry) * (size_t)nc);
+    if (!ne) return -1;
+    b->e = ne;
+    b->cap = nc;
+  }
+  b->e[b->n++] = *x;
+  return 0;
+}
+
+/* Adjoint of one segment.  Inputs: the blended hits (in order) and the
+ * segment, adjoints of the raw composites gN, gD, gR, gP, gA (E and the
+ * emissive term carry none).  Accumulates surfel gradients into gb and
+ * dL/dO, dL/dw of the ray. */
+static int segment_adjoint(const world* W, const ora_scene* sc, const double O[3], const double w[3], int mode,
+                           const hitbuf* b, const ora_segment* seg, const double gN[3], double gD,
+                           const double gR[3], const double gP[3], double gA, gradbuf* gb, double dO[3],
+                           double dw[3]) {
+  const ora_params* prm = W->prm;
+  const int64_t nh = b->n;
+  if (nh == 0) return 0;
+  const double Tn = 1.0 - seg->A;
+  /* suffix sums S_i = sum_{j>i} w_j v_j, built back to front */
+  double SN[3] = {0, 0, 0}, SD = 0, SR[3] = {0, 0, 0}, SP[3] = {0, 0, 0};
+  /* transmittance before each hit */
+  double* Tb = (double*)malloc(sizeof(double) * (size_t)nh);
+  if (!Tb) return -1;
+  double T = 1.0;
+  for (int64_t k = 0; k < nh; ++k) {
+    Tb[k] = T;
+    T *= 1.0 - b->h[k].alpha;
+  }
+  for (int64_t k = nh - 1; k >= 0; --k) {
+    const hit64* h = &b->h[k];
+    const surfel64* g = &W->s[h->idx];
+    const double a = h->alpha, Tp = Tb[k], wgt = Tp * a;
+    const double sgn = h->d > 0 ? -1.0 : 1.0;
+    const double remit = (mode == 1 && !(g->e > prm->tau_E)) ? 0.0 : 1.0;
+    double vN[3] = {sgn * g->n[0], sgn * g->n[1], sgn * g->n[2]};
+    double vR[3] = {remit * g->r[0], remit * g->r[1], remit * g->r[2]};
+    /* dL/dalpha_i (Eq. 2): T_{i-1} v_i - S_i / (1 - alpha_i), and dA/dalpha_i */
+    double da = gA * Tn / (1.0 - a);
+    for (int c = 0; c < 3; ++c) {
+      da += gN[c] * (Tp * vN[c] - SN[c] / (1.0 - a));
+      da += gR[c] * (Tp * vR[c] - SR[c] / (1.0 - a));
+      da += gP[c] * (Tp * g->rho[c] - SP[c] / (1.0 - a));
+    }
+    da += gD * (Tp * h->t - SD / (1.0 - a));
+    /* update suffix sums to include hit k for the next (earlier) hit */
+    for (int c = 0; c < 3; ++c) {
+      SN[c] += wgt * vN[c];
+      SR[c] += wgt * vR[c];
+      SP[c] += wgt * g->rho[c];
+    }
+    SD += wgt * h->t;
+
+    grad_entry ge;
+    memset(&ge, 0, sizeof(ge));
+    ge.idx = h->idx;
+    /* albedo and radiance */
+    for (int c = 0; c < 3; ++c) {
+      ge.g[10 + c] = wgt * gP[c];
+      ge.g[13 + c] = wgt * gR[c] * remit;
+    }
+    /* alpha = sigma * g (unclamped) */
+    double dG = 0.0;
+    if (!h->clamped) {
+      ge.g[9] = da * h->g;
+      dG = da * g->sigma;
+    }
+    double du = -dG * h->g * h->u;
+    double dv = -dG * h->g * h->v;
+    double Dx[3] = {O[0] - g->p[0] + h->t * w[0], O[1] - g->p[1] + h->t * w[1], O[2] - g->p[2] + h->t * w[2]};
+    double dDx[3], dtu[3], dtv[3], dn[3];
+    for (int c = 0; c < 3; ++c) {
+      dDx[c] = du * g->tu[c] / g->su + dv * g->tv[c] / g->sv;
+      dtu[c] = du * Dx[c] / g->su;
+      dtv[c] = dv * Dx[c] / g->sv;
+      dn[c] = wgt * gN[c] * sgn; /* from the facing normal */
+    }
+    ge.g[7] = -du * h->u / g->su;
+    ge.g[8] = -dv * h->v / g->sv;
+    double dt = wgt * gD + dot3(dDx, w);
+    /* Dx = O - p + t w */
+    for (int c = 0; c < 3; ++c) {
+      dO[c] += dDx[c];
+      ge.g[c] -= dDx[c];
+      dw[c] += h->t * dDx[c];
+    }
+    /* t = ((p - O) . n) / (w . n) */
+    double pO[3] = {g->p[0] - O[0], g->p[1] - O[1], g->p[2] - O[2]};
+    for (int c = 0; c < 3; ++c) {
+      ge.g[c] += dt * g->n[c] / h->d;
+      dO[c] -= dt * g->n[c] / h->d;
+      dn[c] += dt * (pO[c] - h->t * w[c]) / h->d;
+      dw[c] -= dt * h->t * g->n[c] / h->d;
+    }
+    quat_frame_adjoint(&sc->quat[4 * h->idx], dtu, dtv, dn, &ge.g[3]);
+    if (gb_push(gb, &ge)) {
+      free(Tb);
+      return -1;
+    }
+  }
+  free(Tb);
+  return 0;
+}
+
+/* dL/dn of w' = l0 b1(n) + l1 b2(n) + l2 n (Duff basis, branch held fixed) */
+static void cosine_direction_adjoint(const double n[3], const double l[3], const double dw[3], double dn[3]) {
+  double sgn = copysign(1.0, n[2]);
+  double a = -1.0 / (sgn + n[2]);
+  double a2 = a * a;
+  /* Jacobians of b1 and b2 (rows: components; cols: n_x, n_y, n_z) */
+  double J1[3][3] = {{2 * sgn * n[0] * a, 0, sgn * n[0] * n[0] * a2},
+                     {sgn * n[1] * a, sgn * n[0] * a, sgn * n[0] * n[1] * a2},
+                     {-sgn, 0, 0}};
+  double J2[3][3] = {{n[1] * a, n[0] * a, n[0] * n[1] * a2}, {0, 2 * n[1] * a, n[1] * n[1] * a2}, {0, -1, 0}};
+  for (int c = 0; c < 3; ++c) {
+    dn[c] = l[2] * dw[c];
+    for (int r = 0; r < 3; ++r) dn[c] += l[0] * J1[r][c] * dw[r] + l[1] * J2[r][c] * dw[r];
+  }
+}
+
+typedef struct {
+  const ora_scene* sc;
+  const ora_camera* cam;
+  int32_t spp;
+  uint64_t seed;
+  const int32_t* pixels;
+  const double* dL;
+  uint32_t* out_flags;
+  gradbuf* per_thread;
+  int32_t n_threads;
+} grad_ctx;
+
+static int grad_pixel(const world* W, grad_ctx* c, int64_t i, hitbuf* b1, hitbuf* b2, gradbuf* gb) {
+  const ora_params* prm = W->prm;
+  const int64_t pix = c->pixels[i];
+  const double* gI = &c->dL[3 * i];
+  double O[3], w[3];
+  primary_ray(c->cam, pix, O, w);
+  ora_segment g1;
+  if (segment(W, O, w, 0.0, 0, b1, &g1)) return -1;
+  uint32_t flags = g1.flags;
+  double zero3[3] = {0, 0, 0};
+  double dO[3] = {0, 0, 0}, dw[3] = {0, 0, 0};
+  if (g1.n_hits == 0) {
+    if (c->out_flags) c->out_flags[i] = flags;
+    return 0;
+  }
+  if (g1.E > prm->tau_E) {
+    /* emitter pixel: I = R_1 */
+    int rc = segment_adjoint(W, c->sc, O, w, 0, b1, &g1, zero3, 0.0, gI, zero3, 0.0, gb, dO, dw);
+    if (c->out_flags) c->out_flags[i] = flags;
+    return rc;
+  }
+  const double invS = 1.0 / c->spp;
+  double gP1[3] = {0, 0, 0}, gNn1[3] = {0, 0, 0}, gDn1 = 0.0;
+  double X[3];
+  for (int k = 0; k < 3; ++k) X[k] = O[k] + g1.Dn * w[k];
+  for (int32_t s = 0; s < c->spp; ++s) {
+    double u[4], l[3], w2[3], O2[3];
+    draws(c->seed, pix, s, 1, u);
+    if (prm->fp32_eps > 0 && fabs(g1.Nn[2]) <= 8.0 * seg_rel(&g1, prm->fp32_eps) + FLAG_K * prm->fp32_eps)
+      flags |= ORA_FLAG_ONB;
+    cosine_local(u[0], u[1], l);
+    ora_cosine_direction(g1.Nn, u[0], u[1], w2);
+    for (int k = 0; k < 3; ++k) O2[k] = X[k] + prm->bounce_offset * g1.Nn[k];
+    ora_segment g2;
+    if (segment(W, O2, w2, 0.0, 0, b2, &g2)) return -1;
+    flags |= g2.flags;
+    if (g2.n_hits == 0) continue;
+    double gR2[3];
+    for (int k = 0; k < 3; ++k) {
+      gP1[k] += invS * gI[k] * g2.R[k];
+      gR2[k] = invS * gI[k] * g1.P[k];
+    }
+    double dO2[3] = {0, 0, 0}, dw2[3] = {0, 0, 0};
+    if (segment_adjoint(W, c->sc, O2, w2, 0, b2, &g2, zero3, 0.0, gR2, zero3, 0.0, gb, dO2, dw2)) return -1;
+    /* O2 = O + Dn1 w + eps Nn1 ; w2 = basis(Nn1) l */
+    gDn1 += dot3(dO2, w);
+    double dn[3];
+    cosine_direction_adjoint(g1.Nn, l, dw2, dn);
+    for (int k = 0; k < 3; ++k) gNn1[k] += prm->bounce_offset * dO2[k] + dn[k];
+  }
+  /* normalisations: Nn = N/|N|, Dn = D/A */
+  double nn = norm3(g1.N);
+  double proj = dot3(g1.Nn, gNn1);
+  double gN1[3];
+  for (int k = 0; k < 3; ++k) gN1[k] = (gNn1[k] - g1.Nn[k] * proj) / nn;
+  double gD1 = gDn1 / g1.A;
+  double gA1 = -gDn1 * g1.D / (g1.A * g1.A);
+  if (segment_adjoint(W, c->sc, O, w, 0, b1, &g1, gN1, gD1, zero3, gP1, gA1, gb, dO, dw)) return -1;
+  if (c->out_flags) c->out_flags[i] = flags;
+  return 0;
+}
+
+typedef struct {
+  const world* W;
+  grad_ctx* c;
+  int64_t n_pix;
+  int32_t tid;
+  int err;
+} gthread;
+
+static void* gworker(void* arg) {
+  gthread* t = (gthread*)arg;
+  hitbuf b1 = {0, 0, 0}, b2 = {0, 0, 0};
+  for (int64_t i = t->tid; i < t->n_pix; i += t->c->n_threads)
+    if (grad_pixel(t->W, t->c, i, &b1, &b2, &t->c->per_thread[t->tid])) t->err = 1;
+  free(b1.h);
+  free(b2.h);
+  return NULL;
+}
+
+int ora_single_bounce_grad(const ora_scene* sc, const ora_camera* cam, const ora_params* prm, int32_t spp,
+                           uint64_t seed, const int32_t* pixels, int64_t n_pix, const double* dL_drgb,
+                           double* grad, uint32_t* out_flags, int32_t n_threads) {
+  if (n_threads < 1) n_threads = 1;
+  if (n_threads > 256) n_threads = 256;
+  surfel64* s = load_surfels(sc);
+  if (!s) return -1;
+  world W = {s, sc->n, prm};
+  gradbuf* per = (gradbuf*)calloc((size_t)n_threads, sizeof(gradbuf));
+  gthread* th = (gthread*)calloc((size_t)n_threads, sizeof(gthread));
+  pthread_t* pt = (pthread_t*)calloc((size_t)n_threads, sizeof(pthread_t));
+  if (!per || !th || !pt) {
+    free(s);
+    free(per);
+    free(th);
+    free(pt);
+    return -1;
+  }
+  grad_ctx c = {sc, cam, spp, seed, pixels, dL_drgb, out_flags, per, n_threads};
+  int started = 0;
+  for (int t = 0; t < n_threads; ++t) {
+    th[t].W = &W;
+    th[t].c = &c;
+    th[t].n_pix = n_pix;
+    th[t].tid = t;
+    th[t].err = 0;
+  }
+  for (int t = 1; t < n_threads; ++t) {
+    if (pthread_create(&pt[t], NULL, gworker, &th[t]) != 0) break;
+    started = t;
+  }
+  /* threads that failed to start: do their share here */
+  gworker(&th[0]);
+  for (int t = started + 1; t < n_threads; ++t) gworker(&th[t]);
+  for (int t = 1; t <= started; ++t) pthread_join(pt[t], NULL);
+  int err = 0;
+  for (int t = 0; t < n_threads; ++t) {
+    err |= th[t].err;
+    for (int64_t k = 0; k < per[t].n; ++k) {
+      const grad_entry* e = &per[t].e[k];
+      for (int j = 0; j < 16; ++j) grad[16 * e->idx + j] += e->g[j];
+    }
+    free(per[t].e);
+  }
+  free(per);
+  free(th);
+  free(pt);
+  free(s);
+  return err ? -1 : 0;
+}
