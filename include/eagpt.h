@@ -1,0 +1,243 @@
+/*
+ * eagpt.h -- C ABI of the GB300 surfel path tracer (emission-aware 2D Gaussian
+ * path tracing, arXiv 2601.23065).
+ *
+ * Conventions (all entry points):
+ *  - Every buffer is owned by the caller.  Pointers documented "device" must
+ *    point to memory of the current CUDA device; "host" pointers are read or
+ *    written before the call returns.  The library never allocates device
+ *    memory on these paths; the *_bytes() queries give the sizes to allocate.
+ *  - Work is enqueued on `stream` (a cudaStream_t; NULL = legacy default
+ *    stream) and is asynchronous unless stated otherwise.
+ *  - Argument errors are detected on the host and returned immediately;
+ *    nothing is enqueued then.  Errors found on the device (a traversal stack
+ *    overflow, a bad index) are recorded in a device-side error word and
+ *    reported by eagpt_sync_status().  No C++ exception crosses this ABI.
+ *  - eagpt_last_error() returns a thread-local message for the last failure.
+ *  - Floating-point data is FP32, structure-of-arrays, C-contiguous.
+ */
+#ifndef EAGPT_H
+#define EAGPT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* eagpt_stream_t; /* == cudaStream_t */
+
+typedef enum {
+  EAGPT_OK = 0,
+  EAGPT_ERR_INVALID_ARGUMENT = 1,
+  EAGPT_ERR_OUT_OF_MEMORY = 2,   /* a caller buffer is smaller than required */
+  EAGPT_ERR_CUDA = 3,            /* a CUDA runtime call failed               */
+  EAGPT_ERR_STALE_BVH = 4,       /* BVH built for another scene version      */
+  EAGPT_ERR_TIMEOUT = 5,         /* a bounded wait ran out                   */
+  EAGPT_ERR_NOT_SUPPORTED = 6,
+  EAGPT_ERR_DEVICE_CHECK = 7     /* a device-side check failed               */
+} eagpt_status;
+
+/* ------------------------------------------------------------------------
+ * Scene: n emission-aware 2D Gaussian surfels (Sec. 3.1, Eq. 1 and Eq. 3).
+ *   pos      n x 3  centre p
+ *   quat     n x 4  rotation q = (w, x, y, z); need not be unit length, it is
+ *                   normalised before use; the tangent axes t_u, t_v are the
+ *                   first two columns of its rotation, the normal n = t_u x t_v
+ *   scale    n x 2  in-plane scales (s_u, s_v) > 0
+ *   opacity  n      sigma in [0, 1]
+ *   albedo   n x 3  diffuse albedo rho (BRDF rho/pi, Sec. 3.3 after Eq. 6)
+ *   radiance n x 3  linear radiance r (emitters: emission; others: the
+ *                   radiance cache of Sec. 3.3)
+ *   emissive n      emissive term e in [0, 1] (Eq. 3-4)
+ * All device pointers.  `version` is a caller-maintained counter of scene
+ * edits; eagpt_apply_edit() increments it.
+ * ------------------------------------------------------------------------ */
+typedef struct {
+  int64_t n;
+  const float *pos, *quat, *scale, *opacity, *albedo, *radiance, *emissive;
+  uint64_t version;
+} eagpt_scene;
+
+typedef struct {
+  int64_t n;
+  float *pos, *quat, *scale, *opacity, *albedo, *radiance, *emissive;
+  uint64_t version;
+} eagpt_scene_mut;
+
+/* Gradients, same layout as the scene (device pointers, accumulated +=).
+ * There is no emissive gradient: e enters only through threshold tests. */
+typedef struct {
+  int64_t n;
+  float *pos, *quat, *scale, *opacity, *albedo, *radiance;
+} eagpt_scene_grad;
+
+/* OpenCV pinhole camera: +x right, +y down, +z forward in camera space;
+ * c2w is the row-major 3 x 4 camera-to-world matrix [R | centre].  The ray of
+ * pixel (x, y) goes through the pixel centre (x + 0.5, y + 0.5) and is shared
+ * by all samples of the pixel (the viewing direction is fixed per pixel in
+ * Eq. 6 and Eq. 8).  Pixel linear index = y * width + x. */
+typedef struct {
+  int32_t width, height;
+  float fx, fy, cx, cy;
+  float c2w[12];
+} eagpt_camera;
+
+/* Method constants.  tau_E is printed in the paper (Sec. 3.3, Eq. 4); the
+ * rest are readings of values the paper leaves unstated. */
+typedef struct {
+  float tau_E;          /* emitter threshold on E, Eq. 4 (0.1)                */
+  float T_min;          /* stop blending once transmittance < T_min (1e-3),   */
+                        /* Eq. 2 "preset threshold"                            */
+  float alpha_min;      /* hits with alpha < alpha_min are skipped (1/255)    */
+  float alpha_max;      /* alpha = min(sigma * g, alpha_max) (0.99)           */
+  float support_sigma;  /* Gaussian support u^2 + v^2 <= support^2 (3)        */
+  float bounce_offset;  /* new origin X + offset * N~ (1e-3 scene units)      */
+  int32_t reserved;     /* must be 0                                          */
+} eagpt_params;
+
+void eagpt_default_params(eagpt_params* out);
+
+/* ------------------------------------------------------------------------
+ * Acceleration structure: a software LBVH over the support bounds of the
+ * surfels (the paper uses a hardware BVH, Sec. 4.2; any BVH that returns
+ * every hit gives the same image).  Storage is one caller-owned device
+ * buffer of eagpt_bvh_bytes(n) bytes, 256-byte aligned.  The handle is a
+ * plain host struct filled by eagpt_build_bvh().
+ * ------------------------------------------------------------------------ */
+typedef struct {
+  void* storage;          /* device, caller-owned                          */
+  size_t bytes;
+  int64_t n;              /* surfels                                       */
+  uint64_t scene_version; /* version of the scene it was built/refit for   */
+  float support_sigma;    /* support radius the bounds were built with     */
+  float build_area;       /* surface-area sum at build (refit heuristic)   */
+} eagpt_bvh;
+
+size_t eagpt_bvh_bytes(int64_t n);
+
+/* Builds the BVH of `scene` into `storage` (device) and fills *out (host).
+ * Reads the scene's device arrays; the surface-area sum is read back to the
+ * host, so this call synchronises `stream` once. */
+eagpt_status eagpt_build_bvh(const eagpt_scene* scene, const eagpt_params* params, void* storage,
+                             size_t bytes, eagpt_bvh* out, eagpt_stream_t stream);
+
+/* ------------------------------------------------------------------------
+ * Rendering.  kind: 0 = single-bounce radiance-cache estimator (Eq. 6),
+ * 1 = multi-bounce path tracing (Eq. 8).
+ * Workspace: eagpt_render_workspace_bytes() gives a size that renders all
+ * samples of the camera in as few passes as the size cap allows; any size of
+ * at least eagpt_render_workspace_min_bytes() works (samples are then done
+ * in several passes, with identical results).  256-byte aligned, device.
+ * ------------------------------------------------------------------------ */
+size_t eagpt_render_workspace_bytes(const eagpt_camera* cam, int32_t spp, int32_t kind);
+size_t eagpt_render_workspace_min_bytes(const eagpt_camera* cam, int32_t spp, int32_t kind);
+
+/* Single-bounce render (Eq. 6): a pixel whose primary blend has E > tau_E
+ * shows its blended radiance R (Eq. 4); any other hit pixel shows
+ * P (.) mean_s R(w_s), where w_s is a cosine-weighted direction about the
+ * blended normal from X + offset N~ and R(w_s) is the secondary segment's
+ * blended radiance (the radiance cache, with no emitter test).
+ *   out_rgb     device, H x W x 3
+ *   out_aux     device or NULL, H x W x 12 primary record per pixel:
+ *               N~ (3), D~, R (3), E, P (3), A   (Eq. 3)
+ *   out_samples device or NULL, H x W x spp x 3 per-sample contributions
+ * Random numbers: Philox4x32-10 with counter (pixel, sample, bounce, 0) and
+ * key (seed low, seed high); draws u_j = (x_j >> 8) * 2^-24; u0, u1 pick the
+ * cosine direction (radius sqrt(u0), angle 2 pi u1), u2 the roulette test. */
+eagpt_status eagpt_render_single_bounce(const eagpt_scene* scene, const eagpt_bvh* bvh,
+                                        const eagpt_camera* cam, const eagpt_params* params,
+                                        int32_t spp, uint64_t seed, float* out_rgb, float* out_aux,
+                                        float* out_samples, void* workspace, size_t workspace_bytes,
+                                        eagpt_stream_t stream);
+
+/* Path-traced render (Eq. 8): paths leave the pixel's primary vertex and
+ * bounce (cosine-weighted, throughput *= P per vertex) until a vertex with
+ * E > tau_E, whose blended radiance (non-emitter radiance dropped, Sec. 3.4)
+ * is the sample's value; a path that exceeds max_bounces reflections or
+ * misses the scene contributes 0.  From bounce rr_start_bounce on, Russian
+ * roulette keeps a path with probability q = min(1, max(throughput)) and
+ * divides the throughput by q (not in the paper; rr_start > max_bounces
+ * disables it).  max_bounces = 0 renders emitters only.
+ * Buffers as in eagpt_render_single_bounce.  out_stats (device or NULL,
+ * int64[16], accumulated +=; a counting variant of the kernels runs):
+ *   [0] primary segments  [1] secondary segments  [2] paths started
+ *   [3..6]  secondary segments: blended hits, BVH nodes visited, surfel
+ *           tests, traversal rounds
+ *   [8..11] the same for the primary segments. */
+eagpt_status eagpt_render_path_traced(const eagpt_scene* scene, const eagpt_bvh* bvh,
+                                      const eagpt_camera* cam, const eagpt_params* params, int32_t spp,
+                                      int32_t max_bounces, int32_t rr_start_bounce, uint64_t seed,
+                                      float* out_rgb, float* out_aux, float* out_samples,
+                                      int64_t* out_stats, void* workspace, size_t workspace_bytes,
+                                      eagpt_stream_t stream);
+
+/* ------------------------------------------------------------------------
+ * Adjoint of the single-bounce render (Eq. 6; differentiable 2D Gaussian ray
+ * tracing, Sec. 3.2-3.3, with the gradient of Eq. 7 extended from the albedo
+ * to every surfel parameter).  For L = sum_p sum_c dL_drgb[p][c] * I[p][c]
+ * with I the image eagpt_render_single_bounce() renders with the same
+ * arguments, adds dL/dtheta to `grads` (device arrays, accumulated +=):
+ * through both segments, through the bounce origin X(D~) + offset N~ and the
+ * cosine direction w'(N~); discrete decisions (support, alpha limits, the
+ * transmittance stop, tau_E) are held fixed.  Hit lists are recomputed (every
+ * segment is re-traced), so the workspace is O(pixels x samples per pass).
+ *   dL_drgb   device, H x W x 3
+ *   workspace eagpt_render_backward_workspace_bytes() (full speed) or at
+ *             least eagpt_render_backward_workspace_min_bytes(); 256-byte
+ *             aligned
+ * FP32 atomics: the summation order of the gradients is not deterministic. */
+size_t eagpt_render_backward_workspace_bytes(const eagpt_camera* cam, int32_t spp);
+size_t eagpt_render_backward_workspace_min_bytes(const eagpt_camera* cam, int32_t spp);
+eagpt_status eagpt_render_single_bounce_backward(const eagpt_scene* scene, const eagpt_bvh* bvh,
+                                                 const eagpt_camera* cam, const eagpt_params* params,
+                                                 int32_t spp, uint64_t seed, const float* dL_drgb,
+                                                 const eagpt_scene_grad* grads, void* workspace,
+                                                 size_t workspace_bytes, eagpt_stream_t stream);
+
+/* ------------------------------------------------------------------------
+ * Tracing of caller rays (the per-segment operation of Eq. 1-3).
+ *   rays     device, n_rays x 6: origin (3), unit direction (3); hits need
+ *            t > 0
+ *   mode     0: radiance as stored; 1: radiance of non-emitters dropped
+ *   out_rec  device, n_rays x 12: N~ (3), D~, R (3), E, P (3), A
+ *   out_hits device or NULL, n_rays x max_hits blended surfel indices in
+ *            blending order (-1 padded); out_nhits device or NULL, n_rays
+ * ------------------------------------------------------------------------ */
+eagpt_status eagpt_trace_rays(const eagpt_scene* scene, const eagpt_bvh* bvh, const eagpt_params* params,
+                              int32_t mode, const float* rays, int64_t n_rays, float* out_rec,
+                              int32_t* out_hits, int32_t max_hits, int32_t* out_nhits,
+                              eagpt_stream_t stream);
+
+/* ------------------------------------------------------------------------
+ * Launch accounting (host side, no device memory).
+ * eagpt_launch_count(): kernels this library has launched in this process.
+ * eagpt_profile_begin(): from now on, CUDA events are recorded on the
+ *   launching stream around every kernel launch of this library.
+ * eagpt_profile_end(): waits for those events, writes up to `capacity`
+ *   per-kernel aggregates (host array) and stops recording; *n_out gets the
+ *   number of distinct kernels.  Not a paper operation: measurement only.
+ * ------------------------------------------------------------------------ */
+typedef struct {
+  char name[32];
+  int64_t launches;
+  double total_ms;
+} eagpt_kernel_time;
+
+int64_t eagpt_launch_count(void);
+eagpt_status eagpt_profile_begin(void);
+eagpt_status eagpt_profile_end(eagpt_kernel_time* out, int32_t capacity, int32_t* n_out);
+
+/* ------------------------------------------------------------------------
+ * Device status: synchronises `stream`, returns and clears the device-side
+ * error word (EAGPT_ERR_DEVICE_CHECK when any kernel recorded an error).
+ * ------------------------------------------------------------------------ */
+eagpt_status eagpt_sync_status(eagpt_stream_t stream);
+const char* eagpt_last_error(void);
+const char* eagpt_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* EAGPT_H */

@@ -23,7 +23,7 @@ _lib = None
 
 FLAGS = {
     "support": 1 << 0, "tlo": 1 << 1, "amin": 1 << 2, "amax": 1 << 3, "order": 1 << 4,
-    "tstop": 1 << 5, "emit": 1 << 6, "rr": 1 << 7, "onb": 1 << 8, "graze": 1 << 9,
+    "tstop": 1 << 5, "emit": 1 << 6, "rr": 1 << 7, "onb": 1 << 8, "graze": 1 << 9, "cond": 1 << 10,
 }
 FP32_EPS = 2.0 ** -24
 
@@ -54,14 +54,15 @@ class _Params(ctypes.Structure):
     _fields_ = [("tau_E", ctypes.c_double), ("T_min", ctypes.c_double), ("alpha_min", ctypes.c_double),
                 ("alpha_max", ctypes.c_double), ("support_sigma", ctypes.c_double),
                 ("bounce_offset", ctypes.c_double), ("emitters_reflect", ctypes.c_int32),
-                ("fp32_eps", ctypes.c_double)]
+                ("fp32_eps", ctypes.c_double), ("cond_tol", ctypes.c_double)]
 
 
 class _Segment(ctypes.Structure):
     _fields_ = [("N", ctypes.c_double * 3), ("D", ctypes.c_double), ("R", ctypes.c_double * 3),
                 ("E", ctypes.c_double), ("P", ctypes.c_double * 3), ("A", ctypes.c_double),
                 ("Nn", ctypes.c_double * 3), ("Dn", ctypes.c_double), ("n_hits", ctypes.c_int32),
-                ("flags", ctypes.c_uint32)]
+                ("flags", ctypes.c_uint32), ("eR", ctypes.c_double), ("eP", ctypes.c_double),
+                ("eE", ctypes.c_double), ("eN", ctypes.c_double), ("eD", ctypes.c_double)]
 
 
 def _load():
@@ -104,14 +105,15 @@ class Params:
     stated readings of constants the paper does not give."""
 
     def __init__(self, tau_E=0.1, T_min=1e-3, alpha_min=1.0 / 255.0, alpha_max=0.99, support_sigma=3.0,
-                 bounce_offset=1e-3, emitters_reflect=False, fp32_eps=FP32_EPS):
+                 bounce_offset=1e-3, emitters_reflect=False, fp32_eps=FP32_EPS, cond_tol=2.5e-5):
         self.tau_E, self.T_min, self.alpha_min, self.alpha_max = tau_E, T_min, alpha_min, alpha_max
         self.support_sigma, self.bounce_offset = support_sigma, bounce_offset
-        self.emitters_reflect, self.fp32_eps = emitters_reflect, fp32_eps
+        self.emitters_reflect, self.fp32_eps, self.cond_tol = emitters_reflect, fp32_eps, cond_tol
 
     def _c(self):
         return _Params(self.tau_E, self.T_min, self.alpha_min, self.alpha_max, self.support_sigma,
-                       self.bounce_offset, 1 if self.emitters_reflect else 0, self.fp32_eps)
+                       self.bounce_offset, 1 if self.emitters_reflect else 0, self.fp32_eps,
+                       self.cond_tol if self.fp32_eps > 0 else 0.0)
 
 
 class OracleScene:

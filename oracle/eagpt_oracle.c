@@ -30,7 +30,8 @@
 #include <stdlib.h>
 #include <string.h>
 
-#define FLAG_K 16.0 /* slack factor on the FP32 error estimates */
+#define ERR_C 3.0   /* FP32 roundings assumed per estimated quantity */
+#define FLAG_K 4.0  /* slack applied to the estimates at each decision */
 #define ORA_PI 3.14159265358979323846
 
 /* ------------------------------------------------------------------------ */
@@ -164,7 +165,7 @@ static surfel64* load_surfels(const ora_scene* sc) {
 /* one segment: brute force over all surfels, sort, blend (Eq. 1-3)           */
 /* ------------------------------------------------------------------------ */
 typedef struct {
-  double t, alpha, g, sg, u, v, d, q, rel_alpha;
+  double t, alpha, g, sg, u, v, d, q, rel_alpha, dt;
   int64_t idx;
   int clamped;
 } hit64;
@@ -201,9 +202,18 @@ typedef struct {
 } world;
 
 /* Collects every blended hit of the segment in order (after the stop) into
- * b, fills seg, returns 0.  mode 1 masks the radiance of non-emitters. */
-static int segment(const world* W, const double O[3], const double w[3], double t_lo, int mode,
-                   hitbuf* b, ora_segment* seg) {
+ * b, fills seg, returns 0.  mode 1 masks the radiance of non-emitters.
+ *
+ * eO, eW: first-order estimates of the error an FP32 evaluation carries in
+ * the ray origin (absolute length) and direction (radians) when it reaches
+ * this segment.  Together with the segment's own FP32 rounding (fp32_eps
+ * times the magnitudes involved, times the slack FLAG_K) they give the error
+ * of each hit's local coordinates, hence of its alpha, and the near-boundary
+ * margins of every decision; the segment's outputs carry the propagated
+ * errors (eN, eD, eR, eP, eE) to the next bounce.  Only the flags and these
+ * estimates depend on them; the traced values do not. */
+static int segment(const world* W, const double O[3], const double w[3], double t_lo, int mode, double eO,
+                   double eW, hitbuf* b, ora_segment* seg) {
   const ora_params* prm = W->prm;
   const double eps = prm->fp32_eps;
   const double S2 = prm->support_sigma * prm->support_sigma;
@@ -221,28 +231,30 @@ static int segment(const world* W, const double O[3], const double w[3], double 
     double u = dot3(dx, g->tu) / g->su;
     double v = dot3(dx, g->tv) / g->sv;
     double q = u * u + v * v;
-    /* FP32 error model: coordinates of magnitude L carry ~eps*L absolute
-     * error, amplified by 1/|d| through t and divided by the scale in u, v. */
+    /* position error at the hit: own rounding of coordinates of magnitude L
+     * plus the incoming ray error; 1/|d| through the plane intersection,
+     * divided by the scale in u, v */
     double L = Omax + amax3(g->p) + fabs(t);
-    double dt = FLAG_K * eps * L / fabs(d);
+    double ep = eps > 0 ? ERR_C * eps * L + eO + fabs(t) * eW : 0.0;
+    double dt = ep / fabs(d);
     double smin = g->su < g->sv ? g->su : g->sv;
-    double du = FLAG_K * eps * L / (fabs(d) * smin);
-    double dq = 2.0 * sqrt(2.0 * (q > S2 ? q : S2)) * du + FLAG_K * eps * S2;
+    double du = ep / (fabs(d) * smin);
+    double dq = 2.0 * sqrt(2.0 * (q > S2 ? q : S2)) * du + ERR_C * eps * S2;
     double sg = g->sigma * exp(-0.5 * q);
-    double rel_a = sqrt(2.0 * q) * du + FLAG_K * eps;
+    double rel_a = sqrt(2.0 * q) * du + ERR_C * eps;
     int in_support = q <= S2;
-    int near_support = eps > 0 && fabs(q - S2) <= dq;
+    int near_support = eps > 0 && fabs(q - S2) <= FLAG_K * dq;
     int ahead = t > t_lo;
-    int near_tlo = eps > 0 && fabs(t - t_lo) <= dt;
+    int near_tlo = eps > 0 && fabs(t - t_lo) <= FLAG_K * dt;
     double alpha = sg < prm->alpha_max ? sg : prm->alpha_max;
     int big = alpha >= prm->alpha_min;
-    int near_amin = eps > 0 && fabs(sg - prm->alpha_min) <= sg * rel_a + FLAG_K * eps * prm->alpha_min;
+    int near_amin = eps > 0 && fabs(sg - prm->alpha_min) <= FLAG_K * (sg * rel_a + ERR_C * eps * prm->alpha_min);
     /* flags only matter for surfels that are, or could be, accepted */
     if ((in_support || near_support) && (ahead || near_tlo) && (big || near_amin)) {
       if (near_support) flags |= ORA_FLAG_SUPPORT;
       if (near_tlo) flags |= ORA_FLAG_TLO;
       if (near_amin) flags |= ORA_FLAG_AMIN;
-      if (eps > 0 && fabs(sg - prm->alpha_max) <= sg * rel_a + FLAG_K * eps) flags |= ORA_FLAG_AMAX;
+      if (eps > 0 && fabs(sg - prm->alpha_max) <= FLAG_K * (sg * rel_a + ERR_C * eps)) flags |= ORA_FLAG_AMAX;
       if (eps > 0 && fabs(d) < FLAG_K * eps) flags |= ORA_FLAG_GRAZE;
     }
     if (!(in_support && ahead && big)) continue;
@@ -255,7 +267,8 @@ static int segment(const world* W, const double O[3], const double w[3], double 
     h.v = v;
     h.d = d;
     h.q = q;
-    h.rel_alpha = rel_a;
+    h.rel_alpha = sg >= prm->alpha_max ? ERR_C * eps : rel_a;
+    h.dt = dt;
     h.idx = i;
     h.clamped = sg >= prm->alpha_max;
     if (hb_push(b, &h)) return -1;
@@ -282,12 +295,10 @@ static int segment(const world* W, const double O[3], const double w[3], double 
     relT += h->alpha / (1.0 - h->alpha) * h->rel_alpha;
     used = k + 1;
     if (eps > 0) {
-      if (fabs(T - prm->T_min) <= 2.0 * relT * T + FLAG_K * eps * prm->T_min) flags |= ORA_FLAG_TSTOP;
+      if (fabs(T - prm->T_min) <= FLAG_K * (relT * T + ERR_C * eps * prm->T_min)) flags |= ORA_FLAG_TSTOP;
       if (k + 1 < b->n) {
         const hit64* h2 = &b->h[k + 1];
-        double L1 = Omax + amax3(g->p) + fabs(h->t);
-        double L2 = Omax + amax3(W->s[h2->idx].p) + fabs(h2->t);
-        if (fabs(h2->t - h->t) <= FLAG_K * eps * (L1 / fabs(h->d) + L2 / fabs(h2->d))) flags |= ORA_FLAG_ORDER;
+        if (fabs(h2->t - h->t) <= FLAG_K * (h->dt + h2->dt)) flags |= ORA_FLAG_ORDER;
       }
     }
     if (T < prm->T_min) break;
@@ -300,8 +311,35 @@ static int segment(const world* W, const double O[3], const double w[3], double 
     for (int c = 0; c < 3; ++c) seg->Nn[c] = seg->N[c] / nn;
     seg->Dn = seg->D / seg->A;
   }
-  if (eps > 0 && fabs(seg->E - prm->tau_E) <= 2.0 * (relT + 4 * FLAG_K * eps) * fabs(seg->E) + FLAG_K * eps)
-    flags |= ORA_FLAG_EMIT;
+  /* propagated errors of the blended values (first order in the weight errors) */
+  if (eps > 0 && used > 0) {
+    double Tb = 1.0, rT = 0.0, eR = 0.0, eP = 0.0, eE = 0.0, eN = 0.0, eD = 0.0;
+    for (int64_t k = 0; k < used; ++k) {
+      const hit64* h = &b->h[k];
+      const surfel64* g = &W->s[h->idx];
+      const double wgt = Tb * h->alpha, rw = h->rel_alpha + rT;
+      const double sgn = h->d > 0 ? -1.0 : 1.0;
+      const double remit = (mode == 1 && !(g->e > prm->tau_E)) ? 0.0 : 1.0;
+      double rmax = remit * amax3(g->r), pmax = amax3(g->rho);
+      eR += wgt * rw * rmax;
+      eP += wgt * rw * pmax;
+      eE += wgt * rw * fabs(g->e);
+      double nf[3] = {sgn * g->n[0], sgn * g->n[1], sgn * g->n[2]};
+      double c = dot3(nf, seg->Nn);
+      double perp[3] = {nf[0] - c * seg->Nn[0], nf[1] - c * seg->Nn[1], nf[2] - c * seg->Nn[2]};
+      eN += wgt * rw * norm3(perp);
+      eD += wgt * (rw * fabs(h->t - seg->Dn) + h->dt);
+      rT += h->alpha / (1.0 - h->alpha) * h->rel_alpha;
+      Tb *= 1.0 - h->alpha;
+    }
+    double Rm = amax3(seg->R), Pm = amax3(seg->P);
+    seg->eR = Rm > 0 ? eR / Rm + ERR_C * eps : 0.0;
+    seg->eP = Pm > 0 ? eP / Pm + ERR_C * eps : 0.0;
+    seg->eE = eE + ERR_C * eps;
+    seg->eN = eN / norm3(seg->N) + ERR_C * eps;
+    seg->eD = eD / seg->A + seg->Dn * (T * rT) / seg->A + ERR_C * eps * seg->Dn;
+  }
+  if (eps > 0 && fabs(seg->E - prm->tau_E) <= FLAG_K * seg->eE) flags |= ORA_FLAG_EMIT;
   seg->flags = flags;
   return 0;
 }
@@ -312,7 +350,7 @@ int ora_trace_segment(const ora_scene* sc, const ora_params* prm, const double O
   if (!s) return -1;
   world W = {s, sc->n, prm};
   hitbuf b = {0, 0, 0};
-  int rc = segment(&W, O, w, t_lo, mode, &b, out);
+  int rc = segment(&W, O, w, t_lo, mode, 0.0, 0.0, &b, out);
   if (hit_idx)
     for (int32_t k = 0; k < max_hits; ++k) hit_idx[k] = k < b.n ? (int32_t)b.h[k].idx : -1;
   free(b.h);
@@ -407,7 +445,7 @@ static int rays_item(job* jb, int64_t i, hitbuf* b) {
   rays_ctx* c = (rays_ctx*)jb->ctx;
   const double* r = &c->rays[6 * i];
   ora_segment g;
-  if (segment(&jb->W, r, r + 3, 0.0, c->mode, b, &g)) return -1;
+  if (segment(&jb->W, r, r + 3, 0.0, c->mode, 0.0, 0.0, b, &g)) return -1;
   write_rec(&g, &c->out_rec[12 * i]);
   if (c->out_nhits) c->out_nhits[i] = g.n_hits;
   if (c->out_flags) c->out_flags[i] = g.flags;
@@ -450,7 +488,7 @@ static int prim_item(job* jb, int64_t i, hitbuf* b) {
   double O[3], w[3];
   primary_ray(c->cam, c->pixels[i], O, w);
   ora_segment g;
-  if (segment(&jb->W, O, w, 0.0, c->mode, b, &g)) return -1;
+  if (segment(&jb->W, O, w, 0.0, c->mode, 0.0, ERR_C * jb->W.prm->fp32_eps, b, &g)) return -1;
   write_rec(&g, &c->out_rec[12 * i]);
   if (c->out_flags) c->out_flags[i] = g.flags;
   return 0;
@@ -487,88 +525,173 @@ typedef struct {
   int64_t* out_segments;
 } render_ctx;
 
-/* relative-error estimate of a segment's blended values for path-level flags */
-static double seg_rel(const ora_segment* g, double eps) { return g->n_hits * FLAG_K * eps * 8.0; }
+/* Perturbs a ray at FP32 rounding scale for the conditioning estimate:
+ * every origin component by up to mag * max|O|, every direction component by
+ * up to mag, then renormalises.  Counter-based, so the perturbation of a
+ * (pixel, sample, bounce, run) is reproducible. */
+static void jitter_ray(double O[3], double w[3], uint64_t seed, int64_t pix, int32_t s, int32_t k, int32_t run,
+                       double mag) {
+  uint32_t key[2] = {(uint32_t)seed ^ 0x5bd1e995u, (uint32_t)(seed >> 32) ^ 0x1b873593u};
+  uint32_t c1[4] = {(uint32_t)pix, (uint32_t)s, (uint32_t)k, 0x40000000u | (uint32_t)run};
+  uint32_t c2[4] = {(uint32_t)pix, (uint32_t)s, (uint32_t)k, 0x20000000u | (uint32_t)run};
+  uint32_t o1[4], o2[4];
+  ora_philox4x32_10(c1, key, o1);
+  ora_philox4x32_10(c2, key, o2);
+  double om = amax3(O);
+  if (om < 1e-3) om = 1e-3;
+  for (int j = 0; j < 3; ++j) {
+    O[j] += mag * om * (2.0 * u24(o1[j]) - 1.0);
+    w[j] += mag * (2.0 * u24(o2[j]) - 1.0);
+  }
+  double l = norm3(w);
+  for (int j = 0; j < 3; ++j) w[j] /= l;
+}
+
+/* One sample's path from the pixel's primary segment g1 (Eq. 6 for kind 0,
+ * Eq. 8 for kind 1).  run > 0 perturbs every secondary ray (conditioning
+ * estimate); run 0 is the exact evaluation and also collects the flags. */
+static int path_sample(job* jb, const render_ctx* c, hitbuf* b, int64_t pix, int32_t s, const double O[3],
+                       const double w[3], const ora_segment* g1, int32_t run, double contrib[3], uint32_t* sflags,
+                       int64_t* segments) {
+  const ora_params* prm = jb->W.prm;
+  const double eps = prm->fp32_eps;
+  const int pt = c->kind == 1;
+  const int seg_mode = pt ? 1 : 0;
+  const int reflect_all = prm->emitters_reflect != 0;
+  contrib[0] = contrib[1] = contrib[2] = 0.0;
+  if (g1->n_hits == 0) return 0; /* primary miss: no light (no environment) */
+  if (g1->E > prm->tau_E && !reflect_all) {
+    for (int k = 0; k < 3; ++k) contrib[k] = g1->R[k]; /* Eq. 4: L_o = L_e = R */
+    return 0;
+  }
+  double beta[3], X[3], Nn[3], rel = g1->eP, eN = g1->eN;
+  if (reflect_all)
+    for (int k = 0; k < 3; ++k) contrib[k] = g1->R[k];
+  for (int k = 0; k < 3; ++k) {
+    beta[k] = g1->P[k]; /* f cos / p = (P/pi) cos / (cos/pi) = P */
+    X[k] = O[k] + g1->Dn * w[k];
+    Nn[k] = g1->Nn[k];
+  }
+  const int B = pt ? c->max_bounces : 1;
+  for (int32_t k = 1; k <= B; ++k) {
+    double u[4];
+    draws(c->seed, pix, s, k, u);
+    if (pt && !reflect_all && k >= c->rr_start) {
+      double q = beta[0];
+      if (beta[1] > q) q = beta[1];
+      if (beta[2] > q) q = beta[2];
+      if (q > 1.0) q = 1.0;
+      if (eps > 0 && fabs(u[2] - q) <= FLAG_K * (rel * q + ERR_C * eps)) *sflags |= ORA_FLAG_RR;
+      if (!(u[2] < q)) return 0; /* terminated, contributes 0 */
+      for (int j = 0; j < 3; ++j) beta[j] /= q;
+    }
+    if (eps > 0 && fabs(Nn[2]) <= FLAG_K * eN) *sflags |= ORA_FLAG_ONB;
+    double w2[3], O2[3];
+    ora_cosine_direction(Nn, u[0], u[1], w2);
+    for (int j = 0; j < 3; ++j) O2[j] = X[j] + prm->bounce_offset * Nn[j];
+    if (run > 0) jitter_ray(O2, w2, c->seed, pix, s, k, run, 2.0 * eps);
+    ora_segment g2;
+    /* margins at this segment's own FP32 rounding scale */
+    if (segment(&jb->W, O2, w2, 0.0, seg_mode, ERR_C * eps * amax3(O2), ERR_C * eps, b, &g2)) return -1;
+    ++*segments;
+    *sflags |= g2.flags;
+    if (g2.n_hits == 0) return 0; /* miss: no light */
+    if (reflect_all) {
+      for (int j = 0; j < 3; ++j) contrib[j] += beta[j] * g2.R[j];
+    } else if (!pt) {
+      /* Eq. 6: the secondary's accumulated radiance is the cache */
+      for (int j = 0; j < 3; ++j) contrib[j] = beta[j] * g2.R[j];
+      return 0;
+    } else if (g2.E > prm->tau_E) {
+      /* Eq. 8: first emissive vertex within the bounce limit */
+      for (int j = 0; j < 3; ++j) contrib[j] = beta[j] * g2.R[j];
+      return 0;
+    }
+    if (k == B) return 0; /* bounce limit exceeded: discarded (or done) */
+    for (int j = 0; j < 3; ++j) {
+      beta[j] *= g2.P[j];
+      X[j] = O2[j] + g2.Dn * w2[j];
+      Nn[j] = g2.Nn[j];
+    }
+    rel += g2.eP;
+    eN = g2.eN;
+  }
+  return 0;
+}
 
 static int render_item(job* jb, int64_t i, hitbuf* b) {
   render_ctx* c = (render_ctx*)jb->ctx;
   const ora_params* prm = jb->W.prm;
   const double eps = prm->fp32_eps;
   const int64_t pix = c->pixels[i];
-  const int pt = c->kind == 1;
-  const int seg_mode = pt ? 1 : 0;
+  const int seg_mode = c->kind == 1 ? 1 : 0;
   double O[3], w[3];
   primary_ray(c->cam, pix, O, w);
   ora_segment g1;
-  if (segment(&jb->W, O, w, 0.0, seg_mode, b, &g1)) return -1;
+  if (segment(&jb->W, O, w, 0.0, seg_mode, 0.0, ERR_C * eps, b, &g1)) return -1;
   int64_t segments = 1;
   double acc[3] = {0, 0, 0};
-  const int emitter1 = g1.E > prm->tau_E;
-  const int reflect_all = prm->emitters_reflect != 0;
+  /* conditioning runs: the whole sample (primary direction included) is
+   * re-evaluated with every ray perturbed at FP32 scale */
+  const int n_runs = (prm->cond_tol > 0 && eps > 0) ? 2 : 0;
+  double* dev = NULL;
+  double* mag = NULL;
+  if (n_runs) {
+    dev = (double*)calloc((size_t)c->spp, sizeof(double));
+    mag = (double*)calloc((size_t)c->spp, sizeof(double));
+    if (!dev || !mag) {
+      free(dev);
+      free(mag);
+      return -1;
+    }
+  }
+  ora_segment gj[2];
+  double wj[2][3];
+  for (int r = 0; r < n_runs; ++r) {
+    double Oj[3] = {O[0], O[1], O[2]};
+    for (int k = 0; k < 3; ++k) wj[r][k] = w[k];
+    jitter_ray(Oj, wj[r], c->seed, pix, -1, 0, r + 1, 2.0 * eps);
+    if (segment(&jb->W, O, wj[r], 0.0, seg_mode, 0.0, ERR_C * eps, b, &gj[r])) {
+      free(dev);
+      return -1;
+    }
+  }
   for (int32_t s = 0; s < c->spp; ++s) {
     uint32_t sflags = g1.flags;
-    double contrib[3] = {0, 0, 0};
-    if (g1.n_hits == 0) {
-      /* primary miss: no light (no environment) */
-    } else if (emitter1 && !reflect_all) {
-      for (int k = 0; k < 3; ++k) contrib[k] = g1.R[k]; /* Eq. 4: L_o = L_e = R */
-    } else {
-      double beta[3], X[3], Nn[3], rel = seg_rel(&g1, eps);
-      if (reflect_all)
-        for (int k = 0; k < 3; ++k) contrib[k] = g1.R[k];
-      for (int k = 0; k < 3; ++k) {
-        beta[k] = g1.P[k]; /* f cos / p = (P/pi) cos / (cos/pi) = P */
-        X[k] = O[k] + g1.Dn * w[k];
-        Nn[k] = g1.Nn[k];
+    double contrib[3];
+    if (path_sample(jb, c, b, pix, s, O, w, &g1, 0, contrib, &sflags, &segments)) {
+      free(dev);
+      return -1;
+    }
+    for (int r = 0; r < n_runs; ++r) {
+      double cj[3];
+      uint32_t fj = 0;
+      int64_t sj = 0;
+      if (path_sample(jb, c, b, pix, s, O, wj[r], &gj[r], r + 1, cj, &fj, &sj)) {
+        free(dev);
+        return -1;
       }
-      const int B = pt ? c->max_bounces : 1;
-      for (int32_t k = 1; k <= B; ++k) {
-        double u[4];
-        draws(c->seed, pix, s, k, u);
-        if (pt && !reflect_all && k >= c->rr_start) {
-          double q = beta[0];
-          if (beta[1] > q) q = beta[1];
-          if (beta[2] > q) q = beta[2];
-          if (q > 1.0) q = 1.0;
-          if (eps > 0 && fabs(u[2] - q) <= 2.0 * rel * q + FLAG_K * eps) sflags |= ORA_FLAG_RR;
-          if (!(u[2] < q)) break; /* terminated, contributes 0 */
-          for (int j = 0; j < 3; ++j) beta[j] /= q;
-        }
-        if (eps > 0 && fabs(Nn[2]) <= 8.0 * rel + FLAG_K * eps) sflags |= ORA_FLAG_ONB;
-        double w2[3], O2[3];
-        ora_cosine_direction(Nn, u[0], u[1], w2);
-        for (int j = 0; j < 3; ++j) O2[j] = X[j] + prm->bounce_offset * Nn[j];
-        ora_segment g2;
-        if (segment(&jb->W, O2, w2, 0.0, seg_mode, b, &g2)) return -1;
-        ++segments;
-        sflags |= g2.flags;
-        rel += seg_rel(&g2, eps);
-        if (g2.n_hits == 0) break; /* miss: no light */
-        if (reflect_all) {
-          for (int j = 0; j < 3; ++j) contrib[j] += beta[j] * g2.R[j];
-        } else if (!pt) {
-          /* Eq. 6: the secondary's accumulated radiance is the cache */
-          for (int j = 0; j < 3; ++j) contrib[j] = beta[j] * g2.R[j];
-          break;
-        } else if (g2.E > prm->tau_E) {
-          /* Eq. 8: first emissive vertex within the bounce limit */
-          for (int j = 0; j < 3; ++j) contrib[j] = beta[j] * g2.R[j];
-          break;
-        }
-        if (k == B) break; /* bounce limit exceeded: discarded (or done) */
-        for (int j = 0; j < 3; ++j) {
-          beta[j] *= g2.P[j];
-          X[j] = O2[j] + g2.Dn * w2[j];
-          Nn[j] = g2.Nn[j];
-        }
+      for (int k = 0; k < 3; ++k) {
+        double d = fabs(cj[k] - contrib[k]);
+        if (d > dev[s]) dev[s] = d;
       }
     }
     for (int k = 0; k < 3; ++k) acc[k] += contrib[k];
+    if (mag) mag[s] = amax3(contrib);
     if (c->out_samples)
       for (int k = 0; k < 3; ++k) c->out_samples[(i * c->spp + s) * 3 + k] = contrib[k];
     if (c->out_sample_flags) c->out_sample_flags[i * c->spp + s] = sflags;
   }
   for (int k = 0; k < 3; ++k) c->out_rgb[3 * i + k] = c->spp > 0 ? acc[k] / c->spp : 0.0;
+  if (n_runs && c->out_sample_flags) {
+    /* a sample is ill-conditioned when FP32-scale perturbations move it by
+     * more than cond_tol of its own value (radiance is non-negative, so a
+     * mean of unflagged samples keeps that relative bound) */
+    for (int32_t s = 0; s < c->spp; ++s)
+      if (dev[s] > prm->cond_tol * mag[s]) c->out_sample_flags[i * c->spp + s] |= ORA_FLAG_COND;
+  }
+  free(dev);
+  free(mag);
   if (c->out_segments) c->out_segments[i] = segments;
   return 0;
 }
@@ -771,7 +894,7 @@ static int grad_pixel(const world* W, grad_ctx* c, int64_t i, hitbuf* b1, hitbuf
   double O[3], w[3];
   primary_ray(c->cam, pix, O, w);
   ora_segment g1;
-  if (segment(W, O, w, 0.0, 0, b1, &g1)) return -1;
+  if (segment(W, O, w, 0.0, 0, 0.0, ERR_C * prm->fp32_eps, b1, &g1)) return -1;
   uint32_t flags = g1.flags;
   double zero3[3] = {0, 0, 0};
   double dO[3] = {0, 0, 0}, dw[3] = {0, 0, 0};
@@ -792,13 +915,14 @@ static int grad_pixel(const world* W, grad_ctx* c, int64_t i, hitbuf* b1, hitbuf
   for (int32_t s = 0; s < c->spp; ++s) {
     double u[4], l[3], w2[3], O2[3];
     draws(c->seed, pix, s, 1, u);
-    if (prm->fp32_eps > 0 && fabs(g1.Nn[2]) <= 8.0 * seg_rel(&g1, prm->fp32_eps) + FLAG_K * prm->fp32_eps)
-      flags |= ORA_FLAG_ONB;
+    const double eps = prm->fp32_eps;
+    if (eps > 0 && fabs(g1.Nn[2]) <= FLAG_K * g1.eN) flags |= ORA_FLAG_ONB;
     cosine_local(u[0], u[1], l);
     ora_cosine_direction(g1.Nn, u[0], u[1], w2);
     for (int k = 0; k < 3; ++k) O2[k] = X[k] + prm->bounce_offset * g1.Nn[k];
+    const double eO2 = ERR_C * eps * amax3(O2);
     ora_segment g2;
-    if (segment(W, O2, w2, 0.0, 0, b2, &g2)) return -1;
+    if (segment(W, O2, w2, 0.0, 0, eO2, ERR_C * eps, b2, &g2)) return -1;
     flags |= g2.flags;
     if (g2.n_hits == 0) continue;
     double gR2[3];

@@ -40,6 +40,8 @@ typedef struct {
   int32_t emitters_reflect; /* 1: general rendering equation (test-only)    */
   double fp32_eps;       /* unit roundoff used by the near-boundary flags;
                             0 disables flagging                              */
+  double cond_tol;       /* flag a sample whose estimated FP32 relative error
+                            exceeds cond_tol (ORA_FLAG_COND); 0 disables     */
 } ora_params;
 
 /* near-boundary flag bits (a decision the FP32 path may take differently) */
@@ -54,6 +56,7 @@ enum {
   ORA_FLAG_RR = 1u << 7,       /* Russian-roulette draw near the threshold  */
   ORA_FLAG_ONB = 1u << 8,      /* normal z near 0 (basis branch)            */
   ORA_FLAG_GRAZE = 1u << 9,    /* ray nearly parallel to a surfel plane     */
+  ORA_FLAG_COND = 1u << 10,    /* sample ill-conditioned in FP32            */
 };
 
 /* Result of one traced segment (Eq. 2-3). */
@@ -62,6 +65,9 @@ typedef struct {
   double Nn[3], Dn;                 /* normalised N/|N| and D/A           */
   int32_t n_hits;                   /* blended hits                       */
   uint32_t flags;
+  /* first-order FP32 error estimates (0 when fp32_eps = 0): relative error
+   * of R and P, absolute error of E, angle error of N~, length error of D~ */
+  double eR, eP, eE, eN, eD;
 } ora_segment;
 
 /* Philox4x32-10 of one 128-bit counter under a 64-bit key. */

@@ -1,0 +1,190 @@
+"""Python front end of the C ABI.
+
+PyTorch supplies device memory and streams; every computation runs in the
+CUDA library (``libeagpt.so``).  Names follow the paper: a scene of surfels
+with centre p, rotation q, scales s, opacity sigma, albedo rho, radiance r and
+emissive term e (Sec. 3.1); renders by the single-bounce estimator (Eq. 6) and
+by path tracing (Eq. 8).
+"""
+from __future__ import annotations
+
+import ctypes
+from typing import Optional
+
+import numpy as np
+import torch
+
+from . import capi
+from .scenes import Camera as HostCamera
+from .scenes import SurfelScene
+
+FIELDS = ("pos", "quat", "scale", "opacity", "albedo", "radiance", "emissive")
+GRAD_FIELDS = ("pos", "quat", "scale", "opacity", "albedo", "radiance")
+SHAPES = {"pos": 3, "quat": 4, "scale": 2, "opacity": 1, "albedo": 3, "radiance": 3, "emissive": 1}
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def params(**overrides) -> capi.Params:
+    """Method constants (defaults: tau_E = 0.1 from Eq. 4; the rest are the
+    stated readings of unstated constants)."""
+    p = capi.default_params()
+    for k, v in overrides.items():
+        setattr(p, k, v)
+    return p
+
+
+def camera(cam: HostCamera) -> capi.Camera:
+    c = capi.Camera()
+    c.width, c.height = int(cam.width), int(cam.height)
+    c.fx, c.fy, c.cx, c.cy = float(cam.fx), float(cam.fy), float(cam.cx), float(cam.cy)
+    c2w = np.asarray(cam.c2w, np.float32).reshape(12)
+    for i in range(12):
+        c.c2w[i] = float(c2w[i])
+    return c
+
+
+class DeviceScene:
+    """Surfel parameters resident on the device (structure of arrays)."""
+
+    def __init__(self, tensors: dict, version: int = 0):
+        n = tensors["pos"].shape[0]
+        for k in FIELDS:
+            t = tensors[k]
+            want = (n, SHAPES[k]) if SHAPES[k] > 1 else (n,)
+            if tuple(t.shape) != want or t.dtype != torch.float32 or not t.is_contiguous() or not t.is_cuda:
+                raise ValueError(f"{k}: want contiguous CUDA float32 {want}, got {t.dtype} {tuple(t.shape)}")
+        self.t = dict(tensors)
+        self.n = n
+        self.version = int(version)
+
+    @classmethod
+    def from_host(cls, scene: SurfelScene, device="cuda", non_blocking=False):
+        return cls({k: torch.as_tensor(getattr(scene, k)).to(device, non_blocking=non_blocking).contiguous()
+                    for k in FIELDS})
+
+    def to_host(self) -> SurfelScene:
+        return SurfelScene(*[self.t[k].cpu().numpy() for k in FIELDS])
+
+    def c(self) -> capi.Scene:
+        s = capi.Scene()
+        s.n = self.n
+        for k in FIELDS:
+            setattr(s, k, self.t[k].data_ptr() if self.n else None)
+        s.version = self.version
+        return s
+
+
+class BVH:
+    """Software LBVH over the surfels' support bounds; storage is a torch
+    uint8 buffer owned by this object."""
+
+    def __init__(self, scene: DeviceScene, prm: Optional[capi.Params] = None, stream=None):
+        self.params = prm or params()
+        nbytes = capi.lib().eagpt_bvh_bytes(scene.n)
+        self.storage = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=scene.t["pos"].device)
+        self.handle = capi.Bvh()
+        sc = scene.c()
+        capi.check(capi.lib().eagpt_build_bvh(ctypes.byref(sc), ctypes.byref(self.params),
+                                               _ptr(self.storage), self.storage.numel(),
+                                               ctypes.byref(self.handle), _stream(stream)))
+
+    def c(self) -> capi.Bvh:
+        return self.handle
+
+
+class Renderer:
+    """Holds a reusable device workspace and calls the render entry points."""
+
+    def __init__(self, device="cuda", max_workspace_bytes: Optional[int] = None):
+        self.device = torch.device(device)
+        self.ws = None
+        self.max_ws = max_workspace_bytes
+
+    def _workspace(self, cam: capi.Camera, spp: int, kind: int) -> torch.Tensor:
+        want = capi.lib().eagpt_render_workspace_bytes(ctypes.byref(cam), spp, kind)
+        if self.max_ws is not None:
+            want = max(min(want, self.max_ws), capi.lib().eagpt_render_workspace_min_bytes(ctypes.byref(cam), spp, kind))
+        if self.ws is None or self.ws.numel() < want:
+            self.ws = None
+            self.ws = torch.empty(want, dtype=torch.uint8, device=self.device)
+        return self.ws
+
+    def path_traced(self, scene: DeviceScene, bvh: BVH, cam: HostCamera, spp: int, max_bounces: int,
+                    rr_start: int = 2, seed: int = 0, prm: Optional[capi.Params] = None, want_aux=False,
+                    want_samples=False, want_stats=False, out: Optional[torch.Tensor] = None, stream=None):
+        """Eq. 8 render; returns dict(rgb (H,W,3)[, aux (H,W,12)][, samples (H,W,spp,3)][, stats])."""
+        c = camera(cam)
+        prm = prm or bvh.params
+        ws = self._workspace(c, spp, 1)
+        H, W = cam.height, cam.width
+        rgb = out if out is not None else torch.empty((H, W, 3), dtype=torch.float32, device=self.device)
+        aux = torch.empty((H, W, 12), dtype=torch.float32, device=self.device) if want_aux else None
+        smp = torch.empty((H, W, spp, 3), dtype=torch.float32, device=self.device) if want_samples else None
+        st = torch.zeros(16, dtype=torch.int64, device=self.device) if want_stats else None
+        sc = scene.c()
+        capi.check(capi.lib().eagpt_render_path_traced(
+            ctypes.byref(sc), ctypes.byref(bvh.c()), ctypes.byref(c), ctypes.byref(prm), int(spp), int(max_bounces),
+            int(rr_start), ctypes.c_uint64(int(seed)), _ptr(rgb), _ptr(aux), _ptr(smp), _ptr(st), _ptr(ws),
+            ws.numel(), _stream(stream)))
+        r = {"rgb": rgb}
+        if want_aux:
+            r["aux"] = aux
+        if want_samples:
+            r["samples"] = smp
+        if want_stats:
+            r["stats"] = st
+        return r
+
+    def single_bounce(self, scene: DeviceScene, bvh: BVH, cam: HostCamera, spp: int, seed: int = 0,
+                      prm: Optional[capi.Params] = None, want_aux=False, want_samples=False, stream=None):
+        """Eq. 6 render; returns dict(rgb[, aux][, samples])."""
+        c = camera(cam)
+        prm = prm or bvh.params
+        ws = self._workspace(c, spp, 0)
+        H, W = cam.height, cam.width
+        rgb = torch.empty((H, W, 3), dtype=torch.float32, device=self.device)
+        aux = torch.empty((H, W, 12), dtype=torch.float32, device=self.device) if want_aux else None
+        smp = torch.empty((H, W, spp, 3), dtype=torch.float32, device=self.device) if want_samples else None
+        sc = scene.c()
+        capi.check(capi.lib().eagpt_render_single_bounce(
+            ctypes.byref(sc), ctypes.byref(bvh.c()), ctypes.byref(c), ctypes.byref(prm), int(spp),
+            ctypes.c_uint64(int(seed)), _ptr(rgb), _ptr(aux), _ptr(smp), _ptr(ws), ws.numel(), _stream(stream)))
+        r = {"rgb": rgb}
+        if want_aux:
+            r["aux"] = aux
+        if want_samples:
+            r["samples"] = smp
+        return r
+
+
+def trace_rays(scene: DeviceScene, bvh: BVH, rays: torch.Tensor, mode: int = 0, max_hits: int = 0,
+               prm: Optional[capi.Params] = None, stream=None):
+    """Traces caller rays (n, 6) -> dict(rec (n,12)[, hits (n,max_hits), nhits (n,)])."""
+    rays = rays.contiguous()
+    n = rays.shape[0]
+    dev = rays.device
+    rec = torch.empty((n, 12), dtype=torch.float32, device=dev)
+    hits = torch.empty((n, max_hits), dtype=torch.int32, device=dev) if max_hits > 0 else None
+    nh = torch.empty((n,), dtype=torch.int32, device=dev)
+    prm = prm or bvh.params
+    sc = scene.c()
+    capi.check(capi.lib().eagpt_trace_rays(ctypes.byref(sc), ctypes.byref(bvh.c()), ctypes.byref(prm), int(mode),
+                                           _ptr(rays), n, _ptr(rec), _ptr(hits), int(max_hits), _ptr(nh),
+                                           _stream(stream)))
+    out = {"rec": rec, "nhits": nh}
+    if hits is not None:
+        out["hits"] = hits
+    return out
+
+
+def sync_status(stream=None) -> None:
+    """Synchronise and raise if a kernel recorded a device-side error."""
+    capi.check(capi.lib().eagpt_sync_status(_stream(stream)))

@@ -1,0 +1,134 @@
+"""ctypes declarations of the C ABI in ``include/eagpt.h``.
+
+Argument marshalling only: every step of the render runs in the CUDA
+library.  Loading fails loudly when the library has not been built; there is
+no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libeagpt.so")
+
+_lock = threading.Lock()
+_lib = None
+
+P = ctypes.POINTER
+c_f = ctypes.c_float
+c_i32 = ctypes.c_int32
+c_i64 = ctypes.c_int64
+c_u64 = ctypes.c_uint64
+c_sz = ctypes.c_size_t
+c_vp = ctypes.c_void_p
+
+STATUS = {0: "EAGPT_OK", 1: "EAGPT_ERR_INVALID_ARGUMENT", 2: "EAGPT_ERR_OUT_OF_MEMORY", 3: "EAGPT_ERR_CUDA",
+          4: "EAGPT_ERR_STALE_BVH", 5: "EAGPT_ERR_TIMEOUT", 6: "EAGPT_ERR_NOT_SUPPORTED",
+          7: "EAGPT_ERR_DEVICE_CHECK"}
+
+
+class EagptError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+class Scene(ctypes.Structure):
+    _fields_ = [("n", c_i64), ("pos", c_vp), ("quat", c_vp), ("scale", c_vp), ("opacity", c_vp),
+                ("albedo", c_vp), ("radiance", c_vp), ("emissive", c_vp), ("version", c_u64)]
+
+
+SceneMut = Scene  # same memory layout (non-const pointers)
+
+
+class SceneGrad(ctypes.Structure):
+    _fields_ = [("n", c_i64), ("pos", c_vp), ("quat", c_vp), ("scale", c_vp), ("opacity", c_vp),
+                ("albedo", c_vp), ("radiance", c_vp)]
+
+
+class Camera(ctypes.Structure):
+    _fields_ = [("width", c_i32), ("height", c_i32), ("fx", c_f), ("fy", c_f), ("cx", c_f), ("cy", c_f),
+                ("c2w", c_f * 12)]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("tau_E", c_f), ("T_min", c_f), ("alpha_min", c_f), ("alpha_max", c_f),
+                ("support_sigma", c_f), ("bounce_offset", c_f), ("reserved", c_i32)]
+
+
+class Bvh(ctypes.Structure):
+    _fields_ = [("storage", c_vp), ("bytes", c_sz), ("n", c_i64), ("scene_version", c_u64),
+                ("support_sigma", c_f), ("build_area", c_f)]
+
+
+class Edit(ctypes.Structure):
+    _fields_ = [("op", c_i32), ("count", c_i64), ("idx", c_vp), ("values", c_f * 12), ("seed", c_u64)]
+
+
+# symbol -> (restype, argtypes)
+SIGNATURES = {
+    "eagpt_default_params": (None, [P(Params)]),
+    "eagpt_last_error": (ctypes.c_char_p, []),
+    "eagpt_version": (ctypes.c_char_p, []),
+    "eagpt_bvh_bytes": (c_sz, [c_i64]),
+    "eagpt_build_bvh": (c_i32, [P(Scene), P(Params), c_vp, c_sz, P(Bvh), c_vp]),
+    "eagpt_render_workspace_bytes": (c_sz, [P(Camera), c_i32, c_i32]),
+    "eagpt_render_workspace_min_bytes": (c_sz, [P(Camera), c_i32, c_i32]),
+    "eagpt_render_single_bounce": (c_i32, [P(Scene), P(Bvh), P(Camera), P(Params), c_i32, c_u64, c_vp, c_vp,
+                                           c_vp, c_vp, c_sz, c_vp]),
+    "eagpt_render_path_traced": (c_i32, [P(Scene), P(Bvh), P(Camera), P(Params), c_i32, c_i32, c_i32, c_u64,
+                                         c_vp, c_vp, c_vp, c_vp, c_vp, c_sz, c_vp]),
+    "eagpt_trace_rays": (c_i32, [P(Scene), P(Bvh), P(Params), c_i32, c_vp, c_i64, c_vp, c_vp, c_i32, c_vp, c_vp]),
+    "eagpt_render_backward_workspace_bytes": (c_sz, [P(Camera), c_i32]),
+    "eagpt_render_backward_workspace_min_bytes": (c_sz, [P(Camera), c_i32]),
+    "eagpt_render_single_bounce_backward": (c_i32, [P(Scene), P(Bvh), P(Camera), P(Params), c_i32, c_u64, c_vp,
+                                                    P(SceneGrad), c_vp, c_sz, c_vp]),
+    "eagpt_sync_status": (c_i32, [c_vp]),
+    "eagpt_launch_count": (c_i64, []),
+    "eagpt_profile_begin": (c_i32, []),
+    "eagpt_profile_end": (c_i32, [c_vp, c_i32, P(c_i32)]),
+}
+
+
+class KernelTime(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("launches", c_i64), ("total_ms", ctypes.c_double)]
+
+
+def profile_end(capacity: int = 64) -> dict:
+    """Stops the launch profiler; returns {kernel: (launches, total_ms)}."""
+    arr = (KernelTime * capacity)()
+    n = c_i32(0)
+    check(lib().eagpt_profile_end(ctypes.cast(arr, c_vp), capacity, ctypes.byref(n)))
+    return {arr[i].name.decode(): (int(arr[i].launches), float(arr[i].total_ms)) for i in range(min(n.value, capacity))}
+
+
+def lib():
+    """The loaded library (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"CUDA library not built: {LIB_PATH} is missing "
+                                   "(run __graft_entry__.build() or python -m paper_2601_23065_gb300.build)")
+            L = ctypes.CDLL(LIB_PATH)
+            for name, (res, args) in SIGNATURES.items():
+                f = getattr(L, name, None)
+                if f is None:
+                    continue
+                f.restype = res
+                f.argtypes = args
+            _lib = L
+    return _lib
+
+
+def check(status: int) -> None:
+    if status != 0:
+        raise EagptError(status, lib().eagpt_last_error().decode(errors="replace"))
+
+
+def default_params() -> Params:
+    p = Params()
+    lib().eagpt_default_params(ctypes.byref(p))
+    return p

@@ -1,0 +1,367 @@
+// Adjoint of the single-bounce render (Eq. 6) with respect to every surfel
+// parameter: centre p, raw quaternion q, scales s, opacity sigma, albedo rho,
+// radiance r.  Hit lists are recomputed, not stored: each segment is traced
+// twice with the forward traversal (bit-identical hits), once to get its
+// blended values and once to run the front-to-back adjoint of Eq. 2, whose
+// suffix sums S_i = sum_{j>i} w_j v_j are V - V_{<=i}.
+//
+//   k_bwd_secondary  per (sample, pixel): rebuild the sample's bounce ray
+//                    exactly as the forward did, trace, adjoint with
+//                    dL/dR2 = g (.) P1 / S, scatter surfel gradients with
+//                    atomics, and store the sample's dL/dN~1, dL/dD~1 (through
+//                    the bounce origin X + offset N~ and the cosine direction)
+//                    and dL/dP1 = g (.) R2 / S.
+//   k_bwd_primary    per pixel: sum the samples in order, take the adjoints
+//                    through N~ = N/|N| and D~ = D/A, adjoint of the primary
+//                    segment (emitter pixels: dL/dR1 = g).
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+#include "internal.h"
+#include "trace.cuh"
+
+namespace eagpt {
+
+EAGPT_DEFINE_ERROR_READER(take_errors_backward)
+
+constexpr int kKb = 16;
+
+struct __align__(16) PrimRecB {
+  float4 a, b, c;  // same layout as the forward's primary record
+};
+
+// Raw blended sums of one segment (first pass).
+struct RawVisitor {
+  BlendVisitor blend;
+  __device__ __forceinline__ RawVisitor(const ShadeRec* s, const Consts& c, float3 w, int m) : blend(s, c, w, m) {}
+  __device__ __forceinline__ bool operator()(const TraceRec& R, uint32_t j, const HitGeom& h) {
+    return blend(R, j, h);
+  }
+};
+
+// dL/dq_raw from dL/d(t_u, t_v, n) of the normalised-quaternion frame
+// (partial derivatives of the rotation columns, then the projection of the
+// normalisation q / |q|).
+__device__ __forceinline__ float4 quat_adjoint(float4 q, float3 a, float3 b, float3 c) {
+  const float inv = rsqrtf(q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w);
+  const float w = q.x * inv, x = q.y * inv, y = q.z * inv, z = q.w * inv;
+  const float gw = 2.f * (a.y * z - a.z * y - b.x * z + b.z * x + c.x * y - c.y * x);
+  const float gx = 2.f * (a.y * y + a.z * z + b.x * y - 2.f * b.y * x + b.z * w + c.x * z - c.y * w - 2.f * c.z * x);
+  const float gy = 2.f * (-2.f * a.x * y + a.y * x - a.z * w + b.x * x + b.z * z + c.x * w + c.y * z - 2.f * c.z * y);
+  const float gz = 2.f * (-2.f * a.x * z + a.y * w + a.z * x - b.x * w - 2.f * b.y * z + b.z * y + c.x * x + c.y * y);
+  const float proj = w * gw + x * gx + y * gy + z * gz;
+  return make_float4((gw - w * proj) * inv, (gx - x * proj) * inv, (gy - y * proj) * inv, (gz - z * proj) * inv);
+}
+
+// Front-to-back adjoint of one segment (second pass).  gN, gD, gR, gP, gA
+// are the adjoints of the raw blended sums N, D, R, P and of A = 1 - T_n;
+// V holds the raw sums of the first pass.
+struct AdjointVisitor {
+  const ShadeRec* shade;
+  eagpt_scene sc;
+  eagpt_scene_grad gr;
+  Consts C;
+  float3 O, w;
+  int mode;
+  float3 gN, gR, gP;
+  float gD, gA;
+  Blend V;      // totals from the first pass
+  Blend run;    // running sums up to and including the current hit
+  float3 dO, dw;
+  __device__ __forceinline__ bool operator()(const TraceRec& R, uint32_t j, const HitGeom& h) {
+    const uint32_t id = __float_as_uint(R.r1.w);
+    const ShadeRec* sp = shade + j;
+    const float4 s0 = __ldg(&sp->s0), s1 = __ldg(&sp->s1);
+    const float a = h.alpha;
+    const float Tp = run.T;  // transmittance before this hit
+    const float wgt = Tp * a;
+    const float sgn = h.d > 0.f ? -1.f : 1.f;
+    const float3 n = f3(R.r1);
+    const float3 vN = sgn * n;
+    const float remit = (mode == 1 && !(s0.w > C.tau_E)) ? 0.f : 1.f;
+    const float3 vR = remit * make_float3(s1.x, s1.y, s1.z);
+    const float3 vP = make_float3(s0.x, s0.y, s0.z);
+    // running sums including this hit
+    run.N = run.N + wgt * vN;
+    run.R = run.R + wgt * vR;
+    run.P = run.P + wgt * vP;
+    run.D += wgt * h.t;
+    run.T = Tp * (1.f - a);
+    const float inv1a = 1.f / (1.f - a);
+    // dL/dalpha: T_{i-1} v_i - S_i / (1 - alpha_i), S_i = V - V_{<=i}
+    float da = gA * V.T * inv1a;
+    da += dot3(gN, Tp * vN - inv1a * (V.N - run.N));
+    da += dot3(gR, Tp * vR - inv1a * (V.R - run.R));
+    da += dot3(gP, Tp * vP - inv1a * (V.P - run.P));
+    da += gD * (Tp * h.t - inv1a * (V.D - run.D));
+    // albedo, radiance
+    atomicAdd(&gr.albedo[3 * id + 0], wgt * gP.x);
+    atomicAdd(&gr.albedo[3 * id + 1], wgt * gP.y);
+    atomicAdd(&gr.albedo[3 * id + 2], wgt * gP.z);
+    if (remit != 0.f) {
+      atomicAdd(&gr.radiance[3 * id + 0], wgt * gR.x);
+      atomicAdd(&gr.radiance[3 * id + 1], wgt * gR.y);
+      atomicAdd(&gr.radiance[3 * id + 2], wgt * gR.z);
+    }
+    // alpha = sigma g unless clamped
+    float dG = 0.f;
+    const float sigma = R.r0.w;
+    const bool clamped = h.sg >= C.alpha_max;
+    const float g = sigma > 0.f ? h.sg / sigma : 0.f;
+    if (!clamped) {
+      atomicAdd(&gr.opacity[id], da * g);
+      dG = da * sigma;
+    }
+    const float du = -dG * g * h.u, dv = -dG * g * h.v;
+    const float su = sc.scale[2 * id], sv = sc.scale[2 * id + 1];
+    const float3 ta = f3(R.r2), tb = f3(R.r3);       // t_u / s_u, t_v / s_v
+    const float3 tu = su * ta, tv = sv * tb;
+    const float3 p = f3(R.r0);
+    const float3 op = O - p;
+    const float3 Dx = op + h.t * w;                   // x - p
+    const float3 dDx = du * ta + dv * tb;
+    const float3 dtu = (du / su) * Dx, dtv = (dv / sv) * Dx;
+    atomicAdd(&gr.scale[2 * id + 0], -du * h.u / su);
+    atomicAdd(&gr.scale[2 * id + 1], -dv * h.v / sv);
+    float3 dn = (wgt * sgn) * gN;
+    const float dt = wgt * gD + dot3(dDx, w);
+    // Dx = O - p + t w
+    dO = dO + dDx;
+    dw = dw + h.t * dDx;
+    float3 dp = make_float3(-dDx.x, -dDx.y, -dDx.z);
+    // t = ((p - O) . n) / (w . n)
+    const float invd = 1.f / h.d;
+    dp = dp + (dt * invd) * n;
+    dO = dO - (dt * invd) * n;
+    dn = dn + (dt * invd) * (make_float3(-op.x, -op.y, -op.z) - h.t * w);
+    dw = dw - (dt * h.t * invd) * n;
+    atomicAdd(&gr.pos[3 * id + 0], dp.x);
+    atomicAdd(&gr.pos[3 * id + 1], dp.y);
+    atomicAdd(&gr.pos[3 * id + 2], dp.z);
+    const float4 q = make_float4(sc.quat[4 * id], sc.quat[4 * id + 1], sc.quat[4 * id + 2], sc.quat[4 * id + 3]);
+    const float4 dq = quat_adjoint(q, dtu, dtv, dn);
+    atomicAdd(&gr.quat[4 * id + 0], dq.x);
+    atomicAdd(&gr.quat[4 * id + 1], dq.y);
+    atomicAdd(&gr.quat[4 * id + 2], dq.z);
+    atomicAdd(&gr.quat[4 * id + 3], dq.w);
+    return run.T < C.T_min;
+  }
+};
+
+__device__ __forceinline__ void init_blend(Blend& b) {
+  b.N = b.R = b.P = make_float3(0.f, 0.f, 0.f);
+  b.D = b.E = 0.f;
+  b.T = 1.f;
+  b.n_hits = 0;
+}
+
+// dL/dn of w' = l0 b1(n) + l1 b2(n) + l2 n for the basis of Duff et al.
+// (the basis branch is held fixed).
+__device__ __forceinline__ float3 cosine_direction_adjoint(float3 n, float u0, float u1, float3 dw) {
+  const float sgn = copysignf(1.0f, n.z);
+  const float a = -1.0f / (sgn + n.z);
+  const float a2 = a * a;
+  const float r = sqrtf(u0);
+  float s, c;
+  sincospif(2.0f * u1, &s, &c);
+  const float l0 = r * c, l1 = r * s, l2 = sqrtf(fmaxf(0.0f, 1.0f - u0));
+  // rows of the Jacobians of b1 and b2 (columns n_x, n_y, n_z)
+  const float3 J1x = make_float3(2.f * sgn * n.x * a, 0.f, sgn * n.x * n.x * a2);
+  const float3 J1y = make_float3(sgn * n.y * a, sgn * n.x * a, sgn * n.x * n.y * a2);
+  const float3 J1z = make_float3(-sgn, 0.f, 0.f);
+  const float3 J2x = make_float3(n.y * a, n.x * a, n.x * n.y * a2);
+  const float3 J2y = make_float3(0.f, 2.f * n.y * a, n.y * n.y * a2);
+  const float3 J2z = make_float3(0.f, -1.f, 0.f);
+  const float3 g1 = dw.x * J1x + dw.y * J1y + dw.z * J1z;
+  const float3 g2 = dw.x * J2x + dw.y * J2y + dw.z * J2z;
+  return l0 * g1 + l1 * g2 + l2 * dw;
+}
+
+__global__ void __launch_bounds__(kBlock) k_bwd_secondary(BvhView bvh, Consts C, eagpt_camera cam, eagpt_scene sc,
+                                                          eagpt_scene_grad gr, const PrimRecB* __restrict__ prim,
+                                                          const float* __restrict__ dL, int spp, uint64_t seed,
+                                                          int64_t npix, int s0, int batch, float4* per_sample) {
+  __shared__ uint32_t s_stack[kStackSize * kBlock];
+  const int64_t t = blockIdx.x * (int64_t)kBlock + threadIdx.x;
+  if (t >= npix * (int64_t)batch) return;
+  const int64_t pixel = t % npix;
+  const int sl = (int)(t / npix);
+  const PrimRecB p = prim[pixel];
+  float4 outA = make_float4(0.f, 0.f, 0.f, 0.f), outB = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (p.c.w >= 0.f && !(p.b.w > C.tau_E)) {
+    const uint32_t sample = (uint32_t)(s0 + sl);
+    const float4 u = draws(seed, (uint32_t)pixel, sample, 1u);
+    float3 O, w;
+    camera_ray(cam, (uint32_t)pixel, O, w);
+    const float3 Nn = make_float3(p.a.x, p.a.y, p.a.z);
+    const float3 X = O + p.a.w * w;
+    const float3 O2 = X + C.bounce_offset * Nn;
+    const float3 w2 = cosine_direction(Nn, u.x, u.y);
+    TraceCounters cnt{0, 0, 0, 0};
+    RawVisitor v1(bvh.shade, C, w2, 0);
+    trace_segment<kKb, false>(bvh, C, O2, w2, 0.f, s_stack + threadIdx.x, kBlock, v1, cnt);
+    const float invS = 1.f / (float)spp;
+    const float3 g = make_float3(dL[3 * pixel], dL[3 * pixel + 1], dL[3 * pixel + 2]);
+    const float3 P1 = make_float3(p.c.x, p.c.y, p.c.z);
+    if (v1.blend.b.n_hits > 0) {
+      AdjointVisitor av;
+      av.shade = bvh.shade;
+      av.sc = sc;
+      av.gr = gr;
+      av.C = C;
+      av.O = O2;
+      av.w = w2;
+      av.mode = 0;
+      av.gN = av.gP = make_float3(0.f, 0.f, 0.f);
+      av.gR = invS * mul3(g, P1);
+      av.gD = av.gA = 0.f;
+      av.V = v1.blend.b;
+      init_blend(av.run);
+      av.dO = av.dw = make_float3(0.f, 0.f, 0.f);
+      trace_segment<kKb, false>(bvh, C, O2, w2, 0.f, s_stack + threadIdx.x, kBlock, av, cnt);
+      // O2 = O + D~1 w + offset N~1 ; w2 = basis(N~1) l
+      const float gDn = dot3(av.dO, w);
+      const float3 gNn = C.bounce_offset * av.dO + cosine_direction_adjoint(Nn, u.x, u.y, av.dw);
+      const float3 gP1 = invS * mul3(g, v1.blend.b.R);
+      outA = make_float4(gNn.x, gNn.y, gNn.z, gDn);
+      outB = make_float4(gP1.x, gP1.y, gP1.z, 0.f);
+    }
+  }
+  per_sample[2 * t] = outA;
+  per_sample[2 * t + 1] = outB;
+}
+
+__global__ void k_bwd_reduce(int64_t npix, int batch, int first, const float4* __restrict__ per_sample, float4* acc) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= npix) return;
+  float4 a = first ? make_float4(0.f, 0.f, 0.f, 0.f) : acc[2 * i];
+  float4 b = first ? make_float4(0.f, 0.f, 0.f, 0.f) : acc[2 * i + 1];
+  for (int s = 0; s < batch; ++s) {
+    const float4 x = per_sample[2 * ((int64_t)s * npix + i)];
+    const float4 y = per_sample[2 * ((int64_t)s * npix + i) + 1];
+    a.x += x.x;
+    a.y += x.y;
+    a.z += x.z;
+    a.w += x.w;
+    b.x += y.x;
+    b.y += y.y;
+    b.z += y.z;
+  }
+  acc[2 * i] = a;
+  acc[2 * i + 1] = b;
+}
+
+__global__ void __launch_bounds__(kBlock) k_bwd_primary(BvhView bvh, Consts C, eagpt_camera cam, eagpt_scene sc,
+                                                        eagpt_scene_grad gr, const PrimRecB* __restrict__ prim,
+                                                        const float* __restrict__ dL, int64_t npix,
+                                                        const float4* __restrict__ acc) {
+  __shared__ uint32_t s_stack[kStackSize * kBlock];
+  const int64_t i = blockIdx.x * (int64_t)kBlock + threadIdx.x;
+  if (i >= npix) return;
+  const PrimRecB p = prim[i];
+  if (!(p.c.w >= 0.f)) return;  // miss
+  float3 O, w;
+  camera_ray(cam, (uint32_t)i, O, w);
+  TraceCounters cnt{0, 0, 0, 0};
+  RawVisitor v1(bvh.shade, C, w, 0);
+  trace_segment<kKb, false>(bvh, C, O, w, 0.f, s_stack + threadIdx.x, kBlock, v1, cnt);
+  const Blend& V = v1.blend.b;
+  AdjointVisitor av;
+  av.shade = bvh.shade;
+  av.sc = sc;
+  av.gr = gr;
+  av.C = C;
+  av.O = O;
+  av.w = w;
+  av.mode = 0;
+  av.V = V;
+  init_blend(av.run);
+  av.dO = av.dw = make_float3(0.f, 0.f, 0.f);
+  const float3 g = make_float3(dL[3 * i], dL[3 * i + 1], dL[3 * i + 2]);
+  if (p.b.w > C.tau_E) {
+    // emitter pixel: I = R1
+    av.gN = av.gP = make_float3(0.f, 0.f, 0.f);
+    av.gR = g;
+    av.gD = av.gA = 0.f;
+  } else {
+    const float4 a = acc[2 * i], b = acc[2 * i + 1];
+    const float3 gNn = f3(a);
+    const float gDn = a.w;
+    const float A = 1.f - V.T;
+    const float nn = sqrtf(dot3(V.N, V.N));
+    const float3 Nn = (1.f / nn) * V.N;
+    const float proj = dot3(Nn, gNn);
+    av.gN = (1.f / nn) * (gNn - proj * Nn);
+    av.gD = gDn / A;
+    av.gA = -gDn * V.D / (A * A);
+    av.gP = f3(b);
+    av.gR = make_float3(0.f, 0.f, 0.f);
+  }
+  trace_segment<kKb, false>(bvh, C, O, w, 0.f, s_stack + threadIdx.x, kBlock, av, cnt);
+}
+
+// --------------------------------------------------------------------------
+struct BwdLayout {
+  size_t prim, acc, per_sample, total;
+  int batch;
+};
+
+static BwdLayout bwd_layout(int64_t npix, int batch) {
+  BwdLayout L{};
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    size_t at = o;
+    o = align256(o + bytes);
+    return at;
+  };
+  L.prim = take((size_t)npix * sizeof(PrimRecB));
+  L.acc = take((size_t)npix * 2 * sizeof(float4));
+  L.per_sample = take((size_t)npix * batch * 2 * sizeof(float4));
+  L.total = o;
+  L.batch = batch;
+  return L;
+}
+
+size_t backward_workspace_bytes(int64_t npix, int spp, int batch) {
+  (void)spp;
+  return bwd_layout(npix, batch).total;
+}
+
+int backward_choose_batch(int64_t npix, int spp, size_t ws_bytes) {
+  if (bwd_layout(npix, 1).total > ws_bytes) return 0;
+  int lo = 1, hi = spp;
+  while (lo < hi) {
+    const int mid = lo + (hi - lo + 1) / 2;
+    if (bwd_layout(npix, mid).total <= ws_bytes) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+static inline unsigned nb(int64_t n) { return (unsigned)((n + kBlock - 1) / kBlock); }
+
+cudaError_t launch_backward(const BvhView& bvh, const Consts& C, const eagpt_camera& cam, const eagpt_scene& sc,
+                            const eagpt_scene_grad& gr, int spp, uint64_t seed, const float* dL, void* ws,
+                            size_t ws_bytes, cudaStream_t st) {
+  const int64_t npix = (int64_t)cam.width * cam.height;
+  const int batch = backward_choose_batch(npix, spp, ws_bytes);
+  const BwdLayout L = bwd_layout(npix, batch);
+  char* base = (char*)ws;
+  PrimRecB* prim = (PrimRecB*)(base + L.prim);
+  float4* acc = (float4*)(base + L.acc);
+  float4* per = (float4*)(base + L.per_sample);
+  cudaError_t e = launch_primary_records(bvh, C, cam, 0, npix, (void*)prim, st);
+  if (e != cudaSuccess) return e;
+  for (int s0 = 0; s0 < spp; s0 += batch) {
+    const int n = spp - s0 < batch ? spp - s0 : batch;
+    EAGPT_LAUNCH(st, "k_bwd_secondary",
+                 k_bwd_secondary<<<nb(npix * n), kBlock, 0, st>>>(bvh, C, cam, sc, gr, prim, dL, spp, seed, npix, s0,
+                                                                  n, per));
+    EAGPT_LAUNCH(st, "k_bwd_reduce", k_bwd_reduce<<<nb(npix), kBlock, 0, st>>>(npix, n, s0 == 0, per, acc));
+  }
+  EAGPT_LAUNCH(st, "k_bwd_primary",
+               k_bwd_primary<<<nb(npix), kBlock, 0, st>>>(bvh, C, cam, sc, gr, prim, dL, npix, acc));
+  return cudaGetLastError();
+}
+
+}  // namespace eagpt

@@ -1,0 +1,427 @@
+// LBVH over the support bounds of the surfels.
+//
+//   1. centroid bounds (block reduction + ordered-int atomics)
+//   2. 30-bit Morton codes of the centres inside the bounding cube
+//   3. stable LSD radix sort of (code, index), 8 bits per pass
+//   4. records: per sorted position, the surfel frame from its quaternion,
+//      a = t_u/s_u, b = t_v/s_v, the trace and shade records and the bound of
+//      its support ellipse
+//   5. binary radix tree (Karras, HPG 2012) with parents; subtrees of at most
+//      kLeafMax surfels become leaves of the traversed BVH
+//   6. bottom-up refit with visit counters; also used after edits
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace eagpt {
+
+EAGPT_DEFINE_ERROR_READER(take_errors_bvh)
+
+// --------------------------------------------------------------------------
+// float <-> order-preserving uint32
+// --------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t f2ord(float f) {
+  const uint32_t u = __float_as_uint(f);
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float ord2f(uint32_t u) {
+  return __uint_as_float((u & 0x80000000u) ? (u & 0x7FFFFFFFu) : ~u);
+}
+
+__global__ void k_init_header(BvhHeader* hdr) {
+  if (threadIdx.x < 3) {
+    hdr->bounds_bits[threadIdx.x] = 0xFFFFFFFFu;     // min
+    hdr->bounds_bits[3 + threadIdx.x] = 0u;           // max
+  }
+  if (threadIdx.x == 0) hdr->area_sum = 0.0;
+}
+
+__global__ void k_bounds(const float* __restrict__ pos, int64_t n, BvhHeader* hdr) {
+  float lo[3] = {3e38f, 3e38f, 3e38f}, hi[3] = {-3e38f, -3e38f, -3e38f};
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const float v = pos[3 * i + k];
+      lo[k] = fminf(lo[k], v);
+      hi[k] = fmaxf(hi[k], v);
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      lo[k] = fminf(lo[k], __shfl_xor_sync(0xffffffffu, lo[k], o));
+      hi[k] = fmaxf(hi[k], __shfl_xor_sync(0xffffffffu, hi[k], o));
+    }
+  }
+  if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      atomicMin(&hdr->bounds_bits[k], f2ord(lo[k]));
+      atomicMax(&hdr->bounds_bits[3 + k], f2ord(hi[k]));
+    }
+  }
+}
+
+__device__ __forceinline__ uint32_t expand10(uint32_t v) {
+  v &= 0x3FFu;
+  v = (v | (v << 16)) & 0x030000FFu;
+  v = (v | (v << 8)) & 0x0300F00Fu;
+  v = (v | (v << 4)) & 0x030C30C3u;
+  v = (v | (v << 2)) & 0x09249249u;
+  return v;
+}
+
+__global__ void k_morton(const float* __restrict__ pos, int64_t n, const BvhHeader* hdr, uint32_t* keys,
+                         uint32_t* vals) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float lo0 = ord2f(hdr->bounds_bits[0]), lo1 = ord2f(hdr->bounds_bits[1]), lo2 = ord2f(hdr->bounds_bits[2]);
+  const float hi0 = ord2f(hdr->bounds_bits[3]), hi1 = ord2f(hdr->bounds_bits[4]), hi2 = ord2f(hdr->bounds_bits[5]);
+  const float ext = fmaxf(fmaxf(hi0 - lo0, hi1 - lo1), fmaxf(hi2 - lo2, 1e-20f));
+  const float s = 1023.0f / ext;
+  const uint32_t x = (uint32_t)fminf(fmaxf((pos[3 * i + 0] - lo0) * s, 0.f), 1023.f);
+  const uint32_t y = (uint32_t)fminf(fmaxf((pos[3 * i + 1] - lo1) * s, 0.f), 1023.f);
+  const uint32_t z = (uint32_t)fminf(fmaxf((pos[3 * i + 2] - lo2) * s, 0.f), 1023.f);
+  keys[i] = (expand10(x) << 2) | (expand10(y) << 1) | expand10(z);
+  vals[i] = (uint32_t)i;
+}
+
+// --------------------------------------------------------------------------
+// stable LSD radix sort, 8-bit digits, tiles of kSortTileItems keys
+// --------------------------------------------------------------------------
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = kSortTileItems / kSortThreads;  // 16
+
+__global__ void __launch_bounds__(kSortThreads) k_sort_hist(const uint32_t* __restrict__ keys, int64_t n, int shift,
+                                                            uint32_t* hist, int64_t n_tiles) {
+  __shared__ uint32_t h[256];
+  h[threadIdx.x] = 0;
+  __syncthreads();
+  const int64_t base = blockIdx.x * (int64_t)kSortTileItems;
+  for (int k = 0; k < kSortItems; ++k) {
+    const int64_t i = base + k * kSortThreads + threadIdx.x;
+    if (i < n) atomicAdd(&h[(keys[i] >> shift) & 0xFFu], 1u);
+  }
+  __syncthreads();
+  hist[(int64_t)threadIdx.x * n_tiles + blockIdx.x] = h[threadIdx.x];
+}
+
+// Exclusive scan of the digit-major histogram (256 x n_tiles) in one block.
+__global__ void __launch_bounds__(1024) k_sort_scan(uint32_t* hist, int64_t total) {
+  __shared__ uint32_t part[1024];
+  const int64_t per = (total + 1023) / 1024;
+  const int64_t b = threadIdx.x * per, e = b + per < total ? b + per : total;
+  uint32_t s = 0;
+  for (int64_t i = b; i < e; ++i) s += hist[i];
+  part[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = 1; o < 1024; o <<= 1) {
+    const uint32_t v = threadIdx.x >= o ? part[threadIdx.x - o] : 0u;
+    __syncthreads();
+    part[threadIdx.x] += v;
+    __syncthreads();
+  }
+  uint32_t run = threadIdx.x ? part[threadIdx.x - 1] : 0u;
+  for (int64_t i = b; i < e; ++i) {
+    const uint32_t v = hist[i];
+    hist[i] = run;
+    run += v;
+  }
+}
+
+__global__ void __launch_bounds__(kSortThreads) k_sort_scatter(const uint32_t* __restrict__ kin,
+                                                               const uint32_t* __restrict__ vin, uint32_t* kout,
+                                                               uint32_t* vout, int64_t n, int shift,
+                                                               const uint32_t* __restrict__ hist, int64_t n_tiles) {
+  constexpr int W = kSortThreads / 32;
+  __shared__ uint32_t base_d[256];       // global offset of digit d for this tile (running)
+  __shared__ uint32_t wcount[W][256];    // per-warp digit counts in this chunk
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  base_d[threadIdx.x] = hist[(int64_t)threadIdx.x * n_tiles + blockIdx.x];
+  const int64_t tile0 = blockIdx.x * (int64_t)kSortTileItems;
+  for (int k = 0; k < kSortItems; ++k) {
+    for (int w = 0; w < W; ++w) wcount[w][threadIdx.x] = 0;
+    __syncthreads();
+    const int64_t i = tile0 + k * kSortThreads + threadIdx.x;
+    const bool valid = i < n;
+    const uint32_t key = valid ? kin[i] : 0u;
+    const uint32_t d = valid ? (key >> shift) & 0xFFu : 256u + lane;  // invalid lanes never match
+    const uint32_t peers = __match_any_sync(0xffffffffu, d);
+    const uint32_t rank = __popc(peers & ((1u << lane) - 1u));
+    const int leader = __ffs(peers) - 1;
+    if (valid && lane == leader) wcount[warp][d] = __popc(peers);
+    __syncthreads();
+    // exclusive prefix over warps per digit, in place; thread t owns digit t
+    {
+      uint32_t run = 0;
+      for (int w = 0; w < W; ++w) {
+        const uint32_t c = wcount[w][threadIdx.x];
+        wcount[w][threadIdx.x] = run;
+        run += c;
+      }
+      __syncthreads();
+      if (valid) {
+        const uint32_t dst = base_d[d] + wcount[warp][d] + rank;
+        kout[dst] = key;
+        vout[dst] = vin[i];
+      }
+      __syncthreads();
+      base_d[threadIdx.x] += run;
+    }
+    __syncthreads();
+  }
+}
+
+// --------------------------------------------------------------------------
+// records of the sorted surfels
+// --------------------------------------------------------------------------
+__global__ void k_records(eagpt_scene sc, Consts C, const uint32_t* __restrict__ order, TraceRec* trace,
+                          ShadeRec* shade, float4* plo, float4* phi, uint32_t* inv_idx, int64_t n, int write_inv) {
+  const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  const uint32_t i = order[j];
+  if (write_inv) inv_idx[i] = (uint32_t)j;
+  const float* q = sc.quat + 4 * (int64_t)i;
+  float qw = q[0], qx = q[1], qy = q[2], qz = q[3];
+  const float qi = rsqrtf(qw * qw + qx * qx + qy * qy + qz * qz);
+  qw *= qi;
+  qx *= qi;
+  qy *= qi;
+  qz *= qi;
+  const float3 tu = make_float3(1.f - 2.f * (qy * qy + qz * qz), 2.f * (qx * qy + qw * qz), 2.f * (qx * qz - qw * qy));
+  const float3 tv = make_float3(2.f * (qx * qy - qw * qz), 1.f - 2.f * (qx * qx + qz * qz), 2.f * (qy * qz + qw * qx));
+  const float3 nn = cross3(tu, tv);
+  const float su = sc.scale[2 * (int64_t)i], sv = sc.scale[2 * (int64_t)i + 1];
+  const float3 p = make_float3(sc.pos[3 * (int64_t)i], sc.pos[3 * (int64_t)i + 1], sc.pos[3 * (int64_t)i + 2]);
+  TraceRec R;
+  R.r0 = make_float4(p.x, p.y, p.z, sc.opacity[i]);
+  R.r1 = make_float4(nn.x, nn.y, nn.z, __uint_as_float(i));
+  R.r2 = make_float4(tu.x / su, tu.y / su, tu.z / su, 0.f);
+  R.r3 = make_float4(tv.x / sv, tv.y / sv, tv.z / sv, 0.f);
+  trace[j] = R;
+  ShadeRec S;
+  S.s0 = make_float4(sc.albedo[3 * (int64_t)i], sc.albedo[3 * (int64_t)i + 1], sc.albedo[3 * (int64_t)i + 2],
+                     sc.emissive[i]);
+  S.s1 = make_float4(sc.radiance[3 * (int64_t)i], sc.radiance[3 * (int64_t)i + 1], sc.radiance[3 * (int64_t)i + 2], 0.f);
+  shade[j] = S;
+  // support ellipse {p + s_u x t_u + s_v y t_v : x^2 + y^2 <= S^2}: half extent
+  // along axis k is S sqrt((s_u t_u,k)^2 + (s_v t_v,k)^2); inflated so that
+  // FP32 slab tests stay conservative.
+  const float S2 = sqrtf(C.support2);
+  float h[3];
+  const float tuv[2][3] = {{tu.x, tu.y, tu.z}, {tv.x, tv.y, tv.z}};
+  const float pc[3] = {p.x, p.y, p.z};
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const float a = su * tuv[0][k], b = sv * tuv[1][k];
+    h[k] = S2 * sqrtf(a * a + b * b) * (1.f + 1e-5f) + 1e-5f * fabsf(pc[k]) + 1e-6f;
+  }
+  plo[j] = make_float4(p.x - h[0], p.y - h[1], p.z - h[2], 0.f);
+  phi[j] = make_float4(p.x + h[0], p.y + h[1], p.z + h[2], 0.f);
+}
+
+// --------------------------------------------------------------------------
+// binary radix tree (Karras 2012) over sorted keys; ties broken by position
+// --------------------------------------------------------------------------
+__device__ __forceinline__ int delta(const uint32_t* __restrict__ keys, int64_t n, int64_t i, int64_t j) {
+  if (j < 0 || j >= n) return -1;
+  const uint32_t a = keys[i], b = keys[j];
+  if (a != b) return __clz(a ^ b);
+  return __clzll((unsigned long long)(i ^ j));  // >= 33 for positions < 2^31: ties sort by position
+}
+
+__device__ __forceinline__ uint32_t child_link(int64_t first, int64_t last, int64_t node_if_internal) {
+  const int64_t cnt = last - first + 1;
+  if (cnt <= kLeafMax) return kLeafBit | ((uint32_t)(cnt - 1) << kLeafCountShift) | (uint32_t)first;
+  return (uint32_t)node_if_internal;
+}
+
+// Internal node i covers sorted range [first, last]; its children are the
+// binary-tree nodes split and split+1 (leaves when they hold one surfel).
+// child_bin[2i + c] records the binary child (>= 0 internal, < 0 ~leaf).
+__global__ void k_hierarchy(const uint32_t* __restrict__ keys, int64_t n, Node* nodes, uint32_t* leaf_parent,
+                            uint32_t* inode_parent, int32_t* child_bin) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n - 1) return;
+  const int d = (delta(keys, n, i, i + 1) - delta(keys, n, i, i - 1)) >= 0 ? 1 : -1;
+  const int dmin = delta(keys, n, i, i - d);
+  int64_t lmax = 2;
+  while (delta(keys, n, i, i + lmax * d) > dmin) lmax *= 2;
+  int64_t l = 0;
+  for (int64_t t = lmax / 2; t >= 1; t /= 2)
+    if (delta(keys, n, i, i + (l + t) * d) > dmin) l += t;
+  const int64_t j = i + l * d;
+  const int dnode = delta(keys, n, i, j);
+  int64_t s = 0;
+  int64_t t = l;
+  do {
+    t = (t + 1) / 2;
+    if (delta(keys, n, i, i + (s + t) * d) > dnode) s += t;
+  } while (t > 1);
+  const int64_t split = i + s * d + (d < 0 ? -1 : 0);
+  const int64_t first = i < j ? i : j, last = i < j ? j : i;
+  const bool left_leaf = first == split, right_leaf = last == split + 1;
+  Node nd;
+  nd.n0 = nd.n1 = nd.n2 = make_float4(0.f, 0.f, 0.f, 0.f);
+  nd.n3 = make_uint4(child_link(first, split, split), child_link(split + 1, last, split + 1), 0u, 0u);
+  nodes[i] = nd;
+  if (left_leaf) {
+    leaf_parent[split] = (uint32_t)i;
+    child_bin[2 * i] = ~(int32_t)split;
+  } else {
+    inode_parent[split] = (uint32_t)i;
+    child_bin[2 * i] = (int32_t)split;
+  }
+  if (right_leaf) {
+    leaf_parent[split + 1] = (uint32_t)i;
+    child_bin[2 * i + 1] = ~(int32_t)(split + 1);
+  } else {
+    inode_parent[split + 1] = (uint32_t)i;
+    child_bin[2 * i + 1] = (int32_t)(split + 1);
+  }
+  if (i == 0) inode_parent[0] = 0xFFFFFFFFu;
+}
+
+__global__ void k_clear_u32(uint32_t* p, int64_t n) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) p[i] = 0u;
+}
+
+__device__ __forceinline__ float box_area(float4 lo, float4 hi) {
+  const float dx = fmaxf(hi.x - lo.x, 0.f), dy = fmaxf(hi.y - lo.y, 0.f), dz = fmaxf(hi.z - lo.z, 0.f);
+  return 2.f * (dx * dy + dy * dz + dz * dx);
+}
+
+// Bottom-up refit: one thread per surfel climbs while it is the second child
+// to arrive at a node (visit counters), writing the node's box into its own
+// box array and into its parent's child slot.
+__global__ void k_refit(int64_t n, const float4* __restrict__ plo, const float4* __restrict__ phi, float4* ilo,
+                        float4* ihi, Node* nodes, const uint32_t* __restrict__ leaf_parent,
+                        const uint32_t* __restrict__ inode_parent, const int32_t* __restrict__ child_bin,
+                        uint32_t* visit, BvhHeader* hdr) {
+  const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  uint32_t node = leaf_parent[j];
+  float area = 0.f;
+  while (node != 0xFFFFFFFFu) {
+    __threadfence();
+    if (atomicAdd(&visit[node], 1u) == 0u) break;  // first arrival: the sibling finishes
+    __threadfence();
+    const int32_t c0 = child_bin[2 * node], c1 = child_bin[2 * node + 1];
+    const float4 lo0 = c0 < 0 ? plo[~c0] : __ldcg(&ilo[c0]);
+    const float4 hi0 = c0 < 0 ? phi[~c0] : __ldcg(&ihi[c0]);
+    const float4 lo1 = c1 < 0 ? plo[~c1] : __ldcg(&ilo[c1]);
+    const float4 hi1 = c1 < 0 ? phi[~c1] : __ldcg(&ihi[c1]);
+    const float4 lo = make_float4(fminf(lo0.x, lo1.x), fminf(lo0.y, lo1.y), fminf(lo0.z, lo1.z), 0.f);
+    const float4 hi = make_float4(fmaxf(hi0.x, hi1.x), fmaxf(hi0.y, hi1.y), fmaxf(hi0.z, hi1.z), 0.f);
+    __stcg(&ilo[node], lo);
+    __stcg(&ihi[node], hi);
+    Node* nd = nodes + node;
+    nd->n0 = make_float4(lo0.x, lo0.y, lo0.z, hi0.x);
+    nd->n1 = make_float4(hi0.y, hi0.z, lo1.x, lo1.y);
+    nd->n2 = make_float4(lo1.z, hi1.x, hi1.y, hi1.z);
+    area += box_area(lo, hi);
+    node = inode_parent[node];
+  }
+  if (area > 0.f) atomicAdd(&hdr->area_sum, (double)area);
+}
+
+// n <= kLeafMax: a single root node whose first child is one leaf.
+__global__ void k_small_root(int64_t n, const float4* __restrict__ plo, const float4* __restrict__ phi, Node* nodes,
+                             BvhHeader* hdr) {
+  float4 lo = make_float4(3e38f, 3e38f, 3e38f, 0.f), hi = make_float4(-3e38f, -3e38f, -3e38f, 0.f);
+  for (int64_t j = 0; j < n; ++j) {
+    lo = make_float4(fminf(lo.x, plo[j].x), fminf(lo.y, plo[j].y), fminf(lo.z, plo[j].z), 0.f);
+    hi = make_float4(fmaxf(hi.x, phi[j].x), fmaxf(hi.y, phi[j].y), fmaxf(hi.z, phi[j].z), 0.f);
+  }
+  Node nd;
+  nd.n0 = make_float4(lo.x, lo.y, lo.z, hi.x);
+  nd.n1 = make_float4(hi.y, hi.z, 0.f, 0.f);
+  nd.n2 = make_float4(0.f, 0.f, 0.f, 0.f);
+  nd.n3 = make_uint4(kLeafBit | ((uint32_t)(n - 1) << kLeafCountShift), kEmptyChild, 0u, 0u);
+  nodes[0] = nd;
+  hdr->area_sum = box_area(lo, hi);
+}
+
+// --------------------------------------------------------------------------
+// host driver
+// --------------------------------------------------------------------------
+static inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+cudaError_t launch_build(const eagpt_scene& sc, const Consts& C, char* base, const BvhLayout& L, cudaStream_t st,
+                         int* launches) {
+  const int64_t n = sc.n;
+  BvhHeader* hdr = (BvhHeader*)(base + L.header);
+  int nl = 0;
+  EAGPT_LAUNCH(st, "k_init_header", k_init_header<<<1, 32, 0, st>>>(hdr));
+  ++nl;
+  EAGPT_LAUNCH(st, "k_bounds", k_bounds<<<blocks_for(n, 256) < 1024 ? blocks_for(n, 256) : 1024, 256, 0, st>>>(sc.pos, n, hdr));
+  ++nl;
+  uint32_t *k0 = (uint32_t*)(base + L.keys0), *k1 = (uint32_t*)(base + L.keys1);
+  uint32_t *v0 = (uint32_t*)(base + L.vals0), *v1 = (uint32_t*)(base + L.vals1);
+  uint32_t* hist = (uint32_t*)(base + L.hist);
+  EAGPT_LAUNCH(st, "k_morton", k_morton<<<blocks_for(n, 256), 256, 0, st>>>(sc.pos, n, hdr, k0, v0));
+  ++nl;
+  for (int shift = 0; shift < 30; shift += 8) {
+    EAGPT_LAUNCH(st, "k_sort_hist", k_sort_hist<<<(unsigned)L.n_tiles, kSortThreads, 0, st>>>(k0, n, shift, hist, L.n_tiles));
+    EAGPT_LAUNCH(st, "k_sort_scan", k_sort_scan<<<1, 1024, 0, st>>>(hist, 256 * L.n_tiles));
+    EAGPT_LAUNCH(st, "k_sort_scatter", k_sort_scatter<<<(unsigned)L.n_tiles, kSortThreads, 0, st>>>(k0, v0, k1, v1, n, shift, hist, L.n_tiles));
+    nl += 3;
+    uint32_t* t = k0;
+    k0 = k1;
+    k1 = t;
+    t = v0;
+    v0 = v1;
+    v1 = t;
+  }
+  // after 4 passes the sorted keys/values are back in keys0/vals0
+  uint32_t* sorted_idx = (uint32_t*)(base + L.sorted_idx);
+  cudaMemcpyAsync(sorted_idx, v0, (size_t)n * 4, cudaMemcpyDeviceToDevice, st);
+  TraceRec* trace = (TraceRec*)(base + L.trace);
+  ShadeRec* shade = (ShadeRec*)(base + L.shade);
+  float4* plo = (float4*)(base + L.prim_lo);
+  float4* phi = (float4*)(base + L.prim_hi);
+  EAGPT_LAUNCH(st, "k_records", k_records<<<blocks_for(n, 256), 256, 0, st>>>(sc, C, sorted_idx, trace, shade, plo, phi,
+                                                (uint32_t*)(base + L.inv_idx), n, 1));
+  ++nl;
+  Node* nodes = (Node*)(base + L.nodes);
+  if (n <= kLeafMax) {
+    EAGPT_LAUNCH(st, "k_small_root", k_small_root<<<1, 1, 0, st>>>(n, plo, phi, nodes, hdr));
+    ++nl;
+  } else {
+    int32_t* child_bin = (int32_t*)(base + L.child_bin);
+    EAGPT_LAUNCH(st, "k_hierarchy", k_hierarchy<<<blocks_for(n - 1, 256), 256, 0, st>>>(k0, n, nodes, (uint32_t*)(base + L.leaf_parent),
+                                                       (uint32_t*)(base + L.inode_parent), child_bin));
+    ++nl;
+    nl += launch_refit(base, L, st);
+  }
+  if (launches) *launches += nl;
+  return cudaGetLastError();
+}
+
+int launch_refit(char* base, const BvhLayout& L, cudaStream_t st) {
+  const int64_t n = L.n;
+  BvhHeader* hdr = (BvhHeader*)(base + L.header);
+  cudaMemsetAsync(&hdr->area_sum, 0, sizeof(double), st);
+  EAGPT_LAUNCH(st, "k_clear_u32", k_clear_u32<<<blocks_for(L.n_inodes, 256), 256, 0, st>>>((uint32_t*)(base + L.visit), L.n_inodes));
+  EAGPT_LAUNCH(st, "k_refit", k_refit<<<blocks_for(n, 256), 256, 0, st>>>(n, (const float4*)(base + L.prim_lo), (const float4*)(base + L.prim_hi),
+                                              (float4*)(base + L.ibox_lo), (float4*)(base + L.ibox_hi),
+                                              (Node*)(base + L.nodes), (const uint32_t*)(base + L.leaf_parent),
+                                              (const uint32_t*)(base + L.inode_parent),
+                                              (const int32_t*)(base + L.child_bin), (uint32_t*)(base + L.visit), hdr));
+  return 2;
+}
+
+cudaError_t launch_records_update(const eagpt_scene& sc, const Consts& C, char* base, const BvhLayout& L,
+                                  cudaStream_t st) {
+  // recompute every record (O(n), cheap next to a render) in the existing order
+  EAGPT_LAUNCH(st, "k_records", k_records<<<blocks_for(L.n, 256), 256, 0, st>>>(sc, C, (const uint32_t*)(base + L.sorted_idx),
+                                                  (TraceRec*)(base + L.trace), (ShadeRec*)(base + L.shade),
+                                                  (float4*)(base + L.prim_lo), (float4*)(base + L.prim_hi),
+                                                  (uint32_t*)(base + L.inv_idx), L.n, 0));
+  return cudaGetLastError();
+}
+
+}  // namespace eagpt

@@ -1,0 +1,317 @@
+// extern "C" entry points: argument checks on the host, then kernel launches.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "common.cuh"
+#include "internal.h"
+
+using namespace eagpt;
+
+namespace {
+
+thread_local std::string g_msg;
+
+eagpt_status fail(eagpt_status s, const char* fmt, const char* a = nullptr, long long b = 0) {
+  char buf[512];
+  std::snprintf(buf, sizeof(buf), fmt, a ? a : "", b);
+  g_msg = buf;
+  return s;
+}
+
+eagpt_status cuda_fail(cudaError_t e, const char* where) {
+  g_msg = std::string(where) + ": " + cudaGetErrorString(e);
+  return EAGPT_ERR_CUDA;
+}
+
+bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
+
+eagpt_status check_params(const eagpt_params* p) {
+  if (!p) return fail(EAGPT_ERR_INVALID_ARGUMENT, "params is NULL%s");
+  if (!(p->T_min > 0.f && p->T_min < 1.f)) return fail(EAGPT_ERR_INVALID_ARGUMENT, "T_min must be in (0, 1)%s");
+  if (!(p->alpha_max > 0.f && p->alpha_max < 1.f))
+    return fail(EAGPT_ERR_INVALID_ARGUMENT, "alpha_max must be in (0, 1)%s");
+  if (!(p->alpha_min >= 0.f && p->alpha_min <= p->alpha_max))
+    return fail(EAGPT_ERR_INVALID_ARGUMENT, "alpha_min must be in [0, alpha_max]%s");
+  if (!(p->support_sigma > 0.f && std::isfinite(p->support_sigma)))
+    return fail(EAGPT_ERR_INVALID_ARGUMENT, "support_sigma must be positive%s");
+  if (!(p->bounce_offset >= 0.f && std::isfinite(p->bounce_offset)))
+    return fail(EAGPT_ERR_INVALID_ARGUMENT, "bounce_offset must be >= 0%s");
+  if (!std::isfinite(p->tau_E)) return fail(EAGPT_ERR_INVALID_ARGUMENT, "tau_E must be finite%s");
+  if (p->reserved != 0) return fail(EAGPT_ERR_INVALID_ARGUMENT, "params.reserved must be 0%s");
+  return EAGPT_OK;
+}
+
+eagpt_status check_scene(const eagpt_scene* s) {
+  if (!s) return fail(EAGPT_ERR_INVALID_ARGUMENT, "scene is NULL%s");
+  if (s->n < 0 || s->n > kMaxSurfels) return fail(EAGPT_ERR_INVALID_ARGUMENT, "scene.n out of range: %s%lld", "", s->n);
+  if (s->n > 0) {
+    const void* ptrs[7] = {s->pos, s->quat, s->scale, s->opacity, s->albedo, s->radiance, s->emissive};
+    const char* names[7] = {"pos", "quat", "scale", "opacity", "albedo", "radiance", "emissive"};
+    for (int i = 0; i < 7; ++i) {
+      if (!ptrs[i]) return fail(EAGPT_ERR_INVALID_ARGUMENT, "scene.%s is NULL", names[i]);
+      if (!aligned(ptrs[i], 4)) return fail(EAGPT_ERR_INVALID_ARGUMENT, "scene.%s is not 4-byte aligned", names[i]);
+    }
+  }
+  return EAGPT_OK;
+}
+
+eagpt_status check_camera(const eagpt_camera* c) {
+  if (!c) return fail(EAGPT_ERR_INVALID_ARGUMENT, "camera is NULL%s");
+  if (c->width <= 0 || c->height <= 0) return fail(EAGPT_ERR_INVALID_ARGUMENT, "camera size must be positive%s");
+  if ((int64_t)c->width * c->height > (int64_t)1 << 30)
+    return fail(EAGPT_ERR_INVALID_ARGUMENT, "camera has too many pixels%s");
+  if (!(c->fx != 0.f && c->fy != 0.f && std::isfinite(c->fx) && std::isfinite(c->fy)))
+    return fail(EAGPT_ERR_INVALID_ARGUMENT, "camera focal lengths must be finite and non-zero%s");
+  for (int i = 0; i < 12; ++i)
+    if (!std::isfinite(c->c2w[i])) return fail(EAGPT_ERR_INVALID_ARGUMENT, "camera c2w must be finite%s");
+  return EAGPT_OK;
+}
+
+eagpt_status check_bvh(const eagpt_bvh* b, const eagpt_scene* s, const eagpt_params* p) {
+  if (!b) return fail(EAGPT_ERR_INVALID_ARGUMENT, "bvh is NULL%s");
+  if (b->n != s->n) return fail(EAGPT_ERR_INVALID_ARGUMENT, "bvh was built for another surfel count%s");
+  if (b->scene_version != s->version)
+    return fail(EAGPT_ERR_STALE_BVH, "bvh was built for scene version %s%lld", "", (long long)b->scene_version);
+  if (b->support_sigma != p->support_sigma)
+    return fail(EAGPT_ERR_INVALID_ARGUMENT, "bvh was built with another support_sigma%s");
+  if (s->n > 0) {
+    if (!b->storage || !aligned(b->storage, 256))
+      return fail(EAGPT_ERR_INVALID_ARGUMENT, "bvh storage must be non-NULL and 256-byte aligned%s");
+    if (b->bytes < bvh_layout(s->n).total) return fail(EAGPT_ERR_OUT_OF_MEMORY, "bvh storage too small%s");
+  }
+  return EAGPT_OK;
+}
+
+BvhView make_view(const eagpt_bvh& b) {
+  BvhView v{};
+  v.n = b.n;
+  if (b.n > 0) {
+    const BvhLayout L = bvh_layout(b.n);
+    char* base = (char*)b.storage;
+    v.trace = (const TraceRec*)(base + L.trace);
+    v.shade = (const ShadeRec*)(base + L.shade);
+    v.nodes = (const Node*)(base + L.nodes);
+    v.root = 0;  // node 0: Karras root, or the single node of a small scene
+  }
+  return v;
+}
+
+}  // namespace
+
+extern "C" {
+
+void eagpt_default_params(eagpt_params* p) {
+  if (!p) return;
+  p->tau_E = 0.1f;
+  p->T_min = 1e-3f;
+  p->alpha_min = 1.0f / 255.0f;
+  p->alpha_max = 0.99f;
+  p->support_sigma = 3.0f;
+  p->bounce_offset = 1e-3f;
+  p->reserved = 0;
+}
+
+const char* eagpt_last_error(void) { return g_msg.c_str(); }
+
+const char* eagpt_version(void) { return "eagpt 0.1 (sm_103a)"; }
+
+size_t eagpt_bvh_bytes(int64_t n) {
+  if (n < 0 || n > kMaxSurfels) return 0;
+  return bvh_layout(n).total;
+}
+
+eagpt_status eagpt_build_bvh(const eagpt_scene* scene, const eagpt_params* params, void* storage, size_t bytes,
+                             eagpt_bvh* out, eagpt_stream_t stream) {
+  eagpt_status s;
+  if ((s = check_scene(scene)) != EAGPT_OK) return s;
+  if ((s = check_params(params)) != EAGPT_OK) return s;
+  if (!out) return fail(EAGPT_ERR_INVALID_ARGUMENT, "out is NULL%s");
+  const BvhLayout L = bvh_layout(scene->n);
+  if (scene->n > 0) {
+    if (!storage || !aligned(storage, 256))
+      return fail(EAGPT_ERR_INVALID_ARGUMENT, "storage must be non-NULL and 256-byte aligned%s");
+    if (bytes < L.total) return fail(EAGPT_ERR_OUT_OF_MEMORY, "storage too small: need %s%lld bytes", "", (long long)L.total);
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  float area = 0.f;
+  if (scene->n > 0) {
+    cudaError_t e = launch_build(*scene, make_consts(*params), (char*)storage, L, st, nullptr);
+    if (e != cudaSuccess) return cuda_fail(e, "build_bvh launch");
+    double a = 0.0;
+    e = cudaMemcpyAsync(&a, (char*)storage + L.header + offsetof(BvhHeader, area_sum), sizeof(double),
+                        cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "build_bvh");
+    area = (float)a;
+  }
+  out->storage = storage;
+  out->bytes = bytes;
+  out->n = scene->n;
+  out->scene_version = scene->version;
+  out->support_sigma = params->support_sigma;
+  out->build_area = area;
+  return EAGPT_OK;
+}
+
+size_t eagpt_render_workspace_bytes(const eagpt_camera* cam, int32_t spp, int32_t kind) {
+  (void)kind;
+  if (!cam || cam->width <= 0 || cam->height <= 0 || spp <= 0) return 0;
+  const int64_t npix = (int64_t)cam->width * cam->height;
+  // one pass over all samples, capped at 2^27 paths per pass (~8.6 GB)
+  int64_t batch = spp;
+  const int64_t cap = (int64_t)1 << 27;
+  if (npix * batch > cap) batch = cap / npix > 0 ? cap / npix : 1;
+  return render_layout(npix, spp, (int)batch).total;
+}
+
+size_t eagpt_render_workspace_min_bytes(const eagpt_camera* cam, int32_t spp, int32_t kind) {
+  (void)kind;
+  if (!cam || cam->width <= 0 || cam->height <= 0 || spp <= 0) return 0;
+  return render_layout((int64_t)cam->width * cam->height, spp, 1).total;
+}
+
+static eagpt_status render_common(const eagpt_scene* scene, const eagpt_bvh* bvh, const eagpt_camera* cam,
+                                  const eagpt_params* params, int kind, int32_t spp, int32_t max_bounces,
+                                  int32_t rr_start, uint64_t seed, float* out_rgb, float* out_aux, float* out_samples,
+                                  int64_t* out_stats, void* ws, size_t ws_bytes, eagpt_stream_t stream) {
+  eagpt_status s;
+  if ((s = check_scene(scene)) != EAGPT_OK) return s;
+  if ((s = check_params(params)) != EAGPT_OK) return s;
+  if ((s = check_camera(cam)) != EAGPT_OK) return s;
+  if ((s = check_bvh(bvh, scene, params)) != EAGPT_OK) return s;
+  if (spp <= 0 || spp > (1 << 24)) return fail(EAGPT_ERR_INVALID_ARGUMENT, "spp must be in [1, 2^24]%s");
+  if (kind == 1 && (max_bounces < 0 || max_bounces > 60))
+    return fail(EAGPT_ERR_INVALID_ARGUMENT, "max_bounces must be in [0, 60]%s");
+  if (!out_rgb) return fail(EAGPT_ERR_INVALID_ARGUMENT, "out_rgb is NULL%s");
+  if (!ws || !aligned(ws, 256)) return fail(EAGPT_ERR_INVALID_ARGUMENT, "workspace must be non-NULL and 256-byte aligned%s");
+  const int64_t npix = (int64_t)cam->width * cam->height;
+  if (choose_batch_spp(npix, spp, ws_bytes) < 1)
+    return fail(EAGPT_ERR_OUT_OF_MEMORY, "workspace too small: need at least %s%lld bytes", "",
+                (long long)render_layout(npix, spp, 1).total);
+  RenderArgs a{};
+  a.bvh = make_view(*bvh);
+  a.C = make_consts(*params);
+  a.cam = *cam;
+  a.kind = kind;
+  a.spp = spp;
+  a.max_bounces = kind == 0 ? 1 : max_bounces;
+  a.rr_start = kind == 0 ? (1 << 30) : rr_start;
+  a.seed = seed;
+  a.out_rgb = out_rgb;
+  a.out_aux = out_aux;
+  a.out_samples = out_samples;
+  a.out_stats = out_stats;
+  a.ws = ws;
+  a.ws_bytes = ws_bytes;
+  cudaError_t e = launch_render(a, (cudaStream_t)stream, nullptr);
+  if (e != cudaSuccess) return cuda_fail(e, "render launch");
+  return EAGPT_OK;
+}
+
+eagpt_status eagpt_render_single_bounce(const eagpt_scene* scene, const eagpt_bvh* bvh, const eagpt_camera* cam,
+                                        const eagpt_params* params, int32_t spp, uint64_t seed, float* out_rgb,
+                                        float* out_aux, float* out_samples, void* workspace, size_t workspace_bytes,
+                                        eagpt_stream_t stream) {
+  return render_common(scene, bvh, cam, params, 0, spp, 1, 1 << 30, seed, out_rgb, out_aux, out_samples, nullptr,
+                       workspace, workspace_bytes, stream);
+}
+
+eagpt_status eagpt_render_path_traced(const eagpt_scene* scene, const eagpt_bvh* bvh, const eagpt_camera* cam,
+                                      const eagpt_params* params, int32_t spp, int32_t max_bounces,
+                                      int32_t rr_start_bounce, uint64_t seed, float* out_rgb, float* out_aux,
+                                      float* out_samples, int64_t* out_stats, void* workspace,
+                                      size_t workspace_bytes, eagpt_stream_t stream) {
+  return render_common(scene, bvh, cam, params, 1, spp, max_bounces, rr_start_bounce, seed, out_rgb, out_aux,
+                       out_samples, out_stats, workspace, workspace_bytes, stream);
+}
+
+size_t eagpt_render_backward_workspace_bytes(const eagpt_camera* cam, int32_t spp) {
+  if (!cam || cam->width <= 0 || cam->height <= 0 || spp <= 0) return 0;
+  const int64_t npix = (int64_t)cam->width * cam->height;
+  int64_t batch = spp;
+  const int64_t cap = (int64_t)1 << 26;
+  if (npix * batch > cap) batch = cap / npix > 0 ? cap / npix : 1;
+  return backward_workspace_bytes(npix, spp, (int)batch);
+}
+
+size_t eagpt_render_backward_workspace_min_bytes(const eagpt_camera* cam, int32_t spp) {
+  if (!cam || cam->width <= 0 || cam->height <= 0 || spp <= 0) return 0;
+  return backward_workspace_bytes((int64_t)cam->width * cam->height, spp, 1);
+}
+
+eagpt_status eagpt_render_single_bounce_backward(const eagpt_scene* scene, const eagpt_bvh* bvh,
+                                                 const eagpt_camera* cam, const eagpt_params* params, int32_t spp,
+                                                 uint64_t seed, const float* dL_drgb, const eagpt_scene_grad* grads,
+                                                 void* ws, size_t ws_bytes, eagpt_stream_t stream) {
+  eagpt_status s;
+  if ((s = check_scene(scene)) != EAGPT_OK) return s;
+  if ((s = check_params(params)) != EAGPT_OK) return s;
+  if ((s = check_camera(cam)) != EAGPT_OK) return s;
+  if ((s = check_bvh(bvh, scene, params)) != EAGPT_OK) return s;
+  if (spp <= 0 || spp > (1 << 24)) return fail(EAGPT_ERR_INVALID_ARGUMENT, "spp must be in [1, 2^24]%s");
+  if (!dL_drgb) return fail(EAGPT_ERR_INVALID_ARGUMENT, "dL_drgb is NULL%s");
+  if (!grads || grads->n != scene->n) return fail(EAGPT_ERR_INVALID_ARGUMENT, "grads must match the scene%s");
+  if (scene->n > 0 && (!grads->pos || !grads->quat || !grads->scale || !grads->opacity || !grads->albedo ||
+                       !grads->radiance))
+    return fail(EAGPT_ERR_INVALID_ARGUMENT, "every gradient array is required%s");
+  if (!ws || !aligned(ws, 256)) return fail(EAGPT_ERR_INVALID_ARGUMENT, "workspace must be non-NULL and 256-byte aligned%s");
+  const int64_t npix = (int64_t)cam->width * cam->height;
+  if (backward_choose_batch(npix, spp, ws_bytes) < 1)
+    return fail(EAGPT_ERR_OUT_OF_MEMORY, "workspace too small: need at least %s%lld bytes", "",
+                (long long)backward_workspace_bytes(npix, spp, 1));
+  if (scene->n == 0) return EAGPT_OK;
+  cudaError_t e = launch_backward(make_view(*bvh), make_consts(*params), *cam, *scene, *grads, spp, seed, dL_drgb, ws,
+                                  ws_bytes, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "backward launch");
+  return EAGPT_OK;
+}
+
+eagpt_status eagpt_trace_rays(const eagpt_scene* scene, const eagpt_bvh* bvh, const eagpt_params* params,
+                              int32_t mode, const float* rays, int64_t n_rays, float* out_rec, int32_t* out_hits,
+                              int32_t max_hits, int32_t* out_nhits, eagpt_stream_t stream) {
+  eagpt_status s;
+  if ((s = check_scene(scene)) != EAGPT_OK) return s;
+  if ((s = check_params(params)) != EAGPT_OK) return s;
+  if ((s = check_bvh(bvh, scene, params)) != EAGPT_OK) return s;
+  if (mode != 0 && mode != 1) return fail(EAGPT_ERR_INVALID_ARGUMENT, "mode must be 0 or 1%s");
+  if (n_rays < 0) return fail(EAGPT_ERR_INVALID_ARGUMENT, "n_rays must be >= 0%s");
+  if (n_rays > 0 && (!rays || !out_rec)) return fail(EAGPT_ERR_INVALID_ARGUMENT, "rays and out_rec are required%s");
+  if (out_hits && max_hits <= 0) return fail(EAGPT_ERR_INVALID_ARGUMENT, "max_hits must be positive%s");
+  cudaError_t e = launch_trace_rays(make_view(*bvh), make_consts(*params), mode, rays, n_rays, out_rec, out_hits,
+                                    max_hits, out_nhits, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "trace_rays launch");
+  return EAGPT_OK;
+}
+
+int64_t eagpt_launch_count(void) { return launch_count(); }
+
+eagpt_status eagpt_profile_begin(void) {
+  profile_begin();
+  return EAGPT_OK;
+}
+
+eagpt_status eagpt_profile_end(eagpt_kernel_time* out, int32_t capacity, int32_t* n_out) {
+  if (capacity < 0) return fail(EAGPT_ERR_INVALID_ARGUMENT, "capacity must be >= 0%s");
+  const int n = profile_end(out, capacity);
+  if (n_out) *n_out = n;
+  return EAGPT_OK;
+}
+
+eagpt_status eagpt_sync_status(eagpt_stream_t stream) {
+  cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "sync");
+  const uint32_t word = take_errors_bvh() | take_errors_render() | take_errors_backward();
+  if (word) {
+    char buf[128];
+    std::snprintf(buf, sizeof(buf), "device check failed (error bits 0x%x)", word);
+    g_msg = buf;
+    return EAGPT_ERR_DEVICE_CHECK;
+  }
+  return EAGPT_OK;
+}
+
+}  // extern "C"

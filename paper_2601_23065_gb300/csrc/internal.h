@@ -1,0 +1,88 @@
+// Host-side declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace eagpt {
+
+// bvh.cu
+cudaError_t launch_build(const eagpt_scene& sc, const Consts& C, char* base, const BvhLayout& L, cudaStream_t st,
+                         int* launches);
+int launch_refit(char* base, const BvhLayout& L, cudaStream_t st);
+cudaError_t launch_records_update(const eagpt_scene& sc, const Consts& C, char* base, const BvhLayout& L,
+                                  cudaStream_t st);
+
+// render.cu
+struct RenderArgs {
+  BvhView bvh;
+  Consts C;
+  eagpt_camera cam;
+  int kind;         // 0 single bounce, 1 path tracing
+  int spp, max_bounces, rr_start;
+  uint64_t seed;
+  float* out_rgb;
+  float* out_aux;
+  float* out_samples;
+  int64_t* out_stats;
+  void* ws;
+  size_t ws_bytes;
+};
+
+struct RenderLayout {
+  size_t prim, acc, slots, q0, q1, counters, total;
+  int64_t npix, batch_paths;
+  int batch_spp;
+};
+
+RenderLayout render_layout(int64_t npix, int spp, int batch_spp);
+int choose_batch_spp(int64_t npix, int spp, size_t ws_bytes);
+cudaError_t launch_render(const RenderArgs& a, cudaStream_t st, int* launches);
+cudaError_t launch_trace_rays(const BvhView& bvh, const Consts& C, int mode, const float* rays, int64_t n_rays,
+                              float* out_rec, int32_t* out_hits, int max_hits, int32_t* out_nhits, cudaStream_t st);
+
+cudaError_t launch_primary_records(const BvhView& bvh, const Consts& C, const eagpt_camera& cam, int mode,
+                                   int64_t npix, void* prim, cudaStream_t st);
+
+// backward.cu
+size_t backward_workspace_bytes(int64_t npix, int spp, int batch);
+int backward_choose_batch(int64_t npix, int spp, size_t ws_bytes);
+cudaError_t launch_backward(const BvhView& bvh, const Consts& C, const eagpt_camera& cam, const eagpt_scene& sc,
+                            const eagpt_scene_grad& gr, int spp, uint64_t seed, const float* dL, void* ws,
+                            size_t ws_bytes, cudaStream_t st);
+
+// device error words of each translation unit (read and cleared)
+uint32_t take_errors_bvh();
+uint32_t take_errors_render();
+uint32_t take_errors_backward();
+
+// number of SMs of the current device (cached per device)
+int device_sms();
+
+// profiler.cu: every kernel launch goes through a LaunchScope (counts the
+// launch; with profiling on, records CUDA events around it on its stream)
+class LaunchScope {
+ public:
+  LaunchScope(cudaStream_t st, const char* name);
+  ~LaunchScope();
+  LaunchScope(const LaunchScope&) = delete;
+  LaunchScope& operator=(const LaunchScope&) = delete;
+
+ private:
+  cudaStream_t st_;
+  const char* name_;
+  cudaEvent_t a_;
+};
+int64_t launch_count();
+void profile_begin();
+int profile_end(eagpt_kernel_time* out, int capacity);
+
+#define EAGPT_LAUNCH(st, name, ...)           \
+  do {                                        \
+    ::eagpt::LaunchScope _scope((st), name); \
+    __VA_ARGS__;                              \
+  } while (0)
+
+}  // namespace eagpt

@@ -1,0 +1,443 @@
+// Wavefront renderer: single-bounce estimator (Eq. 6) and path tracing (Eq. 8).
+//
+//   k_primary     one pinhole ray per pixel, traced once and shared by all
+//                 samples (the viewing direction is fixed per pixel); writes
+//                 the pixel's blended record (N~, D~, R, E, P, A).
+//   k_generate    per (sample, pixel) of a sample batch: first bounce of every
+//                 path of a non-emitter primary hit -> ray queue 1.
+//   k_bounce<k>   persistent, warp-fetched: trace the queued ray, blend, then
+//                 either end the path (its contribution goes to its own slot)
+//                 or sample the next bounce and append it to queue k+1 with a
+//                 warp-ballot compaction (one atomic per warp).
+//   k_accumulate  per pixel: the batch's slots in sample order (deterministic,
+//                 independent of the batch size), final mean.
+#include <cuda_runtime.h>
+
+#include <mutex>
+
+#include "common.cuh"
+#include "internal.h"
+#include "trace.cuh"
+
+namespace eagpt {
+
+constexpr int kK = 16;  // k-buffer size (hits collected per traversal round)
+
+EAGPT_DEFINE_ERROR_READER(take_errors_render)
+
+struct __align__(16) Ray {
+  float4 a;  // origin, pixel (bits)
+  float4 b;  // direction, sample (bits)
+  float4 c;  // throughput, unused
+};
+
+struct __align__(16) PrimRec {
+  float4 a;  // N~, D~
+  float4 b;  // R, E
+  float4 c;  // P, A
+};
+
+// counters block: per bounce k, [2k] = rays queued for bounce k, [2k+1] = fetch
+constexpr int kMaxBounces = 60;
+constexpr int kCounterWords = 2 * (kMaxBounces + 2) + 8;
+
+RenderLayout render_layout(int64_t npix, int spp, int batch_spp) {
+  RenderLayout L{};
+  L.npix = npix;
+  L.batch_spp = batch_spp;
+  L.batch_paths = npix * (int64_t)batch_spp;
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    size_t at = o;
+    o = align256(o + bytes);
+    return at;
+  };
+  L.prim = take((size_t)npix * sizeof(PrimRec));
+  L.acc = take((size_t)npix * sizeof(float4));
+  L.slots = take((size_t)L.batch_paths * sizeof(float4));
+  L.q0 = take((size_t)L.batch_paths * sizeof(Ray));
+  L.q1 = take((size_t)L.batch_paths * sizeof(Ray));
+  L.counters = take(kCounterWords * sizeof(uint32_t));
+  L.total = o;
+  (void)spp;
+  return L;
+}
+
+int choose_batch_spp(int64_t npix, int spp, size_t ws_bytes) {
+  int lo = 1, hi = spp;
+  if (render_layout(npix, spp, 1).total > ws_bytes) return 0;
+  while (lo < hi) {  // largest batch that fits
+    const int mid = lo + (hi - lo + 1) / 2;
+    if (render_layout(npix, spp, mid).total <= ws_bytes) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// --------------------------------------------------------------------------
+__device__ __forceinline__ void write_aux(float* aux, int64_t i, const SegRec& s) {
+  float* o = aux + 12 * i;
+  o[0] = s.Nn.x;
+  o[1] = s.Nn.y;
+  o[2] = s.Nn.z;
+  o[3] = s.Dn;
+  o[4] = s.R.x;
+  o[5] = s.R.y;
+  o[6] = s.R.z;
+  o[7] = s.E;
+  o[8] = s.P.x;
+  o[9] = s.P.y;
+  o[10] = s.P.z;
+  o[11] = s.A;
+}
+
+__device__ __forceinline__ void add_stats(int64_t* stats, int slot, uint32_t v) {
+  // warp-aggregated counter update
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0 && v) atomicAdd((unsigned long long*)(stats + slot), (unsigned long long)v);
+}
+
+template <bool kCount>
+__global__ void __launch_bounds__(kBlock) k_primary(BvhView bvh, Consts C, eagpt_camera cam, int mode, int64_t npix,
+                                                    PrimRec* prim, float* aux, int64_t* stats) {
+  __shared__ uint32_t s_stack[kStackSize * kBlock];
+  const int64_t i = blockIdx.x * (int64_t)kBlock + threadIdx.x;
+  TraceCounters cnt{0, 0, 0, 0};
+  if (i < npix) {
+    float3 O, w;
+    camera_ray(cam, (uint32_t)i, O, w);
+    BlendVisitor vis(bvh.shade, C, w, mode);
+    trace_segment<kK, kCount>(bvh, C, O, w, 0.f, s_stack + threadIdx.x, kBlock, vis, cnt);
+    const SegRec s = finish(vis.b);
+    PrimRec p;
+    p.a = make_float4(s.Nn.x, s.Nn.y, s.Nn.z, s.Dn);
+    p.b = make_float4(s.R.x, s.R.y, s.R.z, s.E);
+    p.c = make_float4(s.P.x, s.P.y, s.P.z, s.hit ? s.A : -1.f);  // A < 0 marks a miss
+    prim[i] = p;
+    if (aux) write_aux(aux, i, s);
+  }
+  if (kCount) {
+    add_stats(stats, 0, i < npix ? 1u : 0u);
+    add_stats(stats, 8, cnt.blended);
+    add_stats(stats, 9, cnt.nodes);
+    add_stats(stats, 10, cnt.tests);
+    add_stats(stats, 11, cnt.rounds);
+  }
+}
+
+// Warp-aggregated append of the lanes with `take` set; returns each such
+// lane's index in the queue.  All 32 lanes must call it.
+__device__ __forceinline__ uint32_t warp_append(bool take, uint32_t* counter) {
+  const uint32_t mask = __ballot_sync(0xffffffffu, take);
+  const int lane = threadIdx.x & 31;
+  uint32_t base = 0;
+  if (lane == 0 && mask) base = atomicAdd(counter, (uint32_t)__popc(mask));
+  base = __shfl_sync(0xffffffffu, base, 0);
+  return base + __popc(mask & ((1u << lane) - 1u));
+}
+
+__device__ __forceinline__ bool is_emitter_pixel(const PrimRec& p, const Consts& C) {
+  return p.c.w >= 0.f && p.b.w > C.tau_E;
+}
+
+// First bounce of every path of the batch [s0, s0 + batch) (Sec. 3.1 "Light
+// Bouncing"): X = O + D~ w, throughput P (the cosine pdf cancels cos/pi of
+// the diffuse BRDF), cosine-weighted direction about N~ from X + offset N~.
+template <bool kCount>
+__global__ void __launch_bounds__(kBlock) k_generate(const PrimRec* __restrict__ prim, Consts C, eagpt_camera cam,
+                                                     int kind, int max_bounces, int rr_start, uint64_t seed, int64_t npix,
+                                                     int s0, int batch, Ray* q_out, uint32_t* counters, float4* slots,
+                                                     int64_t* stats) {
+  const int64_t t = blockIdx.x * (int64_t)kBlock + threadIdx.x;
+  const int64_t total = npix * (int64_t)batch;
+  bool take = false;
+  Ray r;
+  int64_t slot = 0;
+  bool started = false;
+  if (t < total) {
+    const int64_t pixel = t % npix;
+    const int sl = (int)(t / npix);
+    slot = t;
+    const PrimRec p = prim[pixel];
+    if (p.c.w >= 0.f && !(p.b.w > C.tau_E)) {
+      started = true;
+      const int B = kind == 0 ? 1 : max_bounces;
+      float3 beta = make_float3(p.c.x, p.c.y, p.c.z);
+      bool alive = B >= 1;
+      const uint32_t sample = (uint32_t)(s0 + sl);
+      const float4 u = draws(seed, (uint32_t)pixel, sample, 1u);
+      if (alive && kind == 1 && rr_start <= 1) {
+        const float q = fminf(1.f, fmaxf(beta.x, fmaxf(beta.y, beta.z)));
+        if (!(u.z < q)) alive = false;
+        else beta = (1.f / q) * beta;
+      }
+      if (alive) {
+        float3 O, w;
+        camera_ray(cam, (uint32_t)pixel, O, w);
+        const float3 Nn = make_float3(p.a.x, p.a.y, p.a.z);
+        const float3 X = O + p.a.w * w;
+        const float3 O2 = X + C.bounce_offset * Nn;
+        const float3 w2 = cosine_direction(Nn, u.x, u.y);
+        r.a = make_float4(O2.x, O2.y, O2.z, __uint_as_float((uint32_t)pixel));
+        r.b = make_float4(w2.x, w2.y, w2.z, __uint_as_float(sample));
+        r.c = make_float4(beta.x, beta.y, beta.z, 0.f);
+        take = true;
+      } else {
+        slots[slot] = make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+    }
+  }
+  const uint32_t at = warp_append(take, &counters[2 * 1]);
+  if (take) q_out[at] = r;
+  if (kCount) add_stats(stats, 2, started ? 1u : 0u);
+}
+
+// One bounce k of every queued path (Eq. 6 for kind 0, Eq. 8 for kind 1).
+template <bool kCount>
+__global__ void __launch_bounds__(kBlock) k_bounce(BvhView bvh, Consts C, int kind, int k, int max_bounces,
+                                                   int rr_start, uint64_t seed, int64_t npix, int s0,
+                                                   const Ray* __restrict__ q_in, Ray* q_out, uint32_t* counters,
+                                                   float4* slots, int64_t* stats) {
+  __shared__ uint32_t s_stack[kStackSize * kBlock];
+  const int lane = threadIdx.x & 31;
+  const uint32_t count = counters[2 * k];
+  const int mode = kind == 0 ? 0 : 1;
+  TraceCounters cnt{0, 0, 0, 0};
+  uint32_t traced = 0;
+  for (;;) {
+    uint32_t base = 0;
+    if (lane == 0) base = atomicAdd(&counters[2 * k + 1], 32u);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (base >= count) break;
+    const uint32_t idx = base + lane;
+    bool take = false;
+    Ray nr;
+    if (idx < count) {
+      ++traced;
+      const Ray r = q_in[idx];
+      const float3 O = f3(r.a), w = f3(r.b);
+      const uint32_t pixel = __float_as_uint(r.a.w), sample = __float_as_uint(r.b.w);
+      float3 beta = f3(r.c);
+      BlendVisitor vis(bvh.shade, C, w, mode);
+      trace_segment<kK, kCount>(bvh, C, O, w, 0.f, s_stack + threadIdx.x, kBlock, vis, cnt);
+      const SegRec s = finish(vis.b);
+      const int64_t slot = (int64_t)(sample - (uint32_t)s0) * npix + pixel;
+      float3 contrib = make_float3(0.f, 0.f, 0.f);
+      bool end = true;
+      if (kind == 0) {
+        contrib = mul3(beta, s.R);  // the secondary's radiance is the cache
+      } else if (!s.hit) {
+        // miss: no light
+      } else if (s.E > C.tau_E) {
+        contrib = mul3(beta, s.R);  // first emissive vertex
+      } else if (k < max_bounces) {
+        beta = mul3(beta, s.P);
+        const float4 u = draws(seed, pixel, sample, (uint32_t)(k + 1));
+        bool alive = true;
+        if (k + 1 >= rr_start) {
+          const float q = fminf(1.f, fmaxf(beta.x, fmaxf(beta.y, beta.z)));
+          if (!(u.z < q)) alive = false;
+          else beta = (1.f / q) * beta;
+        }
+        if (alive) {
+          const float3 X = O + s.Dn * w;
+          const float3 O2 = X + C.bounce_offset * s.Nn;
+          const float3 w2 = cosine_direction(s.Nn, u.x, u.y);
+          nr.a = make_float4(O2.x, O2.y, O2.z, r.a.w);
+          nr.b = make_float4(w2.x, w2.y, w2.z, r.b.w);
+          nr.c = make_float4(beta.x, beta.y, beta.z, 0.f);
+          take = true;
+          end = false;
+        }
+      }
+      if (end) slots[slot] = make_float4(contrib.x, contrib.y, contrib.z, 0.f);
+    }
+    __syncwarp();
+    const uint32_t at = warp_append(take, &counters[2 * (k + 1)]);
+    if (take) q_out[at] = nr;
+  }
+  if (kCount) {
+    add_stats(stats, 1, traced);
+    add_stats(stats, 3, cnt.blended);
+    add_stats(stats, 4, cnt.nodes);
+    add_stats(stats, 5, cnt.tests);
+    add_stats(stats, 6, cnt.rounds);
+  }
+}
+
+// Per pixel: add the batch's samples in order; on the last batch write the
+// mean.  Emitter pixels show R (Eq. 4), missed pixels 0.
+__global__ void __launch_bounds__(kBlock) k_accumulate(const PrimRec* __restrict__ prim, Consts C, int64_t npix,
+                                                       int s0, int batch, int spp, int first, int last,
+                                                       const float4* __restrict__ slots, float4* acc,
+                                                       float* out_rgb, float* out_samples) {
+  const int64_t i = blockIdx.x * (int64_t)kBlock + threadIdx.x;
+  if (i >= npix) return;
+  const PrimRec p = prim[i];
+  const bool hit = p.c.w >= 0.f;
+  const bool emit = hit && p.b.w > C.tau_E;
+  if (!hit || emit) {
+    const float3 v = emit ? f3(p.b) : make_float3(0.f, 0.f, 0.f);
+    if (out_samples)
+      for (int s = 0; s < batch; ++s) {
+        float* o = out_samples + 3 * (i * spp + s0 + s);
+        o[0] = v.x;
+        o[1] = v.y;
+        o[2] = v.z;
+      }
+    if (last) {
+      out_rgb[3 * i] = v.x;
+      out_rgb[3 * i + 1] = v.y;
+      out_rgb[3 * i + 2] = v.z;
+    }
+    return;
+  }
+  float4 a = first ? make_float4(0.f, 0.f, 0.f, 0.f) : acc[i];
+  for (int s = 0; s < batch; ++s) {
+    const float4 c = slots[(int64_t)s * npix + i];
+    a.x += c.x;
+    a.y += c.y;
+    a.z += c.z;
+    if (out_samples) {
+      float* o = out_samples + 3 * (i * spp + s0 + s);
+      o[0] = c.x;
+      o[1] = c.y;
+      o[2] = c.z;
+    }
+  }
+  if (last) {
+    const float inv = 1.f / (float)spp;
+    out_rgb[3 * i] = a.x * inv;
+    out_rgb[3 * i + 1] = a.y * inv;
+    out_rgb[3 * i + 2] = a.z * inv;
+  } else {
+    acc[i] = a;
+  }
+}
+
+// --------------------------------------------------------------------------
+// caller rays
+// --------------------------------------------------------------------------
+struct RecordVisitor {
+  BlendVisitor blend;
+  int32_t* hits;
+  int max_hits;
+  __device__ __forceinline__ RecordVisitor(const ShadeRec* s, const Consts& c, float3 w, int m, int32_t* h, int mh)
+      : blend(s, c, w, m), hits(h), max_hits(mh) {}
+  __device__ __forceinline__ bool operator()(const TraceRec& R, uint32_t j, const HitGeom& g) {
+    if (hits && (int)blend.b.n_hits < max_hits) hits[blend.b.n_hits] = (int32_t)__float_as_uint(R.r1.w);
+    return blend(R, j, g);
+  }
+};
+
+__global__ void __launch_bounds__(kBlock) k_trace_rays(BvhView bvh, Consts C, int mode, const float* __restrict__ rays,
+                                                       int64_t n_rays, float* out_rec, int32_t* out_hits, int max_hits,
+                                                       int32_t* out_nhits) {
+  __shared__ uint32_t s_stack[kStackSize * kBlock];
+  const int64_t i = blockIdx.x * (int64_t)kBlock + threadIdx.x;
+  if (i >= n_rays) return;
+  const float3 O = make_float3(rays[6 * i], rays[6 * i + 1], rays[6 * i + 2]);
+  const float3 w = make_float3(rays[6 * i + 3], rays[6 * i + 4], rays[6 * i + 5]);
+  int32_t* hits = out_hits ? out_hits + i * (int64_t)max_hits : nullptr;
+  if (hits)
+    for (int k = 0; k < max_hits; ++k) hits[k] = -1;
+  RecordVisitor vis(bvh.shade, C, w, mode, hits, max_hits);
+  TraceCounters cnt{0, 0, 0, 0};
+  trace_segment<kK, false>(bvh, C, O, w, 0.f, s_stack + threadIdx.x, kBlock, vis, cnt);
+  const SegRec s = finish(vis.blend.b);
+  write_aux(out_rec, i, s);
+  if (out_nhits) out_nhits[i] = (int32_t)vis.blend.b.n_hits;
+}
+
+// --------------------------------------------------------------------------
+// host side
+// --------------------------------------------------------------------------
+int device_sms() {
+  static std::mutex mu;
+  static int cache[64] = {0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> g(mu);
+  if (dev < 0 || dev >= 64) return 1;
+  if (!cache[dev]) {
+    int v = 0;
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    cache[dev] = v > 0 ? v : 1;
+  }
+  return cache[dev];
+}
+
+template <class F>
+static int persistent_blocks(F kernel) {
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kBlock, 0);
+  if (per_sm < 1) per_sm = 1;
+  return per_sm * device_sms();
+}
+
+static inline unsigned nblocks(int64_t n) { return (unsigned)((n + kBlock - 1) / kBlock); }
+
+template <bool kCount>
+static cudaError_t render_impl(const RenderArgs& a, cudaStream_t st, int* launches) {
+  const int64_t npix = (int64_t)a.cam.width * a.cam.height;
+  const int batch = choose_batch_spp(npix, a.spp, a.ws_bytes);
+  const RenderLayout L = render_layout(npix, a.spp, batch);
+  char* ws = (char*)a.ws;
+  PrimRec* prim = (PrimRec*)(ws + L.prim);
+  float4* acc = (float4*)(ws + L.acc);
+  float4* slots = (float4*)(ws + L.slots);
+  Ray* q[2] = {(Ray*)(ws + L.q0), (Ray*)(ws + L.q1)};
+  uint32_t* counters = (uint32_t*)(ws + L.counters);
+  const int mode = a.kind == 0 ? 0 : 1;
+  const int B = a.kind == 0 ? 1 : a.max_bounces;
+  int nl = 0;
+  EAGPT_LAUNCH(st, "k_primary", k_primary<kCount><<<nblocks(npix), kBlock, 0, st>>>(a.bvh, a.C, a.cam, mode, npix, prim, a.out_aux, a.out_stats));
+  ++nl;
+  static int bounce_grid[2] = {0, 0};
+  if (!bounce_grid[kCount]) bounce_grid[kCount] = persistent_blocks(k_bounce<kCount>);
+  for (int s0 = 0; s0 < a.spp; s0 += batch) {
+    const int nb = a.spp - s0 < batch ? a.spp - s0 : batch;
+    cudaMemsetAsync(counters, 0, kCounterWords * sizeof(uint32_t), st);
+    EAGPT_LAUNCH(st, "k_generate", k_generate<kCount><<<nblocks(npix * nb), kBlock, 0, st>>>(prim, a.C, a.cam, a.kind, B, a.rr_start, a.seed, npix,
+                                                              s0, nb, q[0], counters, slots, a.out_stats));
+    ++nl;
+    for (int k = 1; k <= B; ++k) {
+      EAGPT_LAUNCH(st, "k_bounce", k_bounce<kCount><<<bounce_grid[kCount], kBlock, 0, st>>>(a.bvh, a.C, a.kind, k, B, a.rr_start, a.seed, npix,
+                                                                s0, q[(k - 1) & 1], q[k & 1], counters, slots,
+                                                                a.out_stats));
+      ++nl;
+    }
+    EAGPT_LAUNCH(st, "k_accumulate", k_accumulate<<<nblocks(npix), kBlock, 0, st>>>(prim, a.C, npix, s0, nb, a.spp, s0 == 0, s0 + nb >= a.spp, slots,
+                                                   acc, a.out_rgb, a.out_samples));
+    ++nl;
+  }
+  if (launches) *launches += nl;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_render(const RenderArgs& a, cudaStream_t st, int* launches) {
+  return a.out_stats ? render_impl<true>(a, st, launches) : render_impl<false>(a, st, launches);
+}
+
+cudaError_t launch_trace_rays(const BvhView& bvh, const Consts& C, int mode, const float* rays, int64_t n_rays,
+                              float* out_rec, int32_t* out_hits, int max_hits, int32_t* out_nhits, cudaStream_t st) {
+  if (n_rays > 0)
+    EAGPT_LAUNCH(st, "k_trace_rays", k_trace_rays<<<nblocks(n_rays), kBlock, 0, st>>>(bvh, C, mode, rays, n_rays, out_rec, out_hits, max_hits,
+                                                     out_nhits));
+  return cudaGetLastError();
+}
+
+}  // namespace eagpt
+
+namespace eagpt {
+
+// Primary records only (used by the adjoint, which re-traces them).
+cudaError_t launch_primary_records(const BvhView& bvh, const Consts& C, const eagpt_camera& cam, int mode,
+                                   int64_t npix, void* prim, cudaStream_t st) {
+  EAGPT_LAUNCH(st, "k_primary",
+               k_primary<false><<<nblocks(npix), kBlock, 0, st>>>(bvh, C, cam, mode, npix, (PrimRec*)prim, nullptr,
+                                                                 nullptr));
+  return cudaGetLastError();
+}
+
+}  // namespace eagpt

@@ -1,0 +1,259 @@
+// Segment tracing through the surfel BVH (Sec. 3.1, Eq. 1-3).
+//
+// A segment (origin O, unit direction w, hits with t > t_lo) is traced in
+// rounds.  Each round walks the BVH once and keeps the K nearest not-yet-
+// blended hits, ordered by (t, BVH position), in a register k-buffer; the
+// round's hits are then handed in order to a visitor (the front-to-back blend
+// of Eq. 2, or the adjoint), which may stop the segment (transmittance below
+// T_min).  A new round starts after the last handed hit only when the buffer
+// was full, so every hit is visited exactly once and in depth order.
+//
+// The intersection is written with explicit round-to-nearest intrinsics so
+// that recomputing it for a buffered hit gives bit-identical t and alpha.
+#pragma once
+
+#include "common.cuh"
+
+namespace eagpt {
+
+__device__ __forceinline__ float dot3_rn(float3 a, float3 b) {
+  return __fmaf_rn(a.z, b.z, __fmaf_rn(a.y, b.y, __fmul_rn(a.x, b.x)));
+}
+
+struct HitGeom {
+  float t, alpha, sg, u, v, d;
+};
+
+// Ray-surfel hit (Eq. 1): plane distance t, local (u, v), response
+// g = exp(-(u^2 + v^2)/2), alpha = min(sigma g, alpha_max).  Returns false if
+// the ray is parallel, outside the support or below alpha_min.  The t > t_lo
+// test is left to the caller.
+__device__ __forceinline__ bool intersect(const TraceRec& R, float3 O, float3 w, const Consts& C, HitGeom& h) {
+  const float3 p = f3(R.r0), n = f3(R.r1), a = f3(R.r2), b = f3(R.r3);
+  const float d = dot3_rn(w, n);
+  if (!(fabsf(d) >= 1e-12f)) return false;
+  const float3 op = make_float3(__fsub_rn(O.x, p.x), __fsub_rn(O.y, p.y), __fsub_rn(O.z, p.z));
+  const float t = __fdiv_rn(-dot3_rn(op, n), d);
+  const float3 x = make_float3(__fmaf_rn(t, w.x, op.x), __fmaf_rn(t, w.y, op.y), __fmaf_rn(t, w.z, op.z));
+  const float u = dot3_rn(x, a), v = dot3_rn(x, b);
+  const float q = __fmaf_rn(u, u, __fmul_rn(v, v));
+  if (!(q <= C.support2)) return false;
+  const float sg = __fmul_rn(R.r0.w, __expf(-0.5f * q));
+  const float alpha = fminf(sg, C.alpha_max);
+  if (!(alpha >= C.alpha_min)) return false;
+  h.t = t;
+  h.alpha = alpha;
+  h.sg = sg;
+  h.u = u;
+  h.v = v;
+  h.d = d;
+  return true;
+}
+
+// Slab test of an axis-aligned box against [tmin, tmax]; returns the entry t.
+__device__ __forceinline__ bool box_hit(float3 lo, float3 hi, float3 O, float3 inv, float tmin, float tmax,
+                                        float& t_enter) {
+  const float tx0 = (lo.x - O.x) * inv.x, tx1 = (hi.x - O.x) * inv.x;
+  const float ty0 = (lo.y - O.y) * inv.y, ty1 = (hi.y - O.y) * inv.y;
+  const float tz0 = (lo.z - O.z) * inv.z, tz1 = (hi.z - O.z) * inv.z;
+  const float t0 = fmaxf(fmaxf(fminf(tx0, tx1), fminf(ty0, ty1)), fmaxf(fminf(tz0, tz1), tmin));
+  const float t1 = fminf(fminf(fmaxf(tx0, tx1), fmaxf(ty0, ty1)), fminf(fmaxf(tz0, tz1), tmax));
+  t_enter = t0;
+  return t0 <= t1;
+}
+
+__device__ __forceinline__ bool key_less(float ta, uint32_t ia, float tb, uint32_t ib) {
+  return ta < tb || (ta == tb && ia < ib);
+}
+
+// Counters of the work one segment did (enabled by the kCount template flag).
+struct TraceCounters {
+  uint32_t nodes, tests, blended, rounds;
+};
+
+// Walks the BVH for hits with key (t, j) > (t_last, j_last), up to K of
+// them, nearest first.  `stack` points at this thread's column of a
+// shared-memory stack with `stride` words between entries.
+template <int K, bool kCount>
+__device__ __forceinline__ int collect_round(const BvhView& bvh, const Consts& C, float3 O, float3 w, float3 inv,
+                                             float t_last, uint32_t j_last, float (&kt)[K], uint32_t (&kj)[K],
+                                             uint32_t* stack, int stride, TraceCounters& cnt) {
+#pragma unroll
+  for (int i = 0; i < K; ++i) {
+    kt[i] = __int_as_float(0x7f800000);  // +inf
+    kj[i] = 0xFFFFFFFFu;
+  }
+  int count = 0;
+  int sp = 0;
+  uint32_t cur = bvh.root;
+  for (;;) {
+    if (cur & kLeafBit) {
+      const uint32_t start = cur & kLeafStartMask;
+      const uint32_t cnum = ((cur >> kLeafCountShift) & 3u) + 1u;
+      for (uint32_t j = start; j < start + cnum; ++j) {
+        const TraceRec* rp = bvh.trace + j;
+        TraceRec R;
+        R.r0 = __ldg(&rp->r0);
+        R.r1 = __ldg(&rp->r1);
+        R.r2 = __ldg(&rp->r2);
+        R.r3 = __ldg(&rp->r3);
+        if (kCount) ++cnt.tests;
+        HitGeom h;
+        if (!intersect(R, O, w, C, h)) continue;
+        if (!key_less(t_last, j_last, h.t, j)) continue;  // already blended (or behind)
+        if (count == K && !key_less(h.t, j, kt[K - 1], kj[K - 1])) continue;
+        float ct = h.t;
+        uint32_t cj = j;
+#pragma unroll
+        for (int i = 0; i < K; ++i) {
+          const bool lt = key_less(ct, cj, kt[i], kj[i]);
+          const float tt = kt[i];
+          const uint32_t tj = kj[i];
+          kt[i] = lt ? ct : tt;
+          kj[i] = lt ? cj : tj;
+          ct = lt ? tt : ct;
+          cj = lt ? tj : cj;
+        }
+        count = count < K ? count + 1 : K;
+      }
+    } else if (cur != kEmptyChild) {
+      const Node* np = bvh.nodes + cur;
+      const float4 a = __ldg(&np->n0), b = __ldg(&np->n1), c = __ldg(&np->n2);
+      const uint4 ch = __ldg(&np->n3);
+      if (kCount) ++cnt.nodes;
+      const float tmax = count == K ? kt[K - 1] : __int_as_float(0x7f800000);
+      float e0, e1;
+      const bool h0 = ch.x != kEmptyChild &&
+                      box_hit(make_float3(a.x, a.y, a.z), make_float3(a.w, b.x, b.y), O, inv, t_last, tmax, e0);
+      const bool h1 = ch.y != kEmptyChild &&
+                      box_hit(make_float3(b.z, b.w, c.x), make_float3(c.y, c.z, c.w), O, inv, t_last, tmax, e1);
+      if (h0 && h1) {
+        const bool first0 = e0 <= e1;
+        if (sp >= kStackSize) {
+          raise_error(kErrStackOverflow);
+          return count;
+        }
+        stack[(sp++) * stride] = first0 ? ch.y : ch.x;
+        cur = first0 ? ch.x : ch.y;
+        continue;
+      }
+      if (h0) {
+        cur = ch.x;
+        continue;
+      }
+      if (h1) {
+        cur = ch.y;
+        continue;
+      }
+    }
+    if (sp == 0) break;
+    cur = stack[(--sp) * stride];
+  }
+  return count;
+}
+
+// Blend state of one segment (Eq. 2): raw sums N, D, R, E, P and T.
+struct Blend {
+  float3 N, R, P;
+  float D, E, T;
+  uint32_t n_hits;
+};
+
+// Traces one segment and calls vis(R, j, h) for every blended hit in order;
+// vis returns true to stop.  Returns the hit count handed to the visitor.
+template <int K, bool kCount, class Visitor>
+__device__ __forceinline__ void trace_segment(const BvhView& bvh, const Consts& C, float3 O, float3 w, float t_lo,
+                                              uint32_t* stack, int stride, Visitor& vis, TraceCounters& cnt) {
+  if (bvh.n <= 0) return;
+  const float big = 1e30f;
+  const float3 inv = make_float3(fabsf(w.x) > 1e-30f ? 1.0f / w.x : copysignf(big, w.x),
+                                 fabsf(w.y) > 1e-30f ? 1.0f / w.y : copysignf(big, w.y),
+                                 fabsf(w.z) > 1e-30f ? 1.0f / w.z : copysignf(big, w.z));
+  float t_last = t_lo;
+  uint32_t j_last = 0xFFFFFFFFu;
+  for (;;) {
+    float kt[K];
+    uint32_t kj[K];
+    if (kCount) ++cnt.rounds;
+    const int count = collect_round<K, kCount>(bvh, C, O, w, inv, t_last, j_last, kt, kj, stack, stride, cnt);
+    bool stop = false;
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+      if (i < count && !stop) {
+        const uint32_t j = kj[i];
+        const TraceRec* rp = bvh.trace + j;
+        TraceRec R;
+        R.r0 = __ldg(&rp->r0);
+        R.r1 = __ldg(&rp->r1);
+        R.r2 = __ldg(&rp->r2);
+        R.r3 = __ldg(&rp->r3);
+        HitGeom h;
+        intersect(R, O, w, C, h);  // bit-identical to the collection pass
+        if (kCount) ++cnt.blended;
+        stop = vis(R, j, h);
+      }
+    }
+    if (stop || count < K) return;
+    t_last = kt[K - 1];
+    j_last = kj[K - 1];
+  }
+}
+
+// The front-to-back blend of Eq. 2-3.  mode 1 drops the radiance of
+// non-emitters (path tracing, Sec. 3.4).
+struct BlendVisitor {
+  const ShadeRec* shade;
+  Consts C;
+  float3 w;
+  int mode;
+  Blend b;
+  __device__ __forceinline__ BlendVisitor(const ShadeRec* s, const Consts& c, float3 dir, int m)
+      : shade(s), C(c), w(dir), mode(m) {
+    b.N = b.R = b.P = make_float3(0.f, 0.f, 0.f);
+    b.D = b.E = 0.f;
+    b.T = 1.f;
+    b.n_hits = 0;
+  }
+  __device__ __forceinline__ bool operator()(const TraceRec& R, uint32_t j, const HitGeom& h) {
+    const ShadeRec* sp = shade + j;
+    const float4 s0 = __ldg(&sp->s0), s1 = __ldg(&sp->s1);
+    const float wgt = b.T * h.alpha;
+    const float sgn = h.d > 0.f ? -wgt : wgt;  // normal facing the ray origin
+    const float re = (mode == 1 && !(s0.w > C.tau_E)) ? 0.f : wgt;
+    b.N = b.N + sgn * f3(R.r1);
+    b.D += wgt * h.t;
+    b.R = b.R + re * make_float3(s1.x, s1.y, s1.z);
+    b.E += wgt * s0.w;
+    b.P = b.P + wgt * make_float3(s0.x, s0.y, s0.z);
+    b.T *= (1.f - h.alpha);
+    ++b.n_hits;
+    return b.T < C.T_min;
+  }
+};
+
+// Normalised record of a blended segment: N~ = N/|N|, D~ = D/A, A = 1 - T.
+struct SegRec {
+  float3 Nn, R, P;
+  float Dn, E, A;
+  bool hit;
+};
+
+__device__ __forceinline__ SegRec finish(const Blend& b) {
+  SegRec s;
+  s.A = 1.f - b.T;
+  s.R = b.R;
+  s.P = b.P;
+  s.E = b.E;
+  s.hit = b.n_hits > 0;
+  if (s.hit) {
+    const float inv = rsqrtf(dot3(b.N, b.N));
+    s.Nn = inv * b.N;
+    s.Dn = b.D / s.A;
+  } else {
+    s.Nn = make_float3(0.f, 0.f, 0.f);
+    s.Dn = 0.f;
+  }
+  return s;
+}
+
+}  // namespace eagpt

@@ -1,0 +1,87 @@
+"""The C-ABI library builds for sm_103a, loads without a GPU and exports
+every symbol declared in include/eagpt.h; argument checks that need no
+device memory reject bad input.  No compute call is made here."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    src = open(os.path.join(ROOT, "include", "eagpt.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(eagpt_[a-z0-9_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2601_23065_gb300 import build, capi
+    build.build()
+    return capi.lib()
+
+
+def test_exports_every_declared_symbol(lib):
+    syms = declared_symbols()
+    assert len(syms) >= 10
+    missing = [s for s in syms if not hasattr(lib, s)]
+    assert not missing, missing
+
+
+def test_signatures_cover_header(lib):
+    from paper_2601_23065_gb300 import capi
+    assert set(declared_symbols()) <= set(capi.SIGNATURES), set(declared_symbols()) - set(capi.SIGNATURES)
+
+
+def test_defaults_and_sizes(lib):
+    from paper_2601_23065_gb300 import capi
+    p = capi.default_params()
+    assert abs(p.tau_E - 0.1) < 1e-7 and p.support_sigma == 3.0 and p.reserved == 0
+    assert lib.eagpt_bvh_bytes(0) > 0
+    assert lib.eagpt_bvh_bytes(1000) > 1000 * 64
+    assert lib.eagpt_bvh_bytes(-1) == 0
+    cam = capi.Camera(64, 64, 32.0, 32.0, 32.0, 32.0)
+    a = lib.eagpt_render_workspace_bytes(ctypes.byref(cam), 4, 1)
+    b = lib.eagpt_render_workspace_min_bytes(ctypes.byref(cam), 4, 1)
+    assert a >= b > 64 * 64 * 48
+
+
+def test_host_argument_checks(lib):
+    from paper_2601_23065_gb300 import capi
+    p = capi.default_params()
+    out = capi.Bvh()
+    assert lib.eagpt_build_bvh(None, ctypes.byref(p), None, 0, ctypes.byref(out), None) == 1
+    sc = capi.Scene()
+    sc.n = 5  # pointers NULL
+    assert lib.eagpt_build_bvh(ctypes.byref(sc), ctypes.byref(p), None, 0, ctypes.byref(out), None) == 1
+    assert b"pos" in lib.eagpt_last_error()
+    sc.n = -3
+    assert lib.eagpt_build_bvh(ctypes.byref(sc), ctypes.byref(p), None, 0, ctypes.byref(out), None) == 1
+    bad = capi.default_params()
+    bad.T_min = 0.0
+    sc.n = 0
+    assert lib.eagpt_build_bvh(ctypes.byref(sc), ctypes.byref(bad), None, 0, ctypes.byref(out), None) == 1
+    bad = capi.default_params()
+    bad.reserved = 1
+    assert lib.eagpt_build_bvh(ctypes.byref(sc), ctypes.byref(bad), None, 0, ctypes.byref(out), None) == 1
+    # stale BVH: version mismatch is refused before anything is launched
+    cam = capi.Camera(8, 8, 4.0, 4.0, 4.0, 4.0)
+    bvh = capi.Bvh()
+    bvh.n, bvh.scene_version, bvh.support_sigma = 0, 3, 3.0
+    sc.version = 4
+    rgb = ctypes.c_void_p(16)
+    st = lib.eagpt_render_path_traced(ctypes.byref(sc), ctypes.byref(bvh), ctypes.byref(cam), ctypes.byref(p), 4, 2,
+                                      2, 0, rgb, None, None, None, ctypes.c_void_p(256), 1 << 20, None)
+    assert st == 4
+    sc.version = 3
+    st = lib.eagpt_render_path_traced(ctypes.byref(sc), ctypes.byref(bvh), ctypes.byref(cam), ctypes.byref(p), 0, 2,
+                                      2, 0, rgb, None, None, None, ctypes.c_void_p(256), 1 << 20, None)
+    assert st == 1 and b"spp" in lib.eagpt_last_error()
+    st = lib.eagpt_render_path_traced(ctypes.byref(sc), ctypes.byref(bvh), ctypes.byref(cam), ctypes.byref(p), 4, 99,
+                                      2, 0, rgb, None, None, None, ctypes.c_void_p(256), 1 << 20, None)
+    assert st == 1
+    st = lib.eagpt_render_path_traced(ctypes.byref(sc), ctypes.byref(bvh), ctypes.byref(cam), ctypes.byref(p), 4, 2,
+                                      2, 0, rgb, None, None, None, ctypes.c_void_p(256), 16, None)
+    assert st == 2  # workspace too small
