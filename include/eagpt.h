@@ -174,6 +174,35 @@ eagpt_status eagpt_render_path_traced(const eagpt_scene* scene, const eagpt_bvh*
                                       eagpt_stream_t stream);
 
 /* ------------------------------------------------------------------------
+ * Allocation-free path-traced render.  The paper has no counterpart: this is
+ * a deployment variant of eagpt_render_path_traced() for callers that cannot
+ * allocate device memory themselves -- a plugin inside a host application
+ * whose memory manager owns the device heap, or a latency-critical loop that
+ * must not pay for cudaMalloc.  It renders exactly what
+ * eagpt_render_path_traced() renders (same kernels, same arguments, no aux,
+ * sample or stats output) but takes its workspace from a fixed scratch array
+ * of eagpt_render_path_traced_noalloc_max_bytes() bytes (32 MiB) compiled
+ * into the library; every GPU that loads the library holds that array until
+ * the process exits.  The call itself allocates nothing.
+ *  - Size limit: a render whose smallest workspace (one sample per pass,
+ *    eagpt_render_workspace_min_bytes()) exceeds the scratch is rejected with
+ *    EAGPT_ERR_INVALID_ARGUMENT and a message naming both sizes.  Larger
+ *    renders fit in fewer samples per pass; results do not depend on it.
+ *  - Set-up: the first call on each device looks up the scratch's device
+ *    address (cudaGetSymbolAddress, with that device current) and caches it;
+ *    make that first call before any stream capture begins.
+ *  - Sharing: all calls on a device share the one scratch array, which keeps
+ *    the last call's contents (the render zeroes what it needs zeroed).  Calls
+ *    whose work overlaps on the GPU (different streams, or different host
+ *    threads) race on it: serialise them, e.g. on one stream.
+ *  - out_rgb: device, H x W x 3. */
+size_t eagpt_render_path_traced_noalloc_max_bytes(void);
+eagpt_status eagpt_render_path_traced_noalloc(const eagpt_scene* scene, const eagpt_bvh* bvh,
+                                              const eagpt_camera* cam, const eagpt_params* params, int32_t spp,
+                                              int32_t max_bounces, int32_t rr_start_bounce, uint64_t seed,
+                                              float* out_rgb, eagpt_stream_t stream);
+
+/* ------------------------------------------------------------------------
  * Adjoint of the single-bounce render (Eq. 6; differentiable 2D Gaussian ray
  * tracing, Sec. 3.2-3.3, with the gradient of Eq. 7 extended from the albedo
  * to every surfel parameter).  For L = sum_p sum_c dL_drgb[p][c] * I[p][c]

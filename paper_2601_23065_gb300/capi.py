@@ -81,6 +81,9 @@ SIGNATURES = {
     "eagpt_render_path_traced": (c_i32, [P(Scene), P(Bvh), P(Camera), P(Params), c_i32, c_i32, c_i32, c_u64,
                                          c_vp, c_vp, c_vp, c_vp, c_vp, c_sz, c_vp]),
     "eagpt_trace_rays": (c_i32, [P(Scene), P(Bvh), P(Params), c_i32, c_vp, c_i64, c_vp, c_vp, c_i32, c_vp, c_vp]),
+    "eagpt_render_path_traced_noalloc_max_bytes": (c_sz, []),
+    "eagpt_render_path_traced_noalloc": (c_i32, [P(Scene), P(Bvh), P(Camera), P(Params), c_i32, c_i32, c_i32, c_u64,
+                                                 c_vp, c_vp]),
     "eagpt_render_backward_workspace_bytes": (c_sz, [P(Camera), c_i32]),
     "eagpt_render_backward_workspace_min_bytes": (c_sz, [P(Camera), c_i32]),
     "eagpt_render_single_bounce_backward": (c_i32, [P(Scene), P(Bvh), P(Camera), P(Params), c_i32, c_u64, c_vp,

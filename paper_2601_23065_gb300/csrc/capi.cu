@@ -174,6 +174,17 @@ size_t eagpt_render_workspace_min_bytes(const eagpt_camera* cam, int32_t spp, in
   return render_layout((int64_t)cam->width * cam->height, spp, 1).total;
 }
 
+}  // extern "C"
+
+namespace eagpt {
+eagpt_status set_error(eagpt_status s, const char* msg) {
+  g_msg = msg;
+  return s;
+}
+}  // namespace eagpt
+
+extern "C" {
+
 static eagpt_status render_common(const eagpt_scene* scene, const eagpt_bvh* bvh, const eagpt_camera* cam,
                                   const eagpt_params* params, int kind, int32_t spp, int32_t max_bounces,
                                   int32_t rr_start, uint64_t seed, float* out_rgb, float* out_aux, float* out_samples,
@@ -211,6 +222,20 @@ static eagpt_status render_common(const eagpt_scene* scene, const eagpt_bvh* bvh
   if (e != cudaSuccess) return cuda_fail(e, "render launch");
   return EAGPT_OK;
 }
+
+}  // extern "C"
+
+namespace eagpt {
+eagpt_status render_entry(const eagpt_scene* scene, const eagpt_bvh* bvh, const eagpt_camera* cam,
+                          const eagpt_params* params, int kind, int32_t spp, int32_t max_bounces, int32_t rr_start,
+                          uint64_t seed, float* out_rgb, float* out_aux, float* out_samples, int64_t* out_stats,
+                          void* ws, size_t ws_bytes, eagpt_stream_t stream) {
+  return render_common(scene, bvh, cam, params, kind, spp, max_bounces, rr_start, seed, out_rgb, out_aux,
+                       out_samples, out_stats, ws, ws_bytes, stream);
+}
+}  // namespace eagpt
+
+extern "C" {
 
 eagpt_status eagpt_render_single_bounce(const eagpt_scene* scene, const eagpt_bvh* bvh, const eagpt_camera* cam,
                                         const eagpt_params* params, int32_t spp, uint64_t seed, float* out_rgb,

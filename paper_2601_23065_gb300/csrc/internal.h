@@ -58,6 +58,14 @@ uint32_t take_errors_bvh();
 uint32_t take_errors_render();
 uint32_t take_errors_backward();
 
+// capi.cu: argument checks + render launch shared by the render entry points;
+// set_error records the thread-local message of eagpt_last_error()
+eagpt_status render_entry(const eagpt_scene* scene, const eagpt_bvh* bvh, const eagpt_camera* cam,
+                          const eagpt_params* params, int kind, int32_t spp, int32_t max_bounces, int32_t rr_start,
+                          uint64_t seed, float* out_rgb, float* out_aux, float* out_samples, int64_t* out_stats,
+                          void* ws, size_t ws_bytes, eagpt_stream_t stream);
+eagpt_status set_error(eagpt_status s, const char* msg);
+
 // number of SMs of the current device (cached per device)
 int device_sms();
 
