@@ -296,7 +296,7 @@ def main():
     # counters of the secondary segments: blended hits, nodes, surfel tests
     cnt2 = r.path_traced(ds, api.BVH(ds), cam, wl.spp, wl.max_bounces, rr_start=wl.rr_start, seed=seed_base,
                          want_stats=True)["stats"].cpu().numpy()
-    blended, nodes, tests = int(cnt2[3]), int(cnt2[4]), int(cnt2[5])
+    blended, nodes, tests, rounds = int(cnt2[3]), int(cnt2[4]), int(cnt2[5]), int(cnt2[6])
     # per-segment algorithmic bytes: 48 B ray read + 48 B ray/slot write +
     # 64 B per node + 64 B per surfel test + 32 B per blended shade record
     bounce_launches_per_step = bounce[0] / max(1, args.steps)
@@ -312,7 +312,8 @@ def main():
                 "bytes_per_launch": alg_bytes_bounce_launch, "ms_per_launch": bounce_ms_per_launch,
                 "share_of_kernel_time": bounce[1] / total_kernel_ms if total_kernel_ms else None,
                 "per_secondary_segment": {"nodes": nodes / max(1, sec_segs), "tests": tests / max(1, sec_segs),
-                                          "blended": blended / max(1, sec_segs)}}
+                                          "blended": blended / max(1, sec_segs),
+                                          "rounds": rounds / max(1, sec_segs)}}
 
     # end to end through the public API with host buffers
     pinned = {k: torch.from_numpy(getattr(host_scene, k)).pin_memory() for k in api.FIELDS}

@@ -174,6 +174,59 @@ eagpt_status eagpt_render_path_traced(const eagpt_scene* scene, const eagpt_bvh*
                                       eagpt_stream_t stream);
 
 /* ------------------------------------------------------------------------
+ * Scene editing (the paper's edits: relight / toggle emitters, recolour,
+ * move selected Gaussians; teaser and Sec. 5, selection by boxes).
+ *
+ * eagpt_select(): indices of the surfels whose centre p lies in a shape, in
+ *   increasing index order.  shape 0: box, params = (lo3, hi3); shape 1:
+ *   sphere, params = (centre3, radius, -, -).  params is a host array of 6.
+ *   out_idx: device int32[capacity]; *out_count (device int64) receives the
+ *   full count even when it exceeds capacity (then only capacity are
+ *   written).  scratch: device, eagpt_select_scratch_bytes(n) bytes.
+ *
+ * eagpt_apply_edit(): modifies the listed surfels in place, updates the BVH
+ *   records and refits; then increments scene->version and sets
+ *   bvh->scene_version to it (both host structs).  Ops (idx: device int32,
+ *   distinct indices; per_index: device or NULL):
+ *   SET_EMISSION     e, r <- per_index (4 per surfel: e, r, g, b) or value[0..3]
+ *   TOGGLE_EMISSION  e <- 1 - e; a surfel that becomes an emitter takes the
+ *                    radiance per_index (3 per surfel) when given
+ *   SCALE_ALBEDO     rho <- clamp(rho * value[0..2], 0, 1)
+ *   TRANSLATE        p <- p + value[0..2]
+ *   RIGID            value = (q_R (w,x,y,z), centre c (3), translation t (3)):
+ *                    p <- R(q_R)(p - c) + c + t,  q <- q_R q
+ *   Geometry ops refit the BVH (surfels keep their BVH positions); when the
+ *   refit's node surface-area sum exceeds rebuild_ratio times the area at
+ *   build (rebuild_ratio > 0), the BVH is rebuilt instead and *out_rebuilt
+ *   (host, nullable) is set to 1.  Geometry ops read the area back, so they
+ *   synchronise `stream` once; appearance ops do not.
+ * ------------------------------------------------------------------------ */
+typedef enum {
+  EAGPT_EDIT_SET_EMISSION = 0,
+  EAGPT_EDIT_TOGGLE_EMISSION = 1,
+  EAGPT_EDIT_SCALE_ALBEDO = 2,
+  EAGPT_EDIT_TRANSLATE = 3,
+  EAGPT_EDIT_RIGID = 4
+} eagpt_edit_op;
+
+typedef struct {
+  int32_t op;             /* eagpt_edit_op */
+  int32_t reserved;       /* must be 0 */
+  int64_t count;          /* listed surfels */
+  const int32_t* idx;     /* device, count indices */
+  const float* per_index; /* device or NULL */
+  float value[16];
+} eagpt_edit;
+
+size_t eagpt_select_scratch_bytes(int64_t n);
+eagpt_status eagpt_select(const eagpt_scene* scene, int32_t shape, const float* params, int32_t* out_idx,
+                          int64_t capacity, int64_t* out_count, void* scratch, size_t scratch_bytes,
+                          eagpt_stream_t stream);
+eagpt_status eagpt_apply_edit(eagpt_scene_mut* scene, eagpt_bvh* bvh, const eagpt_params* params,
+                              const eagpt_edit* edit, float rebuild_ratio, int32_t* out_rebuilt,
+                              eagpt_stream_t stream);
+
+/* ------------------------------------------------------------------------
  * Allocation-free path-traced render.  The paper has no counterpart: this is
  * a deployment variant of eagpt_render_path_traced() for callers that cannot
  * allocate device memory themselves -- a plugin inside a host application

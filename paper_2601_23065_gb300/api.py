@@ -188,3 +188,109 @@ def trace_rays(scene: DeviceScene, bvh: BVH, rays: torch.Tensor, mode: int = 0, 
 def sync_status(stream=None) -> None:
     """Synchronise and raise if a kernel recorded a device-side error."""
     capi.check(capi.lib().eagpt_sync_status(_stream(stream)))
+
+
+def single_bounce_backward(scene: DeviceScene, bvh: BVH, cam: HostCamera, spp: int, seed: int, dL_drgb: torch.Tensor,
+                           grads: Optional[dict] = None, prm: Optional[capi.Params] = None, stream=None,
+                           workspace: Optional[torch.Tensor] = None) -> dict:
+    """Adjoint of the single-bounce render: accumulates dL/dtheta for
+    L = sum(dL_drgb * image) into ``grads`` (created zeroed if None)."""
+    dev = scene.t["pos"].device
+    if grads is None:
+        grads = {k: torch.zeros_like(scene.t[k]) for k in GRAD_FIELDS}
+    g = capi.SceneGrad()
+    g.n = scene.n
+    for k in GRAD_FIELDS:
+        setattr(g, k, grads[k].data_ptr() if scene.n else None)
+    c = camera(cam)
+    prm = prm or bvh.params
+    L = capi.lib()
+    need = L.eagpt_render_backward_workspace_bytes(ctypes.byref(c), spp)
+    ws = workspace if workspace is not None and workspace.numel() >= need else torch.empty(
+        need, dtype=torch.uint8, device=dev)
+    dL = dL_drgb.contiguous().to(torch.float32)
+    sc = scene.c()
+    capi.check(L.eagpt_render_single_bounce_backward(ctypes.byref(sc), ctypes.byref(bvh.c()), ctypes.byref(c),
+                                                     ctypes.byref(prm), int(spp), ctypes.c_uint64(int(seed)),
+                                                     _ptr(dL), ctypes.byref(g), _ptr(ws), ws.numel(),
+                                                     _stream(stream)))
+    return grads
+
+
+class _SingleBounceFn(torch.autograd.Function):
+    """Differentiable single-bounce render (Eq. 6): forward and hand-written
+    adjoint both run in the CUDA library; PyTorch only carries the tensors."""
+
+    @staticmethod
+    def forward(ctx, pos, quat, scale, opacity, albedo, radiance, emissive, cam, spp, seed, renderer, prm):
+        ds = DeviceScene({"pos": pos.detach().contiguous(), "quat": quat.detach().contiguous(),
+                          "scale": scale.detach().contiguous(), "opacity": opacity.detach().contiguous(),
+                          "albedo": albedo.detach().contiguous(), "radiance": radiance.detach().contiguous(),
+                          "emissive": emissive.detach().contiguous()})
+        bvh = BVH(ds, prm)
+        out = renderer.single_bounce(ds, bvh, cam, spp, seed=seed, prm=prm)
+        ctx.state = (ds, bvh, cam, spp, seed, prm)
+        return out["rgb"]
+
+    @staticmethod
+    def backward(ctx, grad_rgb):
+        ds, bvh, cam, spp, seed, prm = ctx.state
+        g = single_bounce_backward(ds, bvh, cam, spp, seed, grad_rgb, prm=prm)
+        return (g["pos"], g["quat"], g["scale"], g["opacity"], g["albedo"], g["radiance"], None, None, None, None,
+                None, None)
+
+
+def render_single_bounce(tensors: dict, cam: HostCamera, spp: int, seed: int = 0,
+                         renderer: Optional[Renderer] = None, prm: Optional[capi.Params] = None) -> torch.Tensor:
+    """Autograd entry point: ``tensors`` maps the scene fields to CUDA float32
+    tensors (any of them may require grad); returns the (H, W, 3) image.  The
+    emissive term gets no gradient (it enters only through threshold tests)."""
+    renderer = renderer or Renderer(device=tensors["pos"].device)
+    prm = prm or params()
+    return _SingleBounceFn.apply(tensors["pos"], tensors["quat"], tensors["scale"], tensors["opacity"],
+                                 tensors["albedo"], tensors["radiance"], tensors["emissive"], cam, spp, seed,
+                                 renderer, prm)
+
+
+EDIT_OPS = {"set_emission": 0, "toggle_emission": 1, "scale_albedo": 2, "translate": 3, "rigid": 4}
+
+
+def select(scene: DeviceScene, shape: str, values, stream=None) -> torch.Tensor:
+    """Indices (int32, increasing) of the surfels whose centre lies in a box
+    (values = lo3 + hi3) or a sphere (values = centre3 + (radius,))."""
+    dev = scene.t["pos"].device
+    sh = {"box": 0, "sphere": 1}[shape]
+    v = (ctypes.c_float * 6)(*[float(x) for x in list(values) + [0.0] * (6 - len(values))])
+    L = capi.lib()
+    scratch = torch.empty(max(L.eagpt_select_scratch_bytes(scene.n), 4), dtype=torch.uint8, device=dev)
+    count = torch.zeros(1, dtype=torch.int64, device=dev)
+    cap = scene.n
+    out = torch.empty(max(cap, 1), dtype=torch.int32, device=dev)
+    sc = scene.c()
+    capi.check(L.eagpt_select(ctypes.byref(sc), sh, v, _ptr(out), cap, _ptr(count), _ptr(scratch), scratch.numel(),
+                              _stream(stream)))
+    return out[:int(count.item())]
+
+
+def apply_edit(scene: DeviceScene, bvh: BVH, op: str, idx: torch.Tensor, value=(), per_index=None,
+               rebuild_ratio: float = 1.5, stream=None) -> bool:
+    """Applies an edit in place (see eagpt_apply_edit); returns True when the
+    BVH was rebuilt instead of refit.  Bumps scene.version."""
+    L = capi.lib()
+    idx = idx.to(torch.int32).contiguous()
+    e = capi.Edit()
+    e.op = EDIT_OPS[op]
+    e.reserved = 0
+    e.count = idx.numel()
+    e.idx = idx.data_ptr() if idx.numel() else None
+    pi = per_index.to(torch.float32).contiguous() if per_index is not None else None
+    e.per_index = pi.data_ptr() if pi is not None else None
+    vals = list(value) + [0.0] * (16 - len(value))
+    for k in range(16):
+        e.value[k] = float(vals[k])
+    sm = scene.c()
+    rebuilt = ctypes.c_int32(0)
+    capi.check(L.eagpt_apply_edit(ctypes.byref(sm), ctypes.byref(bvh.handle), ctypes.byref(bvh.params),
+                                  ctypes.byref(e), float(rebuild_ratio), ctypes.byref(rebuilt), _stream(stream)))
+    scene.version = int(sm.version)
+    return bool(rebuilt.value)

@@ -64,7 +64,8 @@ class Bvh(ctypes.Structure):
 
 
 class Edit(ctypes.Structure):
-    _fields_ = [("op", c_i32), ("count", c_i64), ("idx", c_vp), ("values", c_f * 12), ("seed", c_u64)]
+    _fields_ = [("op", c_i32), ("reserved", c_i32), ("count", c_i64), ("idx", c_vp), ("per_index", c_vp),
+                ("value", c_f * 16)]
 
 
 # symbol -> (restype, argtypes)
@@ -81,6 +82,9 @@ SIGNATURES = {
     "eagpt_render_path_traced": (c_i32, [P(Scene), P(Bvh), P(Camera), P(Params), c_i32, c_i32, c_i32, c_u64,
                                          c_vp, c_vp, c_vp, c_vp, c_vp, c_sz, c_vp]),
     "eagpt_trace_rays": (c_i32, [P(Scene), P(Bvh), P(Params), c_i32, c_vp, c_i64, c_vp, c_vp, c_i32, c_vp, c_vp]),
+    "eagpt_select_scratch_bytes": (c_sz, [c_i64]),
+    "eagpt_select": (c_i32, [P(Scene), c_i32, P(c_f), c_vp, c_i64, c_vp, c_vp, c_sz, c_vp]),
+    "eagpt_apply_edit": (c_i32, [P(Scene), P(Bvh), P(Params), P(Edit), c_f, P(c_i32), c_vp]),
     "eagpt_render_path_traced_noalloc_max_bytes": (c_sz, []),
     "eagpt_render_path_traced_noalloc": (c_i32, [P(Scene), P(Bvh), P(Camera), P(Params), c_i32, c_i32, c_i32, c_u64,
                                                  c_vp, c_vp]),

@@ -6,9 +6,8 @@
 //   4. records: per sorted position, the surfel frame from its quaternion,
 //      a = t_u/s_u, b = t_v/s_v, the trace and shade records and the bound of
 //      its support ellipse
-//   5. binary radix tree (Karras, HPG 2012) with parents; subtrees of at most
-//      kLeafMax surfels become leaves of the traversed BVH
-//   6. bottom-up refit with visit counters; also used after edits
+//   5. tree stage (bvh_tree.cu): binary radix tree, bottom-up boxes, collapse
+//      into the 4-wide BVH that the renderer traverses
 #include <cuda_runtime.h>
 
 #include "common.cuh"
@@ -223,129 +222,6 @@ __global__ void k_records(eagpt_scene sc, Consts C, const uint32_t* __restrict__
 }
 
 // --------------------------------------------------------------------------
-// binary radix tree (Karras 2012) over sorted keys; ties broken by position
-// --------------------------------------------------------------------------
-__device__ __forceinline__ int delta(const uint32_t* __restrict__ keys, int64_t n, int64_t i, int64_t j) {
-  if (j < 0 || j >= n) return -1;
-  const uint32_t a = keys[i], b = keys[j];
-  if (a != b) return __clz(a ^ b);
-  return __clzll((unsigned long long)(i ^ j));  // >= 33 for positions < 2^31: ties sort by position
-}
-
-__device__ __forceinline__ uint32_t child_link(int64_t first, int64_t last, int64_t node_if_internal) {
-  const int64_t cnt = last - first + 1;
-  if (cnt <= kLeafMax) return kLeafBit | ((uint32_t)(cnt - 1) << kLeafCountShift) | (uint32_t)first;
-  return (uint32_t)node_if_internal;
-}
-
-// Internal node i covers sorted range [first, last]; its children are the
-// binary-tree nodes split and split+1 (leaves when they hold one surfel).
-// child_bin[2i + c] records the binary child (>= 0 internal, < 0 ~leaf).
-__global__ void k_hierarchy(const uint32_t* __restrict__ keys, int64_t n, Node* nodes, uint32_t* leaf_parent,
-                            uint32_t* inode_parent, int32_t* child_bin) {
-  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= n - 1) return;
-  const int d = (delta(keys, n, i, i + 1) - delta(keys, n, i, i - 1)) >= 0 ? 1 : -1;
-  const int dmin = delta(keys, n, i, i - d);
-  int64_t lmax = 2;
-  while (delta(keys, n, i, i + lmax * d) > dmin) lmax *= 2;
-  int64_t l = 0;
-  for (int64_t t = lmax / 2; t >= 1; t /= 2)
-    if (delta(keys, n, i, i + (l + t) * d) > dmin) l += t;
-  const int64_t j = i + l * d;
-  const int dnode = delta(keys, n, i, j);
-  int64_t s = 0;
-  int64_t t = l;
-  do {
-    t = (t + 1) / 2;
-    if (delta(keys, n, i, i + (s + t) * d) > dnode) s += t;
-  } while (t > 1);
-  const int64_t split = i + s * d + (d < 0 ? -1 : 0);
-  const int64_t first = i < j ? i : j, last = i < j ? j : i;
-  const bool left_leaf = first == split, right_leaf = last == split + 1;
-  Node nd;
-  nd.n0 = nd.n1 = nd.n2 = make_float4(0.f, 0.f, 0.f, 0.f);
-  nd.n3 = make_uint4(child_link(first, split, split), child_link(split + 1, last, split + 1), 0u, 0u);
-  nodes[i] = nd;
-  if (left_leaf) {
-    leaf_parent[split] = (uint32_t)i;
-    child_bin[2 * i] = ~(int32_t)split;
-  } else {
-    inode_parent[split] = (uint32_t)i;
-    child_bin[2 * i] = (int32_t)split;
-  }
-  if (right_leaf) {
-    leaf_parent[split + 1] = (uint32_t)i;
-    child_bin[2 * i + 1] = ~(int32_t)(split + 1);
-  } else {
-    inode_parent[split + 1] = (uint32_t)i;
-    child_bin[2 * i + 1] = (int32_t)(split + 1);
-  }
-  if (i == 0) inode_parent[0] = 0xFFFFFFFFu;
-}
-
-__global__ void k_clear_u32(uint32_t* p, int64_t n) {
-  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i < n) p[i] = 0u;
-}
-
-__device__ __forceinline__ float box_area(float4 lo, float4 hi) {
-  const float dx = fmaxf(hi.x - lo.x, 0.f), dy = fmaxf(hi.y - lo.y, 0.f), dz = fmaxf(hi.z - lo.z, 0.f);
-  return 2.f * (dx * dy + dy * dz + dz * dx);
-}
-
-// Bottom-up refit: one thread per surfel climbs while it is the second child
-// to arrive at a node (visit counters), writing the node's box into its own
-// box array and into its parent's child slot.
-__global__ void k_refit(int64_t n, const float4* __restrict__ plo, const float4* __restrict__ phi, float4* ilo,
-                        float4* ihi, Node* nodes, const uint32_t* __restrict__ leaf_parent,
-                        const uint32_t* __restrict__ inode_parent, const int32_t* __restrict__ child_bin,
-                        uint32_t* visit, BvhHeader* hdr) {
-  const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (j >= n) return;
-  uint32_t node = leaf_parent[j];
-  float area = 0.f;
-  while (node != 0xFFFFFFFFu) {
-    __threadfence();
-    if (atomicAdd(&visit[node], 1u) == 0u) break;  // first arrival: the sibling finishes
-    __threadfence();
-    const int32_t c0 = child_bin[2 * node], c1 = child_bin[2 * node + 1];
-    const float4 lo0 = c0 < 0 ? plo[~c0] : __ldcg(&ilo[c0]);
-    const float4 hi0 = c0 < 0 ? phi[~c0] : __ldcg(&ihi[c0]);
-    const float4 lo1 = c1 < 0 ? plo[~c1] : __ldcg(&ilo[c1]);
-    const float4 hi1 = c1 < 0 ? phi[~c1] : __ldcg(&ihi[c1]);
-    const float4 lo = make_float4(fminf(lo0.x, lo1.x), fminf(lo0.y, lo1.y), fminf(lo0.z, lo1.z), 0.f);
-    const float4 hi = make_float4(fmaxf(hi0.x, hi1.x), fmaxf(hi0.y, hi1.y), fmaxf(hi0.z, hi1.z), 0.f);
-    __stcg(&ilo[node], lo);
-    __stcg(&ihi[node], hi);
-    Node* nd = nodes + node;
-    nd->n0 = make_float4(lo0.x, lo0.y, lo0.z, hi0.x);
-    nd->n1 = make_float4(hi0.y, hi0.z, lo1.x, lo1.y);
-    nd->n2 = make_float4(lo1.z, hi1.x, hi1.y, hi1.z);
-    area += box_area(lo, hi);
-    node = inode_parent[node];
-  }
-  if (area > 0.f) atomicAdd(&hdr->area_sum, (double)area);
-}
-
-// n <= kLeafMax: a single root node whose first child is one leaf.
-__global__ void k_small_root(int64_t n, const float4* __restrict__ plo, const float4* __restrict__ phi, Node* nodes,
-                             BvhHeader* hdr) {
-  float4 lo = make_float4(3e38f, 3e38f, 3e38f, 0.f), hi = make_float4(-3e38f, -3e38f, -3e38f, 0.f);
-  for (int64_t j = 0; j < n; ++j) {
-    lo = make_float4(fminf(lo.x, plo[j].x), fminf(lo.y, plo[j].y), fminf(lo.z, plo[j].z), 0.f);
-    hi = make_float4(fmaxf(hi.x, phi[j].x), fmaxf(hi.y, phi[j].y), fmaxf(hi.z, phi[j].z), 0.f);
-  }
-  Node nd;
-  nd.n0 = make_float4(lo.x, lo.y, lo.z, hi.x);
-  nd.n1 = make_float4(hi.y, hi.z, 0.f, 0.f);
-  nd.n2 = make_float4(0.f, 0.f, 0.f, 0.f);
-  nd.n3 = make_uint4(kLeafBit | ((uint32_t)(n - 1) << kLeafCountShift), kEmptyChild, 0u, 0u);
-  nodes[0] = nd;
-  hdr->area_sum = box_area(lo, hi);
-}
-
-// --------------------------------------------------------------------------
 // host driver
 // --------------------------------------------------------------------------
 static inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
@@ -386,32 +262,10 @@ cudaError_t launch_build(const eagpt_scene& sc, const Consts& C, char* base, con
   EAGPT_LAUNCH(st, "k_records", k_records<<<blocks_for(n, 256), 256, 0, st>>>(sc, C, sorted_idx, trace, shade, plo, phi,
                                                 (uint32_t*)(base + L.inv_idx), n, 1));
   ++nl;
-  Node* nodes = (Node*)(base + L.nodes);
-  if (n <= kLeafMax) {
-    EAGPT_LAUNCH(st, "k_small_root", k_small_root<<<1, 1, 0, st>>>(n, plo, phi, nodes, hdr));
-    ++nl;
-  } else {
-    int32_t* child_bin = (int32_t*)(base + L.child_bin);
-    EAGPT_LAUNCH(st, "k_hierarchy", k_hierarchy<<<blocks_for(n - 1, 256), 256, 0, st>>>(k0, n, nodes, (uint32_t*)(base + L.leaf_parent),
-                                                       (uint32_t*)(base + L.inode_parent), child_bin));
-    ++nl;
-    nl += launch_refit(base, L, st);
-  }
+  cudaError_t e = launch_tree(k0, base, L, st);
+  if (e != cudaSuccess) return e;
   if (launches) *launches += nl;
   return cudaGetLastError();
-}
-
-int launch_refit(char* base, const BvhLayout& L, cudaStream_t st) {
-  const int64_t n = L.n;
-  BvhHeader* hdr = (BvhHeader*)(base + L.header);
-  cudaMemsetAsync(&hdr->area_sum, 0, sizeof(double), st);
-  EAGPT_LAUNCH(st, "k_clear_u32", k_clear_u32<<<blocks_for(L.n_inodes, 256), 256, 0, st>>>((uint32_t*)(base + L.visit), L.n_inodes));
-  EAGPT_LAUNCH(st, "k_refit", k_refit<<<blocks_for(n, 256), 256, 0, st>>>(n, (const float4*)(base + L.prim_lo), (const float4*)(base + L.prim_hi),
-                                              (float4*)(base + L.ibox_lo), (float4*)(base + L.ibox_hi),
-                                              (Node*)(base + L.nodes), (const uint32_t*)(base + L.leaf_parent),
-                                              (const uint32_t*)(base + L.inode_parent),
-                                              (const int32_t*)(base + L.child_bin), (uint32_t*)(base + L.visit), hdr));
-  return 2;
 }
 
 cudaError_t launch_records_update(const eagpt_scene& sc, const Consts& C, char* base, const BvhLayout& L,

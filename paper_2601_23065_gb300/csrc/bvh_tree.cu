@@ -1,0 +1,341 @@
+// Tree stage of the BVH build, and refits.
+//
+//   k_hierarchy   binary radix tree over the sorted Morton codes (Karras,
+//                 "Maximizing parallelism in the construction of BVHs,
+//                 octrees, and k-d trees", HPG 2012); ties between equal codes
+//                 are broken by position, so the tree is always complete.
+//                 Records children, parents and the surfel range of every
+//                 internal node.
+//   k_refit       bottom-up boxes of the binary tree (visit counters: the
+//                 second child to arrive computes the parent), and the sum of
+//                 node surface areas (the refit-quality measure).
+//   k_collapse    top-down, one level per launch: every BVH4 node takes a
+//                 binary node and opens its largest-area internal child until
+//                 it has four children; subtrees of at most kLeafMax surfels
+//                 become leaves.  Records, per BVH4 child, the binary node it
+//                 stands for, so a refit only has to copy boxes.
+//   k_bvh4_boxes  copies refit binary boxes into the BVH4 child slots.
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace eagpt {
+
+EAGPT_DEFINE_ERROR_READER(take_errors_tree)
+
+__device__ __forceinline__ int delta(const uint32_t* __restrict__ keys, int64_t n, int64_t i, int64_t j) {
+  if (j < 0 || j >= n) return -1;
+  const uint32_t a = keys[i], b = keys[j];
+  if (a != b) return __clz(a ^ b);
+  return __clzll((unsigned long long)(i ^ j));  // >= 33 for positions < 2^31: ties sort by position
+}
+
+// child code: >= 0 binary internal node, < 0 ~surfel position
+__global__ void k_hierarchy(const uint32_t* __restrict__ keys, int64_t n, uint32_t* leaf_parent,
+                            uint32_t* inode_parent, int32_t* child_bin, int2* irange) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n - 1) return;
+  const int d = (delta(keys, n, i, i + 1) - delta(keys, n, i, i - 1)) >= 0 ? 1 : -1;
+  const int dmin = delta(keys, n, i, i - d);
+  int64_t lmax = 2;
+  while (delta(keys, n, i, i + lmax * d) > dmin) lmax *= 2;
+  int64_t l = 0;
+  for (int64_t t = lmax / 2; t >= 1; t /= 2)
+    if (delta(keys, n, i, i + (l + t) * d) > dmin) l += t;
+  const int64_t j = i + l * d;
+  const int dnode = delta(keys, n, i, j);
+  int64_t s = 0;
+  int64_t t = l;
+  do {
+    t = (t + 1) / 2;
+    if (delta(keys, n, i, i + (s + t) * d) > dnode) s += t;
+  } while (t > 1);
+  const int64_t split = i + s * d + (d < 0 ? -1 : 0);
+  const int64_t first = i < j ? i : j, last = i < j ? j : i;
+  irange[i] = make_int2((int)first, (int)last);
+  if (first == split) {
+    leaf_parent[split] = (uint32_t)i;
+    child_bin[2 * i] = ~(int32_t)split;
+  } else {
+    inode_parent[split] = (uint32_t)i;
+    child_bin[2 * i] = (int32_t)split;
+  }
+  if (last == split + 1) {
+    leaf_parent[split + 1] = (uint32_t)i;
+    child_bin[2 * i + 1] = ~(int32_t)(split + 1);
+  } else {
+    inode_parent[split + 1] = (uint32_t)i;
+    child_bin[2 * i + 1] = (int32_t)(split + 1);
+  }
+  if (i == 0) inode_parent[0] = 0xFFFFFFFFu;
+}
+
+__global__ void k_clear_u32(uint32_t* p, int64_t n) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) p[i] = 0u;
+}
+
+__device__ __forceinline__ float box_area(float4 lo, float4 hi) {
+  const float dx = fmaxf(hi.x - lo.x, 0.f), dy = fmaxf(hi.y - lo.y, 0.f), dz = fmaxf(hi.z - lo.z, 0.f);
+  return 2.f * (dx * dy + dy * dz + dz * dx);
+}
+
+__global__ void k_refit(int64_t n, const float4* __restrict__ plo, const float4* __restrict__ phi, float4* ilo,
+                        float4* ihi, const uint32_t* __restrict__ leaf_parent,
+                        const uint32_t* __restrict__ inode_parent, const int32_t* __restrict__ child_bin,
+                        uint32_t* visit, BvhHeader* hdr) {
+  const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  uint32_t node = leaf_parent[j];
+  float area = 0.f;
+  while (node != 0xFFFFFFFFu) {
+    __threadfence();
+    if (atomicAdd(&visit[node], 1u) == 0u) break;  // first arrival: the sibling finishes
+    __threadfence();
+    const int32_t c0 = child_bin[2 * node], c1 = child_bin[2 * node + 1];
+    const float4 lo0 = c0 < 0 ? plo[~c0] : __ldcg(&ilo[c0]);
+    const float4 hi0 = c0 < 0 ? phi[~c0] : __ldcg(&ihi[c0]);
+    const float4 lo1 = c1 < 0 ? plo[~c1] : __ldcg(&ilo[c1]);
+    const float4 hi1 = c1 < 0 ? phi[~c1] : __ldcg(&ihi[c1]);
+    const float4 lo = make_float4(fminf(lo0.x, lo1.x), fminf(lo0.y, lo1.y), fminf(lo0.z, lo1.z), 0.f);
+    const float4 hi = make_float4(fmaxf(hi0.x, hi1.x), fmaxf(hi0.y, hi1.y), fmaxf(hi0.z, hi1.z), 0.f);
+    __stcg(&ilo[node], lo);
+    __stcg(&ihi[node], hi);
+    area += box_area(lo, hi);
+    node = inode_parent[node];
+  }
+  if (area > 0.f) atomicAdd(&hdr->area_sum, (double)area);
+}
+
+struct TreeArrays {
+  const float4 *plo, *phi, *ilo, *ihi;
+  const int32_t* child_bin;
+  const int2* irange;
+};
+
+__device__ __forceinline__ int64_t subtree_count(const TreeArrays& T, int32_t code) {
+  if (code < 0) return 1;
+  const int2 r = T.irange[code];
+  return (int64_t)r.y - r.x + 1;
+}
+
+__device__ __forceinline__ void code_box(const TreeArrays& T, int32_t code, float4& lo, float4& hi) {
+  if (code < 0) {
+    lo = T.plo[~code];
+    hi = T.phi[~code];
+  } else {
+    lo = T.ilo[code];
+    hi = T.ihi[code];
+  }
+}
+
+__device__ __forceinline__ void set_child_box(Node4& nd, int k, float4 lo, float4 hi) {
+  float* lx = &nd.lox.x;
+  float* ly = &nd.loy.x;
+  float* lz = &nd.loz.x;
+  float* hx = &nd.hix.x;
+  float* hy = &nd.hiy.x;
+  float* hz = &nd.hiz.x;
+  lx[k] = lo.x;
+  ly[k] = lo.y;
+  lz[k] = lo.z;
+  hx[k] = hi.x;
+  hy[k] = hi.y;
+  hz[k] = hi.z;
+}
+
+// One level of the top-down collapse.  Frontier entries are (binary node,
+// BVH4 node).  levels[lv] holds this level's frontier size, levels[lv + 1]
+// collects the next one; levels[kMaxCollapseLevels + 1] counts BVH4 nodes.
+__global__ void k_collapse(TreeArrays T, Node4* nodes, int32_t* src4, const int2* __restrict__ front_in,
+                           int2* front_out, uint32_t* levels, int lv, int64_t cap) {
+  const uint32_t count = levels[lv];
+  for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < count; f += (int64_t)gridDim.x * blockDim.x) {
+    const int2 e = front_in[f];
+    int32_t ch[4];
+    int nc = 2;
+    ch[0] = T.child_bin[2 * e.x];
+    ch[1] = T.child_bin[2 * e.x + 1];
+    while (nc < 4) {
+      int best = -1;
+      float best_area = -1.f;
+      for (int k = 0; k < nc; ++k) {
+        if (ch[k] >= 0 && subtree_count(T, ch[k]) > kLeafMax) {
+          float4 lo, hi;
+          code_box(T, ch[k], lo, hi);
+          const float a = box_area(lo, hi);
+          if (a > best_area) {
+            best_area = a;
+            best = k;
+          }
+        }
+      }
+      if (best < 0) break;
+      const int32_t b = ch[best];
+      ch[best] = T.child_bin[2 * b];
+      ch[nc++] = T.child_bin[2 * b + 1];
+    }
+    Node4 nd;
+    nd.lox = nd.loy = nd.loz = make_float4(1e30f, 1e30f, 1e30f, 1e30f);
+    nd.hix = nd.hiy = nd.hiz = make_float4(-1e30f, -1e30f, -1e30f, -1e30f);
+    uint32_t link[4] = {kEmptyChild, kEmptyChild, kEmptyChild, kEmptyChild};
+    for (int k = 0; k < 4; ++k) {
+      src4[4 * (int64_t)e.y + k] = k < nc ? ch[k] : INT32_MIN;
+      if (k >= nc) continue;
+      float4 lo, hi;
+      code_box(T, ch[k], lo, hi);
+      set_child_box(nd, k, lo, hi);
+      const int64_t cnt = subtree_count(T, ch[k]);
+      if (cnt <= kLeafMax) {
+        const int64_t first = ch[k] < 0 ? (int64_t)~ch[k] : (int64_t)T.irange[ch[k]].x;
+        link[k] = kLeafBit | ((uint32_t)(cnt - 1) << kLeafCountShift) | (uint32_t)first;
+      } else {
+        const uint32_t id = atomicAdd(&levels[kMaxCollapseLevels + 1], 1u);
+        if ((int64_t)id >= cap) {
+          raise_error(kErrBadIndex);
+          continue;
+        }
+        const uint32_t slot = atomicAdd(&levels[lv + 1], 1u);
+        front_out[slot] = make_int2(ch[k], (int)id);
+        link[k] = id;
+      }
+    }
+    nd.child = make_uint4(link[0], link[1], link[2], link[3]);
+    nd.pad = make_uint4(0u, 0u, 0u, 0u);
+    nodes[e.y] = nd;
+  }
+}
+
+__global__ void k_collapse_init(uint32_t* levels, int2* front0) {
+  const int i = threadIdx.x;
+  for (int k = i; k < kMaxCollapseLevels + 2; k += blockDim.x) levels[k] = 0u;
+  __syncthreads();
+  if (i == 0) {
+    levels[0] = 1u;                        // the root's frontier
+    levels[kMaxCollapseLevels + 1] = 1u;   // BVH4 node 0 is the root
+    front0[0] = make_int2(0, 0);
+  }
+}
+
+// A frontier left after the last level means the tree was deeper than the
+// collapse budget: recorded as a device error.
+__global__ void k_collapse_check(const uint32_t* levels) {
+  if (threadIdx.x == 0 && levels[kMaxCollapseLevels] != 0u) raise_error(kErrBadIndex);
+}
+
+// Refresh the child boxes of every BVH4 node from the binary boxes.
+__global__ void k_bvh4_boxes(TreeArrays T, Node4* nodes, const int32_t* __restrict__ src4,
+                             const uint32_t* __restrict__ levels) {
+  const uint32_t count = levels[kMaxCollapseLevels + 1];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
+    Node4 nd = nodes[i];
+    for (int k = 0; k < 4; ++k) {
+      const int32_t c = src4[4 * i + k];
+      if (c == INT32_MIN) continue;
+      float4 lo, hi;
+      code_box(T, c, lo, hi);
+      set_child_box(nd, k, lo, hi);
+    }
+    nodes[i] = nd;
+  }
+}
+
+// n <= kLeafMax: a single BVH4 node whose first child is one leaf.
+__global__ void k_small_root(int64_t n, const float4* __restrict__ plo, const float4* __restrict__ phi, Node4* nodes,
+                             int32_t* src4, uint32_t* levels, BvhHeader* hdr) {
+  float4 lo = make_float4(3e38f, 3e38f, 3e38f, 0.f), hi = make_float4(-3e38f, -3e38f, -3e38f, 0.f);
+  for (int64_t j = 0; j < n; ++j) {
+    lo = make_float4(fminf(lo.x, plo[j].x), fminf(lo.y, plo[j].y), fminf(lo.z, plo[j].z), 0.f);
+    hi = make_float4(fmaxf(hi.x, phi[j].x), fmaxf(hi.y, phi[j].y), fmaxf(hi.z, phi[j].z), 0.f);
+  }
+  Node4 nd;
+  nd.lox = nd.loy = nd.loz = make_float4(1e30f, 1e30f, 1e30f, 1e30f);
+  nd.hix = nd.hiy = nd.hiz = make_float4(-1e30f, -1e30f, -1e30f, -1e30f);
+  set_child_box(nd, 0, lo, hi);
+  nd.child = make_uint4(kLeafBit | ((uint32_t)(n - 1) << kLeafCountShift), kEmptyChild, kEmptyChild, kEmptyChild);
+  nd.pad = make_uint4(0u, 0u, 0u, 0u);
+  nodes[0] = nd;
+  for (int k = 0; k < 4; ++k) src4[k] = INT32_MIN;
+  for (int k = 0; k < kMaxCollapseLevels + 2; ++k) levels[k] = 0u;
+  levels[kMaxCollapseLevels + 1] = 1u;
+  hdr->area_sum = box_area(lo, hi);
+}
+
+// --------------------------------------------------------------------------
+static inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+static TreeArrays tree_arrays(char* base, const BvhLayout& L) {
+  TreeArrays T;
+  T.plo = (const float4*)(base + L.prim_lo);
+  T.phi = (const float4*)(base + L.prim_hi);
+  T.ilo = (const float4*)(base + L.ibox_lo);
+  T.ihi = (const float4*)(base + L.ibox_hi);
+  T.child_bin = (const int32_t*)(base + L.child_bin);
+  T.irange = (const int2*)(base + L.irange);
+  return T;
+}
+
+static void launch_binary_refit(char* base, const BvhLayout& L, cudaStream_t st) {
+  BvhHeader* hdr = (BvhHeader*)(base + L.header);
+  cudaMemsetAsync(&hdr->area_sum, 0, sizeof(double), st);
+  EAGPT_LAUNCH(st, "k_clear_u32",
+               k_clear_u32<<<blocks_for(L.n_inodes, 256), 256, 0, st>>>((uint32_t*)(base + L.visit), L.n_inodes));
+  EAGPT_LAUNCH(st, "k_refit",
+               k_refit<<<blocks_for(L.n, 256), 256, 0, st>>>(
+                   L.n, (const float4*)(base + L.prim_lo), (const float4*)(base + L.prim_hi),
+                   (float4*)(base + L.ibox_lo), (float4*)(base + L.ibox_hi), (const uint32_t*)(base + L.leaf_parent),
+                   (const uint32_t*)(base + L.inode_parent), (const int32_t*)(base + L.child_bin),
+                   (uint32_t*)(base + L.visit), hdr));
+}
+
+cudaError_t launch_tree(const uint32_t* sorted_keys, char* base, const BvhLayout& L, cudaStream_t st) {
+  const int64_t n = L.n;
+  BvhHeader* hdr = (BvhHeader*)(base + L.header);
+  Node4* nodes = (Node4*)(base + L.nodes);
+  int32_t* src4 = (int32_t*)(base + L.src4);
+  uint32_t* levels = (uint32_t*)(base + L.levels);
+  if (n <= kLeafMax) {
+    EAGPT_LAUNCH(st, "k_small_root",
+                 k_small_root<<<1, 1, 0, st>>>(n, (const float4*)(base + L.prim_lo), (const float4*)(base + L.prim_hi),
+                                               nodes, src4, levels, hdr));
+    return cudaGetLastError();
+  }
+  EAGPT_LAUNCH(st, "k_hierarchy",
+               k_hierarchy<<<blocks_for(n - 1, 256), 256, 0, st>>>(
+                   sorted_keys, n, (uint32_t*)(base + L.leaf_parent), (uint32_t*)(base + L.inode_parent),
+                   (int32_t*)(base + L.child_bin), (int2*)(base + L.irange)));
+  launch_binary_refit(base, L, st);
+  int2* fr[2] = {(int2*)(base + L.front0), (int2*)(base + L.front1)};
+  EAGPT_LAUNCH(st, "k_collapse_init", k_collapse_init<<<1, 128, 0, st>>>(levels, fr[0]));
+  const TreeArrays T = tree_arrays(base, L);
+  // the frontier of a level never exceeds the node count; a grid of a few
+  // blocks per SM strides over it
+  const unsigned grid = (unsigned)(4 * device_sms());
+  for (int lv = 0; lv < kMaxCollapseLevels; ++lv) {
+    EAGPT_LAUNCH(st, "k_collapse",
+                 k_collapse<<<grid, 256, 0, st>>>(T, nodes, src4, fr[lv & 1], fr[(lv + 1) & 1], levels, lv,
+                                                 L.n_inodes));
+  }
+  EAGPT_LAUNCH(st, "k_collapse_check", k_collapse_check<<<1, 32, 0, st>>>(levels));
+  return cudaGetLastError();
+}
+
+int launch_refit(char* base, const BvhLayout& L, cudaStream_t st) {
+  if (L.n <= kLeafMax) {
+    EAGPT_LAUNCH(st, "k_small_root",
+                 k_small_root<<<1, 1, 0, st>>>(L.n, (const float4*)(base + L.prim_lo),
+                                               (const float4*)(base + L.prim_hi), (Node4*)(base + L.nodes),
+                                               (int32_t*)(base + L.src4), (uint32_t*)(base + L.levels),
+                                               (BvhHeader*)(base + L.header)));
+    return 1;
+  }
+  launch_binary_refit(base, L, st);
+  EAGPT_LAUNCH(st, "k_bvh4_boxes",
+               k_bvh4_boxes<<<(unsigned)(4 * device_sms()), 256, 0, st>>>(
+                   tree_arrays(base, L), (Node4*)(base + L.nodes), (const int32_t*)(base + L.src4),
+                   (const uint32_t*)(base + L.levels)));
+  return 3;
+}
+
+}  // namespace eagpt

@@ -94,7 +94,7 @@ BvhView make_view(const eagpt_bvh& b) {
     char* base = (char*)b.storage;
     v.trace = (const TraceRec*)(base + L.trace);
     v.shade = (const ShadeRec*)(base + L.shade);
-    v.nodes = (const Node*)(base + L.nodes);
+    v.nodes = (const Node4*)(base + L.nodes);
     v.root = 0;  // node 0: Karras root, or the single node of a small scene
   }
   return v;
@@ -295,6 +295,76 @@ eagpt_status eagpt_render_single_bounce_backward(const eagpt_scene* scene, const
   return EAGPT_OK;
 }
 
+size_t eagpt_select_scratch_bytes(int64_t n) { return n < 0 ? 0 : select_scratch_bytes(n); }
+
+eagpt_status eagpt_select(const eagpt_scene* scene, int32_t shape, const float* params, int32_t* out_idx,
+                          int64_t capacity, int64_t* out_count, void* scratch, size_t scratch_bytes,
+                          eagpt_stream_t stream) {
+  eagpt_status s;
+  if ((s = check_scene(scene)) != EAGPT_OK) return s;
+  if (shape != 0 && shape != 1) return fail(EAGPT_ERR_INVALID_ARGUMENT, "shape must be 0 (box) or 1 (sphere)%s");
+  if (!params || !out_count) return fail(EAGPT_ERR_INVALID_ARGUMENT, "params and out_count are required%s");
+  if (capacity < 0 || (capacity > 0 && !out_idx)) return fail(EAGPT_ERR_INVALID_ARGUMENT, "bad out_idx/capacity%s");
+  if (scene->n > 0 && (!scratch || scratch_bytes < select_scratch_bytes(scene->n)))
+    return fail(EAGPT_ERR_OUT_OF_MEMORY, "select scratch too small%s");
+  cudaError_t e = launch_select(*scene, shape, params, out_idx, capacity, out_count, (uint32_t*)scratch,
+                                (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "select launch");
+  return EAGPT_OK;
+}
+
+eagpt_status eagpt_apply_edit(eagpt_scene_mut* scene, eagpt_bvh* bvh, const eagpt_params* params,
+                              const eagpt_edit* edit, float rebuild_ratio, int32_t* out_rebuilt,
+                              eagpt_stream_t stream) {
+  if (!scene || !edit) return fail(EAGPT_ERR_INVALID_ARGUMENT, "scene and edit are required%s");
+  eagpt_scene cs;
+  std::memcpy(&cs, scene, sizeof(cs));  // same layout, const view
+  eagpt_status s;
+  if ((s = check_scene(&cs)) != EAGPT_OK) return s;
+  if ((s = check_params(params)) != EAGPT_OK) return s;
+  if ((s = check_bvh(bvh, &cs, params)) != EAGPT_OK) return s;
+  if (edit->op < EAGPT_EDIT_SET_EMISSION || edit->op > EAGPT_EDIT_RIGID)
+    return fail(EAGPT_ERR_INVALID_ARGUMENT, "unknown edit op%s");
+  if (edit->reserved != 0) return fail(EAGPT_ERR_INVALID_ARGUMENT, "edit.reserved must be 0%s");
+  if (edit->count < 0 || edit->count > scene->n || (edit->count > 0 && !edit->idx))
+    return fail(EAGPT_ERR_INVALID_ARGUMENT, "edit count/idx invalid%s");
+  for (int k = 0; k < 16; ++k)
+    if (!std::isfinite(edit->value[k])) return fail(EAGPT_ERR_INVALID_ARGUMENT, "edit values must be finite%s");
+  if (out_rebuilt) *out_rebuilt = 0;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = launch_edit(*scene, *edit, st);
+  if (e != cudaSuccess) return cuda_fail(e, "edit launch");
+  if (scene->n > 0) {
+    const BvhLayout L = bvh_layout(scene->n);
+    char* base = (char*)bvh->storage;
+    const Consts C = make_consts(*params);
+    e = launch_records_update(cs, C, base, L, st);
+    if (e != cudaSuccess) return cuda_fail(e, "edit records");
+    if (edit->op == EAGPT_EDIT_TRANSLATE || edit->op == EAGPT_EDIT_RIGID) {
+      launch_refit(base, L, st);
+      double a = 0.0;
+      e = cudaMemcpyAsync(&a, base + L.header + offsetof(BvhHeader, area_sum), sizeof(double),
+                          cudaMemcpyDeviceToHost, st);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+      if (e != cudaSuccess) return cuda_fail(e, "refit");
+      if (rebuild_ratio > 0.f && a > (double)rebuild_ratio * (double)bvh->build_area) {
+        e = launch_build(cs, C, base, L, st, nullptr);
+        double b = 0.0;
+        if (e == cudaSuccess)
+          e = cudaMemcpyAsync(&b, base + L.header + offsetof(BvhHeader, area_sum), sizeof(double),
+                              cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return cuda_fail(e, "rebuild");
+        bvh->build_area = (float)b;
+        if (out_rebuilt) *out_rebuilt = 1;
+      }
+    }
+  }
+  scene->version += 1;
+  bvh->scene_version = scene->version;
+  return EAGPT_OK;
+}
+
 eagpt_status eagpt_trace_rays(const eagpt_scene* scene, const eagpt_bvh* bvh, const eagpt_params* params,
                               int32_t mode, const float* rays, int64_t n_rays, float* out_rec, int32_t* out_hits,
                               int32_t max_hits, int32_t* out_nhits, eagpt_stream_t stream) {
@@ -329,7 +399,8 @@ eagpt_status eagpt_profile_end(eagpt_kernel_time* out, int32_t capacity, int32_t
 eagpt_status eagpt_sync_status(eagpt_stream_t stream) {
   cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "sync");
-  const uint32_t word = take_errors_bvh() | take_errors_render() | take_errors_backward();
+  const uint32_t word =
+      take_errors_bvh() | take_errors_render() | take_errors_backward() | take_errors_tree() | take_errors_edit();
   if (word) {
     char buf[128];
     std::snprintf(buf, sizeof(buf), "device check failed (error bits 0x%x)", word);

@@ -39,11 +39,10 @@ enum : uint32_t {
 // Shade record, 32 B, same order:
 //   s0 = (rho.r, rho.g, rho.b, e)
 //   s1 = (r.r, r.g, r.b, 0)
-// BVH2 node, 64 B: the boxes of both children and the child links
-//   n0 = (lo0.x, lo0.y, lo0.z, hi0.x)
-//   n1 = (hi0.y, hi0.z, lo1.x, lo1.y)
-//   n2 = (lo1.z, hi1.x, hi1.y, hi1.z)
-//   n3 = (child0, child1, -, -) as uint32 bits
+// BVH4 node, 128 B (one cache line): the boxes of its four children in
+// structure-of-arrays form and the four child links
+//   lox = (lo.x of children 0..3), loy, loz, hix, hiy, hiz likewise
+//   child = (link0..link3): node index, encoded leaf, or kEmptyChild
 // ---------------------------------------------------------------------------
 struct __align__(16) TraceRec {
   float4 r0, r1, r2, r3;
@@ -51,16 +50,20 @@ struct __align__(16) TraceRec {
 struct __align__(16) ShadeRec {
   float4 s0, s1;
 };
-struct __align__(16) Node {
-  float4 n0, n1, n2;
-  uint4 n3;
+struct __align__(128) Node4 {
+  float4 lox, loy, loz, hix, hiy, hiz;
+  uint4 child;
+  uint4 pad;
 };
+
+constexpr int kMaxCollapseLevels = 96;  // BVH4 levels built top-down
 
 // Offsets of the arrays inside the caller's BVH storage buffer (a pure
 // function of n, so the host never reads the device to find them).
 struct BvhLayout {
   size_t header, trace, shade, nodes, prim_lo, prim_hi, ibox_lo, ibox_hi, leaf_parent, inode_parent,
-      sorted_idx, inv_idx, keys0, keys1, vals0, vals1, hist, visit, child_bin, total;
+      sorted_idx, inv_idx, keys0, keys1, vals0, vals1, hist, visit, child_bin, irange, src4, front0, front1,
+      levels, total;
   int64_t n, n_inodes, n_tiles;
 };
 
@@ -93,7 +96,7 @@ inline BvhLayout bvh_layout(int64_t n) {
   L.header = take(sizeof(BvhHeader));
   L.trace = take(nn * sizeof(TraceRec));
   L.shade = take(nn * sizeof(ShadeRec));
-  L.nodes = take((size_t)L.n_inodes * sizeof(Node));
+  L.nodes = take((size_t)L.n_inodes * sizeof(Node4));
   L.prim_lo = take(nn * sizeof(float4));
   L.prim_hi = take(nn * sizeof(float4));
   L.ibox_lo = take((size_t)L.n_inodes * sizeof(float4));
@@ -109,6 +112,11 @@ inline BvhLayout bvh_layout(int64_t n) {
   L.hist = take((size_t)256 * L.n_tiles * 4);
   L.visit = take((size_t)L.n_inodes * 4);
   L.child_bin = take((size_t)L.n_inodes * 8);
+  L.irange = take((size_t)L.n_inodes * 8);
+  L.src4 = take((size_t)L.n_inodes * 16);
+  L.front0 = take((size_t)L.n_inodes * 8);
+  L.front1 = take((size_t)L.n_inodes * 8);
+  L.levels = take((size_t)(kMaxCollapseLevels + 2) * 4);
   L.total = o;
   return L;
 }
@@ -117,7 +125,7 @@ inline BvhLayout bvh_layout(int64_t n) {
 struct BvhView {
   const TraceRec* trace;
   const ShadeRec* shade;
-  const Node* nodes;
+  const Node4* nodes;
   uint32_t root;  // node index, or an encoded leaf when n <= kLeafMax
   int64_t n;
 };

@@ -12,6 +12,8 @@ namespace eagpt {
 cudaError_t launch_build(const eagpt_scene& sc, const Consts& C, char* base, const BvhLayout& L, cudaStream_t st,
                          int* launches);
 int launch_refit(char* base, const BvhLayout& L, cudaStream_t st);
+// bvh_tree.cu
+cudaError_t launch_tree(const uint32_t* sorted_keys, char* base, const BvhLayout& L, cudaStream_t st);
 cudaError_t launch_records_update(const eagpt_scene& sc, const Consts& C, char* base, const BvhLayout& L,
                                   cudaStream_t st);
 
@@ -57,6 +59,14 @@ cudaError_t launch_backward(const BvhView& bvh, const Consts& C, const eagpt_cam
 uint32_t take_errors_bvh();
 uint32_t take_errors_render();
 uint32_t take_errors_backward();
+uint32_t take_errors_tree();
+uint32_t take_errors_edit();
+
+// edit.cu
+cudaError_t launch_select(const eagpt_scene& sc, int shape, const float* v, int32_t* out, int64_t capacity,
+                          int64_t* out_count, uint32_t* scratch_blocks, cudaStream_t st);
+size_t select_scratch_bytes(int64_t n);
+cudaError_t launch_edit(const eagpt_scene_mut& sc, const eagpt_edit& e, cudaStream_t st);
 
 // capi.cu: argument checks + render launch shared by the render entry points;
 // set_error records the thread-local message of eagpt_last_error()

@@ -117,32 +117,54 @@ __device__ __forceinline__ int collect_round(const BvhView& bvh, const Consts& C
         count = count < K ? count + 1 : K;
       }
     } else if (cur != kEmptyChild) {
-      const Node* np = bvh.nodes + cur;
-      const float4 a = __ldg(&np->n0), b = __ldg(&np->n1), c = __ldg(&np->n2);
-      const uint4 ch = __ldg(&np->n3);
+      const Node4* np = bvh.nodes + cur;
+      const float4 lx = __ldg(&np->lox), ly = __ldg(&np->loy), lz = __ldg(&np->loz);
+      const float4 hx = __ldg(&np->hix), hy = __ldg(&np->hiy), hz = __ldg(&np->hiz);
+      const uint4 ch = __ldg(&np->child);
       if (kCount) ++cnt.nodes;
-      const float tmax = count == K ? kt[K - 1] : __int_as_float(0x7f800000);
-      float e0, e1;
-      const bool h0 = ch.x != kEmptyChild &&
-                      box_hit(make_float3(a.x, a.y, a.z), make_float3(a.w, b.x, b.y), O, inv, t_last, tmax, e0);
-      const bool h1 = ch.y != kEmptyChild &&
-                      box_hit(make_float3(b.z, b.w, c.x), make_float3(c.y, c.z, c.w), O, inv, t_last, tmax, e1);
-      if (h0 && h1) {
-        const bool first0 = e0 <= e1;
-        if (sp >= kStackSize) {
+      const float inf = __int_as_float(0x7f800000);
+      const float tmax = count == K ? kt[K - 1] : inf;
+      // entry distance of each child box, +inf when missed or empty
+      float e[4];
+      uint32_t c[4] = {ch.x, ch.y, ch.z, ch.w};
+      {
+        const float lxa[4] = {lx.x, lx.y, lx.z, lx.w}, lya[4] = {ly.x, ly.y, ly.z, ly.w};
+        const float lza[4] = {lz.x, lz.y, lz.z, lz.w}, hxa[4] = {hx.x, hx.y, hx.z, hx.w};
+        const float hya[4] = {hy.x, hy.y, hy.z, hy.w}, hza[4] = {hz.x, hz.y, hz.z, hz.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          float te;
+          const bool h = box_hit(make_float3(lxa[k], lya[k], lza[k]), make_float3(hxa[k], hya[k], hza[k]), O, inv,
+                                 t_last, tmax, te);
+          e[k] = (h && c[k] != kEmptyChild) ? te : inf;
+        }
+      }
+      // front-to-back order: sorting network on (entry, link)
+#define EAGPT_CSWAP(i, j)                         \
+  if (e[j] < e[i]) {                              \
+    const float tf = e[i];                        \
+    e[i] = e[j];                                  \
+    e[j] = tf;                                    \
+    const uint32_t tc = c[i];                     \
+    c[i] = c[j];                                  \
+    c[j] = tc;                                    \
+  }
+      EAGPT_CSWAP(0, 1)
+      EAGPT_CSWAP(2, 3)
+      EAGPT_CSWAP(0, 2)
+      EAGPT_CSWAP(1, 3)
+      EAGPT_CSWAP(1, 2)
+#undef EAGPT_CSWAP
+      if (e[0] != inf) {
+        const int m = (e[1] != inf) + (e[2] != inf) + (e[3] != inf);
+        if (sp + m > kStackSize) {
           raise_error(kErrStackOverflow);
           return count;
         }
-        stack[(sp++) * stride] = first0 ? ch.y : ch.x;
-        cur = first0 ? ch.x : ch.y;
-        continue;
-      }
-      if (h0) {
-        cur = ch.x;
-        continue;
-      }
-      if (h1) {
-        cur = ch.y;
+        if (e[3] != inf) stack[(sp++) * stride] = c[3];
+        if (e[2] != inf) stack[(sp++) * stride] = c[2];
+        if (e[1] != inf) stack[(sp++) * stride] = c[1];
+        cur = c[0];
         continue;
       }
     }
