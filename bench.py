@@ -15,6 +15,7 @@ of the samples (independent paths; no collective on the data path).
 from __future__ import annotations
 
 import argparse
+import ctypes
 import hashlib
 import glob
 import json
@@ -37,7 +38,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--workload", default="medium", choices=["tiny", "medium", "diff", "large"])
+    ap.add_argument("--workload", default="medium", choices=["tiny", "medium", "diff", "large", "serving"])
+    ap.add_argument("--requests", type=int, default=16, help="serving: requests in the stream")
     ap.add_argument("--spp", type=int, default=None, help="override samples per pixel")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -194,9 +196,125 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def run_serving(args):
+    """Serving room (3M surfels): a seeded request stream (renders of
+    256x256..1920x1080, 16/64/256 spp, 1-5 bounces, 10 % edits) served (a)
+    by plain sequential launches, (b) by the continuous-batching server at
+    Poisson arrival rates of 0.8x and 1.2x the plain capacity.  Reports
+    throughput (pixel samples/s), p50/p99 latency, and whether every served
+    image equals its plain render bit for bit."""
+    import numpy as np
+    import torch
+
+    from paper_2601_23065_gb300 import api, build
+    from paper_2601_23065_gb300 import scenes as S
+
+    build.build()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    host = S.serving_room()
+    reqs = S.serving_requests(host, args.requests, seed=13)
+    n_render = sum(1 for r in reqs if r["type"] == "render")
+    samples = sum(r["camera"].width * r["camera"].height * r["spp"] for r in reqs if r["type"] == "render")
+
+    def resolve_edit(ds, r):
+        idx = torch.from_numpy(r["idx"]).to(dev) if "idx" in r else api.select(ds, "sphere", r["sphere"])
+        per = torch.from_numpy(r["per_index"]).to(dev) if "per_index" in r else None
+        return idx, per
+
+    # (a) plain launches, one request after the other
+    ds = api.DeviceScene.from_host(host, device=dev)
+    bvh = api.BVH(ds)
+    rend = api.Renderer(device=dev)
+    for _ in range(max(1, args.warmup)):
+        rend.path_traced(ds, bvh, S.horizontal_camera(256, 256), 4, 2)
+    torch.cuda.synchronize(dev)
+    plain_out, t0 = [], time.perf_counter()
+    for r in reqs:
+        if r["type"] == "render":
+            o = rend.path_traced(ds, bvh, r["camera"], r["spp"], r["max_bounces"], rr_start=2, seed=r["seed"])
+            plain_out.append(o["rgb"].clone())
+        else:
+            idx, per = resolve_edit(ds, r)
+            api.apply_edit(ds, bvh, r["op"], idx, value=r.get("value", ()), per_index=per)
+    torch.cuda.synchronize(dev)
+    t_plain = time.perf_counter() - t0
+    mu = n_render / t_plain
+    del ds, bvh, rend
+    torch.cuda.empty_cache()
+
+    results = {}
+    for load in (0.8, 1.2):
+        ds = api.DeviceScene.from_host(host, device=dev)
+        bvh = api.BVH(ds)
+        srv = api.Server(ds, bvh, queue_paths=1 << 24, max_active=16)
+        rng = np.random.default_rng(int(load * 100))
+        arrivals = np.cumsum(rng.exponential(1.0 / (load * mu), len(reqs)))
+        ids = []
+        start = time.perf_counter()
+        for r, ta in zip(reqs, arrivals):
+            delay = start + ta - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            if r["type"] == "render":
+                ids.append(("render", srv.submit_render(r["camera"], r["spp"], r["max_bounces"], rr_start=2,
+                                                        seed=r["seed"])))
+            else:
+                idx, per = resolve_edit(ds, r) if "idx" in r else (None, None)
+                if idx is None:
+                    # the selection runs on the scene the edit will apply to:
+                    # wait for the edits before it, then select on the server's
+                    # current scene
+                    for kind, x in ids:
+                        if kind == "edit":
+                            srv.wait(x, 600.0)
+                    cur = api.capi.Scene()
+                    api.capi.check(api.capi.lib().eagpt_server_scene(srv.h, ctypes.byref(cur), None))
+                    view = api.DeviceScene.__new__(api.DeviceScene)
+                    view.n, view.version = ds.n, cur.version
+                    view.t = {"pos": torch.empty(0, device=dev)}
+                    view.c = lambda cur=cur: cur
+                    idx = api.select(view, "sphere", r["sphere"])
+                ids.append(("edit", srv.submit_edit(r["op"], idx, value=r.get("value", ()), per_index=per)))
+        lat, equal, t_end = [], True, start
+        k = 0
+        for kind, x in ids:
+            if kind == "render":
+                rid, out = x
+                info = srv.wait(rid, 1200.0)
+                lat.append(info["t_done"] - info["t_submit"])
+                t_end = max(t_end, info["t_done"])
+                torch.cuda.synchronize(dev)
+                equal &= bool(torch.equal(out, plain_out[k]))
+                k += 1
+            else:
+                srv.wait(x, 1200.0)
+        st = srv.stats()
+        first_submit = start + arrivals[0]
+        span = max(1e-9, time.perf_counter() - first_submit)
+        results[f"load_{load}"] = {"throughput": samples / span, "p50_s": float(np.percentile(lat, 50)),
+                                   "p99_s": float(np.percentile(lat, 99)), "equal_to_plain": equal,
+                                   "segments_per_s_busy": st["segments"] / max(st["busy_s"], 1e-9),
+                                   "waves": st["waves"], "edits": st["edits"], "rebuilds": st["rebuilds"]}
+        srv.close()
+        del ds, bvh
+        torch.cuda.empty_cache()
+    line = {"metric": "pixel samples/s (serving)", "value": results["load_1.2"]["throughput"],
+            "unit": "pixel samples/s", "n_gpus": 1, "steps": 1, "warmup": args.warmup, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "serving room 3M surfels, Poisson request stream", "requests": len(reqs),
+                       "renders": n_render, "pixel_samples": samples},
+            "plain": {"throughput": samples / t_plain, "capacity_req_per_s": mu, "seconds": t_plain},
+            "served": results}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
+    if args.workload == "serving":
+        run_serving(args)
+        return
     if args.impl == "reference":
         if world > 1:
             import torch.distributed as dist

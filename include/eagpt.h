@@ -227,6 +227,87 @@ eagpt_status eagpt_apply_edit(eagpt_scene_mut* scene, eagpt_bvh* bvh, const eagp
                               eagpt_stream_t stream);
 
 /* ------------------------------------------------------------------------
+ * Serving: a persistent request loop over one resident scene (the paper's
+ * edit-then-path-trace use, Sec. 3.4, served to many clients).
+ *
+ * A host thread runs waves: each wave takes the next slice of samples of
+ * every admitted render, puts all their paths into one shared wavefront
+ * queue (rays carry a request id) and runs the path-tracing kernels once over
+ * it (continuous batching).  Submitted renders are admitted before the next
+ * wave, in submission order, when one of max_active request slots and enough
+ * arena memory (primary records, sums and one slice of per-sample values of
+ * the request) are free.  A request's image equals, bit for bit, what
+ * eagpt_render_path_traced() renders with the same arguments: it does not
+ * depend on the other requests in the mix.
+ * Edits apply in submission order: renders submitted earlier finish on the
+ * scene before the edit, later ones see the edit.  Two scene+BVH versions
+ * are kept (the caller's and one in the arena): an edit copies the current
+ * version into the other slot once no running render uses it, edits and
+ * refits the copy and makes it current.  The caller's scene arrays and BVH
+ * storage belong to the server until eagpt_server_destroy() returns; the
+ * final scene is in the slot eagpt_server_scene() reports.
+ * Memory: all device memory comes from the caller's arena (device, 256-byte
+ * aligned, eagpt_server_arena_bytes() for a start); nothing is allocated on
+ * the device.  The server creates one CUDA stream of its own.
+ * Failure handling: a request past its timeout (timeout_s > 0) ends as
+ * TIMED_OUT; eagpt_server_wait() takes its own timeout and returns
+ * EAGPT_ERR_TIMEOUT; a CUDA error fails the running requests.
+ * ------------------------------------------------------------------------ */
+typedef struct eagpt_server_t* eagpt_server;
+
+typedef struct {
+  void* arena;            /* device, caller-owned */
+  size_t arena_bytes;
+  int64_t queue_paths;    /* paths of one wave (all requests), >= the largest image's pixels */
+  int32_t max_active;     /* request slots, 1..64 */
+  float rebuild_ratio;    /* refit-vs-rebuild threshold for geometry edits (e.g. 1.5) */
+} eagpt_server_config;
+
+typedef struct {
+  eagpt_camera cam;
+  int32_t spp, max_bounces, rr_start_bounce;
+  uint64_t seed;
+  float* out_rgb;         /* device, H x W x 3; written when the request is done */
+  double timeout_s;       /* 0: none */
+} eagpt_render_request;
+
+typedef enum {
+  EAGPT_REQ_QUEUED = 0,
+  EAGPT_REQ_RUNNING = 1,
+  EAGPT_REQ_DONE = 2,
+  EAGPT_REQ_FAILED = 3,
+  EAGPT_REQ_CANCELLED = 4,
+  EAGPT_REQ_TIMED_OUT = 5
+} eagpt_request_state;
+
+typedef struct {
+  int32_t state;          /* eagpt_request_state */
+  int32_t rebuilt;        /* edits: the BVH was rebuilt */
+  double t_submit, t_admit, t_done;  /* seconds, steady clock */
+  uint64_t scene_version; /* version the request rendered (or produced) */
+} eagpt_request_info;
+
+typedef struct {
+  int64_t submitted, admitted, completed, failed, edits, rebuilds, waves;
+  int64_t segments, paths;  /* traced in all waves (primary segments included) */
+  double busy_s;            /* wall time spent in waves */
+  int64_t arena_free_bytes;
+} eagpt_server_stats;
+
+size_t eagpt_server_arena_bytes(int64_t n, int64_t queue_paths);
+eagpt_status eagpt_server_create(const eagpt_scene_mut* scene, const eagpt_bvh* bvh, const eagpt_params* params,
+                                 const eagpt_server_config* cfg, eagpt_server* out);
+eagpt_status eagpt_server_submit_render(eagpt_server server, const eagpt_render_request* req, uint64_t* out_id);
+/* idx and per_index of the edit must stay valid until the edit is done */
+eagpt_status eagpt_server_submit_edit(eagpt_server server, const eagpt_edit* edit, uint64_t* out_id);
+eagpt_status eagpt_server_poll(eagpt_server server, uint64_t id, eagpt_request_info* out);
+eagpt_status eagpt_server_wait(eagpt_server server, uint64_t id, double timeout_s, eagpt_request_info* out);
+eagpt_status eagpt_server_cancel(eagpt_server server, uint64_t id);
+eagpt_status eagpt_server_get_stats(eagpt_server server, eagpt_server_stats* out);
+eagpt_status eagpt_server_scene(eagpt_server server, eagpt_scene_mut* scene, eagpt_bvh* bvh);
+eagpt_status eagpt_server_destroy(eagpt_server server);
+
+/* ------------------------------------------------------------------------
  * Allocation-free path-traced render.  The paper has no counterpart: this is
  * a deployment variant of eagpt_render_path_traced() for callers that cannot
  * allocate device memory themselves -- a plugin inside a host application

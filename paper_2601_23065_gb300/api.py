@@ -294,3 +294,97 @@ def apply_edit(scene: DeviceScene, bvh: BVH, op: str, idx: torch.Tensor, value=(
                                   ctypes.byref(e), float(rebuild_ratio), ctypes.byref(rebuilt), _stream(stream)))
     scene.version = int(sm.version)
     return bool(rebuilt.value)
+
+
+class Server:
+    """Continuous-batching request loop (eagpt_server_*): renders and edits
+    are submitted from any thread; the library's own thread batches them."""
+
+    def __init__(self, scene: DeviceScene, bvh: BVH, queue_paths: int = 1 << 24, max_active: int = 16,
+                 arena_bytes: Optional[int] = None, rebuild_ratio: float = 1.5):
+        L = capi.lib()
+        need = L.eagpt_server_arena_bytes(scene.n, queue_paths)
+        self.arena = torch.empty(arena_bytes or need, dtype=torch.uint8, device=scene.t["pos"].device)
+        cfg = capi.ServerConfig()
+        cfg.arena = self.arena.data_ptr()
+        cfg.arena_bytes = self.arena.numel()
+        cfg.queue_paths = int(queue_paths)
+        cfg.max_active = int(max_active)
+        cfg.rebuild_ratio = float(rebuild_ratio)
+        self.scene, self.bvh = scene, bvh
+        self.h = ctypes.c_void_p()
+        sm = scene.c()
+        capi.check(L.eagpt_server_create(ctypes.byref(sm), ctypes.byref(bvh.handle), ctypes.byref(bvh.params),
+                                         ctypes.byref(cfg), ctypes.byref(self.h)))
+        self._keep = {}
+        self.device = scene.t["pos"].device
+
+    def submit_render(self, cam: HostCamera, spp: int, max_bounces: int, rr_start: int = 2, seed: int = 0,
+                      out: Optional[torch.Tensor] = None, timeout_s: float = 0.0):
+        """Returns (request id, output tensor written when the request is done)."""
+        out = out if out is not None else torch.empty((cam.height, cam.width, 3), dtype=torch.float32,
+                                                       device=self.device)
+        r = capi.RenderRequest()
+        r.cam = camera(cam)
+        r.spp, r.max_bounces, r.rr_start_bounce = int(spp), int(max_bounces), int(rr_start)
+        r.seed = int(seed)
+        r.out_rgb = out.data_ptr()
+        r.timeout_s = float(timeout_s)
+        rid = ctypes.c_uint64()
+        capi.check(capi.lib().eagpt_server_submit_render(self.h, ctypes.byref(r), ctypes.byref(rid)))
+        self._keep[rid.value] = (out,)
+        return rid.value, out
+
+    def submit_edit(self, op: str, idx: torch.Tensor, value=(), per_index: Optional[torch.Tensor] = None) -> int:
+        idx = idx.to(torch.int32).contiguous()
+        pi = per_index.to(torch.float32).contiguous() if per_index is not None else None
+        e = capi.Edit()
+        e.op = EDIT_OPS[op]
+        e.reserved = 0
+        e.count = idx.numel()
+        e.idx = idx.data_ptr() if idx.numel() else None
+        e.per_index = pi.data_ptr() if pi is not None else None
+        vals = list(value) + [0.0] * (16 - len(value))
+        for k in range(16):
+            e.value[k] = float(vals[k])
+        torch.cuda.current_stream(self.device).synchronize()  # the edit's inputs are ready before the server reads them
+        rid = ctypes.c_uint64()
+        capi.check(capi.lib().eagpt_server_submit_edit(self.h, ctypes.byref(e), ctypes.byref(rid)))
+        self._keep[rid.value] = (idx, pi)
+        return rid.value
+
+    @staticmethod
+    def _info(i: "capi.RequestInfo") -> dict:
+        return {"state": capi.REQ_STATES.get(i.state, i.state), "rebuilt": bool(i.rebuilt), "t_submit": i.t_submit,
+                "t_admit": i.t_admit, "t_done": i.t_done, "scene_version": i.scene_version}
+
+    def poll(self, rid: int) -> dict:
+        i = capi.RequestInfo()
+        capi.check(capi.lib().eagpt_server_poll(self.h, ctypes.c_uint64(rid), ctypes.byref(i)))
+        return self._info(i)
+
+    def wait(self, rid: int, timeout_s: float = 0.0) -> dict:
+        i = capi.RequestInfo()
+        capi.check(capi.lib().eagpt_server_wait(self.h, ctypes.c_uint64(rid), float(timeout_s), ctypes.byref(i)))
+        self._keep.pop(rid, None)
+        return self._info(i)
+
+    def cancel(self, rid: int) -> None:
+        capi.check(capi.lib().eagpt_server_cancel(self.h, ctypes.c_uint64(rid)))
+
+    def stats(self) -> dict:
+        s = capi.ServerStats()
+        capi.check(capi.lib().eagpt_server_get_stats(self.h, ctypes.byref(s)))
+        return {k: getattr(s, k) for k, _ in capi.ServerStats._fields_}
+
+    def close(self) -> None:
+        if self.h:
+            capi.check(capi.lib().eagpt_server_destroy(self.h))
+            self.h = None
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -68,6 +68,29 @@ class Edit(ctypes.Structure):
                 ("value", c_f * 16)]
 
 
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("arena", c_vp), ("arena_bytes", c_sz), ("queue_paths", c_i64), ("max_active", c_i32),
+                ("rebuild_ratio", c_f)]
+
+
+class RenderRequest(ctypes.Structure):
+    _fields_ = [("cam", Camera), ("spp", c_i32), ("max_bounces", c_i32), ("rr_start_bounce", c_i32),
+                ("seed", c_u64), ("out_rgb", c_vp), ("timeout_s", ctypes.c_double)]
+
+
+class RequestInfo(ctypes.Structure):
+    _fields_ = [("state", c_i32), ("rebuilt", c_i32), ("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double),
+                ("t_done", ctypes.c_double), ("scene_version", c_u64)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", c_i64), ("admitted", c_i64), ("completed", c_i64), ("failed", c_i64),
+                ("edits", c_i64), ("rebuilds", c_i64), ("waves", c_i64), ("segments", c_i64), ("paths", c_i64),
+                ("busy_s", ctypes.c_double), ("arena_free_bytes", c_i64)]
+
+
+REQ_STATES = {0: "queued", 1: "running", 2: "done", 3: "failed", 4: "cancelled", 5: "timed_out"}
+
 # symbol -> (restype, argtypes)
 SIGNATURES = {
     "eagpt_default_params": (None, [P(Params)]),
@@ -85,6 +108,16 @@ SIGNATURES = {
     "eagpt_select_scratch_bytes": (c_sz, [c_i64]),
     "eagpt_select": (c_i32, [P(Scene), c_i32, P(c_f), c_vp, c_i64, c_vp, c_vp, c_sz, c_vp]),
     "eagpt_apply_edit": (c_i32, [P(Scene), P(Bvh), P(Params), P(Edit), c_f, P(c_i32), c_vp]),
+    "eagpt_server_arena_bytes": (c_sz, [c_i64, c_i64]),
+    "eagpt_server_create": (c_i32, [P(Scene), P(Bvh), P(Params), P(ServerConfig), P(c_vp)]),
+    "eagpt_server_submit_render": (c_i32, [c_vp, P(RenderRequest), P(c_u64)]),
+    "eagpt_server_submit_edit": (c_i32, [c_vp, P(Edit), P(c_u64)]),
+    "eagpt_server_poll": (c_i32, [c_vp, c_u64, P(RequestInfo)]),
+    "eagpt_server_wait": (c_i32, [c_vp, c_u64, ctypes.c_double, P(RequestInfo)]),
+    "eagpt_server_cancel": (c_i32, [c_vp, c_u64]),
+    "eagpt_server_get_stats": (c_i32, [c_vp, P(ServerStats)]),
+    "eagpt_server_scene": (c_i32, [c_vp, P(Scene), P(Bvh)]),
+    "eagpt_server_destroy": (c_i32, [c_vp]),
     "eagpt_render_path_traced_noalloc_max_bytes": (c_sz, []),
     "eagpt_render_path_traced_noalloc": (c_i32, [P(Scene), P(Bvh), P(Camera), P(Params), c_i32, c_i32, c_i32, c_u64,
                                                  c_vp, c_vp]),

@@ -330,8 +330,22 @@ eagpt_status eagpt_apply_edit(eagpt_scene_mut* scene, eagpt_bvh* bvh, const eagp
     return fail(EAGPT_ERR_INVALID_ARGUMENT, "edit count/idx invalid%s");
   for (int k = 0; k < 16; ++k)
     if (!std::isfinite(edit->value[k])) return fail(EAGPT_ERR_INVALID_ARGUMENT, "edit values must be finite%s");
+  return apply_edit_core(scene, bvh, params, edit, rebuild_ratio, out_rebuilt, (cudaStream_t)stream);
+}
+
+}  // extern "C"
+
+namespace eagpt {
+
+BvhView bvh_view(const eagpt_bvh& b) { return make_view(b); }
+
+// The edit after its arguments were checked: edit, records, refit or
+// rebuild, version bump.
+eagpt_status apply_edit_core(eagpt_scene_mut* scene, eagpt_bvh* bvh, const eagpt_params* params,
+                             const eagpt_edit* edit, float rebuild_ratio, int32_t* out_rebuilt, cudaStream_t st) {
+  eagpt_scene cs;
+  std::memcpy(&cs, scene, sizeof(cs));
   if (out_rebuilt) *out_rebuilt = 0;
-  cudaStream_t st = (cudaStream_t)stream;
   cudaError_t e = launch_edit(*scene, *edit, st);
   if (e != cudaSuccess) return cuda_fail(e, "edit launch");
   if (scene->n > 0) {
@@ -364,6 +378,10 @@ eagpt_status eagpt_apply_edit(eagpt_scene_mut* scene, eagpt_bvh* bvh, const eagp
   bvh->scene_version = scene->version;
   return EAGPT_OK;
 }
+
+}  // namespace eagpt
+
+extern "C" {
 
 eagpt_status eagpt_trace_rays(const eagpt_scene* scene, const eagpt_bvh* bvh, const eagpt_params* params,
                               int32_t mode, const float* rays, int64_t n_rays, float* out_rec, int32_t* out_hits,
@@ -400,7 +418,8 @@ eagpt_status eagpt_sync_status(eagpt_stream_t stream) {
   cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "sync");
   const uint32_t word =
-      take_errors_bvh() | take_errors_render() | take_errors_backward() | take_errors_tree() | take_errors_edit();
+      take_errors_bvh() | take_errors_render() | take_errors_backward() | take_errors_tree() | take_errors_edit() |
+      take_errors_serve();
   if (word) {
     char buf[128];
     std::snprintf(buf, sizeof(buf), "device check failed (error bits 0x%x)", word);

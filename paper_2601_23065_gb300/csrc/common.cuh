@@ -12,7 +12,10 @@ namespace eagpt {
 // ---------------------------------------------------------------------------
 // Sizes and encodings
 // ---------------------------------------------------------------------------
-constexpr int kLeafMax = 4;          // surfels per collapsed BVH leaf
+#ifndef EAGPT_LEAF_MAX
+#define EAGPT_LEAF_MAX 4
+#endif
+constexpr int kLeafMax = EAGPT_LEAF_MAX;  // surfels per BVH leaf (1..4)
 constexpr int kStackSize = 64;       // traversal stack entries per ray
 constexpr int kBlock = 128;          // threads per block of the trace kernels
 constexpr uint32_t kLeafBit = 0x80000000u;

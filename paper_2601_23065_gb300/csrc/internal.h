@@ -61,6 +61,7 @@ uint32_t take_errors_render();
 uint32_t take_errors_backward();
 uint32_t take_errors_tree();
 uint32_t take_errors_edit();
+uint32_t take_errors_serve();
 
 // edit.cu
 cudaError_t launch_select(const eagpt_scene& sc, int shape, const float* v, int32_t* out, int64_t capacity,
@@ -75,6 +76,9 @@ eagpt_status render_entry(const eagpt_scene* scene, const eagpt_bvh* bvh, const 
                           uint64_t seed, float* out_rgb, float* out_aux, float* out_samples, int64_t* out_stats,
                           void* ws, size_t ws_bytes, eagpt_stream_t stream);
 eagpt_status set_error(eagpt_status s, const char* msg);
+BvhView bvh_view(const eagpt_bvh& b);
+eagpt_status apply_edit_core(eagpt_scene_mut* scene, eagpt_bvh* bvh, const eagpt_params* params,
+                             const eagpt_edit* edit, float rebuild_ratio, int32_t* out_rebuilt, cudaStream_t st);
 
 // number of SMs of the current device (cached per device)
 int device_sms();

@@ -18,24 +18,16 @@
 #include "common.cuh"
 #include "internal.h"
 #include "trace.cuh"
+#include "wave.cuh"
 
 namespace eagpt {
 
-constexpr int kK = 16;  // k-buffer size (hits collected per traversal round)
+#ifndef EAGPT_KBUF
+#define EAGPT_KBUF 16
+#endif
+constexpr int kK = EAGPT_KBUF;  // k-buffer size (hits collected per traversal round)
 
 EAGPT_DEFINE_ERROR_READER(take_errors_render)
-
-struct __align__(16) Ray {
-  float4 a;  // origin, pixel (bits)
-  float4 b;  // direction, sample (bits)
-  float4 c;  // throughput, unused
-};
-
-struct __align__(16) PrimRec {
-  float4 a;  // N~, D~
-  float4 b;  // R, E
-  float4 c;  // P, A
-};
 
 // counters block: per bounce k, [2k] = rays queued for bounce k, [2k+1] = fetch
 constexpr int kMaxBounces = 60;
@@ -125,21 +117,6 @@ __global__ void __launch_bounds__(kBlock) k_primary(BvhView bvh, Consts C, eagpt
   }
 }
 
-// Warp-aggregated append of the lanes with `take` set; returns each such
-// lane's index in the queue.  All 32 lanes must call it.
-__device__ __forceinline__ uint32_t warp_append(bool take, uint32_t* counter) {
-  const uint32_t mask = __ballot_sync(0xffffffffu, take);
-  const int lane = threadIdx.x & 31;
-  uint32_t base = 0;
-  if (lane == 0 && mask) base = atomicAdd(counter, (uint32_t)__popc(mask));
-  base = __shfl_sync(0xffffffffu, base, 0);
-  return base + __popc(mask & ((1u << lane) - 1u));
-}
-
-__device__ __forceinline__ bool is_emitter_pixel(const PrimRec& p, const Consts& C) {
-  return p.c.w >= 0.f && p.b.w > C.tau_E;
-}
-
 // First bounce of every path of the batch [s0, s0 + batch) (Sec. 3.1 "Light
 // Bouncing"): X = O + D~ w, throughput P (the cosine pdf cancels cos/pi of
 // the diffuse BRDF), cosine-weighted direction about N~ from X + offset N~.
@@ -159,32 +136,10 @@ __global__ void __launch_bounds__(kBlock) k_generate(const PrimRec* __restrict__
     const int sl = (int)(t / npix);
     slot = t;
     const PrimRec p = prim[pixel];
-    if (p.c.w >= 0.f && !(p.b.w > C.tau_E)) {
+    if (prim_is_path_start(p, C)) {
       started = true;
-      const int B = kind == 0 ? 1 : max_bounces;
-      float3 beta = make_float3(p.c.x, p.c.y, p.c.z);
-      bool alive = B >= 1;
-      const uint32_t sample = (uint32_t)(s0 + sl);
-      const float4 u = draws(seed, (uint32_t)pixel, sample, 1u);
-      if (alive && kind == 1 && rr_start <= 1) {
-        const float q = fminf(1.f, fmaxf(beta.x, fmaxf(beta.y, beta.z)));
-        if (!(u.z < q)) alive = false;
-        else beta = (1.f / q) * beta;
-      }
-      if (alive) {
-        float3 O, w;
-        camera_ray(cam, (uint32_t)pixel, O, w);
-        const float3 Nn = make_float3(p.a.x, p.a.y, p.a.z);
-        const float3 X = O + p.a.w * w;
-        const float3 O2 = X + C.bounce_offset * Nn;
-        const float3 w2 = cosine_direction(Nn, u.x, u.y);
-        r.a = make_float4(O2.x, O2.y, O2.z, __uint_as_float((uint32_t)pixel));
-        r.b = make_float4(w2.x, w2.y, w2.z, __uint_as_float(sample));
-        r.c = make_float4(beta.x, beta.y, beta.z, 0.f);
-        take = true;
-      } else {
-        slots[slot] = make_float4(0.f, 0.f, 0.f, 0.f);
-      }
+      take = first_bounce(p, C, cam, kind, max_bounces, rr_start, seed, (uint32_t)pixel, (uint32_t)(s0 + sl), 0u, r);
+      if (!take) slots[slot] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
   }
   const uint32_t at = warp_append(take, &counters[2 * 1]);
@@ -217,40 +172,12 @@ __global__ void __launch_bounds__(kBlock) k_bounce(BvhView bvh, Consts C, int ki
       const Ray r = q_in[idx];
       const float3 O = f3(r.a), w = f3(r.b);
       const uint32_t pixel = __float_as_uint(r.a.w), sample = __float_as_uint(r.b.w);
-      float3 beta = f3(r.c);
       BlendVisitor vis(bvh.shade, C, w, mode);
       trace_segment<kK, kCount>(bvh, C, O, w, 0.f, s_stack + threadIdx.x, kBlock, vis, cnt);
       const SegRec s = finish(vis.b);
-      const int64_t slot = (int64_t)(sample - (uint32_t)s0) * npix + pixel;
-      float3 contrib = make_float3(0.f, 0.f, 0.f);
-      bool end = true;
-      if (kind == 0) {
-        contrib = mul3(beta, s.R);  // the secondary's radiance is the cache
-      } else if (!s.hit) {
-        // miss: no light
-      } else if (s.E > C.tau_E) {
-        contrib = mul3(beta, s.R);  // first emissive vertex
-      } else if (k < max_bounces) {
-        beta = mul3(beta, s.P);
-        const float4 u = draws(seed, pixel, sample, (uint32_t)(k + 1));
-        bool alive = true;
-        if (k + 1 >= rr_start) {
-          const float q = fminf(1.f, fmaxf(beta.x, fmaxf(beta.y, beta.z)));
-          if (!(u.z < q)) alive = false;
-          else beta = (1.f / q) * beta;
-        }
-        if (alive) {
-          const float3 X = O + s.Dn * w;
-          const float3 O2 = X + C.bounce_offset * s.Nn;
-          const float3 w2 = cosine_direction(s.Nn, u.x, u.y);
-          nr.a = make_float4(O2.x, O2.y, O2.z, r.a.w);
-          nr.b = make_float4(w2.x, w2.y, w2.z, r.b.w);
-          nr.c = make_float4(beta.x, beta.y, beta.z, 0.f);
-          take = true;
-          end = false;
-        }
-      }
-      if (end) slots[slot] = make_float4(contrib.x, contrib.y, contrib.z, 0.f);
+      float3 contrib;
+      take = shade_bounce(kind, k, max_bounces, rr_start, seed, C, r, s, contrib, nr);
+      if (!take) slots[(int64_t)(sample - (uint32_t)s0) * npix + pixel] = make_float4(contrib.x, contrib.y, contrib.z, 0.f);
     }
     __syncwarp();
     const uint32_t at = warp_append(take, &counters[2 * (k + 1)]);

@@ -1,0 +1,708 @@
+// Continuous-batching serving loop for path-traced renders and scene edits.
+//
+// One host thread owns a CUDA stream and runs waves.  A wave takes the next
+// slice of samples of every admitted render, generates their first bounces
+// into one shared ray queue (each ray carries its request id), runs the
+// bounce kernels over the shared queue, and accumulates every request's
+// samples into its own pixels in sample order.  Requests submitted while a
+// wave runs are admitted before the next wave when a request slot and arena
+// memory are free, so their paths share the device with the running ones.
+// A path's arithmetic and its random numbers depend only on its request
+// (seed, pixel, sample, bounce), and every pixel adds its samples in order,
+// so a request's image is bitwise the same alone and in any mix.
+//
+// Edits are applied in submission order: renders submitted before an edit see
+// the old scene, later ones the new.  The server keeps two scene+BVH
+// versions: an edit copies the current version into the other slot (once no
+// running request uses it), edits and refits the copy and makes it current,
+// while requests admitted earlier finish on the old version.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "common.cuh"
+#include "internal.h"
+#include "trace.cuh"
+#include "wave.cuh"
+
+namespace eagpt {
+
+EAGPT_DEFINE_ERROR_READER(take_errors_serve)
+
+constexpr int kSrvMaxActive = 64;
+constexpr int kSrvMaxBounces = 60;
+constexpr int kSrvCounterWords = 2 * (kSrvMaxBounces + 2) + 8;
+#ifndef EAGPT_SERVE_KBUF
+#define EAGPT_SERVE_KBUF 16
+#endif
+constexpr int kSrvK = EAGPT_SERVE_KBUF;
+
+struct __align__(16) ReqDev {
+  eagpt_camera cam;
+  uint64_t seed;
+  int64_t npix;
+  int64_t path_off;  // first flattened path of this request in the wave
+  int64_t pix_off;   // first flattened pixel of this request in the wave
+  PrimRec* prim;
+  float4* acc;
+  float4* slots;
+  float* out_rgb;
+  int32_t spp, max_bounces, rr_start, s0, batch, version, first, last;
+};
+
+__device__ __forceinline__ int find_req(const int64_t* offs, int nreq, int64_t t) {
+  int r = 0;
+  for (int k = 1; k < nreq; ++k) r = offs[k] <= t ? k : r;
+  return r;
+}
+
+__global__ void __launch_bounds__(kBlock) k_srv_generate(const ReqDev* __restrict__ reqs, int nreq, int64_t total,
+                                                         Consts C, Ray* q_out, uint32_t* counters) {
+  __shared__ int64_t offs[kSrvMaxActive];
+  for (int k = threadIdx.x; k < nreq; k += blockDim.x) offs[k] = reqs[k].path_off;
+  __syncthreads();
+  const int64_t t = blockIdx.x * (int64_t)kBlock + threadIdx.x;
+  bool take = false;
+  Ray r;
+  if (t < total) {
+    const int q = find_req(offs, nreq, t);
+    const ReqDev& R = reqs[q];
+    const int64_t local = t - R.path_off;
+    const int64_t pixel = local % R.npix;
+    const int sl = (int)(local / R.npix);
+    const PrimRec p = R.prim[pixel];
+    if (prim_is_path_start(p, C)) {
+      take = first_bounce(p, C, R.cam, 1, R.max_bounces, R.rr_start, R.seed, (uint32_t)pixel, (uint32_t)(R.s0 + sl),
+                          (uint32_t)q, r);
+      if (!take) R.slots[local] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+  }
+  const uint32_t at = warp_append(take, &counters[2 * 1]);
+  if (take) q_out[at] = r;
+}
+
+__global__ void __launch_bounds__(kBlock) k_srv_bounce(BvhView v0, BvhView v1, const ReqDev* __restrict__ reqs,
+                                                       Consts C, int k, const Ray* __restrict__ q_in, Ray* q_out,
+                                                       uint32_t* counters) {
+  __shared__ uint32_t s_stack[kStackSize * kBlock];
+  const int lane = threadIdx.x & 31;
+  const uint32_t count = counters[2 * k];
+  TraceCounters cnt{0, 0, 0, 0};
+  for (;;) {
+    uint32_t base = 0;
+    if (lane == 0) base = atomicAdd(&counters[2 * k + 1], 32u);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (base >= count) break;
+    const uint32_t idx = base + lane;
+    bool take = false;
+    Ray nr;
+    if (idx < count) {
+      const Ray r = q_in[idx];
+      const ReqDev& R = reqs[__float_as_uint(r.c.w)];
+      const BvhView& bvh = R.version ? v1 : v0;
+      const float3 O = f3(r.a), w = f3(r.b);
+      const uint32_t pixel = __float_as_uint(r.a.w), sample = __float_as_uint(r.b.w);
+      BlendVisitor vis(bvh.shade, C, w, 1);
+      trace_segment<kSrvK, false>(bvh, C, O, w, 0.f, s_stack + threadIdx.x, kBlock, vis, cnt);
+      const SegRec s = finish(vis.b);
+      float3 contrib;
+      take = shade_bounce(1, k, R.max_bounces, R.rr_start, R.seed, C, r, s, contrib, nr);
+      if (!take)
+        R.slots[(int64_t)(sample - (uint32_t)R.s0) * R.npix + pixel] = make_float4(contrib.x, contrib.y, contrib.z, 0.f);
+    }
+    __syncwarp();
+    const uint32_t at = warp_append(take, &counters[2 * (k + 1)]);
+    if (take) q_out[at] = nr;
+  }
+}
+
+__global__ void __launch_bounds__(kBlock) k_srv_accumulate(const ReqDev* __restrict__ reqs, int nreq,
+                                                           int64_t total_pix, Consts C) {
+  __shared__ int64_t offs[kSrvMaxActive];
+  for (int k = threadIdx.x; k < nreq; k += blockDim.x) offs[k] = reqs[k].pix_off;
+  __syncthreads();
+  const int64_t t = blockIdx.x * (int64_t)kBlock + threadIdx.x;
+  if (t >= total_pix) return;
+  const ReqDev& R = reqs[find_req(offs, nreq, t)];
+  const int64_t i = t - R.pix_off;
+  const PrimRec p = R.prim[i];
+  const bool hit = p.c.w >= 0.f;
+  const bool emit = hit && p.b.w > C.tau_E;
+  if (!hit || emit) {
+    if (R.last) {
+      const float3 v = emit ? f3(p.b) : make_float3(0.f, 0.f, 0.f);
+      R.out_rgb[3 * i] = v.x;
+      R.out_rgb[3 * i + 1] = v.y;
+      R.out_rgb[3 * i + 2] = v.z;
+    }
+    return;
+  }
+  float4 a = R.first ? make_float4(0.f, 0.f, 0.f, 0.f) : R.acc[i];
+  for (int s = 0; s < R.batch; ++s) {
+    const float4 c = R.slots[(int64_t)s * R.npix + i];
+    a.x += c.x;
+    a.y += c.y;
+    a.z += c.z;
+  }
+  if (R.last) {
+    const float inv = 1.f / (float)R.spp;
+    R.out_rgb[3 * i] = a.x * inv;
+    R.out_rgb[3 * i + 1] = a.y * inv;
+    R.out_rgb[3 * i + 2] = a.z * inv;
+  } else {
+    R.acc[i] = a;
+  }
+}
+
+// --------------------------------------------------------------------------
+// host side
+// --------------------------------------------------------------------------
+namespace {
+
+double now_s() {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+// First-fit allocator over a fixed device range (256-byte granules).
+class Arena {
+ public:
+  void init(size_t base, size_t bytes) {
+    free_.clear();
+    if (bytes) free_[base] = bytes;
+  }
+  bool alloc(size_t bytes, size_t* out) {
+    bytes = align256(bytes ? bytes : 1);
+    for (auto it = free_.begin(); it != free_.end(); ++it) {
+      if (it->second >= bytes) {
+        *out = it->first;
+        const size_t rest = it->second - bytes, at = it->first + bytes;
+        free_.erase(it);
+        if (rest) free_[at] = rest;
+        return true;
+      }
+    }
+    return false;
+  }
+  void release(size_t off, size_t bytes) {
+    bytes = align256(bytes ? bytes : 1);
+    auto it = free_.emplace(off, bytes).first;
+    auto nx = std::next(it);
+    if (nx != free_.end() && it->first + it->second == nx->first) {
+      it->second += nx->second;
+      free_.erase(nx);
+    }
+    if (it != free_.begin()) {
+      auto pv = std::prev(it);
+      if (pv->first + pv->second == it->first) {
+        pv->second += it->second;
+        free_.erase(it);
+      }
+    }
+  }
+  size_t free_bytes() const {
+    size_t s = 0;
+    for (auto& kv : free_) s += kv.second;
+    return s;
+  }
+
+ private:
+  std::map<size_t, size_t> free_;
+};
+
+struct Req {
+  uint64_t id = 0;
+  int kind = 0;  // 0 render, 1 edit
+  eagpt_render_request rr{};
+  eagpt_edit edit{};
+  int32_t state = EAGPT_REQ_QUEUED;
+  double t_submit = 0, t_admit = 0, t_done = 0, deadline = 0;
+  int version = 0;
+  uint64_t scene_version = 0;
+  int64_t npix = 0;
+  int s_next = 0, batch_cap = 1;
+  size_t off = 0, bytes = 0;
+  int32_t rebuilt = 0;
+};
+
+}  // namespace
+
+struct Server {
+  eagpt_params params{};
+  eagpt_server_config cfg{};
+  eagpt_scene_mut scene[2]{};
+  eagpt_bvh bvh[2]{};
+  int current = 0;
+  int users[2] = {0, 0};  // running renders per version
+  char* base = nullptr;
+  cudaStream_t stream = nullptr;
+  Ray* q[2] = {nullptr, nullptr};
+  uint32_t* counters = nullptr;
+  ReqDev* table = nullptr;
+  int64_t queue_cap = 0;
+  Arena arena;
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  std::deque<uint64_t> pending;
+  std::map<uint64_t, Req> reqs;
+  std::vector<uint64_t> active;
+  uint64_t next_id = 1;
+  bool stop = false;
+  std::thread worker;
+  eagpt_server_stats stats{};
+  std::string error;
+
+  void run();
+  bool admit_locked(Req& r);
+  void finish_locked(Req& r, int32_t state);
+  bool apply_edit_locked(Req& r, std::unique_lock<std::mutex>& lk);
+  void wave(std::unique_lock<std::mutex>& lk);
+};
+
+static size_t scene_bytes(int64_t n) { return align256((size_t)(n > 0 ? n : 1) * 19 * sizeof(float)); }
+
+bool Server::admit_locked(Req& r) {
+  const int64_t npix = (int64_t)r.rr.cam.width * r.rr.cam.height;
+  // paths per wave of this request: its share of the queue, at least one
+  // sample per pixel
+  int64_t share = queue_cap / std::max<int64_t>(1, cfg.max_active);
+  int64_t cap = std::max<int64_t>(1, share / std::max<int64_t>(1, npix));
+  cap = std::min<int64_t>(cap, r.rr.spp);
+  int64_t in_use = 0;
+  for (uint64_t id : active) in_use += reqs[id].npix * reqs[id].batch_cap;
+  if (in_use + npix * cap > queue_cap) {
+    cap = std::min<int64_t>(cap, (queue_cap - in_use) / std::max<int64_t>(1, npix));
+    if (cap < 1) return false;
+  }
+  const size_t bytes = align256((size_t)npix * sizeof(PrimRec)) + align256((size_t)npix * sizeof(float4)) +
+                       align256((size_t)npix * cap * sizeof(float4));
+  size_t off = 0;
+  if (!arena.alloc(bytes, &off)) return false;
+  r.npix = npix;
+  r.batch_cap = (int)cap;
+  r.off = off;
+  r.bytes = bytes;
+  r.version = current;
+  r.scene_version = scene[current].version;
+  r.s_next = 0;
+  r.state = EAGPT_REQ_RUNNING;
+  r.t_admit = now_s();
+  users[current] += 1;
+  active.push_back(r.id);
+  // primary records of the request on its scene version
+  PrimRec* prim = (PrimRec*)(base + off);
+  launch_primary_records(bvh_view(bvh[current]), make_consts(params), r.rr.cam, 1, npix, prim, stream);
+  stats.admitted += 1;
+  return true;
+}
+
+void Server::finish_locked(Req& r, int32_t state) {
+  if (r.state == EAGPT_REQ_RUNNING) {
+    arena.release(r.off, r.bytes);
+    users[r.version] -= 1;
+    active.erase(std::remove(active.begin(), active.end(), r.id), active.end());
+  }
+  r.state = state;
+  r.t_done = now_s();
+  if (state == EAGPT_REQ_DONE) stats.completed += 1;
+  else stats.failed += 1;
+  cv_done.notify_all();
+}
+
+bool Server::apply_edit_locked(Req& r, std::unique_lock<std::mutex>& lk) {
+  const int target = 1 - current;
+  if (users[target] > 0) return false;  // the other version is still rendering
+  (void)lk;
+  const int64_t n = scene[current].n;
+  // copy the current version into the target slot, then edit the copy
+  const float* src[7] = {scene[current].pos, scene[current].quat, scene[current].scale, scene[current].opacity,
+                         scene[current].albedo, scene[current].radiance, scene[current].emissive};
+  float* dst[7] = {scene[target].pos, scene[target].quat, scene[target].scale, scene[target].opacity,
+                   scene[target].albedo, scene[target].radiance, scene[target].emissive};
+  const int width[7] = {3, 4, 2, 1, 3, 3, 1};
+  cudaError_t e = cudaSuccess;
+  for (int k = 0; k < 7 && e == cudaSuccess; ++k)
+    e = cudaMemcpyAsync(dst[k], src[k], (size_t)n * width[k] * sizeof(float), cudaMemcpyDeviceToDevice, stream);
+  if (e == cudaSuccess && n > 0)
+    e = cudaMemcpyAsync(bvh[target].storage, bvh[current].storage, bvh_layout(n).total, cudaMemcpyDeviceToDevice,
+                        stream);
+  if (e != cudaSuccess) {
+    error = cudaGetErrorString(e);
+    finish_locked(r, EAGPT_REQ_FAILED);
+    return true;
+  }
+  scene[target].version = scene[current].version;
+  void* storage = bvh[target].storage;
+  const size_t sbytes = bvh[target].bytes;
+  bvh[target] = bvh[current];
+  bvh[target].storage = storage;
+  bvh[target].bytes = sbytes;
+  const eagpt_status st =
+      apply_edit_core(&scene[target], &bvh[target], &params, &r.edit, cfg.rebuild_ratio, &r.rebuilt, stream);
+  if (st != EAGPT_OK) {
+    error = "edit failed";
+    finish_locked(r, EAGPT_REQ_FAILED);
+    return true;
+  }
+  current = target;
+  r.scene_version = scene[current].version;
+  r.t_admit = now_s();
+  r.state = EAGPT_REQ_RUNNING;
+  stats.edits += 1;
+  if (r.rebuilt) stats.rebuilds += 1;
+  r.state = EAGPT_REQ_DONE;
+  r.t_done = now_s();
+  stats.completed += 1;
+  cv_done.notify_all();
+  return true;
+}
+
+void Server::wave(std::unique_lock<std::mutex>& lk) {
+  std::vector<ReqDev> tab;
+  tab.reserve(active.size());
+  int64_t paths = 0, pixels = 0;
+  int maxB = 0;
+  for (uint64_t id : active) {
+    Req& r = reqs[id];
+    ReqDev d{};
+    d.cam = r.rr.cam;
+    d.seed = r.rr.seed;
+    d.npix = r.npix;
+    d.path_off = paths;
+    d.pix_off = pixels;
+    d.prim = (PrimRec*)(base + r.off);
+    d.acc = (float4*)(base + r.off + align256((size_t)r.npix * sizeof(PrimRec)));
+    d.slots = (float4*)((char*)d.acc + align256((size_t)r.npix * sizeof(float4)));
+    d.out_rgb = r.rr.out_rgb;
+    d.spp = r.rr.spp;
+    d.max_bounces = r.rr.max_bounces;
+    d.rr_start = r.rr.rr_start_bounce;
+    d.s0 = r.s_next;
+    d.batch = std::min(r.batch_cap, r.rr.spp - r.s_next);
+    d.version = r.version;
+    d.first = r.s_next == 0;
+    d.last = r.s_next + d.batch >= r.rr.spp;
+    paths += r.npix * d.batch;
+    pixels += r.npix;
+    maxB = std::max(maxB, r.rr.max_bounces);
+    tab.push_back(d);
+  }
+  const int nreq = (int)tab.size();
+  const BvhView v0 = bvh_view(bvh[0]), v1 = bvh_view(bvh[1]);
+  const Consts C = make_consts(params);
+  lk.unlock();
+  cudaError_t e = cudaMemcpyAsync(table, tab.data(), tab.size() * sizeof(ReqDev), cudaMemcpyHostToDevice, stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(counters, 0, kSrvCounterWords * sizeof(uint32_t), stream);
+  static int grid = 0;
+  if (!grid) {
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_srv_bounce, kBlock, 0);
+    grid = std::max(1, per_sm) * device_sms();
+  }
+  if (e == cudaSuccess) {
+    EAGPT_LAUNCH(stream, "k_srv_generate",
+                 k_srv_generate<<<(unsigned)((paths + kBlock - 1) / kBlock), kBlock, 0, stream>>>(table, nreq, paths, C,
+                                                                                                  q[0], counters));
+    for (int k = 1; k <= maxB; ++k)
+      EAGPT_LAUNCH(stream, "k_srv_bounce",
+                   k_srv_bounce<<<grid, kBlock, 0, stream>>>(v0, v1, table, C, k, q[(k - 1) & 1], q[k & 1], counters));
+    EAGPT_LAUNCH(stream, "k_srv_accumulate",
+                 k_srv_accumulate<<<(unsigned)((pixels + kBlock - 1) / kBlock), kBlock, 0, stream>>>(table, nreq,
+                                                                                                    pixels, C));
+    e = cudaGetLastError();
+  }
+  std::vector<uint32_t> cnt(kSrvCounterWords, 0);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(cnt.data(), counters, kSrvCounterWords * sizeof(uint32_t), cudaMemcpyDeviceToHost, stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+  lk.lock();
+  stats.waves += 1;
+  if (e != cudaSuccess) {
+    error = cudaGetErrorString(e);
+    std::vector<uint64_t> ids = active;
+    for (uint64_t id : ids) finish_locked(reqs[id], EAGPT_REQ_FAILED);
+    return;
+  }
+  int64_t segs = pixels;
+  for (int k = 1; k <= maxB; ++k) segs += cnt[2 * k];
+  stats.segments += segs;
+  stats.paths += paths;
+  const double t = now_s();
+  std::vector<uint64_t> ids = active;
+  for (size_t k = 0; k < ids.size(); ++k) {
+    Req& r = reqs[ids[k]];
+    r.s_next += tab[k].batch;
+    if (r.state == EAGPT_REQ_RUNNING && r.s_next >= r.rr.spp) finish_locked(r, EAGPT_REQ_DONE);
+    else if (r.state == EAGPT_REQ_RUNNING && r.deadline > 0 && t > r.deadline) finish_locked(r, EAGPT_REQ_TIMED_OUT);
+  }
+}
+
+void Server::run() {
+  std::unique_lock<std::mutex> lk(mu);
+  for (;;) {
+    // requests cancelled or past their deadline while queued
+    const double t = now_s();
+    for (auto it = pending.begin(); it != pending.end();) {
+      Req& r = reqs[*it];
+      if (r.state == EAGPT_REQ_CANCELLED || (r.deadline > 0 && t > r.deadline)) {
+        if (r.state != EAGPT_REQ_CANCELLED) finish_locked(r, EAGPT_REQ_TIMED_OUT);
+        it = pending.erase(it);
+      } else {
+        ++it;
+      }
+    }
+    // running requests cancelled by the caller
+    std::vector<uint64_t> ids = active;
+    for (uint64_t id : ids)
+      if (reqs[id].state == EAGPT_REQ_CANCELLED) {
+        Req& r = reqs[id];
+        r.state = EAGPT_REQ_RUNNING;
+        finish_locked(r, EAGPT_REQ_CANCELLED);
+      }
+    // admission in submission order
+    while (!pending.empty()) {
+      Req& r = reqs[pending.front()];
+      bool done;
+      if (r.kind == 1) {
+        done = apply_edit_locked(r, lk);
+      } else {
+        done = (int)active.size() < cfg.max_active && admit_locked(r);
+      }
+      if (!done) break;
+      pending.pop_front();
+    }
+    if (active.empty()) {
+      if (stop && pending.empty()) break;
+      if (stop) {
+        // nothing can be admitted any more: fail what is left
+        for (uint64_t id : pending) finish_locked(reqs[id], EAGPT_REQ_FAILED);
+        pending.clear();
+        break;
+      }
+      cv_work.wait_for(lk, std::chrono::milliseconds(5));
+      continue;
+    }
+    const double t0 = now_s();
+    wave(lk);
+    stats.busy_s += now_s() - t0;
+  }
+}
+
+}  // namespace eagpt
+
+using namespace eagpt;
+
+struct eagpt_server_t {
+  Server s;
+};
+
+extern "C" {
+
+size_t eagpt_server_arena_bytes(int64_t n, int64_t queue_paths) {
+  if (n < 0 || queue_paths <= 0) return 0;
+  // second scene version + its BVH, two ray queues, counters, request table,
+  // and as much again as the queues for per-request buffers
+  return scene_bytes(n) + align256(bvh_layout(n).total) + 2 * align256((size_t)queue_paths * sizeof(Ray)) +
+         align256(kSrvCounterWords * 4) + align256(kSrvMaxActive * sizeof(ReqDev)) +
+         (size_t)queue_paths * (sizeof(float4) * 2 + sizeof(PrimRec));
+}
+
+eagpt_status eagpt_server_create(const eagpt_scene_mut* scene, const eagpt_bvh* bvh, const eagpt_params* params,
+                                 const eagpt_server_config* cfg, eagpt_server* out) {
+  if (!scene || !bvh || !params || !cfg || !out) return set_error(EAGPT_ERR_INVALID_ARGUMENT, "null argument");
+  if (cfg->max_active < 1 || cfg->max_active > kSrvMaxActive)
+    return set_error(EAGPT_ERR_INVALID_ARGUMENT, "max_active must be in [1, 64]");
+  if (cfg->queue_paths < 1) return set_error(EAGPT_ERR_INVALID_ARGUMENT, "queue_paths must be positive");
+  if (!cfg->arena || ((uintptr_t)cfg->arena & 255))
+    return set_error(EAGPT_ERR_INVALID_ARGUMENT, "arena must be non-NULL and 256-byte aligned");
+  if (bvh->scene_version != scene->version || bvh->n != scene->n)
+    return set_error(EAGPT_ERR_STALE_BVH, "bvh does not match the scene");
+  const int64_t n = scene->n;
+  const size_t fixed = scene_bytes(n) + align256(bvh_layout(n).total) +
+                       2 * align256((size_t)cfg->queue_paths * sizeof(Ray)) + align256(kSrvCounterWords * 4) +
+                       align256(kSrvMaxActive * sizeof(ReqDev));
+  if (cfg->arena_bytes < fixed + 4096)
+    return set_error(EAGPT_ERR_OUT_OF_MEMORY, "arena too small for the second scene version and the queues");
+  eagpt_server_t* h = new eagpt_server_t();
+  Server& S = h->s;
+  S.params = *params;
+  S.cfg = *cfg;
+  S.base = (char*)cfg->arena;
+  size_t o = 0;
+  auto take = [&](size_t b) {
+    size_t at = o;
+    o += align256(b);
+    return at;
+  };
+  S.scene[0] = *scene;
+  S.bvh[0] = *bvh;
+  // version slot 1 lives in the arena
+  const size_t sc = take(scene_bytes(n));
+  float* f = (float*)(S.base + sc);
+  S.scene[1] = *scene;
+  S.scene[1].pos = f;
+  S.scene[1].quat = f + 3 * n;
+  S.scene[1].scale = f + 7 * n;
+  S.scene[1].opacity = f + 9 * n;
+  S.scene[1].albedo = f + 10 * n;
+  S.scene[1].radiance = f + 13 * n;
+  S.scene[1].emissive = f + 16 * n;
+  S.bvh[1] = *bvh;
+  S.bvh[1].bytes = bvh_layout(n).total;
+  S.bvh[1].storage = S.base + take(S.bvh[1].bytes);
+  S.q[0] = (Ray*)(S.base + take((size_t)cfg->queue_paths * sizeof(Ray)));
+  S.q[1] = (Ray*)(S.base + take((size_t)cfg->queue_paths * sizeof(Ray)));
+  S.counters = (uint32_t*)(S.base + take(kSrvCounterWords * 4));
+  S.table = (ReqDev*)(S.base + take(kSrvMaxActive * sizeof(ReqDev)));
+  S.queue_cap = cfg->queue_paths;
+  S.arena.init(o, cfg->arena_bytes - o);
+  cudaError_t e = cudaStreamCreateWithFlags(&S.stream, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    delete h;
+    return set_error(EAGPT_ERR_CUDA, cudaGetErrorString(e));
+  }
+  int dev = 0;
+  cudaGetDevice(&dev);
+  S.worker = std::thread([&S, dev]() {
+    cudaSetDevice(dev);
+    S.run();
+  });
+  *out = h;
+  return EAGPT_OK;
+}
+
+static eagpt_status submit(eagpt_server h, Req&& r, uint64_t* out_id) {
+  if (!h) return set_error(EAGPT_ERR_INVALID_ARGUMENT, "server is NULL");
+  Server& S = h->s;
+  std::lock_guard<std::mutex> g(S.mu);
+  if (S.stop) return set_error(EAGPT_ERR_INVALID_ARGUMENT, "server is shutting down");
+  r.id = S.next_id++;
+  r.t_submit = now_s();
+  r.state = EAGPT_REQ_QUEUED;
+  if (out_id) *out_id = r.id;
+  S.pending.push_back(r.id);
+  S.reqs[r.id] = r;
+  S.stats.submitted += 1;
+  S.cv_work.notify_one();
+  return EAGPT_OK;
+}
+
+eagpt_status eagpt_server_submit_render(eagpt_server h, const eagpt_render_request* req, uint64_t* out_id) {
+  if (!req || !req->out_rgb) return set_error(EAGPT_ERR_INVALID_ARGUMENT, "request and out_rgb are required");
+  if (req->cam.width <= 0 || req->cam.height <= 0 || req->spp <= 0 || req->max_bounces < 0 ||
+      req->max_bounces > kSrvMaxBounces)
+    return set_error(EAGPT_ERR_INVALID_ARGUMENT, "bad camera size, spp or max_bounces");
+  if (h && (int64_t)req->cam.width * req->cam.height > h->s.queue_cap)
+    return set_error(EAGPT_ERR_OUT_OF_MEMORY, "image has more pixels than the server's queue holds paths");
+  Req r;
+  r.kind = 0;
+  r.rr = *req;
+  r.deadline = req->timeout_s > 0 ? now_s() + req->timeout_s : 0.0;
+  return submit(h, std::move(r), out_id);
+}
+
+eagpt_status eagpt_server_submit_edit(eagpt_server h, const eagpt_edit* edit, uint64_t* out_id) {
+  if (!edit || edit->reserved != 0 || edit->op < EAGPT_EDIT_SET_EMISSION || edit->op > EAGPT_EDIT_RIGID ||
+      edit->count < 0 || (edit->count > 0 && !edit->idx))
+    return set_error(EAGPT_ERR_INVALID_ARGUMENT, "bad edit");
+  Req r;
+  r.kind = 1;
+  r.edit = *edit;
+  return submit(h, std::move(r), out_id);
+}
+
+static void fill_info(const Req& r, eagpt_request_info* out) {
+  out->state = r.state;
+  out->rebuilt = r.rebuilt;
+  out->t_submit = r.t_submit;
+  out->t_admit = r.t_admit;
+  out->t_done = r.t_done;
+  out->scene_version = r.scene_version;
+}
+
+eagpt_status eagpt_server_poll(eagpt_server h, uint64_t id, eagpt_request_info* out) {
+  if (!h || !out) return set_error(EAGPT_ERR_INVALID_ARGUMENT, "null argument");
+  std::lock_guard<std::mutex> g(h->s.mu);
+  auto it = h->s.reqs.find(id);
+  if (it == h->s.reqs.end()) return set_error(EAGPT_ERR_INVALID_ARGUMENT, "unknown request id");
+  fill_info(it->second, out);
+  return EAGPT_OK;
+}
+
+eagpt_status eagpt_server_wait(eagpt_server h, uint64_t id, double timeout_s, eagpt_request_info* out) {
+  if (!h) return set_error(EAGPT_ERR_INVALID_ARGUMENT, "server is NULL");
+  Server& S = h->s;
+  std::unique_lock<std::mutex> lk(S.mu);
+  auto it = S.reqs.find(id);
+  if (it == S.reqs.end()) return set_error(EAGPT_ERR_INVALID_ARGUMENT, "unknown request id");
+  auto finished = [&]() { return it->second.state >= EAGPT_REQ_DONE; };
+  if (timeout_s > 0) {
+    if (!S.cv_done.wait_for(lk, std::chrono::duration<double>(timeout_s), finished)) {
+      if (out) fill_info(it->second, out);
+      return set_error(EAGPT_ERR_TIMEOUT, "request not finished within the timeout");
+    }
+  } else {
+    S.cv_done.wait(lk, finished);
+  }
+  if (out) fill_info(it->second, out);
+  return EAGPT_OK;
+}
+
+eagpt_status eagpt_server_cancel(eagpt_server h, uint64_t id) {
+  if (!h) return set_error(EAGPT_ERR_INVALID_ARGUMENT, "server is NULL");
+  std::lock_guard<std::mutex> g(h->s.mu);
+  auto it = h->s.reqs.find(id);
+  if (it == h->s.reqs.end()) return set_error(EAGPT_ERR_INVALID_ARGUMENT, "unknown request id");
+  Req& r = it->second;
+  if (r.state == EAGPT_REQ_QUEUED) {
+    r.state = EAGPT_REQ_CANCELLED;
+    r.t_done = now_s();
+    h->s.stats.failed += 1;
+    h->s.cv_done.notify_all();
+  } else if (r.state == EAGPT_REQ_RUNNING) {
+    r.state = EAGPT_REQ_CANCELLED;  // released by the loop before the next wave
+  }
+  h->s.cv_work.notify_one();
+  return EAGPT_OK;
+}
+
+eagpt_status eagpt_server_get_stats(eagpt_server h, eagpt_server_stats* out) {
+  if (!h || !out) return set_error(EAGPT_ERR_INVALID_ARGUMENT, "null argument");
+  std::lock_guard<std::mutex> g(h->s.mu);
+  *out = h->s.stats;
+  out->arena_free_bytes = (int64_t)h->s.arena.free_bytes();
+  return EAGPT_OK;
+}
+
+eagpt_status eagpt_server_scene(eagpt_server h, eagpt_scene_mut* scene, eagpt_bvh* bvh) {
+  if (!h) return set_error(EAGPT_ERR_INVALID_ARGUMENT, "server is NULL");
+  std::lock_guard<std::mutex> g(h->s.mu);
+  if (scene) *scene = h->s.scene[h->s.current];
+  if (bvh) *bvh = h->s.bvh[h->s.current];
+  return EAGPT_OK;
+}
+
+eagpt_status eagpt_server_destroy(eagpt_server h) {
+  if (!h) return EAGPT_OK;
+  {
+    std::lock_guard<std::mutex> g(h->s.mu);
+    h->s.stop = true;
+    h->s.cv_work.notify_all();
+  }
+  if (h->s.worker.joinable()) h->s.worker.join();
+  cudaStreamSynchronize(h->s.stream);
+  cudaStreamDestroy(h->s.stream);
+  delete h;
+  return EAGPT_OK;
+}
+
+}  // extern "C"

@@ -14,6 +14,10 @@
 
 #include "common.cuh"
 
+#ifndef EAGPT_WHILE_WHILE
+#define EAGPT_WHILE_WHILE 0
+#endif
+
 namespace eagpt {
 
 __device__ __forceinline__ float dot3_rn(float3 a, float3 b) {
@@ -71,6 +75,101 @@ struct TraceCounters {
   uint32_t nodes, tests, blended, rounds;
 };
 
+// One leaf: test its surfels and keep the K nearest keys above the last
+// blended key in the sorted register buffer.
+template <int K, bool kCount>
+__device__ __forceinline__ void leaf_step(const BvhView& bvh, const Consts& C, float3 O, float3 w, uint32_t leaf,
+                                          float t_last, uint32_t j_last, float (&kt)[K], uint32_t (&kj)[K],
+                                          int& count, TraceCounters& cnt) {
+  const uint32_t start = leaf & kLeafStartMask;
+  const uint32_t cnum = ((leaf >> kLeafCountShift) & 3u) + 1u;
+  for (uint32_t j = start; j < start + cnum; ++j) {
+    const TraceRec* rp = bvh.trace + j;
+    TraceRec R;
+    R.r0 = __ldg(&rp->r0);
+    R.r1 = __ldg(&rp->r1);
+    R.r2 = __ldg(&rp->r2);
+    R.r3 = __ldg(&rp->r3);
+    if (kCount) ++cnt.tests;
+    HitGeom h;
+    if (!intersect(R, O, w, C, h)) continue;
+    if (!key_less(t_last, j_last, h.t, j)) continue;  // already blended (or behind)
+    if (count == K && !key_less(h.t, j, kt[K - 1], kj[K - 1])) continue;
+    float ct = h.t;
+    uint32_t cj = j;
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+      const bool lt = key_less(ct, cj, kt[i], kj[i]);
+      const float tt = kt[i];
+      const uint32_t tj = kj[i];
+      kt[i] = lt ? ct : tt;
+      kj[i] = lt ? cj : tj;
+      ct = lt ? tt : ct;
+      cj = lt ? tj : cj;
+    }
+    count = count < K ? count + 1 : K;
+  }
+}
+
+// One BVH4 node: slab-test the four child boxes against [t_last, tmax],
+// push the hit children but the nearest (farthest first) and return the
+// nearest, or kEmptyChild when none is hit.  Returns false on stack overflow.
+__device__ __forceinline__ bool node_step(const BvhView& bvh, uint32_t node, float3 O, float3 inv, float t_last,
+                                          float tmax, uint32_t* stack, int stride, int& sp, uint32_t& next) {
+  const Node4* np = bvh.nodes + node;
+  const float4 lx = __ldg(&np->lox), ly = __ldg(&np->loy), lz = __ldg(&np->loz);
+  const float4 hx = __ldg(&np->hix), hy = __ldg(&np->hiy), hz = __ldg(&np->hiz);
+  const uint4 ch = __ldg(&np->child);
+  const float inf = __int_as_float(0x7f800000);
+  float e[4];
+  uint32_t c[4] = {ch.x, ch.y, ch.z, ch.w};
+  {
+    const float lxa[4] = {lx.x, lx.y, lx.z, lx.w}, lya[4] = {ly.x, ly.y, ly.z, ly.w};
+    const float lza[4] = {lz.x, lz.y, lz.z, lz.w}, hxa[4] = {hx.x, hx.y, hx.z, hx.w};
+    const float hya[4] = {hy.x, hy.y, hy.z, hy.w}, hza[4] = {hz.x, hz.y, hz.z, hz.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      float te;
+      const bool h = box_hit(make_float3(lxa[k], lya[k], lza[k]), make_float3(hxa[k], hya[k], hza[k]), O, inv,
+                             t_last, tmax, te);
+      e[k] = (h && c[k] != kEmptyChild) ? te : inf;
+    }
+  }
+  // front-to-back order: sorting network on (entry, link)
+#define EAGPT_CSWAP(i, j)                         \
+  if (e[j] < e[i]) {                              \
+    const float tf = e[i];                        \
+    e[i] = e[j];                                  \
+    e[j] = tf;                                    \
+    const uint32_t tc = c[i];                     \
+    c[i] = c[j];                                  \
+    c[j] = tc;                                    \
+  }
+  EAGPT_CSWAP(0, 1)
+  EAGPT_CSWAP(2, 3)
+  EAGPT_CSWAP(0, 2)
+  EAGPT_CSWAP(1, 3)
+  EAGPT_CSWAP(1, 2)
+#undef EAGPT_CSWAP
+  next = kEmptyChild;
+  if (e[0] != inf) {
+    const int m = (e[1] != inf) + (e[2] != inf) + (e[3] != inf);
+    if (sp + m > kStackSize) {
+      raise_error(kErrStackOverflow);
+      return false;
+    }
+    if (e[3] != inf) stack[(sp++) * stride] = c[3];
+    if (e[2] != inf) stack[(sp++) * stride] = c[2];
+    if (e[1] != inf) stack[(sp++) * stride] = c[1];
+    next = c[0];
+  }
+  return true;
+}
+
+__device__ __forceinline__ uint32_t pop(const uint32_t* stack, int stride, int& sp) {
+  return sp > 0 ? stack[(--sp) * stride] : kEmptyChild;
+}
+
 // Walks the BVH for hits with key (t, j) > (t_last, j_last), up to K of
 // them, nearest first.  `stack` points at this thread's column of a
 // shared-memory stack with `stride` words between entries.
@@ -85,92 +184,49 @@ __device__ __forceinline__ int collect_round(const BvhView& bvh, const Consts& C
   }
   int count = 0;
   int sp = 0;
-  uint32_t cur = bvh.root;
+#if EAGPT_WHILE_WHILE
+  // Inner nodes are walked until every lane of the warp holds a leaf (or is
+  // done), then the leaves are processed together (Aila and Laine,
+  // "Understanding the efficiency of ray traversal on GPUs", HPG 2009).
+  uint32_t node = bvh.root, leaf = kEmptyChild;
   for (;;) {
-    if (cur & kLeafBit) {
-      const uint32_t start = cur & kLeafStartMask;
-      const uint32_t cnum = ((cur >> kLeafCountShift) & 3u) + 1u;
-      for (uint32_t j = start; j < start + cnum; ++j) {
-        const TraceRec* rp = bvh.trace + j;
-        TraceRec R;
-        R.r0 = __ldg(&rp->r0);
-        R.r1 = __ldg(&rp->r1);
-        R.r2 = __ldg(&rp->r2);
-        R.r3 = __ldg(&rp->r3);
-        if (kCount) ++cnt.tests;
-        HitGeom h;
-        if (!intersect(R, O, w, C, h)) continue;
-        if (!key_less(t_last, j_last, h.t, j)) continue;  // already blended (or behind)
-        if (count == K && !key_less(h.t, j, kt[K - 1], kj[K - 1])) continue;
-        float ct = h.t;
-        uint32_t cj = j;
-#pragma unroll
-        for (int i = 0; i < K; ++i) {
-          const bool lt = key_less(ct, cj, kt[i], kj[i]);
-          const float tt = kt[i];
-          const uint32_t tj = kj[i];
-          kt[i] = lt ? ct : tt;
-          kj[i] = lt ? cj : tj;
-          ct = lt ? tt : ct;
-          cj = lt ? tj : cj;
-        }
-        count = count < K ? count + 1 : K;
-      }
-    } else if (cur != kEmptyChild) {
-      const Node4* np = bvh.nodes + cur;
-      const float4 lx = __ldg(&np->lox), ly = __ldg(&np->loy), lz = __ldg(&np->loz);
-      const float4 hx = __ldg(&np->hix), hy = __ldg(&np->hiy), hz = __ldg(&np->hiz);
-      const uint4 ch = __ldg(&np->child);
+    while (node != kEmptyChild && !(node & kLeafBit)) {
       if (kCount) ++cnt.nodes;
-      const float inf = __int_as_float(0x7f800000);
-      const float tmax = count == K ? kt[K - 1] : inf;
-      // entry distance of each child box, +inf when missed or empty
-      float e[4];
-      uint32_t c[4] = {ch.x, ch.y, ch.z, ch.w};
-      {
-        const float lxa[4] = {lx.x, lx.y, lx.z, lx.w}, lya[4] = {ly.x, ly.y, ly.z, ly.w};
-        const float lza[4] = {lz.x, lz.y, lz.z, lz.w}, hxa[4] = {hx.x, hx.y, hx.z, hx.w};
-        const float hya[4] = {hy.x, hy.y, hy.z, hy.w}, hza[4] = {hz.x, hz.y, hz.z, hz.w};
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          float te;
-          const bool h = box_hit(make_float3(lxa[k], lya[k], lza[k]), make_float3(hxa[k], hya[k], hza[k]), O, inv,
-                                 t_last, tmax, te);
-          e[k] = (h && c[k] != kEmptyChild) ? te : inf;
-        }
+      const float tmax = count == K ? kt[K - 1] : __int_as_float(0x7f800000);
+      uint32_t next;
+      if (!node_step(bvh, node, O, inv, t_last, tmax, stack, stride, sp, next)) return count;
+      node = next != kEmptyChild ? next : pop(stack, stride, sp);
+      if (node != kEmptyChild && (node & kLeafBit) && leaf == kEmptyChild) {
+        leaf = node;
+        node = pop(stack, stride, sp);
       }
-      // front-to-back order: sorting network on (entry, link)
-#define EAGPT_CSWAP(i, j)                         \
-  if (e[j] < e[i]) {                              \
-    const float tf = e[i];                        \
-    e[i] = e[j];                                  \
-    e[j] = tf;                                    \
-    const uint32_t tc = c[i];                     \
-    c[i] = c[j];                                  \
-    c[j] = tc;                                    \
-  }
-      EAGPT_CSWAP(0, 1)
-      EAGPT_CSWAP(2, 3)
-      EAGPT_CSWAP(0, 2)
-      EAGPT_CSWAP(1, 3)
-      EAGPT_CSWAP(1, 2)
-#undef EAGPT_CSWAP
-      if (e[0] != inf) {
-        const int m = (e[1] != inf) + (e[2] != inf) + (e[3] != inf);
-        if (sp + m > kStackSize) {
-          raise_error(kErrStackOverflow);
-          return count;
-        }
-        if (e[3] != inf) stack[(sp++) * stride] = c[3];
-        if (e[2] != inf) stack[(sp++) * stride] = c[2];
-        if (e[1] != inf) stack[(sp++) * stride] = c[1];
-        cur = c[0];
-        continue;
+      if (!__any_sync(__activemask(), leaf == kEmptyChild)) break;
+    }
+    while (leaf != kEmptyChild) {
+      leaf_step<K, kCount>(bvh, C, O, w, leaf, t_last, j_last, kt, kj, count, cnt);
+      leaf = kEmptyChild;
+      if (node != kEmptyChild && (node & kLeafBit)) {
+        leaf = node;
+        node = pop(stack, stride, sp);
       }
     }
-    if (sp == 0) break;
-    cur = stack[(--sp) * stride];
+    if (node == kEmptyChild) break;
   }
+#else
+  uint32_t cur = bvh.root;
+  while (cur != kEmptyChild) {
+    if (cur & kLeafBit) {
+      leaf_step<K, kCount>(bvh, C, O, w, cur, t_last, j_last, kt, kj, count, cnt);
+      cur = pop(stack, stride, sp);
+    } else {
+      if (kCount) ++cnt.nodes;
+      const float tmax = count == K ? kt[K - 1] : __int_as_float(0x7f800000);
+      uint32_t next;
+      if (!node_step(bvh, cur, O, inv, t_last, tmax, stack, stride, sp, next)) return count;
+      cur = next != kEmptyChild ? next : pop(stack, stride, sp);
+    }
+  }
+#endif
   return count;
 }
 

@@ -469,3 +469,54 @@ def random_small_scene(n: int, seed: int, spread=0.3, emit_frac=0.3) -> SurfelSc
     emissive[idx] = 1.0
     radiance[idx] = rng.uniform(1.0, 10.0, (k, 3))
     return _pack(pos, quat, scale, opacity, albedo, radiance, emissive)
+
+
+# ----------------------------------------------------------------------------
+# serving request stream (serving room, 10 x 8 x 3 m)
+# ----------------------------------------------------------------------------
+
+SERVING_RESOLUTIONS = [(256, 256), (512, 512), (1280, 720), (1920, 1080)]
+SERVING_SPP = [16, 64, 256]
+
+
+def serving_requests(scene: SurfelScene, n: int, seed: int = 13, edit_frac: float = 0.1,
+                     lo=(-5.0, -4.0, -1.5), hi=(5.0, 4.0, 1.5), spp_choices=None, res_choices=None):
+    """Seeded request list: renders with a random horizontal camera pose inside
+    the room, resolution and spp uniform over the serving sets, bounces
+    uniform in 1..5; a fraction ``edit_frac`` are edits, uniform over:
+    toggle emission on 5 % of the surfels (new emitters get radiance
+    U[1, 10]); albedo scale U[0.5, 1.5] for the surfels within 0.5 m of a
+    random centre; move the surfels within 0.25 m of a random surfel centre
+    (about a thousand on a wall of this room) by a random vector of length
+    <= 0.2 m.  Returns a list of dicts (no rendering arithmetic here)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    lo = np.asarray(lo)
+    hi = np.asarray(hi)
+    spp_choices = spp_choices or SERVING_SPP
+    res_choices = res_choices or SERVING_RESOLUTIONS
+    out = []
+    for k in range(n):
+        if rng.random() < edit_frac:
+            kind = int(rng.integers(0, 3))
+            if kind == 0:
+                idx = np.sort(rng.choice(scene.n, max(1, scene.n // 20), replace=False)).astype(np.int32)
+                rad = rng.uniform(1.0, 10.0, (len(idx), 3)).astype(np.float32)
+                out.append({"type": "edit", "op": "toggle_emission", "idx": idx, "per_index": rad})
+            elif kind == 1:
+                c = rng.uniform(lo * 0.9, hi * 0.9)
+                out.append({"type": "edit", "op": "scale_albedo", "sphere": list(c) + [0.5],
+                            "value": [float(rng.uniform(0.5, 1.5))] * 3})
+            else:
+                c = scene.pos[int(rng.integers(0, scene.n))].astype(np.float64)
+                v = rng.normal(size=3)
+                v *= rng.uniform(0.0, 0.2) / np.linalg.norm(v)
+                out.append({"type": "edit", "op": "translate", "sphere": list(c) + [0.25], "value": list(v)})
+        else:
+            w, h = res_choices[int(rng.integers(0, len(res_choices)))]
+            centre = rng.uniform(lo * 0.8, hi * 0.8)
+            yaw = rng.uniform(0, 2 * np.pi)
+            fwd = (np.cos(yaw), np.sin(yaw), 0.0)
+            out.append({"type": "render", "camera": look_at_camera(w, h, 90.0, centre, fwd, (0.0, 0.0, 1.0)),
+                        "spp": int(spp_choices[int(rng.integers(0, len(spp_choices)))]),
+                        "max_bounces": int(rng.integers(1, 6)), "seed": int(rng.integers(0, 2 ** 31))})
+    return out

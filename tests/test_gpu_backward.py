@@ -30,7 +30,11 @@ def _weights(scene, cam, pixels, spp, seed, wseed):
     w = np.zeros((npix, 3))
     w[pixels] = rng.uniform(-1, 1, (len(pixels), 3))
     ref = O.render(scene, cam, np.asarray(pixels, np.int32), "single", spp, seed=seed)
-    bad = (ref["sample_flags"] != 0).any(axis=1)
+    # discrete decisions near their FP32 boundary change a sample's hit set;
+    # the value-conditioning flag (2.5e-5 of the sample) is far below the
+    # 1e-3 gradient tolerance and is not used here
+    decision = np.uint32(~O.FLAGS["cond"] & 0xFFFFFFFF)
+    bad = ((ref["sample_flags"] & decision) != 0).any(axis=1)
     w[np.asarray(pixels)[bad]] = 0.0
     return w, int(bad.sum())
 
