@@ -13,7 +13,7 @@ namespace eagpt {
 // Sizes and encodings
 // ---------------------------------------------------------------------------
 #ifndef EAGPT_LEAF_MAX
-#define EAGPT_LEAF_MAX 4
+#define EAGPT_LEAF_MAX 1
 #endif
 constexpr int kLeafMax = EAGPT_LEAF_MAX;  // surfels per BVH leaf (1..4)
 constexpr int kStackSize = 64;       // traversal stack entries per ray
