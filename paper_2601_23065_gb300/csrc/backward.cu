@@ -197,7 +197,7 @@ __global__ void __launch_bounds__(kBlock) k_bwd_secondary(BvhView bvh, Consts C,
     const float3 X = O + p.a.w * w;
     const float3 O2 = X + C.bounce_offset * Nn;
     const float3 w2 = cosine_direction(Nn, u.x, u.y);
-    TraceCounters cnt{0, 0, 0, 0};
+    TraceCounters cnt{0, 0, 0, 0, 0};
     RawVisitor v1(bvh.shade, C, w2, 0);
     trace_segment<kKb, false>(bvh, C, O2, w2, 0.f, s_stack + threadIdx.x, kBlock, v1, cnt);
     const float invS = 1.f / (float)spp;
@@ -262,7 +262,7 @@ __global__ void __launch_bounds__(kBlock) k_bwd_primary(BvhView bvh, Consts C, e
   if (!(p.c.w >= 0.f)) return;  // miss
   float3 O, w;
   camera_ray(cam, (uint32_t)i, O, w);
-  TraceCounters cnt{0, 0, 0, 0};
+  TraceCounters cnt{0, 0, 0, 0, 0};
   RawVisitor v1(bvh.shade, C, w, 0);
   trace_segment<kKb, false>(bvh, C, O, w, 0.f, s_stack + threadIdx.x, kBlock, v1, cnt);
   const Blend& V = v1.blend.b;

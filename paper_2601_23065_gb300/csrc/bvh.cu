@@ -17,17 +17,6 @@ namespace eagpt {
 
 EAGPT_DEFINE_ERROR_READER(take_errors_bvh)
 
-// --------------------------------------------------------------------------
-// float <-> order-preserving uint32
-// --------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t f2ord(float f) {
-  const uint32_t u = __float_as_uint(f);
-  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
-}
-__device__ __forceinline__ float ord2f(uint32_t u) {
-  return __uint_as_float((u & 0x80000000u) ? (u & 0x7FFFFFFFu) : ~u);
-}
-
 __global__ void k_init_header(BvhHeader* hdr) {
   if (threadIdx.x < 3) {
     hdr->bounds_bits[threadIdx.x] = 0xFFFFFFFFu;     // min
@@ -63,15 +52,6 @@ __global__ void k_bounds(const float* __restrict__ pos, int64_t n, BvhHeader* hd
   }
 }
 
-__device__ __forceinline__ uint32_t expand10(uint32_t v) {
-  v &= 0x3FFu;
-  v = (v | (v << 16)) & 0x030000FFu;
-  v = (v | (v << 8)) & 0x0300F00Fu;
-  v = (v | (v << 4)) & 0x030C30C3u;
-  v = (v | (v << 2)) & 0x09249249u;
-  return v;
-}
-
 __global__ void k_morton(const float* __restrict__ pos, int64_t n, const BvhHeader* hdr, uint32_t* keys,
                          uint32_t* vals) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -83,7 +63,7 @@ __global__ void k_morton(const float* __restrict__ pos, int64_t n, const BvhHead
   const uint32_t x = (uint32_t)fminf(fmaxf((pos[3 * i + 0] - lo0) * s, 0.f), 1023.f);
   const uint32_t y = (uint32_t)fminf(fmaxf((pos[3 * i + 1] - lo1) * s, 0.f), 1023.f);
   const uint32_t z = (uint32_t)fminf(fmaxf((pos[3 * i + 2] - lo2) * s, 0.f), 1023.f);
-  keys[i] = (expand10(x) << 2) | (expand10(y) << 1) | expand10(z);
+  keys[i] = (expand_bits10(x) << 2) | (expand_bits10(y) << 1) | expand_bits10(z);
   vals[i] = (uint32_t)i;
 }
 
@@ -276,6 +256,31 @@ cudaError_t launch_records_update(const eagpt_scene& sc, const Consts& C, char* 
                                                   (float4*)(base + L.prim_lo), (float4*)(base + L.prim_hi),
                                                   (uint32_t*)(base + L.inv_idx), L.n, 0));
   return cudaGetLastError();
+}
+
+}  // namespace eagpt
+
+namespace eagpt {
+
+// Stable LSD radix sort of (key, value) pairs, 8 bits per pass, 4 passes
+// (32-bit keys); the sorted pairs end in k0 / v0.  hist holds 256 words per
+// tile of kSortTileItems keys.
+void launch_sort_pairs(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, uint32_t* hist, int64_t n,
+                       cudaStream_t st) {
+  const int64_t tiles = (n + kSortTileItems - 1) / kSortTileItems;
+  if (n <= 0) return;
+  for (int shift = 0; shift < 32; shift += 8) {
+    EAGPT_LAUNCH(st, "k_sort_hist", k_sort_hist<<<(unsigned)tiles, kSortThreads, 0, st>>>(k0, n, shift, hist, tiles));
+    EAGPT_LAUNCH(st, "k_sort_scan", k_sort_scan<<<1, 1024, 0, st>>>(hist, 256 * tiles));
+    EAGPT_LAUNCH(st, "k_sort_scatter",
+                 k_sort_scatter<<<(unsigned)tiles, kSortThreads, 0, st>>>(k0, v0, k1, v1, n, shift, hist, tiles));
+    uint32_t* t = k0;
+    k0 = k1;
+    k1 = t;
+    t = v0;
+    v0 = v1;
+    v1 = t;
+  }
 }
 
 }  // namespace eagpt

@@ -96,6 +96,7 @@ BvhView make_view(const eagpt_bvh& b) {
     v.shade = (const ShadeRec*)(base + L.shade);
     v.nodes = (const Node4*)(base + L.nodes);
     v.root = 0;  // node 0: Karras root, or the single node of a small scene
+    v.bounds_bits = (const uint32_t*)(base + L.header);
   }
   return v;
 }

@@ -16,7 +16,14 @@ namespace eagpt {
 #define EAGPT_LEAF_MAX 1
 #endif
 constexpr int kLeafMax = EAGPT_LEAF_MAX;  // surfels per BVH leaf (1..4)
-constexpr int kStackSize = 64;       // traversal stack entries per ray
+#ifndef EAGPT_STACK
+#define EAGPT_STACK 48
+#endif
+constexpr int kStackSize = EAGPT_STACK;  // traversal stack entries per ray
+#ifndef EAGPT_MIN_BLOCKS
+#define EAGPT_MIN_BLOCKS 6
+#endif
+constexpr int kMinBlocks = EAGPT_MIN_BLOCKS;  // resident trace blocks per SM the compiler must allow
 constexpr int kBlock = 128;          // threads per block of the trace kernels
 constexpr uint32_t kLeafBit = 0x80000000u;
 constexpr int kLeafCountShift = 29;  // leaf: bit31 | (count-1) << 29 | start
@@ -131,6 +138,7 @@ struct BvhView {
   const Node4* nodes;
   uint32_t root;  // node index, or an encoded leaf when n <= kLeafMax
   int64_t n;
+  const uint32_t* bounds_bits;  // scene centroid bounds (BvhHeader), ordered-int encoded
 };
 
 // Method constants as passed to kernels.
@@ -167,6 +175,24 @@ static __device__ uint32_t g_error_word = 0;
   }
 
 __device__ __forceinline__ void raise_error(uint32_t bits) { atomicOr(&g_error_word, bits); }
+
+// float <-> order-preserving uint32 (bounds kept as atomically updatable ints)
+__device__ __forceinline__ uint32_t f2ord(float f) {
+  const uint32_t u = __float_as_uint(f);
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float ord2f(uint32_t u) {
+  return __uint_as_float((u & 0x80000000u) ? (u & 0x7FFFFFFFu) : ~u);
+}
+
+__device__ __forceinline__ uint32_t expand_bits10(uint32_t v) {
+  v &= 0x3FFu;
+  v = (v | (v << 16)) & 0x030000FFu;
+  v = (v | (v << 8)) & 0x0300F00Fu;
+  v = (v | (v << 4)) & 0x030C30C3u;
+  v = (v | (v << 2)) & 0x09249249u;
+  return v;
+}
 
 // ---------------------------------------------------------------------------
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): 10 rounds with

@@ -12,6 +12,8 @@ namespace eagpt {
 cudaError_t launch_build(const eagpt_scene& sc, const Consts& C, char* base, const BvhLayout& L, cudaStream_t st,
                          int* launches);
 int launch_refit(char* base, const BvhLayout& L, cudaStream_t st);
+void launch_sort_pairs(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, uint32_t* hist, int64_t n,
+                       cudaStream_t st);
 // bvh_tree.cu
 cudaError_t launch_tree(const uint32_t* sorted_keys, char* base, const BvhLayout& L, cudaStream_t st);
 cudaError_t launch_records_update(const eagpt_scene& sc, const Consts& C, char* base, const BvhLayout& L,
@@ -34,7 +36,7 @@ struct RenderArgs {
 };
 
 struct RenderLayout {
-  size_t prim, acc, slots, q0, q1, counters, total;
+  size_t prim, acc, slots, q0, q1, counters, sk0, sk1, sv0, sv1, shist, total;
   int64_t npix, batch_paths;
   int batch_spp;
 };

@@ -29,6 +29,35 @@ constexpr int kK = EAGPT_KBUF;  // k-buffer size (hits collected per traversal r
 
 EAGPT_DEFINE_ERROR_READER(take_errors_render)
 
+// Reorder each bounce's ray queue by (direction octant, origin Morton code)
+// so that the rays of a warp walk similar parts of the BVH.
+#ifndef EAGPT_SORT_RAYS
+#define EAGPT_SORT_RAYS 0
+#endif
+constexpr bool kSortRays = EAGPT_SORT_RAYS != 0;
+
+__global__ void k_ray_keys(const Ray* __restrict__ q, const uint32_t* __restrict__ count_ptr, int64_t cap,
+                           const uint32_t* __restrict__ bounds_bits, uint32_t* keys, uint32_t* vals) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= cap) return;
+  const uint32_t count = *count_ptr;
+  uint32_t key = 0xFFFFFFFFu;
+  if (i < count) {
+    const float4 a = q[i].a, b = q[i].b;
+    const float lo0 = ord2f(bounds_bits[0]), lo1 = ord2f(bounds_bits[1]), lo2 = ord2f(bounds_bits[2]);
+    const float hi0 = ord2f(bounds_bits[3]), hi1 = ord2f(bounds_bits[4]), hi2 = ord2f(bounds_bits[5]);
+    const float ext = fmaxf(fmaxf(hi0 - lo0, hi1 - lo1), fmaxf(hi2 - lo2, 1e-20f));
+    const float sc = 511.0f / ext;
+    const uint32_t x = (uint32_t)fminf(fmaxf((a.x - lo0) * sc, 0.f), 511.f);
+    const uint32_t y = (uint32_t)fminf(fmaxf((a.y - lo1) * sc, 0.f), 511.f);
+    const uint32_t z = (uint32_t)fminf(fmaxf((a.z - lo2) * sc, 0.f), 511.f);
+    const uint32_t oct = (b.x < 0.f ? 4u : 0u) | (b.y < 0.f ? 2u : 0u) | (b.z < 0.f ? 1u : 0u);
+    key = (oct << 27) | (expand_bits10(x) << 2) | (expand_bits10(y) << 1) | expand_bits10(z);
+  }
+  keys[i] = key;
+  vals[i] = (uint32_t)i;
+}
+
 // counters block: per bounce k, [2k] = rays queued for bounce k, [2k+1] = fetch
 constexpr int kMaxBounces = 60;
 constexpr int kCounterWords = 2 * (kMaxBounces + 2) + 8;
@@ -50,6 +79,13 @@ RenderLayout render_layout(int64_t npix, int spp, int batch_spp) {
   L.q0 = take((size_t)L.batch_paths * sizeof(Ray));
   L.q1 = take((size_t)L.batch_paths * sizeof(Ray));
   L.counters = take(kCounterWords * sizeof(uint32_t));
+  if (kSortRays) {
+    L.sk0 = take((size_t)L.batch_paths * 4);
+    L.sk1 = take((size_t)L.batch_paths * 4);
+    L.sv0 = take((size_t)L.batch_paths * 4);
+    L.sv1 = take((size_t)L.batch_paths * 4);
+    L.shist = take((size_t)256 * ((L.batch_paths + kSortTileItems - 1) / kSortTileItems) * 4);
+  }
   L.total = o;
   (void)spp;
   return L;
@@ -90,11 +126,11 @@ __device__ __forceinline__ void add_stats(int64_t* stats, int slot, uint32_t v) 
 }
 
 template <bool kCount>
-__global__ void __launch_bounds__(kBlock) k_primary(BvhView bvh, Consts C, eagpt_camera cam, int mode, int64_t npix,
+__global__ void __launch_bounds__(kBlock, kMinBlocks) k_primary(BvhView bvh, Consts C, eagpt_camera cam, int mode, int64_t npix,
                                                     PrimRec* prim, float* aux, int64_t* stats) {
   __shared__ uint32_t s_stack[kStackSize * kBlock];
   const int64_t i = blockIdx.x * (int64_t)kBlock + threadIdx.x;
-  TraceCounters cnt{0, 0, 0, 0};
+  TraceCounters cnt{0, 0, 0, 0, 0};
   if (i < npix) {
     float3 O, w;
     camera_ray(cam, (uint32_t)i, O, w);
@@ -149,15 +185,15 @@ __global__ void __launch_bounds__(kBlock) k_generate(const PrimRec* __restrict__
 
 // One bounce k of every queued path (Eq. 6 for kind 0, Eq. 8 for kind 1).
 template <bool kCount>
-__global__ void __launch_bounds__(kBlock) k_bounce(BvhView bvh, Consts C, int kind, int k, int max_bounces,
+__global__ void __launch_bounds__(kBlock, kMinBlocks) k_bounce(BvhView bvh, Consts C, int kind, int k, int max_bounces,
                                                    int rr_start, uint64_t seed, int64_t npix, int s0,
                                                    const Ray* __restrict__ q_in, Ray* q_out, uint32_t* counters,
-                                                   float4* slots, int64_t* stats) {
+                                                   float4* slots, int64_t* stats, const uint32_t* __restrict__ perm) {
   __shared__ uint32_t s_stack[kStackSize * kBlock];
   const int lane = threadIdx.x & 31;
   const uint32_t count = counters[2 * k];
   const int mode = kind == 0 ? 0 : 1;
-  TraceCounters cnt{0, 0, 0, 0};
+  TraceCounters cnt{0, 0, 0, 0, 0};
   uint32_t traced = 0;
   for (;;) {
     uint32_t base = 0;
@@ -169,7 +205,7 @@ __global__ void __launch_bounds__(kBlock) k_bounce(BvhView bvh, Consts C, int ki
     Ray nr;
     if (idx < count) {
       ++traced;
-      const Ray r = q_in[idx];
+      const Ray r = q_in[perm ? perm[idx] : idx];
       const float3 O = f3(r.a), w = f3(r.b);
       const uint32_t pixel = __float_as_uint(r.a.w), sample = __float_as_uint(r.b.w);
       BlendVisitor vis(bvh.shade, C, w, mode);
@@ -189,6 +225,9 @@ __global__ void __launch_bounds__(kBlock) k_bounce(BvhView bvh, Consts C, int ki
     add_stats(stats, 4, cnt.nodes);
     add_stats(stats, 5, cnt.tests);
     add_stats(stats, 6, cnt.rounds);
+    uint32_t m = cnt.max_stack;
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0 && m) atomicMax((unsigned long long*)(stats + 7), (unsigned long long)m);
   }
 }
 
@@ -269,7 +308,7 @@ __global__ void __launch_bounds__(kBlock) k_trace_rays(BvhView bvh, Consts C, in
   if (hits)
     for (int k = 0; k < max_hits; ++k) hits[k] = -1;
   RecordVisitor vis(bvh.shade, C, w, mode, hits, max_hits);
-  TraceCounters cnt{0, 0, 0, 0};
+  TraceCounters cnt{0, 0, 0, 0, 0};
   trace_segment<kK, false>(bvh, C, O, w, 0.f, s_stack + threadIdx.x, kBlock, vis, cnt);
   const SegRec s = finish(vis.blend.b);
   write_aux(out_rec, i, s);
@@ -329,9 +368,19 @@ static cudaError_t render_impl(const RenderArgs& a, cudaStream_t st, int* launch
                                                               s0, nb, q[0], counters, slots, a.out_stats));
     ++nl;
     for (int k = 1; k <= B; ++k) {
+      const uint32_t* perm = nullptr;
+      if (kSortRays) {
+        uint32_t *k0 = (uint32_t*)(ws + L.sk0), *k1 = (uint32_t*)(ws + L.sk1);
+        uint32_t *v0 = (uint32_t*)(ws + L.sv0), *v1 = (uint32_t*)(ws + L.sv1);
+        const int64_t cap = npix * nb;
+        EAGPT_LAUNCH(st, "k_ray_keys", k_ray_keys<<<nblocks(cap), kBlock, 0, st>>>(q[(k - 1) & 1], &counters[2 * k], cap,
+                                                                                   a.bvh.bounds_bits, k0, v0));
+        launch_sort_pairs(k0, v0, k1, v1, (uint32_t*)(ws + L.shist), cap, st);
+        perm = v0;
+      }
       EAGPT_LAUNCH(st, "k_bounce", k_bounce<kCount><<<bounce_grid[kCount], kBlock, 0, st>>>(a.bvh, a.C, a.kind, k, B, a.rr_start, a.seed, npix,
                                                                 s0, q[(k - 1) & 1], q[k & 1], counters, slots,
-                                                                a.out_stats));
+                                                                a.out_stats, perm));
       ++nl;
     }
     EAGPT_LAUNCH(st, "k_accumulate", k_accumulate<<<nblocks(npix), kBlock, 0, st>>>(prim, a.C, npix, s0, nb, a.spp, s0 == 0, s0 + nb >= a.spp, slots,

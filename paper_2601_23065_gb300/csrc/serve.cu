@@ -97,7 +97,7 @@ __global__ void __launch_bounds__(kBlock) k_srv_bounce(BvhView v0, BvhView v1, c
   __shared__ uint32_t s_stack[kStackSize * kBlock];
   const int lane = threadIdx.x & 31;
   const uint32_t count = counters[2 * k];
-  TraceCounters cnt{0, 0, 0, 0};
+  TraceCounters cnt{0, 0, 0, 0, 0};
   for (;;) {
     uint32_t base = 0;
     if (lane == 0) base = atomicAdd(&counters[2 * k + 1], 32u);

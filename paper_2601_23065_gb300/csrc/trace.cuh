@@ -17,6 +17,9 @@
 #ifndef EAGPT_WHILE_WHILE
 #define EAGPT_WHILE_WHILE 0
 #endif
+#ifndef EAGPT_INLINE_LEAVES
+#define EAGPT_INLINE_LEAVES 0
+#endif
 
 namespace eagpt {
 
@@ -72,7 +75,7 @@ __device__ __forceinline__ bool key_less(float ta, uint32_t ia, float tb, uint32
 
 // Counters of the work one segment did (enabled by the kCount template flag).
 struct TraceCounters {
-  uint32_t nodes, tests, blended, rounds;
+  uint32_t nodes, tests, blended, rounds, max_stack;
 };
 
 // One leaf: test its surfels and keep the K nearest keys above the last
@@ -166,6 +169,64 @@ __device__ __forceinline__ bool node_step(const BvhView& bvh, uint32_t node, flo
   return true;
 }
 
+// Like node_step, but the hit leaf children are returned in `leaves` (nl of
+// them) instead of being pushed; only inner children are ordered and pushed.
+__device__ __forceinline__ bool node_step_split(const BvhView& bvh, uint32_t node, float3 O, float3 inv,
+                                                float t_last, float tmax, uint32_t* stack, int stride, int& sp,
+                                                uint32_t& next, uint32_t (&leaves)[4], int& nl) {
+  const Node4* np = bvh.nodes + node;
+  const float4 lx = __ldg(&np->lox), ly = __ldg(&np->loy), lz = __ldg(&np->loz);
+  const float4 hx = __ldg(&np->hix), hy = __ldg(&np->hiy), hz = __ldg(&np->hiz);
+  const uint4 ch = __ldg(&np->child);
+  const float inf = __int_as_float(0x7f800000);
+  float e[4];
+  uint32_t c[4] = {ch.x, ch.y, ch.z, ch.w};
+  {
+    const float lxa[4] = {lx.x, lx.y, lx.z, lx.w}, lya[4] = {ly.x, ly.y, ly.z, ly.w};
+    const float lza[4] = {lz.x, lz.y, lz.z, lz.w}, hxa[4] = {hx.x, hx.y, hx.z, hx.w};
+    const float hya[4] = {hy.x, hy.y, hy.z, hy.w}, hza[4] = {hz.x, hz.y, hz.z, hz.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      float te;
+      const bool h = box_hit(make_float3(lxa[k], lya[k], lza[k]), make_float3(hxa[k], hya[k], hza[k]), O, inv,
+                             t_last, tmax, te);
+      const bool ok = h && c[k] != kEmptyChild;
+      const bool leaf = ok && (c[k] & kLeafBit);
+      leaves[k] = leaf ? c[k] : kEmptyChild;
+      nl += leaf;
+      e[k] = (ok && !leaf) ? te : inf;
+    }
+  }
+#define EAGPT_CSWAP(i, j)                         \
+  if (e[j] < e[i]) {                              \
+    const float tf = e[i];                        \
+    e[i] = e[j];                                  \
+    e[j] = tf;                                    \
+    const uint32_t tc = c[i];                     \
+    c[i] = c[j];                                  \
+    c[j] = tc;                                    \
+  }
+  EAGPT_CSWAP(0, 1)
+  EAGPT_CSWAP(2, 3)
+  EAGPT_CSWAP(0, 2)
+  EAGPT_CSWAP(1, 3)
+  EAGPT_CSWAP(1, 2)
+#undef EAGPT_CSWAP
+  next = kEmptyChild;
+  if (e[0] != inf) {
+    const int m = (e[1] != inf) + (e[2] != inf) + (e[3] != inf);
+    if (sp + m > kStackSize) {
+      raise_error(kErrStackOverflow);
+      return false;
+    }
+    if (e[3] != inf) stack[(sp++) * stride] = c[3];
+    if (e[2] != inf) stack[(sp++) * stride] = c[2];
+    if (e[1] != inf) stack[(sp++) * stride] = c[1];
+    next = c[0];
+  }
+  return true;
+}
+
 __device__ __forceinline__ uint32_t pop(const uint32_t* stack, int stride, int& sp) {
   return sp > 0 ? stack[(--sp) * stride] : kEmptyChild;
 }
@@ -212,6 +273,23 @@ __device__ __forceinline__ int collect_round(const BvhView& bvh, const Consts& C
     }
     if (node == kEmptyChild) break;
   }
+#elif EAGPT_INLINE_LEAVES
+  // Leaf children are tested during their parent's visit; only inner nodes
+  // go through the stack.
+  uint32_t cur = bvh.root;
+  while (cur != kEmptyChild) {
+    if (kCount) ++cnt.nodes;
+    const float tmax = count == K ? kt[K - 1] : __int_as_float(0x7f800000);
+    uint32_t next, leaves[4];
+    int nl = 0;
+    if (!node_step_split(bvh, cur, O, inv, t_last, tmax, stack, stride, sp, next, leaves, nl)) return count;
+    if (nl) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        if (leaves[k] != kEmptyChild) leaf_step<K, kCount>(bvh, C, O, w, leaves[k], t_last, j_last, kt, kj, count, cnt);
+    }
+    cur = next != kEmptyChild ? next : pop(stack, stride, sp);
+  }
 #else
   uint32_t cur = bvh.root;
   while (cur != kEmptyChild) {
@@ -223,6 +301,7 @@ __device__ __forceinline__ int collect_round(const BvhView& bvh, const Consts& C
       const float tmax = count == K ? kt[K - 1] : __int_as_float(0x7f800000);
       uint32_t next;
       if (!node_step(bvh, cur, O, inv, t_last, tmax, stack, stride, sp, next)) return count;
+      if (kCount && (uint32_t)sp > cnt.max_stack) cnt.max_stack = (uint32_t)sp;
       cur = next != kEmptyChild ? next : pop(stack, stride, sp);
     }
   }
