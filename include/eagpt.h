@@ -360,6 +360,26 @@ eagpt_status eagpt_render_single_bounce_backward(const eagpt_scene* scene, const
                                                  size_t workspace_bytes, eagpt_stream_t stream);
 
 /* ------------------------------------------------------------------------
+ * Radiant-scene (0-bounce) render and its adjoint.  Each pixel shows the
+ * blended radiance R of its pixel-centre primary segment (Eq. 1-2 applied to
+ * the per-surfel radiance r), the image a radiant scene (Sec. 3.2) and a
+ * light-baked scene (Eq. 10) are viewed as.  No sampling; deterministic.
+ *   out_rgb  device, H x W x 3 (written; 0 where the ray misses)
+ *   out_aux  device or NULL, H x W x 12: the primary record per pixel in
+ *            the layout eagpt_render_single_bounce() writes
+ * The backward adds, for L = sum dL_drgb[p][c] * R[p][c], dL/dtheta into
+ * `grads` (device arrays, +=) through the positions, rotations, scales,
+ * opacities and radiances of every blended surfel; support, alpha limits and
+ * the transmittance stop are held fixed.  FP32 atomics: the summation order is
+ * not deterministic.  No workspace; no allocation. */
+eagpt_status eagpt_render_radiance(const eagpt_scene* scene, const eagpt_bvh* bvh, const eagpt_camera* cam,
+                                   const eagpt_params* params, float* out_rgb, float* out_aux,
+                                   eagpt_stream_t stream);
+eagpt_status eagpt_render_radiance_backward(const eagpt_scene* scene, const eagpt_bvh* bvh, const eagpt_camera* cam,
+                                            const eagpt_params* params, const float* dL_drgb,
+                                            const eagpt_scene_grad* grads, eagpt_stream_t stream);
+
+/* ------------------------------------------------------------------------
  * Tracing of caller rays (the per-segment operation of Eq. 1-3).
  *   rays     device, n_rays x 6: origin (3), unit direction (3); hits need
  *            t > 0

@@ -82,8 +82,10 @@ def _load():
                                        P(d), P(d), P(u32), P(i64), i32]
             lib.ora_single_bounce_grad.argtypes = [P(_Scene), P(_Camera), P(_Params), i32, u64, P(i32), i64,
                                                    P(d), P(d), P(u32), i32]
+            lib.ora_radiance_grad.argtypes = [P(_Scene), P(_Camera), P(_Params), P(i32), i64, P(d), P(d), P(u32),
+                                              i32]
             for f in ("ora_trace_segment", "ora_trace_rays", "ora_primary", "ora_render",
-                      "ora_single_bounce_grad"):
+                      "ora_single_bounce_grad", "ora_radiance_grad"):
                 getattr(lib, f).restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -250,6 +252,24 @@ def single_bounce_grad(scene, camera, pixels, dL_drgb, spp, seed=0, params=None,
                                     _ptr(fl, ctypes.c_uint32), n_threads or default_threads())
     if rc:
         raise RuntimeError("oracle grad failed")
+    return grad, fl
+
+
+def radiance_grad(scene, camera, pixels, dL_drgb, params=None, n_threads=None):
+    """Gradient of sum(dL_drgb * R_primary) (0-bounce render); returns (grad (n,16), flags)."""
+    lib = _load()
+    sc = _oscene(scene)
+    pixels = np.ascontiguousarray(pixels, np.int32)
+    dL = np.ascontiguousarray(dL_drgb, np.float64).reshape(pixels.size, 3)
+    grad = np.zeros((sc.n, 16))
+    fl = np.zeros(pixels.size, np.uint32)
+    prm = (params or Params())._c()
+    cam = _cam(camera)
+    rc = lib.ora_radiance_grad(ctypes.byref(sc._c), ctypes.byref(cam), ctypes.byref(prm),
+                               _ptr(pixels, ctypes.c_int32), pixels.size, _ptr(dL, ctypes.c_double),
+                               _ptr(grad, ctypes.c_double), _ptr(fl, ctypes.c_uint32), n_threads or default_threads())
+    if rc:
+        raise RuntimeError("oracle radiance grad failed")
     return grad, fl
 
 

@@ -885,6 +885,7 @@ typedef struct {
   uint32_t* out_flags;
   gradbuf* per_thread;
   int32_t n_threads;
+  int32_t radiance_only; /* 0-bounce render: I = R_1 for every pixel */
 } grad_ctx;
 
 static int grad_pixel(const world* W, grad_ctx* c, int64_t i, hitbuf* b1, hitbuf* b2, gradbuf* gb) {
@@ -902,8 +903,8 @@ static int grad_pixel(const world* W, grad_ctx* c, int64_t i, hitbuf* b1, hitbuf
     if (c->out_flags) c->out_flags[i] = flags;
     return 0;
   }
-  if (g1.E > prm->tau_E) {
-    /* emitter pixel: I = R_1 */
+  if (c->radiance_only || g1.E > prm->tau_E) {
+    /* 0-bounce render, or emitter pixel: I = R_1 */
     int rc = segment_adjoint(W, c->sc, O, w, 0, b1, &g1, zero3, 0.0, gI, zero3, 0.0, gb, dO, dw);
     if (c->out_flags) c->out_flags[i] = flags;
     return rc;
@@ -968,9 +969,24 @@ static void* gworker(void* arg) {
   return NULL;
 }
 
+static int grad_common(const ora_scene* sc, const ora_camera* cam, const ora_params* prm, int32_t spp,
+                       uint64_t seed, const int32_t* pixels, int64_t n_pix, const double* dL_drgb, double* grad,
+                       uint32_t* out_flags, int32_t n_threads, int32_t radiance_only);
+
 int ora_single_bounce_grad(const ora_scene* sc, const ora_camera* cam, const ora_params* prm, int32_t spp,
                            uint64_t seed, const int32_t* pixels, int64_t n_pix, const double* dL_drgb,
                            double* grad, uint32_t* out_flags, int32_t n_threads) {
+  return grad_common(sc, cam, prm, spp, seed, pixels, n_pix, dL_drgb, grad, out_flags, n_threads, 0);
+}
+
+int ora_radiance_grad(const ora_scene* sc, const ora_camera* cam, const ora_params* prm, const int32_t* pixels,
+                      int64_t n_pix, const double* dL_drgb, double* grad, uint32_t* out_flags, int32_t n_threads) {
+  return grad_common(sc, cam, prm, 1, 0, pixels, n_pix, dL_drgb, grad, out_flags, n_threads, 1);
+}
+
+static int grad_common(const ora_scene* sc, const ora_camera* cam, const ora_params* prm, int32_t spp,
+                       uint64_t seed, const int32_t* pixels, int64_t n_pix, const double* dL_drgb, double* grad,
+                       uint32_t* out_flags, int32_t n_threads, int32_t radiance_only) {
   if (n_threads < 1) n_threads = 1;
   if (n_threads > 256) n_threads = 256;
   surfel64* s = load_surfels(sc);
@@ -986,7 +1002,7 @@ int ora_single_bounce_grad(const ora_scene* sc, const ora_camera* cam, const ora
     free(pt);
     return -1;
   }
-  grad_ctx c = {sc, cam, spp, seed, pixels, dL_drgb, out_flags, per, n_threads};
+  grad_ctx c = {sc, cam, spp, seed, pixels, dL_drgb, out_flags, per, n_threads, radiance_only};
   int started = 0;
   for (int t = 0; t < n_threads; ++t) {
     th[t].W = &W;

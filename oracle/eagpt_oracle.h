@@ -124,6 +124,13 @@ int ora_single_bounce_grad(const ora_scene* sc, const ora_camera* cam, const ora
                            const double* dL_drgb, double* grad, uint32_t* out_flags,
                            int32_t n_threads);
 
+/* Gradient of L = sum dL_drgb . I for the 0-bounce (radiance) render, whose
+ * pixel value is the primary segment's blended radiance R (the radiant scene
+ * of Sec. 3.2; light baking, Eq. 10).  Same layout and accumulation as
+ * ora_single_bounce_grad. */
+int ora_radiance_grad(const ora_scene* sc, const ora_camera* cam, const ora_params* prm, const int32_t* pixels,
+                      int64_t n_pix, const double* dL_drgb, double* grad, uint32_t* out_flags, int32_t n_threads);
+
 #ifdef __cplusplus
 }
 #endif

@@ -252,6 +252,74 @@ def render_single_bounce(tensors: dict, cam: HostCamera, spp: int, seed: int = 0
                                  renderer, prm)
 
 
+def radiance(scene: DeviceScene, bvh: BVH, cam: HostCamera, prm: Optional[capi.Params] = None, want_aux=False,
+             stream=None) -> dict:
+    """0-bounce render of the radiant scene: per pixel the blended radiance R
+    of its primary segment; returns dict(rgb[, aux])."""
+    dev = scene.t["pos"].device
+    c = camera(cam)
+    prm = prm or bvh.params
+    H, W = cam.height, cam.width
+    rgb = torch.empty((H, W, 3), dtype=torch.float32, device=dev)
+    aux = torch.empty((H, W, 12), dtype=torch.float32, device=dev) if want_aux else None
+    sc = scene.c()
+    capi.check(capi.lib().eagpt_render_radiance(ctypes.byref(sc), ctypes.byref(bvh.c()), ctypes.byref(c),
+                                                ctypes.byref(prm), _ptr(rgb), _ptr(aux), _stream(stream)))
+    r = {"rgb": rgb}
+    if want_aux:
+        r["aux"] = aux
+    return r
+
+
+def radiance_backward(scene: DeviceScene, bvh: BVH, cam: HostCamera, dL_drgb: torch.Tensor,
+                      grads: Optional[dict] = None, prm: Optional[capi.Params] = None, stream=None) -> dict:
+    """Adjoint of :func:`radiance`: accumulates dL/dtheta for
+    L = sum(dL_drgb * R) into ``grads`` (created zeroed if None)."""
+    if grads is None:
+        grads = {k: torch.zeros_like(scene.t[k]) for k in GRAD_FIELDS}
+    g = capi.SceneGrad()
+    g.n = scene.n
+    for k in GRAD_FIELDS:
+        setattr(g, k, grads[k].data_ptr() if scene.n else None)
+    c = camera(cam)
+    prm = prm or bvh.params
+    dL = dL_drgb.contiguous().to(torch.float32)
+    sc = scene.c()
+    capi.check(capi.lib().eagpt_render_radiance_backward(ctypes.byref(sc), ctypes.byref(bvh.c()), ctypes.byref(c),
+                                                         ctypes.byref(prm), _ptr(dL), ctypes.byref(g),
+                                                         _stream(stream)))
+    return grads
+
+
+class _RadianceFn(torch.autograd.Function):
+    """Differentiable 0-bounce render; forward and adjoint run in the CUDA
+    library."""
+
+    @staticmethod
+    def forward(ctx, pos, quat, scale, opacity, albedo, radiance_, emissive, cam, prm):
+        ds = DeviceScene({"pos": pos.detach().contiguous(), "quat": quat.detach().contiguous(),
+                          "scale": scale.detach().contiguous(), "opacity": opacity.detach().contiguous(),
+                          "albedo": albedo.detach().contiguous(), "radiance": radiance_.detach().contiguous(),
+                          "emissive": emissive.detach().contiguous()})
+        bvh = BVH(ds, prm)
+        out = radiance(ds, bvh, cam, prm=prm)
+        ctx.state = (ds, bvh, cam, prm)
+        return out["rgb"]
+
+    @staticmethod
+    def backward(ctx, grad_rgb):
+        ds, bvh, cam, prm = ctx.state
+        g = radiance_backward(ds, bvh, cam, grad_rgb, prm=prm)
+        return (g["pos"], g["quat"], g["scale"], g["opacity"], g["albedo"], g["radiance"], None, None, None)
+
+
+def render_radiance(tensors: dict, cam: HostCamera, prm: Optional[capi.Params] = None) -> torch.Tensor:
+    """Autograd entry point of the 0-bounce render (radiant scene, Sec. 3.2)."""
+    prm = prm or params()
+    return _RadianceFn.apply(tensors["pos"], tensors["quat"], tensors["scale"], tensors["opacity"],
+                             tensors["albedo"], tensors["radiance"], tensors["emissive"], cam, prm)
+
+
 EDIT_OPS = {"set_emission": 0, "toggle_emission": 1, "scale_albedo": 2, "translate": 3, "rigid": 4}
 
 

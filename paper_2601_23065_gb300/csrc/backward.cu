@@ -365,3 +365,46 @@ cudaError_t launch_backward(const BvhView& bvh, const Consts& C, const eagpt_cam
 }
 
 }  // namespace eagpt
+
+namespace eagpt {
+
+// Adjoint of the 0-bounce render: dL/dR of each pixel's primary segment.
+__global__ void __launch_bounds__(kBlock) k_radiance_bwd(BvhView bvh, Consts C, eagpt_camera cam, eagpt_scene sc,
+                                                         eagpt_scene_grad gr, const float* __restrict__ dL,
+                                                         int64_t npix) {
+  __shared__ uint32_t s_stack[kStackSize * kBlock];
+  const int64_t i = blockIdx.x * (int64_t)kBlock + threadIdx.x;
+  if (i >= npix) return;
+  float3 O, w;
+  camera_ray(cam, (uint32_t)i, O, w);
+  TraceCounters cnt{0, 0, 0, 0, 0};
+  RawVisitor v1(bvh.shade, C, w, 0);
+  trace_segment<kKb, false>(bvh, C, O, w, 0.f, s_stack + threadIdx.x, kBlock, v1, cnt);
+  if (v1.blend.b.n_hits == 0) return;
+  AdjointVisitor av;
+  av.shade = bvh.shade;
+  av.sc = sc;
+  av.gr = gr;
+  av.C = C;
+  av.O = O;
+  av.w = w;
+  av.mode = 0;
+  av.V = v1.blend.b;
+  init_blend(av.run);
+  av.dO = av.dw = make_float3(0.f, 0.f, 0.f);
+  av.gN = av.gP = make_float3(0.f, 0.f, 0.f);
+  av.gR = make_float3(dL[3 * i], dL[3 * i + 1], dL[3 * i + 2]);
+  av.gD = av.gA = 0.f;
+  trace_segment<kKb, false>(bvh, C, O, w, 0.f, s_stack + threadIdx.x, kBlock, av, cnt);
+}
+
+cudaError_t launch_radiance_backward(const BvhView& bvh, const Consts& C, const eagpt_camera& cam,
+                                     const eagpt_scene& sc, const eagpt_scene_grad& gr, const float* dL,
+                                     cudaStream_t st) {
+  const int64_t npix = (int64_t)cam.width * cam.height;
+  if (bvh.n <= 0) return cudaSuccess;
+  EAGPT_LAUNCH(st, "k_radiance_bwd", k_radiance_bwd<<<nb(npix), kBlock, 0, st>>>(bvh, C, cam, sc, gr, dL, npix));
+  return cudaGetLastError();
+}
+
+}  // namespace eagpt

@@ -9,12 +9,13 @@
 //   k_refit       bottom-up boxes of the binary tree (visit counters: the
 //                 second child to arrive computes the parent), and the sum of
 //                 node surface areas (the refit-quality measure).
-//   k_collapse    top-down, one level per launch: every BVH4 node takes a
+//   k_collapse    top-down, one level per launch: every BVH node takes a
 //                 binary node and opens its largest-area internal child until
-//                 it has four children; subtrees of at most kLeafMax surfels
+//                 it has four (or eight) children; subtrees of at most kLeafMax surfels
 //                 become leaves.  Records, per BVH4 child, the binary node it
 //                 stands for, so a refit only has to copy boxes.
-//   k_bvh4_boxes  copies refit binary boxes into the BVH4 child slots.
+//   k_bvh_boxes   copies refit binary boxes into the BVH child slots
+//                 (re-quantising them for the 8-wide quantised nodes).
 #include <cuda_runtime.h>
 
 #include "common.cuh"
@@ -145,19 +146,72 @@ __device__ __forceinline__ void set_child_box(Node4& nd, int k, float4 lo, float
   hz[k] = hi.z;
 }
 
+// Quantises the child boxes of a BVH8 node (see Node8): origin = union lo,
+// quantum 2^e per axis with extent / quantum <= 254, lower bounds rounded
+// down and upper bounds up, each checked against the exact decode
+// origin + q * quantum the traversal uses.
+__device__ __forceinline__ Node8 make_node8(const float4* lo, const float4* hi, const uint32_t* link, int nc) {
+  float o[3] = {3e38f, 3e38f, 3e38f}, top[3] = {-3e38f, -3e38f, -3e38f};
+  for (int k = 0; k < nc; ++k) {
+    const float l[3] = {lo[k].x, lo[k].y, lo[k].z}, h[3] = {hi[k].x, hi[k].y, hi[k].z};
+    for (int a = 0; a < 3; ++a) {
+      o[a] = fminf(o[a], l[a]);
+      top[a] = fmaxf(top[a], h[a]);
+    }
+  }
+  uint32_t eb[3];
+  float s[3];
+  for (int a = 0; a < 3; ++a) {
+    int e = -100;
+    const float x = (top[a] - o[a]) / 254.0f;
+    if (x > 0.f) {
+      frexpf(x, &e);  // x <= 2^e
+      e = max(-100, min(100, e));
+    }
+    eb[a] = (uint32_t)(e + 127);
+    s[a] = __int_as_float((int)(eb[a] << 23));
+  }
+  uint32_t qlo[3][2] = {{0, 0}, {0, 0}, {0, 0}}, qhi[3][2] = {{0, 0}, {0, 0}, {0, 0}};
+  for (int k = 0; k < nc; ++k) {
+    const float l[3] = {lo[k].x, lo[k].y, lo[k].z}, h[3] = {hi[k].x, hi[k].y, hi[k].z};
+    for (int a = 0; a < 3; ++a) {
+      int ql = (int)floorf((l[a] - o[a]) / s[a]);
+      ql = max(0, min(255, ql));
+      while (ql > 0 && __fmaf_rn((float)ql, s[a], o[a]) > l[a]) --ql;
+      int qh = (int)ceilf((h[a] - o[a]) / s[a]);
+      qh = max(0, min(255, qh));
+      while (qh < 255 && __fmaf_rn((float)qh, s[a], o[a]) < h[a]) ++qh;
+      qlo[a][k >> 2] |= (uint32_t)ql << (8 * (k & 3));
+      qhi[a][k >> 2] |= (uint32_t)qh << (8 * (k & 3));
+    }
+  }
+  Node8 n;
+  n.u0 = make_uint4(__float_as_uint(o[0]), __float_as_uint(o[1]), __float_as_uint(o[2]),
+                    eb[0] | (eb[1] << 8) | (eb[2] << 16));
+  uint32_t L[8];
+  for (int k = 0; k < 8; ++k) L[k] = k < nc ? link[k] : kEmptyChild;
+  n.u1 = make_uint4(L[0], L[1], L[2], L[3]);
+  n.u2 = make_uint4(L[4], L[5], L[6], L[7]);
+  n.u3 = make_uint4(qlo[0][0], qlo[0][1], qlo[1][0], qlo[1][1]);
+  n.u4 = make_uint4(qlo[2][0], qlo[2][1], qhi[0][0], qhi[0][1]);
+  n.u5 = make_uint4(qhi[1][0], qhi[1][1], qhi[2][0], qhi[2][1]);
+  return n;
+}
+
 // One level of the top-down collapse.  Frontier entries are (binary node,
-// BVH4 node).  levels[lv] holds this level's frontier size, levels[lv + 1]
-// collects the next one; levels[kMaxCollapseLevels + 1] counts BVH4 nodes.
-__global__ void k_collapse(TreeArrays T, Node4* nodes, int32_t* src4, const int2* __restrict__ front_in,
+// BVH node).  levels[lv] holds this level's frontier size, levels[lv + 1]
+// collects the next one; levels[kMaxCollapseLevels + 1] counts BVH nodes.
+template <int W>
+__global__ void k_collapse(TreeArrays T, void* nodes_out, int32_t* src4, const int2* __restrict__ front_in,
                            int2* front_out, uint32_t* levels, int lv, int64_t cap) {
   const uint32_t count = levels[lv];
   for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < count; f += (int64_t)gridDim.x * blockDim.x) {
     const int2 e = front_in[f];
-    int32_t ch[4];
+    int32_t ch[W];
     int nc = 2;
     ch[0] = T.child_bin[2 * e.x];
     ch[1] = T.child_bin[2 * e.x + 1];
-    while (nc < 4) {
+    while (nc < W) {
       int best = -1;
       float best_area = -1.f;
       for (int k = 0; k < nc; ++k) {
@@ -176,16 +230,13 @@ __global__ void k_collapse(TreeArrays T, Node4* nodes, int32_t* src4, const int2
       ch[best] = T.child_bin[2 * b];
       ch[nc++] = T.child_bin[2 * b + 1];
     }
-    Node4 nd;
-    nd.lox = nd.loy = nd.loz = make_float4(1e30f, 1e30f, 1e30f, 1e30f);
-    nd.hix = nd.hiy = nd.hiz = make_float4(-1e30f, -1e30f, -1e30f, -1e30f);
-    uint32_t link[4] = {kEmptyChild, kEmptyChild, kEmptyChild, kEmptyChild};
-    for (int k = 0; k < 4; ++k) {
-      src4[4 * (int64_t)e.y + k] = k < nc ? ch[k] : INT32_MIN;
+    uint32_t link[W];
+    float4 blo[W], bhi[W];
+    for (int k = 0; k < W; ++k) {
+      link[k] = kEmptyChild;
+      src4[8 * (int64_t)e.y + k] = k < nc ? ch[k] : INT32_MIN;
       if (k >= nc) continue;
-      float4 lo, hi;
-      code_box(T, ch[k], lo, hi);
-      set_child_box(nd, k, lo, hi);
+      code_box(T, ch[k], blo[k], bhi[k]);
       const int64_t cnt = subtree_count(T, ch[k]);
       if (cnt <= kLeafMax) {
         const int64_t first = ch[k] < 0 ? (int64_t)~ch[k] : (int64_t)T.irange[ch[k]].x;
@@ -201,9 +252,17 @@ __global__ void k_collapse(TreeArrays T, Node4* nodes, int32_t* src4, const int2
         link[k] = id;
       }
     }
-    nd.child = make_uint4(link[0], link[1], link[2], link[3]);
-    nd.pad = make_uint4(0u, 0u, 0u, 0u);
-    nodes[e.y] = nd;
+    if (W == 8) {
+      ((Node8*)nodes_out)[e.y] = make_node8(blo, bhi, link, nc);
+    } else {
+      Node4 nd;
+      nd.lox = nd.loy = nd.loz = make_float4(1e30f, 1e30f, 1e30f, 1e30f);
+      nd.hix = nd.hiy = nd.hiz = make_float4(-1e30f, -1e30f, -1e30f, -1e30f);
+      for (int k = 0; k < nc && k < 4; ++k) set_child_box(nd, k, blo[k], bhi[k]);
+      nd.child = make_uint4(link[0], link[1 % W], link[2 % W], link[3 % W]);
+      nd.pad = make_uint4(0u, 0u, 0u, 0u);
+      ((Node4*)nodes_out)[e.y] = nd;
+    }
   }
 }
 
@@ -224,39 +283,61 @@ __global__ void k_collapse_check(const uint32_t* levels) {
   if (threadIdx.x == 0 && levels[kMaxCollapseLevels] != 0u) raise_error(kErrBadIndex);
 }
 
-// Refresh the child boxes of every BVH4 node from the binary boxes.
-__global__ void k_bvh4_boxes(TreeArrays T, Node4* nodes, const int32_t* __restrict__ src4,
-                             const uint32_t* __restrict__ levels) {
+// Refresh the child boxes of every BVH node from the binary boxes (links
+// unchanged).
+__global__ void k_bvh_boxes(TreeArrays T, void* nodes_out, const int32_t* __restrict__ src4,
+                            const uint32_t* __restrict__ levels) {
   const uint32_t count = levels[kMaxCollapseLevels + 1];
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
-    Node4 nd = nodes[i];
-    for (int k = 0; k < 4; ++k) {
-      const int32_t c = src4[4 * i + k];
-      if (c == INT32_MIN) continue;
-      float4 lo, hi;
-      code_box(T, c, lo, hi);
-      set_child_box(nd, k, lo, hi);
+    if (kBvh8) {
+      Node8* nodes = (Node8*)nodes_out;
+      const Node8 old = nodes[i];
+      const uint32_t link[8] = {old.u1.x, old.u1.y, old.u1.z, old.u1.w, old.u2.x, old.u2.y, old.u2.z, old.u2.w};
+      float4 lo[8], hi[8];
+      int nc = 0;
+      for (int k = 0; k < 8; ++k) {
+        const int32_t c = src4[8 * i + k];
+        if (c == INT32_MIN) break;
+        code_box(T, c, lo[k], hi[k]);
+        nc = k + 1;
+      }
+      nodes[i] = make_node8(lo, hi, link, nc);
+    } else {
+      Node4* nodes = (Node4*)nodes_out;
+      Node4 nd = nodes[i];
+      for (int k = 0; k < 4; ++k) {
+        const int32_t c = src4[8 * i + k];
+        if (c == INT32_MIN) continue;
+        float4 lo, hi;
+        code_box(T, c, lo, hi);
+        set_child_box(nd, k, lo, hi);
+      }
+      nodes[i] = nd;
     }
-    nodes[i] = nd;
   }
 }
 
-// n <= kLeafMax: a single BVH4 node whose first child is one leaf.
-__global__ void k_small_root(int64_t n, const float4* __restrict__ plo, const float4* __restrict__ phi, Node4* nodes,
-                             int32_t* src4, uint32_t* levels, BvhHeader* hdr) {
+// n <= kLeafMax: a single node whose first child is one leaf.
+__global__ void k_small_root(int64_t n, const float4* __restrict__ plo, const float4* __restrict__ phi,
+                             void* nodes_out, int32_t* src4, uint32_t* levels, BvhHeader* hdr) {
   float4 lo = make_float4(3e38f, 3e38f, 3e38f, 0.f), hi = make_float4(-3e38f, -3e38f, -3e38f, 0.f);
   for (int64_t j = 0; j < n; ++j) {
     lo = make_float4(fminf(lo.x, plo[j].x), fminf(lo.y, plo[j].y), fminf(lo.z, plo[j].z), 0.f);
     hi = make_float4(fmaxf(hi.x, phi[j].x), fmaxf(hi.y, phi[j].y), fmaxf(hi.z, phi[j].z), 0.f);
   }
-  Node4 nd;
-  nd.lox = nd.loy = nd.loz = make_float4(1e30f, 1e30f, 1e30f, 1e30f);
-  nd.hix = nd.hiy = nd.hiz = make_float4(-1e30f, -1e30f, -1e30f, -1e30f);
-  set_child_box(nd, 0, lo, hi);
-  nd.child = make_uint4(kLeafBit | ((uint32_t)(n - 1) << kLeafCountShift), kEmptyChild, kEmptyChild, kEmptyChild);
-  nd.pad = make_uint4(0u, 0u, 0u, 0u);
-  nodes[0] = nd;
-  for (int k = 0; k < 4; ++k) src4[k] = INT32_MIN;
+  const uint32_t leaf = kLeafBit | ((uint32_t)(n - 1) << kLeafCountShift);
+  if (kBvh8) {
+    ((Node8*)nodes_out)[0] = make_node8(&lo, &hi, &leaf, 1);
+  } else {
+    Node4 nd;
+    nd.lox = nd.loy = nd.loz = make_float4(1e30f, 1e30f, 1e30f, 1e30f);
+    nd.hix = nd.hiy = nd.hiz = make_float4(-1e30f, -1e30f, -1e30f, -1e30f);
+    set_child_box(nd, 0, lo, hi);
+    nd.child = make_uint4(leaf, kEmptyChild, kEmptyChild, kEmptyChild);
+    nd.pad = make_uint4(0u, 0u, 0u, 0u);
+    ((Node4*)nodes_out)[0] = nd;
+  }
+  for (int k = 0; k < 8; ++k) src4[k] = INT32_MIN;
   for (int k = 0; k < kMaxCollapseLevels + 2; ++k) levels[k] = 0u;
   levels[kMaxCollapseLevels + 1] = 1u;
   hdr->area_sum = box_area(lo, hi);
@@ -292,7 +373,7 @@ static void launch_binary_refit(char* base, const BvhLayout& L, cudaStream_t st)
 cudaError_t launch_tree(const uint32_t* sorted_keys, char* base, const BvhLayout& L, cudaStream_t st) {
   const int64_t n = L.n;
   BvhHeader* hdr = (BvhHeader*)(base + L.header);
-  Node4* nodes = (Node4*)(base + L.nodes);
+  void* nodes = (void*)(base + L.nodes);
   int32_t* src4 = (int32_t*)(base + L.src4);
   uint32_t* levels = (uint32_t*)(base + L.levels);
   if (n <= kLeafMax) {
@@ -314,7 +395,7 @@ cudaError_t launch_tree(const uint32_t* sorted_keys, char* base, const BvhLayout
   const unsigned grid = (unsigned)(4 * device_sms());
   for (int lv = 0; lv < kMaxCollapseLevels; ++lv) {
     EAGPT_LAUNCH(st, "k_collapse",
-                 k_collapse<<<grid, 256, 0, st>>>(T, nodes, src4, fr[lv & 1], fr[(lv + 1) & 1], levels, lv,
+                 k_collapse<kBvhWidth><<<grid, 256, 0, st>>>(T, nodes, src4, fr[lv & 1], fr[(lv + 1) & 1], levels, lv,
                                                  L.n_inodes));
   }
   EAGPT_LAUNCH(st, "k_collapse_check", k_collapse_check<<<1, 32, 0, st>>>(levels));
@@ -325,15 +406,15 @@ int launch_refit(char* base, const BvhLayout& L, cudaStream_t st) {
   if (L.n <= kLeafMax) {
     EAGPT_LAUNCH(st, "k_small_root",
                  k_small_root<<<1, 1, 0, st>>>(L.n, (const float4*)(base + L.prim_lo),
-                                               (const float4*)(base + L.prim_hi), (Node4*)(base + L.nodes),
+                                               (const float4*)(base + L.prim_hi), (void*)(base + L.nodes),
                                                (int32_t*)(base + L.src4), (uint32_t*)(base + L.levels),
                                                (BvhHeader*)(base + L.header)));
     return 1;
   }
   launch_binary_refit(base, L, st);
-  EAGPT_LAUNCH(st, "k_bvh4_boxes",
-               k_bvh4_boxes<<<(unsigned)(4 * device_sms()), 256, 0, st>>>(
-                   tree_arrays(base, L), (Node4*)(base + L.nodes), (const int32_t*)(base + L.src4),
+  EAGPT_LAUNCH(st, "k_bvh_boxes",
+               k_bvh_boxes<<<(unsigned)(4 * device_sms()), 256, 0, st>>>(
+                   tree_arrays(base, L), (void*)(base + L.nodes), (const int32_t*)(base + L.src4),
                    (const uint32_t*)(base + L.levels)));
   return 3;
 }

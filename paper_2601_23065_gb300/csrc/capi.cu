@@ -95,6 +95,7 @@ BvhView make_view(const eagpt_bvh& b) {
     v.trace = (const TraceRec*)(base + L.trace);
     v.shade = (const ShadeRec*)(base + L.shade);
     v.nodes = (const Node4*)(base + L.nodes);
+    v.nodes8 = (const Node8*)(base + L.nodes);
     v.root = 0;  // node 0: Karras root, or the single node of a small scene
     v.bounds_bits = (const uint32_t*)(base + L.header);
   }
@@ -293,6 +294,40 @@ eagpt_status eagpt_render_single_bounce_backward(const eagpt_scene* scene, const
   cudaError_t e = launch_backward(make_view(*bvh), make_consts(*params), *cam, *scene, *grads, spp, seed, dL_drgb, ws,
                                   ws_bytes, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "backward launch");
+  return EAGPT_OK;
+}
+
+eagpt_status eagpt_render_radiance(const eagpt_scene* scene, const eagpt_bvh* bvh, const eagpt_camera* cam,
+                                   const eagpt_params* params, float* out_rgb, float* out_aux,
+                                   eagpt_stream_t stream) {
+  eagpt_status s;
+  if ((s = check_scene(scene)) != EAGPT_OK) return s;
+  if ((s = check_params(params)) != EAGPT_OK) return s;
+  if ((s = check_camera(cam)) != EAGPT_OK) return s;
+  if ((s = check_bvh(bvh, scene, params)) != EAGPT_OK) return s;
+  if (!out_rgb) return fail(EAGPT_ERR_INVALID_ARGUMENT, "out_rgb is NULL%s");
+  cudaError_t e = launch_radiance(make_view(*bvh), make_consts(*params), *cam, out_rgb, out_aux, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "radiance launch");
+  return EAGPT_OK;
+}
+
+eagpt_status eagpt_render_radiance_backward(const eagpt_scene* scene, const eagpt_bvh* bvh, const eagpt_camera* cam,
+                                            const eagpt_params* params, const float* dL_drgb,
+                                            const eagpt_scene_grad* grads, eagpt_stream_t stream) {
+  eagpt_status s;
+  if ((s = check_scene(scene)) != EAGPT_OK) return s;
+  if ((s = check_params(params)) != EAGPT_OK) return s;
+  if ((s = check_camera(cam)) != EAGPT_OK) return s;
+  if ((s = check_bvh(bvh, scene, params)) != EAGPT_OK) return s;
+  if (!dL_drgb) return fail(EAGPT_ERR_INVALID_ARGUMENT, "dL_drgb is NULL%s");
+  if (!grads || grads->n != scene->n) return fail(EAGPT_ERR_INVALID_ARGUMENT, "grads must match the scene%s");
+  if (scene->n > 0 && (!grads->pos || !grads->quat || !grads->scale || !grads->opacity || !grads->albedo ||
+                       !grads->radiance))
+    return fail(EAGPT_ERR_INVALID_ARGUMENT, "every gradient array is required%s");
+  if (scene->n == 0) return EAGPT_OK;
+  cudaError_t e = launch_radiance_backward(make_view(*bvh), make_consts(*params), *cam, *scene, *grads, dL_drgb,
+                                           (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "radiance backward launch");
   return EAGPT_OK;
 }
 

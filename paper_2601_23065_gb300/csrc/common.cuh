@@ -66,7 +66,27 @@ struct __align__(128) Node4 {
   uint4 pad;
 };
 
-constexpr int kMaxCollapseLevels = 96;  // BVH4 levels built top-down
+// BVH8 node, 96 B (six 16-byte loads): eight child links and eight child
+// boxes quantised to 8 bits per bound relative to the node's box.
+//   u0 = (origin.x, origin.y, origin.z, exps)  exps bytes 0..2: biased
+//        exponents e of the per-axis quantum 2^(e - 127)
+//   u1, u2 = child links 0..3, 4..7
+//   u3 = qlo.x[0..7], qlo.y[0..7]; u4 = qlo.z[0..7], qhi.x[0..7];
+//   u5 = qhi.y[0..7], qhi.z[0..7]   (bytes)
+// A child box decodes as origin + q * quantum (fused multiply-add); the
+// build rounds lower bounds down and upper bounds up, checked against this
+// exact decode, so decoded boxes contain the true ones.
+struct __align__(16) Node8 {
+  uint4 u0, u1, u2, u3, u4, u5;
+};
+
+#ifndef EAGPT_BVH8
+#define EAGPT_BVH8 0
+#endif
+constexpr bool kBvh8 = EAGPT_BVH8 != 0;
+constexpr int kBvhWidth = kBvh8 ? 8 : 4;
+
+constexpr int kMaxCollapseLevels = 96;  // BVH levels built top-down
 
 // Offsets of the arrays inside the caller's BVH storage buffer (a pure
 // function of n, so the host never reads the device to find them).
@@ -123,7 +143,7 @@ inline BvhLayout bvh_layout(int64_t n) {
   L.visit = take((size_t)L.n_inodes * 4);
   L.child_bin = take((size_t)L.n_inodes * 8);
   L.irange = take((size_t)L.n_inodes * 8);
-  L.src4 = take((size_t)L.n_inodes * 16);
+  L.src4 = take((size_t)L.n_inodes * 32);  // per node: the binary code of each of up to 8 children
   L.front0 = take((size_t)L.n_inodes * 8);
   L.front1 = take((size_t)L.n_inodes * 8);
   L.levels = take((size_t)(kMaxCollapseLevels + 2) * 4);
@@ -135,7 +155,8 @@ inline BvhLayout bvh_layout(int64_t n) {
 struct BvhView {
   const TraceRec* trace;
   const ShadeRec* shade;
-  const Node4* nodes;
+  const Node4* nodes;    // BVH4 nodes (kBvh8 == false)
+  const Node8* nodes8;   // BVH8 nodes (kBvh8 == true), same storage
   uint32_t root;  // node index, or an encoded leaf when n <= kLeafMax
   int64_t n;
   const uint32_t* bounds_bits;  // scene centroid bounds (BvhHeader), ordered-int encoded

@@ -50,7 +50,13 @@ cudaError_t launch_trace_rays(const BvhView& bvh, const Consts& C, int mode, con
 cudaError_t launch_primary_records(const BvhView& bvh, const Consts& C, const eagpt_camera& cam, int mode,
                                    int64_t npix, void* prim, cudaStream_t st);
 
+cudaError_t launch_radiance(const BvhView& bvh, const Consts& C, const eagpt_camera& cam, float* out_rgb, float* aux,
+                            cudaStream_t st);
+
 // backward.cu
+cudaError_t launch_radiance_backward(const BvhView& bvh, const Consts& C, const eagpt_camera& cam,
+                                     const eagpt_scene& sc, const eagpt_scene_grad& gr, const float* dL,
+                                     cudaStream_t st);
 size_t backward_workspace_bytes(int64_t npix, int spp, int batch);
 int backward_choose_batch(int64_t npix, int spp, size_t ws_bytes);
 cudaError_t launch_backward(const BvhView& bvh, const Consts& C, const eagpt_camera& cam, const eagpt_scene& sc,

@@ -417,3 +417,35 @@ cudaError_t launch_primary_records(const BvhView& bvh, const Consts& C, const ea
 }
 
 }  // namespace eagpt
+
+namespace eagpt {
+
+// 0-bounce (radiance) render: every pixel shows the blended radiance R of its
+// primary segment (the radiant scene of Sec. 3.2; light-baked scenes are
+// viewed this way, Eq. 10).
+__global__ void __launch_bounds__(kBlock, kMinBlocks) k_radiance(BvhView bvh, Consts C, eagpt_camera cam, int64_t npix,
+                                                                 float* out_rgb, float* aux) {
+  __shared__ uint32_t s_stack[kStackSize * kBlock];
+  const int64_t i = blockIdx.x * (int64_t)kBlock + threadIdx.x;
+  if (i >= npix) return;
+  float3 O, w;
+  camera_ray(cam, (uint32_t)i, O, w);
+  BlendVisitor vis(bvh.shade, C, w, 0);
+  TraceCounters cnt{0, 0, 0, 0, 0};
+  trace_segment<kK, false>(bvh, C, O, w, 0.f, s_stack + threadIdx.x, kBlock, vis, cnt);
+  const SegRec s = finish(vis.b);
+  out_rgb[3 * i] = s.R.x;
+  out_rgb[3 * i + 1] = s.R.y;
+  out_rgb[3 * i + 2] = s.R.z;
+  if (aux) write_aux(aux, i, s);
+}
+
+cudaError_t launch_radiance(const BvhView& bvh, const Consts& C, const eagpt_camera& cam, float* out_rgb, float* aux,
+                            cudaStream_t st) {
+  const int64_t npix = (int64_t)cam.width * cam.height;
+  if (bvh.n <= 0) return cudaMemsetAsync(out_rgb, 0, (size_t)npix * 3 * sizeof(float), st);
+  EAGPT_LAUNCH(st, "k_radiance", k_radiance<<<nblocks(npix), kBlock, 0, st>>>(bvh, C, cam, npix, out_rgb, aux));
+  return cudaGetLastError();
+}
+
+}  // namespace eagpt

@@ -169,6 +169,68 @@ __device__ __forceinline__ bool node_step(const BvhView& bvh, uint32_t node, flo
   return true;
 }
 
+// One quantised BVH8 node (see Node8): decode the eight child boxes, slab-
+// test them, order the hit children front to back (Batcher's 19-comparator
+// network for 8 keys), push all but the nearest.
+__device__ __forceinline__ bool node_step8(const BvhView& bvh, uint32_t node, float3 O, float3 inv, float t_last,
+                                           float tmax, uint32_t* stack, int stride, int& sp, uint32_t& next) {
+  const Node8* np = bvh.nodes8 + node;
+  const uint4 u0 = __ldg(&np->u0), u1 = __ldg(&np->u1), u2 = __ldg(&np->u2);
+  const uint4 u3 = __ldg(&np->u3), u4 = __ldg(&np->u4), u5 = __ldg(&np->u5);
+  const float ox = __uint_as_float(u0.x), oy = __uint_as_float(u0.y), oz = __uint_as_float(u0.z);
+  const float sx = __uint_as_float((u0.w & 0xFFu) << 23), sy = __uint_as_float(((u0.w >> 8) & 0xFFu) << 23);
+  const float sz = __uint_as_float(((u0.w >> 16) & 0xFFu) << 23);
+  const float inf = __int_as_float(0x7f800000);
+  float e[8];
+  uint32_t c[8] = {u1.x, u1.y, u1.z, u1.w, u2.x, u2.y, u2.z, u2.w};
+  const uint32_t qlx[2] = {u3.x, u3.y}, qly[2] = {u3.z, u3.w}, qlz[2] = {u4.x, u4.y};
+  const uint32_t qhx[2] = {u4.z, u4.w}, qhy[2] = {u5.x, u5.y}, qhz[2] = {u5.z, u5.w};
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const int w = k >> 2, sh = 8 * (k & 3);
+    const float3 lo = make_float3(__fmaf_rn((float)((qlx[w] >> sh) & 0xFFu), sx, ox),
+                                  __fmaf_rn((float)((qly[w] >> sh) & 0xFFu), sy, oy),
+                                  __fmaf_rn((float)((qlz[w] >> sh) & 0xFFu), sz, oz));
+    const float3 hi = make_float3(__fmaf_rn((float)((qhx[w] >> sh) & 0xFFu), sx, ox),
+                                  __fmaf_rn((float)((qhy[w] >> sh) & 0xFFu), sy, oy),
+                                  __fmaf_rn((float)((qhz[w] >> sh) & 0xFFu), sz, oz));
+    float te;
+    const bool h = box_hit(lo, hi, O, inv, t_last, tmax, te);
+    e[k] = (h && c[k] != kEmptyChild) ? te : inf;
+  }
+#define EAGPT_CSWAP(i, j)                         \
+  if (e[j] < e[i]) {                              \
+    const float tf = e[i];                        \
+    e[i] = e[j];                                  \
+    e[j] = tf;                                    \
+    const uint32_t tc = c[i];                     \
+    c[i] = c[j];                                  \
+    c[j] = tc;                                    \
+  }
+  EAGPT_CSWAP(0, 1) EAGPT_CSWAP(2, 3) EAGPT_CSWAP(4, 5) EAGPT_CSWAP(6, 7)
+  EAGPT_CSWAP(0, 2) EAGPT_CSWAP(1, 3) EAGPT_CSWAP(4, 6) EAGPT_CSWAP(5, 7)
+  EAGPT_CSWAP(1, 2) EAGPT_CSWAP(5, 6)
+  EAGPT_CSWAP(0, 4) EAGPT_CSWAP(1, 5) EAGPT_CSWAP(2, 6) EAGPT_CSWAP(3, 7)
+  EAGPT_CSWAP(2, 4) EAGPT_CSWAP(3, 5)
+  EAGPT_CSWAP(1, 2) EAGPT_CSWAP(3, 4) EAGPT_CSWAP(5, 6)
+#undef EAGPT_CSWAP
+  next = kEmptyChild;
+  if (e[0] != inf) {
+    int m = 0;
+#pragma unroll
+    for (int k = 1; k < 8; ++k) m += e[k] != inf;
+    if (sp + m > kStackSize) {
+      raise_error(kErrStackOverflow);
+      return false;
+    }
+#pragma unroll
+    for (int k = 7; k >= 1; --k)
+      if (e[k] != inf) stack[(sp++) * stride] = c[k];
+    next = c[0];
+  }
+  return true;
+}
+
 // Like node_step, but the hit leaf children are returned in `leaves` (nl of
 // them) instead of being pushed; only inner children are ordered and pushed.
 __device__ __forceinline__ bool node_step_split(const BvhView& bvh, uint32_t node, float3 O, float3 inv,
@@ -300,7 +362,9 @@ __device__ __forceinline__ int collect_round(const BvhView& bvh, const Consts& C
       if (kCount) ++cnt.nodes;
       const float tmax = count == K ? kt[K - 1] : __int_as_float(0x7f800000);
       uint32_t next;
-      if (!node_step(bvh, cur, O, inv, t_last, tmax, stack, stride, sp, next)) return count;
+      const bool ok = kBvh8 ? node_step8(bvh, cur, O, inv, t_last, tmax, stack, stride, sp, next)
+                            : node_step(bvh, cur, O, inv, t_last, tmax, stack, stride, sp, next);
+      if (!ok) return count;
       if (kCount && (uint32_t)sp > cnt.max_stack) cnt.max_stack = (uint32_t)sp;
       cur = next != kEmptyChild ? next : pop(stack, stride, sp);
     }
