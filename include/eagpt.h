@@ -380,6 +380,95 @@ eagpt_status eagpt_render_radiance_backward(const eagpt_scene* scene, const eagp
                                             const eagpt_scene_grad* grads, eagpt_stream_t stream);
 
 /* ------------------------------------------------------------------------
+ * Optimisation of the shading parameters (Stage 1, Eq. 7: albedo rho through
+ * the single-bounce render with r fixed; light baking, Eq. 10: radiance r
+ * through the 0-bounce render).  Geometry is not changed, so the BVH stays
+ * valid; the updates are written to the scene and to the BVH's own copy.
+ * ------------------------------------------------------------------------ */
+
+/* Single-bounce render (Eq. 6) that also writes, per pixel, the incident
+ * radiance estimate L_i = mean_s R(w_s) that multiplies P in Eq. 6 (0 for
+ * emitter and missed pixels), the factor the albedo gradient needs.  out_rgb
+ * equals eagpt_render_single_bounce()'s up to FP32 rounding (P is applied to
+ * the sample mean instead of to each sample).  out_li: device, H x W x 3.
+ * Workspace as for eagpt_render_single_bounce(). */
+eagpt_status eagpt_render_single_bounce_incident(const eagpt_scene* scene, const eagpt_bvh* bvh,
+                                                 const eagpt_camera* cam, const eagpt_params* params, int32_t spp,
+                                                 uint64_t seed, float* out_rgb, float* out_li, void* workspace,
+                                                 size_t workspace_bytes, eagpt_stream_t stream);
+
+/* Gradient of L = sum dL_drgb[p][c] * I[p][c] with respect to one shading
+ * field, through the primary segment's blend (Eq. 2) with its decisions held
+ * fixed: each blended surfel i of pixel p gets w_i g_p added (w_i =
+ * T_{i-1} alpha_i).
+ *   field 0: albedo rho of the single-bounce image (Eq. 6-7), g_p =
+ *            dL_drgb[p] (.) li[p], li from eagpt_render_single_bounce_incident
+ *            with the same scene, camera, spp and seed
+ *   field 1: radiance r of the 0-bounce image (Eq. 10), g_p = dL_drgb[p];
+ *            li must be NULL
+ *   grad     device, n x 3, accumulated (+=); FP32 atomics (the summation
+ *            order is not deterministic). */
+eagpt_status eagpt_render_shading_backward(const eagpt_scene* scene, const eagpt_bvh* bvh, const eagpt_camera* cam,
+                                           const eagpt_params* params, int32_t field, const float* dL_drgb,
+                                           const float* li, float* grad, eagpt_stream_t stream);
+
+/* The colour loss of Eq. 7 and Eq. 10 on n linear values (e.g. H x W x 3):
+ *   L = lambda_c / n * sum_k | PQ(pred_k / peak) - PQ(target_k / peak) |
+ * with PQ the SMPTE ST 2084 inverse EOTF (Sec. 3.2) and the normalised value
+ * clamped to [1e-10, 1] (derivative 0 where the clamp is active); peak = the
+ * linear value mapped to PQ 1 (10000 cd/m^2).  out_grad (device, n, written,
+ * or NULL) = dL/dpred, sign(0) = 0; out_loss (device, one double, or NULL).
+ * The loss is summed in FP64 in a fixed order (deterministic).  scratch:
+ * device, eagpt_pq_l1_scratch_bytes(n) bytes, 8-byte aligned. */
+size_t eagpt_pq_l1_scratch_bytes(int64_t n);
+eagpt_status eagpt_pq_l1_loss(const float* pred, const float* target, int64_t n, float peak, float lambda_c,
+                              float* out_grad, double* out_loss, void* scratch, size_t scratch_bytes,
+                              eagpt_stream_t stream);
+
+/* Adam (Kingma and Ba 2015, Algorithm 1) with bias correction, followed by a
+ * projection of the parameter onto [lo, hi]. */
+typedef struct {
+  float lr, beta1, beta2, eps;
+  float lo, hi;
+} eagpt_adam;
+
+/* One Adam step t = step (>= 1) on n parameters (device arrays, updated in
+ * place; m and v start at 0 for step 1).  zero_grad != 0 clears grad after
+ * reading it. */
+eagpt_status eagpt_adam_step(float* param, float* grad, float* m, float* v, int64_t n, const eagpt_adam* cfg,
+                             int64_t step, int32_t zero_grad, eagpt_stream_t stream);
+
+/* The optimisation loop, one call for `iters` steps with no host
+ * synchronisation: per step, view v = view_order[k] (host, iters entries) or,
+ * when view_order is NULL, (first_step + k) mod n_views; render (field 0:
+ * eagpt_render_single_bounce_incident with spp and seed + step; field 1:
+ * eagpt_render_radiance), the PQ-L1 loss against targets[v], the shading
+ * gradient, an Adam step t = first_step + k + 1 on the field (lo/hi
+ * projection), written to the scene and the BVH.  Afterwards scene->version
+ * and bvh->scene_version are both incremented once.
+ *   cams         host, n_views cameras
+ *   targets      host array of n_views device pointers (H_v x W_v x 3)
+ *   m, v         device, n x 3 each: the Adam moments (caller-owned; zero
+ *                before the first step)
+ *   out_loss     device, iters doubles (the loss of each step before its
+ *                update), or NULL
+ *   workspace    eagpt_fit_workspace_bytes(); 256-byte aligned */
+typedef struct {
+  int32_t field;      /* 0 albedo (Eq. 7), 1 radiance (Eq. 10) */
+  int32_t spp;        /* single-bounce samples per pixel (field 0) */
+  uint64_t seed;      /* step t renders with seed + t */
+  float peak;         /* PQ normalisation (see eagpt_pq_l1_loss) */
+  float lambda_c;
+  eagpt_adam adam;
+} eagpt_fit_config;
+
+size_t eagpt_fit_workspace_bytes(const eagpt_fit_config* cfg, const eagpt_camera* cams, int32_t n_views, int64_t n);
+eagpt_status eagpt_fit(const eagpt_fit_config* cfg, eagpt_scene_mut* scene, eagpt_bvh* bvh, const eagpt_params* params,
+                       const eagpt_camera* cams, const float* const* targets, int32_t n_views,
+                       const int32_t* view_order, int64_t first_step, int32_t iters, float* m, float* v,
+                       double* out_loss, void* workspace, size_t workspace_bytes, eagpt_stream_t stream);
+
+/* ------------------------------------------------------------------------
  * Tracing of caller rays (the per-segment operation of Eq. 1-3).
  *   rays     device, n_rays x 6: origin (3), unit direction (3); hits need
  *            t > 0

@@ -320,6 +320,126 @@ def render_radiance(tensors: dict, cam: HostCamera, prm: Optional[capi.Params] =
                              tensors["albedo"], tensors["radiance"], tensors["emissive"], cam, prm)
 
 
+# ---------------------------------------------------------------------------
+# optimisation of the shading parameters (Stage 1, Eq. 7; light baking, Eq. 10)
+# ---------------------------------------------------------------------------
+FIELDS_OPT = {"albedo": 0, "radiance": 1}
+
+
+def single_bounce_incident(scene: DeviceScene, bvh: BVH, cam: HostCamera, spp: int, seed: int = 0,
+                           renderer: Optional[Renderer] = None, prm: Optional[capi.Params] = None,
+                           stream=None) -> dict:
+    """Single-bounce render plus the per-pixel incident radiance estimate
+    L_i = mean_s R(w_s); returns dict(rgb, li)."""
+    renderer = renderer or Renderer(device=scene.t["pos"].device)
+    c = camera(cam)
+    prm = prm or bvh.params
+    ws = renderer._workspace(c, spp, 0)
+    H, W = cam.height, cam.width
+    rgb = torch.empty((H, W, 3), dtype=torch.float32, device=renderer.device)
+    li = torch.empty((H, W, 3), dtype=torch.float32, device=renderer.device)
+    sc = scene.c()
+    capi.check(capi.lib().eagpt_render_single_bounce_incident(
+        ctypes.byref(sc), ctypes.byref(bvh.c()), ctypes.byref(c), ctypes.byref(prm), int(spp),
+        ctypes.c_uint64(int(seed)), _ptr(rgb), _ptr(li), _ptr(ws), ws.numel(), _stream(stream)))
+    return {"rgb": rgb, "li": li}
+
+
+def shading_backward(scene: DeviceScene, bvh: BVH, cam: HostCamera, field: str, dL_drgb: torch.Tensor,
+                     li: Optional[torch.Tensor] = None, grad: Optional[torch.Tensor] = None,
+                     prm: Optional[capi.Params] = None, stream=None) -> torch.Tensor:
+    """Gradient (n, 3), accumulated into ``grad``, of sum(dL_drgb * image) with
+    respect to the albedo (single-bounce image; needs ``li``) or the radiance
+    (0-bounce image)."""
+    if grad is None:
+        grad = torch.zeros((scene.n, 3), dtype=torch.float32, device=scene.t["pos"].device)
+    c = camera(cam)
+    prm = prm or bvh.params
+    dL = dL_drgb.contiguous().to(torch.float32)
+    lic = li.contiguous() if li is not None else None
+    sc = scene.c()
+    capi.check(capi.lib().eagpt_render_shading_backward(ctypes.byref(sc), ctypes.byref(bvh.c()), ctypes.byref(c),
+                                                        ctypes.byref(prm), FIELDS_OPT[field], _ptr(dL), _ptr(lic),
+                                                        _ptr(grad), _stream(stream)))
+    return grad
+
+
+def pq_l1_loss(pred: torch.Tensor, target: torch.Tensor, peak: float = 100.0, lambda_c: float = 1.0,
+               want_grad: bool = True, stream=None):
+    """(loss (device float64 scalar tensor), dL/dpred or None) of
+    lambda_c * mean |PQ(pred / peak) - PQ(target / peak)|."""
+    pred = pred.contiguous()
+    target = target.contiguous()
+    n = pred.numel()
+    dev = pred.device
+    L = capi.lib()
+    scratch = torch.empty(max(L.eagpt_pq_l1_scratch_bytes(n) // 8, 1), dtype=torch.float64, device=dev)
+    loss = torch.empty((), dtype=torch.float64, device=dev)
+    grad = torch.empty_like(pred) if want_grad else None
+    capi.check(L.eagpt_pq_l1_loss(_ptr(pred), _ptr(target), n, float(peak), float(lambda_c), _ptr(grad), _ptr(loss),
+                                  _ptr(scratch), scratch.numel() * 8, _stream(stream)))
+    return loss, grad
+
+
+def adam_config(lr=0.01, beta1=0.9, beta2=0.999, eps=1e-8, lo=-float("inf"), hi=float("inf")) -> capi.Adam:
+    a = capi.Adam()
+    a.lr, a.beta1, a.beta2, a.eps, a.lo, a.hi = lr, beta1, beta2, eps, lo, hi
+    return a
+
+
+def adam_step(param: torch.Tensor, grad: torch.Tensor, m: torch.Tensor, v: torch.Tensor, step: int,
+              cfg: Optional[capi.Adam] = None, zero_grad: bool = False, stream=None) -> None:
+    """One Adam step t = step, in place on contiguous float32 tensors."""
+    cfg = cfg or adam_config()
+    capi.check(capi.lib().eagpt_adam_step(_ptr(param), _ptr(grad), _ptr(m), _ptr(v), param.numel(),
+                                          ctypes.byref(cfg), int(step), int(zero_grad), _stream(stream)))
+
+
+class ShadingFit:
+    """The native optimisation loop (eagpt_fit) over one field: 'albedo'
+    (Stage 1, Eq. 7, single-bounce render at ``spp``) or 'radiance' (light
+    baking, Eq. 10, 0-bounce render).  Keeps the Adam moments, the step count
+    and the workspace between calls."""
+
+    def __init__(self, scene: DeviceScene, bvh: BVH, cams, targets, field: str, spp: int = 1, seed: int = 0,
+                 peak: float = 100.0, lambda_c: float = 1.0, adam: Optional[capi.Adam] = None):
+        self.scene, self.bvh = scene, bvh
+        self.cfg = capi.FitConfig()
+        self.cfg.field = FIELDS_OPT[field]
+        self.cfg.spp = int(spp)
+        self.cfg.seed = int(seed)
+        self.cfg.peak = float(peak)
+        self.cfg.lambda_c = float(lambda_c)
+        if adam is None:
+            adam = adam_config(lr=0.01, lo=0.0, hi=1.0) if field == "albedo" else adam_config(lr=0.01, lo=0.0)
+        self.cfg.adam = adam
+        self.cams = (capi.Camera * len(cams))(*[camera(c) for c in cams])
+        self.targets = [t.contiguous().to(torch.float32) for t in targets]
+        self.tptrs = (ctypes.c_void_p * len(cams))(*[t.data_ptr() for t in self.targets])
+        dev = scene.t["pos"].device
+        self.m = torch.zeros((scene.n, 3), dtype=torch.float32, device=dev)
+        self.v = torch.zeros((scene.n, 3), dtype=torch.float32, device=dev)
+        self.step = 0
+        need = capi.lib().eagpt_fit_workspace_bytes(ctypes.byref(self.cfg), self.cams, len(cams), scene.n)
+        self.ws = torch.empty(max(need, 256), dtype=torch.uint8, device=dev)
+
+    def run(self, iters: int, view_order=None, stream=None) -> torch.Tensor:
+        """Runs ``iters`` steps; returns the per-step losses (device float64)."""
+        dev = self.scene.t["pos"].device
+        losses = torch.empty(max(iters, 1), dtype=torch.float64, device=dev)
+        order = None
+        if view_order is not None:
+            order = (ctypes.c_int32 * iters)(*[int(x) for x in view_order])
+        sm = self.scene.c()
+        capi.check(capi.lib().eagpt_fit(ctypes.byref(self.cfg), ctypes.byref(sm), ctypes.byref(self.bvh.handle),
+                                        ctypes.byref(self.bvh.params), self.cams, self.tptrs, len(self.targets),
+                                        order, int(self.step), int(iters), _ptr(self.m), _ptr(self.v),
+                                        _ptr(losses), _ptr(self.ws), self.ws.numel(), _stream(stream)))
+        self.scene.version = int(sm.version)
+        self.step += iters
+        return losses[:iters]
+
+
 EDIT_OPS = {"set_emission": 0, "toggle_emission": 1, "scale_albedo": 2, "translate": 3, "rigid": 4}
 
 

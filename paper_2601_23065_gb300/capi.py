@@ -89,6 +89,15 @@ class ServerStats(ctypes.Structure):
                 ("busy_s", ctypes.c_double), ("arena_free_bytes", c_i64)]
 
 
+class Adam(ctypes.Structure):
+    _fields_ = [("lr", c_f), ("beta1", c_f), ("beta2", c_f), ("eps", c_f), ("lo", c_f), ("hi", c_f)]
+
+
+class FitConfig(ctypes.Structure):
+    _fields_ = [("field", c_i32), ("spp", c_i32), ("seed", c_u64), ("peak", c_f), ("lambda_c", c_f),
+                ("adam", Adam)]
+
+
 REQ_STATES = {0: "queued", 1: "running", 2: "done", 3: "failed", 4: "cancelled", 5: "timed_out"}
 
 # symbol -> (restype, argtypes)
@@ -127,6 +136,16 @@ SIGNATURES = {
                                                     P(SceneGrad), c_vp, c_sz, c_vp]),
     "eagpt_render_radiance": (c_i32, [P(Scene), P(Bvh), P(Camera), P(Params), c_vp, c_vp, c_vp]),
     "eagpt_render_radiance_backward": (c_i32, [P(Scene), P(Bvh), P(Camera), P(Params), c_vp, P(SceneGrad), c_vp]),
+    "eagpt_render_single_bounce_incident": (c_i32, [P(Scene), P(Bvh), P(Camera), P(Params), c_i32, c_u64, c_vp,
+                                                    c_vp, c_vp, c_sz, c_vp]),
+    "eagpt_render_shading_backward": (c_i32, [P(Scene), P(Bvh), P(Camera), P(Params), c_i32, c_vp, c_vp, c_vp,
+                                              c_vp]),
+    "eagpt_pq_l1_scratch_bytes": (c_sz, [c_i64]),
+    "eagpt_pq_l1_loss": (c_i32, [c_vp, c_vp, c_i64, c_f, c_f, c_vp, c_vp, c_vp, c_sz, c_vp]),
+    "eagpt_adam_step": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_i64, P(Adam), c_i64, c_i32, c_vp]),
+    "eagpt_fit_workspace_bytes": (c_sz, [P(FitConfig), c_vp, c_i32, c_i64]),
+    "eagpt_fit": (c_i32, [P(FitConfig), P(Scene), P(Bvh), P(Params), c_vp, c_vp, c_i32, c_vp, c_i64, c_i32,
+                          c_vp, c_vp, c_vp, c_vp, c_sz, c_vp]),
     "eagpt_sync_status": (c_i32, [c_vp]),
     "eagpt_launch_count": (c_i64, []),
     "eagpt_profile_begin": (c_i32, []),

@@ -190,7 +190,8 @@ extern "C" {
 static eagpt_status render_common(const eagpt_scene* scene, const eagpt_bvh* bvh, const eagpt_camera* cam,
                                   const eagpt_params* params, int kind, int32_t spp, int32_t max_bounces,
                                   int32_t rr_start, uint64_t seed, float* out_rgb, float* out_aux, float* out_samples,
-                                  int64_t* out_stats, void* ws, size_t ws_bytes, eagpt_stream_t stream) {
+                                  int64_t* out_stats, void* ws, size_t ws_bytes, eagpt_stream_t stream,
+                                  float* out_li = nullptr) {
   eagpt_status s;
   if ((s = check_scene(scene)) != EAGPT_OK) return s;
   if ((s = check_params(params)) != EAGPT_OK) return s;
@@ -209,7 +210,8 @@ static eagpt_status render_common(const eagpt_scene* scene, const eagpt_bvh* bvh
   a.bvh = make_view(*bvh);
   a.C = make_consts(*params);
   a.cam = *cam;
-  a.kind = kind;
+  a.kind = kind == 0 && out_li ? 2 : kind;
+  a.out_li = out_li;
   a.spp = spp;
   a.max_bounces = kind == 0 ? 1 : max_bounces;
   a.rr_start = kind == 0 ? (1 << 30) : rr_start;
@@ -245,6 +247,15 @@ eagpt_status eagpt_render_single_bounce(const eagpt_scene* scene, const eagpt_bv
                                         eagpt_stream_t stream) {
   return render_common(scene, bvh, cam, params, 0, spp, 1, 1 << 30, seed, out_rgb, out_aux, out_samples, nullptr,
                        workspace, workspace_bytes, stream);
+}
+
+eagpt_status eagpt_render_single_bounce_incident(const eagpt_scene* scene, const eagpt_bvh* bvh,
+                                                 const eagpt_camera* cam, const eagpt_params* params, int32_t spp,
+                                                 uint64_t seed, float* out_rgb, float* out_li, void* workspace,
+                                                 size_t workspace_bytes, eagpt_stream_t stream) {
+  if (!out_li) return fail(EAGPT_ERR_INVALID_ARGUMENT, "out_li is NULL%s");
+  return render_common(scene, bvh, cam, params, 0, spp, 1, 1 << 30, seed, out_rgb, nullptr, nullptr, nullptr,
+                       workspace, workspace_bytes, stream, out_li);
 }
 
 eagpt_status eagpt_render_path_traced(const eagpt_scene* scene, const eagpt_bvh* bvh, const eagpt_camera* cam,
@@ -455,13 +466,232 @@ eagpt_status eagpt_sync_status(eagpt_stream_t stream) {
   if (e != cudaSuccess) return cuda_fail(e, "sync");
   const uint32_t word =
       take_errors_bvh() | take_errors_render() | take_errors_backward() | take_errors_tree() | take_errors_edit() |
-      take_errors_serve();
+      take_errors_serve() | take_errors_optim();
   if (word) {
     char buf[128];
     std::snprintf(buf, sizeof(buf), "device check failed (error bits 0x%x)", word);
     g_msg = buf;
     return EAGPT_ERR_DEVICE_CHECK;
   }
+  return EAGPT_OK;
+}
+
+}  // extern "C"
+
+// --------------------------------------------------------------------------
+// optimisation of the shading parameters (Eq. 7, Eq. 10)
+// --------------------------------------------------------------------------
+namespace {
+
+inline size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct FitLayout {
+  size_t pred, li, dL, grad, partials, render, total;
+};
+
+FitLayout fit_layout(int field, int64_t npix_max, int64_t n, size_t render_bytes) {
+  FitLayout L{};
+  size_t o = 0;
+  const size_t img = up256((size_t)npix_max * 3 * sizeof(float));
+  L.pred = o;
+  o += img;
+  L.li = o;
+  if (field == 0) o += img;
+  L.dL = o;
+  o += img;
+  L.grad = o;
+  o += up256((size_t)(n > 0 ? n : 1) * 3 * sizeof(float));
+  L.partials = o;
+  o += up256((size_t)pq_partials(3 * npix_max) * sizeof(double) + sizeof(double));
+  L.render = o;
+  o += render_bytes;
+  L.total = o;
+  return L;
+}
+
+eagpt_status check_adam(const eagpt_adam* a) {
+  if (!a) return fail(EAGPT_ERR_INVALID_ARGUMENT, "adam config is NULL%s");
+  if (!(a->lr > 0.f && std::isfinite(a->lr))) return fail(EAGPT_ERR_INVALID_ARGUMENT, "adam.lr must be > 0%s");
+  if (!(a->beta1 >= 0.f && a->beta1 < 1.f && a->beta2 >= 0.f && a->beta2 < 1.f))
+    return fail(EAGPT_ERR_INVALID_ARGUMENT, "adam betas must be in [0, 1)%s");
+  if (!(a->eps > 0.f && std::isfinite(a->eps))) return fail(EAGPT_ERR_INVALID_ARGUMENT, "adam.eps must be > 0%s");
+  if (!(a->lo <= a->hi)) return fail(EAGPT_ERR_INVALID_ARGUMENT, "adam.lo must be <= adam.hi%s");
+  return EAGPT_OK;
+}
+
+eagpt_status check_fit(const eagpt_fit_config* c) {
+  if (!c) return fail(EAGPT_ERR_INVALID_ARGUMENT, "fit config is NULL%s");
+  if (c->field != 0 && c->field != 1) return fail(EAGPT_ERR_INVALID_ARGUMENT, "field must be 0 or 1%s");
+  if (c->field == 0 && (c->spp <= 0 || c->spp > (1 << 24)))
+    return fail(EAGPT_ERR_INVALID_ARGUMENT, "spp must be in [1, 2^24]%s");
+  if (!(c->peak > 0.f && std::isfinite(c->peak))) return fail(EAGPT_ERR_INVALID_ARGUMENT, "peak must be > 0%s");
+  if (!std::isfinite(c->lambda_c)) return fail(EAGPT_ERR_INVALID_ARGUMENT, "lambda_c must be finite%s");
+  return check_adam(&c->adam);
+}
+
+size_t fit_render_bytes(const eagpt_fit_config* cfg, int64_t npix_max, bool full) {
+  if (cfg->field != 0) return 0;
+  int64_t batch = cfg->spp;
+  const int64_t cap = (int64_t)1 << 27;
+  if (!full) batch = 1;
+  else if (npix_max * batch > cap) batch = cap / npix_max > 0 ? cap / npix_max : 1;
+  return render_layout(npix_max, cfg->spp, (int)batch).total;
+}
+
+}  // namespace
+
+extern "C" {
+
+eagpt_status eagpt_render_shading_backward(const eagpt_scene* scene, const eagpt_bvh* bvh, const eagpt_camera* cam,
+                                           const eagpt_params* params, int32_t field, const float* dL_drgb,
+                                           const float* li, float* grad, eagpt_stream_t stream) {
+  eagpt_status s;
+  if ((s = check_scene(scene)) != EAGPT_OK) return s;
+  if ((s = check_params(params)) != EAGPT_OK) return s;
+  if ((s = check_camera(cam)) != EAGPT_OK) return s;
+  if ((s = check_bvh(bvh, scene, params)) != EAGPT_OK) return s;
+  if (field != 0 && field != 1) return fail(EAGPT_ERR_INVALID_ARGUMENT, "field must be 0 (albedo) or 1 (radiance)%s");
+  if (field == 0 && !li) return fail(EAGPT_ERR_INVALID_ARGUMENT, "the albedo gradient needs li%s");
+  if (field == 1 && li) return fail(EAGPT_ERR_INVALID_ARGUMENT, "li must be NULL for the radiance gradient%s");
+  if (!dL_drgb) return fail(EAGPT_ERR_INVALID_ARGUMENT, "dL_drgb is NULL%s");
+  if (scene->n > 0 && !grad) return fail(EAGPT_ERR_INVALID_ARGUMENT, "grad is NULL%s");
+  if (scene->n == 0) return EAGPT_OK;
+  cudaError_t e = launch_shade_adjoint(make_view(*bvh), make_consts(*params), *cam, dL_drgb, li, grad,
+                                       (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "shading backward launch");
+  return EAGPT_OK;
+}
+
+size_t eagpt_pq_l1_scratch_bytes(int64_t n) {
+  if (n < 0) return 0;
+  return (size_t)(pq_partials(n) + 1) * sizeof(double);
+}
+
+eagpt_status eagpt_pq_l1_loss(const float* pred, const float* target, int64_t n, float peak, float lambda_c,
+                              float* out_grad, double* out_loss, void* scratch, size_t scratch_bytes,
+                              eagpt_stream_t stream) {
+  if (n < 0) return fail(EAGPT_ERR_INVALID_ARGUMENT, "n must be >= 0%s");
+  if (n > 0 && (!pred || !target)) return fail(EAGPT_ERR_INVALID_ARGUMENT, "pred and target are required%s");
+  if (!(peak > 0.f && std::isfinite(peak))) return fail(EAGPT_ERR_INVALID_ARGUMENT, "peak must be > 0%s");
+  if (!std::isfinite(lambda_c)) return fail(EAGPT_ERR_INVALID_ARGUMENT, "lambda_c must be finite%s");
+  if (n > 0 && (!scratch || !aligned(scratch, 8) || scratch_bytes < eagpt_pq_l1_scratch_bytes(n)))
+    return fail(EAGPT_ERR_OUT_OF_MEMORY, "scratch too small or misaligned%s");
+  cudaError_t e = launch_pq_l1(pred, target, n, peak, lambda_c, out_grad, out_loss, (double*)scratch,
+                               (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "pq_l1 launch");
+  return EAGPT_OK;
+}
+
+eagpt_status eagpt_adam_step(float* param, float* grad, float* m, float* v, int64_t n, const eagpt_adam* cfg,
+                             int64_t step, int32_t zero_grad, eagpt_stream_t stream) {
+  eagpt_status s;
+  if ((s = check_adam(cfg)) != EAGPT_OK) return s;
+  if (n < 0 || step < 1) return fail(EAGPT_ERR_INVALID_ARGUMENT, "n must be >= 0 and step >= 1%s");
+  if (n > 0 && (!param || !grad || !m || !v)) return fail(EAGPT_ERR_INVALID_ARGUMENT, "every array is required%s");
+  cudaError_t e = launch_adam(param, grad, m, v, n, *cfg, step, zero_grad != 0, nullptr, nullptr, 0,
+                              (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "adam launch");
+  return EAGPT_OK;
+}
+
+size_t eagpt_fit_workspace_bytes(const eagpt_fit_config* cfg, const eagpt_camera* cams, int32_t n_views, int64_t n) {
+  if (!cfg || !cams || n_views <= 0 || n < 0 || (cfg->field != 0 && cfg->field != 1)) return 0;
+  if (cfg->field == 0 && cfg->spp <= 0) return 0;
+  int64_t npix = 0;
+  for (int v = 0; v < n_views; ++v) {
+    if (cams[v].width <= 0 || cams[v].height <= 0) return 0;
+    const int64_t p = (int64_t)cams[v].width * cams[v].height;
+    npix = p > npix ? p : npix;
+  }
+  return fit_layout(cfg->field, npix, n, fit_render_bytes(cfg, npix, true)).total;
+}
+
+eagpt_status eagpt_fit(const eagpt_fit_config* cfg, eagpt_scene_mut* scene, eagpt_bvh* bvh, const eagpt_params* params,
+                       const eagpt_camera* cams, const float* const* targets, int32_t n_views,
+                       const int32_t* view_order, int64_t first_step, int32_t iters, float* m, float* v,
+                       double* out_loss, void* ws, size_t ws_bytes, eagpt_stream_t stream) {
+  eagpt_status s;
+  if ((s = check_fit(cfg)) != EAGPT_OK) return s;
+  if (!scene) return fail(EAGPT_ERR_INVALID_ARGUMENT, "scene is NULL%s");
+  eagpt_scene cs;
+  std::memcpy(&cs, scene, sizeof(cs));
+  if ((s = check_scene(&cs)) != EAGPT_OK) return s;
+  if ((s = check_params(params)) != EAGPT_OK) return s;
+  if ((s = check_bvh(bvh, &cs, params)) != EAGPT_OK) return s;
+  if (n_views <= 0 || !cams || !targets) return fail(EAGPT_ERR_INVALID_ARGUMENT, "need n_views >= 1 cameras and targets%s");
+  if (iters < 0 || first_step < 0) return fail(EAGPT_ERR_INVALID_ARGUMENT, "iters and first_step must be >= 0%s");
+  int64_t npix_max = 0;
+  for (int k = 0; k < n_views; ++k) {
+    if ((s = check_camera(&cams[k])) != EAGPT_OK) return s;
+    if (!targets[k]) return fail(EAGPT_ERR_INVALID_ARGUMENT, "targets[%s%lld] is NULL", "", k);
+    const int64_t p = (int64_t)cams[k].width * cams[k].height;
+    npix_max = p > npix_max ? p : npix_max;
+  }
+  if (view_order)
+    for (int k = 0; k < iters; ++k)
+      if (view_order[k] < 0 || view_order[k] >= n_views)
+        return fail(EAGPT_ERR_INVALID_ARGUMENT, "view_order[%s%lld] out of range", "", k);
+  if (cs.n > 0 && (!m || !v)) return fail(EAGPT_ERR_INVALID_ARGUMENT, "adam moments m and v are required%s");
+  if (!ws || !aligned(ws, 256)) return fail(EAGPT_ERR_INVALID_ARGUMENT, "workspace must be non-NULL and 256-byte aligned%s");
+  const size_t need_min = fit_layout(cfg->field, npix_max, cs.n, fit_render_bytes(cfg, npix_max, false)).total;
+  if (ws_bytes < need_min)
+    return fail(EAGPT_ERR_OUT_OF_MEMORY, "workspace too small: need at least %s%lld bytes", "", (long long)need_min);
+  if (iters == 0 || cs.n == 0) return EAGPT_OK;
+
+  cudaStream_t st = (cudaStream_t)stream;
+  const FitLayout L = fit_layout(cfg->field, npix_max, cs.n, 0);
+  char* base = (char*)ws;
+  float* pred = (float*)(base + L.pred);
+  float* li = cfg->field == 0 ? (float*)(base + L.li) : nullptr;
+  float* dL = (float*)(base + L.dL);
+  float* grad = (float*)(base + L.grad);
+  double* partials = (double*)(base + L.partials);
+  void* rws = base + L.render;
+  const size_t rws_bytes = ws_bytes - L.render;
+  const BvhView view = make_view(*bvh);
+  const Consts C = make_consts(*params);
+  const BvhLayout BL = bvh_layout(cs.n);
+  float* mirror = (float*)((char*)bvh->storage + BL.shade);
+  const uint32_t* inv_idx = (const uint32_t*)((char*)bvh->storage + BL.inv_idx);
+  float* field_ptr = cfg->field == 0 ? scene->albedo : scene->radiance;
+  const int mirror_field = cfg->field == 0 ? 0 : 4;
+  const int64_t np = cs.n * 3;
+
+  cudaError_t e = cudaMemsetAsync(grad, 0, (size_t)np * sizeof(float), st);
+  for (int k = 0; k < iters && e == cudaSuccess; ++k) {
+    const int64_t t = first_step + k + 1;
+    const int vi = view_order ? view_order[k] : (int)((first_step + k) % n_views);
+    const eagpt_camera& cam = cams[vi];
+    const int64_t npix = (int64_t)cam.width * cam.height;
+    if (cfg->field == 0) {
+      if (choose_batch_spp(npix, cfg->spp, rws_bytes) < 1) return fail(EAGPT_ERR_OUT_OF_MEMORY, "render workspace%s");
+      RenderArgs a{};
+      a.bvh = view;
+      a.C = C;
+      a.cam = cam;
+      a.kind = 2;
+      a.spp = cfg->spp;
+      a.max_bounces = 1;
+      a.rr_start = 1 << 30;
+      a.seed = cfg->seed + (uint64_t)t;
+      a.out_rgb = pred;
+      a.out_li = li;
+      a.ws = rws;
+      a.ws_bytes = rws_bytes;
+      e = launch_render(a, st, nullptr);
+    } else {
+      e = launch_radiance(view, C, cam, pred, nullptr, st);
+    }
+    if (e == cudaSuccess)
+      e = launch_pq_l1(pred, targets[vi], 3 * npix, cfg->peak, cfg->lambda_c, dL, out_loss ? out_loss + k : nullptr,
+                       partials, st);
+    if (e == cudaSuccess) e = launch_shade_adjoint(view, C, cam, dL, li, grad, st);
+    if (e == cudaSuccess)
+      e = launch_adam(field_ptr, grad, m, v, np, cfg->adam, t, 1, mirror, inv_idx, mirror_field, st);
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "fit launch");
+  scene->version += 1;
+  bvh->scene_version = scene->version;
   return EAGPT_OK;
 }
 

@@ -24,12 +24,13 @@ struct RenderArgs {
   BvhView bvh;
   Consts C;
   eagpt_camera cam;
-  int kind;         // 0 single bounce, 1 path tracing
+  int kind;         // 0 single bounce, 1 path tracing, 2 single bounce with incident radiance (out_li)
   int spp, max_bounces, rr_start;
   uint64_t seed;
   float* out_rgb;
   float* out_aux;
   float* out_samples;
+  float* out_li;
   int64_t* out_stats;
   void* ws;
   size_t ws_bytes;
@@ -63,6 +64,15 @@ cudaError_t launch_backward(const BvhView& bvh, const Consts& C, const eagpt_cam
                             const eagpt_scene_grad& gr, int spp, uint64_t seed, const float* dL, void* ws,
                             size_t ws_bytes, cudaStream_t st);
 
+// optim.cu
+int64_t pq_partials(int64_t n);
+cudaError_t launch_pq_l1(const float* pred, const float* target, int64_t n, float peak, float lambda_c, float* grad,
+                         double* out_loss, double* partials, cudaStream_t st);
+cudaError_t launch_shade_adjoint(const BvhView& bvh, const Consts& C, const eagpt_camera& cam, const float* dL,
+                                 const float* li, float* grad, cudaStream_t st);
+cudaError_t launch_adam(float* p, float* g, float* m, float* v, int64_t n, const eagpt_adam& cfg, int64_t step,
+                        int zero_grad, float* mirror, const uint32_t* inv_idx, int field, cudaStream_t st);
+
 // device error words of each translation unit (read and cleared)
 uint32_t take_errors_bvh();
 uint32_t take_errors_render();
@@ -70,6 +80,7 @@ uint32_t take_errors_backward();
 uint32_t take_errors_tree();
 uint32_t take_errors_edit();
 uint32_t take_errors_serve();
+uint32_t take_errors_optim();
 
 // edit.cu
 cudaError_t launch_select(const eagpt_scene& sc, int shape, const float* v, int32_t* out, int64_t capacity,

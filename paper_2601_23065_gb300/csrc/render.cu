@@ -192,7 +192,7 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_bounce(BvhView bvh, Cons
   __shared__ uint32_t s_stack[kStackSize * kBlock];
   const int lane = threadIdx.x & 31;
   const uint32_t count = counters[2 * k];
-  const int mode = kind == 0 ? 0 : 1;
+  const int mode = kind == 1 ? 1 : 0;
   TraceCounters cnt{0, 0, 0, 0, 0};
   uint32_t traced = 0;
   for (;;) {
@@ -232,11 +232,14 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_bounce(BvhView bvh, Cons
 }
 
 // Per pixel: add the batch's samples in order; on the last batch write the
-// mean.  Emitter pixels show R (Eq. 4), missed pixels 0.
+// mean.  Emitter pixels show R (Eq. 4), missed pixels 0.  With out_li (the
+// incident-radiance variant of the single-bounce render) the slots hold the
+// secondary radiance R(w_s) alone: L_i = mean_s R(w_s) is written to out_li
+// and P (.) L_i to out_rgb; emitter and missed pixels get L_i = 0.
 __global__ void __launch_bounds__(kBlock) k_accumulate(const PrimRec* __restrict__ prim, Consts C, int64_t npix,
                                                        int s0, int batch, int spp, int first, int last,
                                                        const float4* __restrict__ slots, float4* acc,
-                                                       float* out_rgb, float* out_samples) {
+                                                       float* out_rgb, float* out_samples, float* out_li) {
   const int64_t i = blockIdx.x * (int64_t)kBlock + threadIdx.x;
   if (i >= npix) return;
   const PrimRec p = prim[i];
@@ -244,6 +247,11 @@ __global__ void __launch_bounds__(kBlock) k_accumulate(const PrimRec* __restrict
   const bool emit = hit && p.b.w > C.tau_E;
   if (!hit || emit) {
     const float3 v = emit ? f3(p.b) : make_float3(0.f, 0.f, 0.f);
+    if (out_li && last) {
+      out_li[3 * i] = 0.f;
+      out_li[3 * i + 1] = 0.f;
+      out_li[3 * i + 2] = 0.f;
+    }
     if (out_samples)
       for (int s = 0; s < batch; ++s) {
         float* o = out_samples + 3 * (i * spp + s0 + s);
@@ -259,6 +267,7 @@ __global__ void __launch_bounds__(kBlock) k_accumulate(const PrimRec* __restrict
     return;
   }
   float4 a = first ? make_float4(0.f, 0.f, 0.f, 0.f) : acc[i];
+  const float3 P = out_li ? make_float3(p.c.x, p.c.y, p.c.z) : make_float3(1.f, 1.f, 1.f);
   for (int s = 0; s < batch; ++s) {
     const float4 c = slots[(int64_t)s * npix + i];
     a.x += c.x;
@@ -266,16 +275,26 @@ __global__ void __launch_bounds__(kBlock) k_accumulate(const PrimRec* __restrict
     a.z += c.z;
     if (out_samples) {
       float* o = out_samples + 3 * (i * spp + s0 + s);
-      o[0] = c.x;
-      o[1] = c.y;
-      o[2] = c.z;
+      o[0] = out_li ? P.x * c.x : c.x;
+      o[1] = out_li ? P.y * c.y : c.y;
+      o[2] = out_li ? P.z * c.z : c.z;
     }
   }
   if (last) {
     const float inv = 1.f / (float)spp;
-    out_rgb[3 * i] = a.x * inv;
-    out_rgb[3 * i + 1] = a.y * inv;
-    out_rgb[3 * i + 2] = a.z * inv;
+    if (out_li) {
+      const float3 li = make_float3(a.x * inv, a.y * inv, a.z * inv);
+      out_li[3 * i] = li.x;
+      out_li[3 * i + 1] = li.y;
+      out_li[3 * i + 2] = li.z;
+      out_rgb[3 * i] = P.x * li.x;
+      out_rgb[3 * i + 1] = P.y * li.y;
+      out_rgb[3 * i + 2] = P.z * li.z;
+    } else {
+      out_rgb[3 * i] = a.x * inv;
+      out_rgb[3 * i + 1] = a.y * inv;
+      out_rgb[3 * i + 2] = a.z * inv;
+    }
   } else {
     acc[i] = a;
   }
@@ -354,8 +373,8 @@ static cudaError_t render_impl(const RenderArgs& a, cudaStream_t st, int* launch
   float4* slots = (float4*)(ws + L.slots);
   Ray* q[2] = {(Ray*)(ws + L.q0), (Ray*)(ws + L.q1)};
   uint32_t* counters = (uint32_t*)(ws + L.counters);
-  const int mode = a.kind == 0 ? 0 : 1;
-  const int B = a.kind == 0 ? 1 : a.max_bounces;
+  const int mode = a.kind == 1 ? 1 : 0;
+  const int B = a.kind == 1 ? a.max_bounces : 1;
   int nl = 0;
   EAGPT_LAUNCH(st, "k_primary", k_primary<kCount><<<nblocks(npix), kBlock, 0, st>>>(a.bvh, a.C, a.cam, mode, npix, prim, a.out_aux, a.out_stats));
   ++nl;
@@ -384,7 +403,7 @@ static cudaError_t render_impl(const RenderArgs& a, cudaStream_t st, int* launch
       ++nl;
     }
     EAGPT_LAUNCH(st, "k_accumulate", k_accumulate<<<nblocks(npix), kBlock, 0, st>>>(prim, a.C, npix, s0, nb, a.spp, s0 == 0, s0 + nb >= a.spp, slots,
-                                                   acc, a.out_rgb, a.out_samples));
+                                                   acc, a.out_rgb, a.out_samples, a.kind == 2 ? a.out_li : nullptr));
     ++nl;
   }
   if (launches) *launches += nl;

@@ -31,8 +31,10 @@ __device__ __forceinline__ bool prim_is_path_start(const PrimRec& p, const Const
 __device__ __forceinline__ bool first_bounce(const PrimRec& p, const Consts& C, const eagpt_camera& cam, int kind,
                                              int max_bounces, int rr_start, uint64_t seed, uint32_t pixel,
                                              uint32_t sample, uint32_t tag, Ray& r) {
-  const int B = kind == 0 ? 1 : max_bounces;
-  float3 beta = make_float3(p.c.x, p.c.y, p.c.z);
+  const int B = kind == 1 ? max_bounces : 1;
+  // kind 2 (single bounce, incident radiance): unit throughput, P is applied
+  // per pixel after the sample mean
+  float3 beta = kind == 2 ? make_float3(1.f, 1.f, 1.f) : make_float3(p.c.x, p.c.y, p.c.z);
   if (B < 1) return false;
   const float4 u = draws(seed, pixel, sample, 1u);
   if (kind == 1 && rr_start <= 1) {
@@ -62,7 +64,7 @@ __device__ __forceinline__ bool shade_bounce(int kind, int k, int max_bounces, i
   const uint32_t pixel = __float_as_uint(r.a.w), sample = __float_as_uint(r.b.w);
   float3 beta = f3(r.c);
   contrib = make_float3(0.f, 0.f, 0.f);
-  if (kind == 0) {
+  if (kind != 1) {
     contrib = mul3(beta, s.R);  // the secondary's radiance is the cache
     return false;
   }
