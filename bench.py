@@ -6,7 +6,9 @@ segments, then per-bounce trace/shade/compact waves, then the deterministic
 accumulation).  Default workload: the medium room (200k surfels, 512x512,
 64 spp, up to 4 bounces, Russian roulette from bounce 2).
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload medium|large|tiny]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload medium|large|tiny|diff]
+  python bench.py --workload serving [--requests R]   (continuous-batching server)
+  python bench.py --workload stage1|bake [--views V]  (Eq. 7 / Eq. 10 optimisation loops)
   python bench.py --impl reference ...    (the FP64 CPU oracle on a bounded sample)
 
 Prints one JSON line (rank 0).  With N > 1 every rank renders its own share
@@ -38,7 +40,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--workload", default="medium", choices=["tiny", "medium", "diff", "large", "serving"])
+    ap.add_argument("--workload", default="medium",
+                    choices=["tiny", "medium", "diff", "large", "serving", "stage1", "bake"])
+    ap.add_argument("--views", type=int, default=8, help="stage1/bake: training views")
     ap.add_argument("--requests", type=int, default=16, help="serving: requests in the stream")
     ap.add_argument("--spp", type=int, default=None, help="override samples per pixel")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -176,6 +180,18 @@ def run_reference(args, rank, world):
     if rank != 0:
         return
     from paper_2601_23065_gb300 import scenes as S
+    if args.workload in ("stage1", "bake"):
+        field = 0 if args.workload == "stage1" else 1
+        spp = args.spp or (256 if field == 0 else 1)
+        cam = fit_views(1)[0]
+        c = fit_cpu_baseline(S.diff_room(), cam, field, spp, args.cpu_seconds)
+        line = {"metric": "Stage-1 iterations/s" if field == 0 else "light-baking iterations/s",
+                "value": c["value"], "unit": c["unit"], "impl": "reference", "n_gpus": world, "steps": 1,
+                "warmup": 0, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic", "config": {"workload": args.workload}, "cpu_baseline": c,
+                "e2e": {"value": c["value"], "unit": c["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return
     wl = S.workload(args.workload)
     if args.spp:
         wl.spp = args.spp
@@ -309,11 +325,174 @@ def run_serving(args):
     print(json.dumps(line), flush=True)
 
 
+# bytes of one BVH4 node visit (six float4 child-box planes + four links, 128 B)
+NODE_BYTES = 128
+
+
+def fit_views(n_views, width=540, height=360):
+    """Training views inside the 1M-surfel room: cameras on a ring of radius
+    1 m around the centre, looking outward and slightly down (the paper
+    optimises at 540x360)."""
+    import math
+
+    from paper_2601_23065_gb300 import scenes as S
+    cams = []
+    for k in range(n_views):
+        a = 2 * math.pi * k / n_views
+        c = (math.cos(a), math.sin(a), 0.2)
+        f = (math.cos(a + 0.4), math.sin(a + 0.4), -0.15)
+        cams.append(S.look_at_camera(width, height, 75.0, c, f, (0.0, 0.0, 1.0)))
+    return cams
+
+
+def fit_cpu_baseline(scene, cam, field, spp, seconds):
+    """The oracle's step (render + PQ-L1 + gradient of the field) on a
+    bounded random-pixel sample of one view, scaled to iterations/s of the
+    full view."""
+    import numpy as np
+
+    import oracle as O
+    from oracle import optim as OP
+    rng = np.random.default_rng(321)
+    osc = O.OracleScene(scene)
+    npix = cam.width * cam.height
+    n_threads = O.default_threads()
+    m, total_t, total_pix = 2, 0.0, 0
+    while True:
+        pix = rng.choice(npix, m, replace=False).astype(np.int32)
+        t0 = time.perf_counter()
+        if field == 0:
+            img = O.render(osc, cam, pix, "single", spp, seed=1, params=O.Params(fp32_eps=0.0),
+                           n_threads=n_threads)["rgb"]
+            _, dL = OP.pq_l1(img, img * 0.9, 100.0)
+            O.single_bounce_grad(osc, cam, pix, dL.reshape(-1, 3), spp, seed=1, n_threads=n_threads)
+        else:
+            img = O.primary(osc, cam, pix, mode=0, n_threads=n_threads)[0][:, 4:7]
+            _, dL = OP.pq_l1(img, img * 0.9, 100.0)
+            O.radiance_grad(osc, cam, pix, dL.reshape(-1, 3), n_threads=n_threads)
+        dt = time.perf_counter() - t0
+        total_t += dt
+        total_pix += m
+        if total_t >= seconds or m >= 4096:
+            break
+        m = int(min(4096, max(m * 2, m * seconds / max(dt, 1e-3) / 2)))
+    per_iter = total_t / total_pix * npix
+    what = f"single bounce {spp} spp + full FP64 adjoint" if field == 0 else "0-bounce + FP64 adjoint"
+    return {"value": 1.0 / per_iter, "unit": "iterations/s", "cores": n_threads, "kind": "oracle",
+            "sample": f"{total_pix} random pixels of one {cam.width}x{cam.height} view ({what}, brute force "
+                      f"over {scene.n} surfels) in {total_t:.1f} s, scaled to the full view"}
+
+
+def run_fit(args):
+    """Stage 1 (Eq. 7, albedo through the single-bounce render) or light
+    baking (Eq. 10, radiance through the 0-bounce render) on the 1M-surfel
+    room with 540x360 training views.  One step = one optimisation
+    iteration (render, PQ-L1 loss and gradient, shading adjoint, Adam,
+    BVH shade-record update) through the native loop."""
+    import numpy as np
+    import torch
+
+    from paper_2601_23065_gb300 import api, build, capi
+    from paper_2601_23065_gb300 import scenes as S
+
+    build.build()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    L = capi.lib()
+    field = "albedo" if args.workload == "stage1" else "radiance"
+    spp = args.spp or (256 if field == "albedo" else 1)
+    host = S.diff_room()
+    cams = fit_views(args.views)
+    ds = api.DeviceScene.from_host(host, device=dev)
+    bvh = api.BVH(ds)
+    r = api.Renderer(device=dev)
+    # targets: the room's own images (Stage 1: single bounce with its albedo;
+    # baking: path-traced, 4 bounces), then the field is reset to a start value
+    if field == "albedo":
+        targets = [api.single_bounce_incident(ds, bvh, c, 64, seed=9, renderer=r)["rgb"].clone() for c in cams]
+        ds.t["albedo"].fill_(0.5)
+    else:
+        targets = [r.path_traced(ds, bvh, c, 64, 4, rr_start=2, seed=9)["rgb"].clone() for c in cams]
+    bvh = api.BVH(ds)
+    fit = api.ShadingFit(ds, bvh, cams, targets, field, spp=spp, seed=1)
+    # counters of one step's segments (same cameras, same samples)
+    st = r.path_traced(ds, bvh, cams[0], spp, 1, rr_start=1 << 20, seed=2, want_stats=True)["stats"].cpu().numpy()
+    prim, sec = int(st[0]), int(st[1])
+    p_blend, p_nodes, p_tests = int(st[8]), int(st[9]), int(st[10])
+    s_blend, s_nodes, s_tests = int(st[3]), int(st[4]), int(st[5])
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    fit.run(max(3, args.warmup))
+    torch.cuda.synchronize(dev)
+    clocks = ClockSampler(0)
+    clocks.start()
+    launches0 = L.eagpt_launch_count()
+    capi.check(L.eagpt_profile_begin())
+    times, losses = [], []
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        lo = fit.run(1)
+        b.record()
+        b.synchronize()
+        times.append(a.elapsed_time(b))
+        losses.append(float(lo[0]))
+    prof = capi.profile_end()
+    launches = L.eagpt_launch_count() - launches0
+    clk = clocks.stop()
+    api.sync_status()
+    ms = sum(times) / len(times)
+    value = 1e3 / ms
+    peak, peak_kind = load_peaks()
+    total_kernel_ms = sum(v[1] for v in prof.values())
+    kname = max(prof.items(), key=lambda kv: kv[1][1])[0]
+    kl, kms = prof[kname]
+    if kname == "k_bounce":
+        unit_bytes = 96 * sec + NODE_BYTES * s_nodes + 64 * s_tests + 32 * s_blend
+    elif kname in ("k_radiance", "k_primary", "k_shade_adjoint"):
+        # one primary segment per pixel: 12 B out (image or gradient read) +
+        # node, test and blended-record bytes; the adjoint adds 12 B of
+        # atomics per blended hit
+        extra = 12 * p_blend if kname == "k_shade_adjoint" else 0
+        unit_bytes = 12 * prim + NODE_BYTES * p_nodes + 64 * p_tests + 32 * p_blend + extra
+    else:
+        unit_bytes = None
+    per_launch_ms = kms / max(1, kl)
+    launches_per_step = kl / max(1, args.steps)
+    achieved = unit_bytes / launches_per_step / (per_launch_ms * 1e-3) / 1e9 if unit_bytes else None
+    npix = cams[0].width * cams[0].height
+    segs = prim + (sec if field == "albedo" else prim)
+    line = {"metric": "Stage-1 iterations/s" if field == "albedo" else "light-baking iterations/s",
+            "value": value, "unit": "iterations/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": ("Stage 1 (Eq. 7): albedo, single bounce" if field == "albedo" else
+                                    "light baking (Eq. 10): radiance, 0-bounce") +
+                       f", 1M-surfel room, {len(cams)} views {cams[0].width}x{cams[0].height}, spp {spp}",
+                       "surfels": host.n, "views": len(cams), "pixels_per_step": npix, "spp": spp,
+                       "segments_per_step": segs, "segments_per_s": segs * value,
+                       "loss_first_last": [losses[0], losses[-1]],
+                       "l2": "flushed between steps (512 MB write)"},
+            "roofline": {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak if achieved else None, "traffic": None,
+                         "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
+                         "share_of_kernel_time": kms / total_kernel_ms if total_kernel_ms else None},
+            "cpu_baseline": fit_cpu_baseline(host, cams[0], 0 if field == "albedo" else 1, spp,
+                                             args.cpu_seconds) if not args.no_cpu_baseline else None,
+            "gpu_launches": int(launches), "clocks": clk,
+            "kernels": {k: {"launches": v[0], "ms": v[1]} for k, v in sorted(prof.items())}}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
     if args.workload == "serving":
         run_serving(args)
+        return
+    if args.workload in ("stage1", "bake") and args.impl == "native":
+        run_fit(args)
         return
     if args.impl == "reference":
         if world > 1:
@@ -416,11 +595,12 @@ def main():
                          want_stats=True)["stats"].cpu().numpy()
     blended, nodes, tests, rounds = int(cnt2[3]), int(cnt2[4]), int(cnt2[5]), int(cnt2[6])
     # per-segment algorithmic bytes: 48 B ray read + 48 B ray/slot write +
-    # 64 B per node + 64 B per surfel test + 32 B per blended shade record
+    # 128 B per BVH4 node visit + 64 B per surfel test + 32 B per blended
+    # shade record
     bounce_launches_per_step = bounce[0] / max(1, args.steps)
     bounce_ms_per_launch = bounce[1] / max(1, bounce[0])
     # bytes of the bounce launches only (secondary segments)
-    alg_bytes_bounce_launch = (96 * sec_segs + 64 * nodes + 64 * tests + 32 * blended) / max(
+    alg_bytes_bounce_launch = (96 * sec_segs + NODE_BYTES * nodes + 64 * tests + 32 * blended) / max(
         1.0, bounce_launches_per_step)
     achieved = alg_bytes_bounce_launch / (bounce_ms_per_launch * 1e-3) / 1e9 if bounce_ms_per_launch else None
     traffic = load_traffic(args.workload)
