@@ -357,6 +357,304 @@ static TreeArrays tree_arrays(char* base, const BvhLayout& L) {
   return T;
 }
 
+// --------------------------------------------------------------------------
+// PLOC hierarchy (Meister and Bittner, "Parallel Locally-Ordered Clustering
+// for Bounding Volume Hierarchy Construction", IEEE TVCG 2018).  Clusters
+// start as the surfels in Morton order.  Every round each cluster looks at
+// the kPlocRadius clusters on either side and picks the one whose union box
+// has the least surface area; mutual nearest neighbours merge into a new
+// binary node that takes the lower position, and the list is compacted in
+// order.  Pairs are ranked by (area, lower position, higher position), a
+// total order, so every nearest-neighbour chain ends in a mutual pair and
+// each round merges at least the closest pair of the list.  Internal nodes
+// are numbered in reverse creation order, so the last merge (the root) is
+// node 0; irange holds (0, leaves - 1) per node, which is all the collapse
+// reads when every leaf holds one surfel.
+// --------------------------------------------------------------------------
+#ifndef EAGPT_PLOC
+#define EAGPT_PLOC 1
+#endif
+constexpr bool kUsePloc = EAGPT_PLOC != 0 && kLeafMax == 1;
+constexpr int kPlocRadius = 16;
+constexpr int kPlocBlock = 256;
+constexpr int kPlocPer = 4;                          // positions per thread in count / scatter
+constexpr int kPlocTile = kPlocBlock * kPlocPer;     // positions per tile
+constexpr int kPlocMaxRounds = 1 << 14;
+
+struct PlocState {  // in the collapse's level counters (cleared by k_collapse_init afterwards)
+  uint32_t m, base, m_next, created;
+};
+
+__device__ __forceinline__ void cluster_box(const TreeArrays& T, int32_t c, float4& lo, float4& hi) {
+  code_box(T, c, lo, hi);
+}
+
+__device__ __forceinline__ float union_half_area(float4 alo, float4 ahi, float4 blo, float4 bhi) {
+  const float dx = fmaxf(ahi.x, bhi.x) - fminf(alo.x, blo.x);
+  const float dy = fmaxf(ahi.y, bhi.y) - fminf(alo.y, blo.y);
+  const float dz = fmaxf(ahi.z, bhi.z) - fminf(alo.z, blo.z);
+  return dx * dy + dy * dz + dz * dx;
+}
+
+__global__ void k_ploc_init(int32_t* cl, int64_t n, PlocState* ps, uint32_t* inode_parent) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) cl[i] = ~(int32_t)i;
+  if (i == 0) {
+    ps->m = (uint32_t)n;
+    ps->base = 0u;
+    ps->m_next = 0u;
+    ps->created = 0u;
+    inode_parent[0] = 0xFFFFFFFFu;  // node 0 is the root
+  }
+}
+
+// Tie-break of equal areas: a hash of the pair (lower, higher position), so
+// that runs of identical boxes resolve like a random matching instead of a
+// chain that merges one pair per round.
+__device__ __forceinline__ uint32_t pair_hash(uint32_t a, uint32_t b) {
+  uint32_t h = a * 0x9E3779B1u ^ (b + 0x7F4A7C15u) * 0x85EBCA77u;
+  h ^= h >> 15;
+  h *= 0x2C1B3C6Du;
+  h ^= h >> 12;
+  return h;
+}
+
+// Nearest neighbour of every cluster within +-kPlocRadius positions, by
+// (area, pair hash, position); the scan runs in increasing position, which
+// for pairs that share i is increasing (lower, higher) order.
+__global__ void __launch_bounds__(kPlocBlock) k_ploc_nn(TreeArrays T, const int32_t* __restrict__ cl,
+                                                        const PlocState* __restrict__ ps, int32_t* nn) {
+  __shared__ float4 s_lo[kPlocBlock + 2 * kPlocRadius], s_hi[kPlocBlock + 2 * kPlocRadius];
+  const int64_t m = ps->m;
+  const int64_t start = (int64_t)blockIdx.x * kPlocBlock;
+  if (start >= m) return;  // uniform for the block
+  for (int k = threadIdx.x; k < kPlocBlock + 2 * kPlocRadius; k += kPlocBlock) {
+    const int64_t p = start - kPlocRadius + k;
+    float4 lo = make_float4(0.f, 0.f, 0.f, 0.f), hi = lo;
+    if (p >= 0 && p < m) cluster_box(T, cl[p], lo, hi);
+    s_lo[k] = lo;
+    s_hi[k] = hi;
+  }
+  __syncthreads();
+  const int64_t i = start + threadIdx.x;
+  if (i >= m) return;
+  const float4 lo = s_lo[threadIdx.x + kPlocRadius], hi = s_hi[threadIdx.x + kPlocRadius];
+  float best = __int_as_float(0x7f800000);
+  uint32_t bh = 0xFFFFFFFFu;
+  int64_t bj = -1;
+#pragma unroll 4
+  for (int d = -kPlocRadius; d <= kPlocRadius; ++d) {
+    const int64_t j = i + d;
+    if (d == 0 || j < 0 || j >= m) continue;
+    const float a = union_half_area(lo, hi, s_lo[threadIdx.x + kPlocRadius + d], s_hi[threadIdx.x + kPlocRadius + d]);
+    const uint32_t h = d < 0 ? pair_hash((uint32_t)j, (uint32_t)i) : pair_hash((uint32_t)i, (uint32_t)j);
+    if (a < best || (a == best && h < bh) || bj < 0) {
+      best = a;
+      bh = h;
+      bj = j;
+    }
+  }
+  nn[i] = (int32_t)bj;
+}
+
+__device__ __forceinline__ void ploc_flags(const int32_t* __restrict__ nn, int64_t i, uint32_t& keep, uint32_t& fresh) {
+  const int32_t j = nn[i];
+  const bool mutual = j >= 0 && nn[j] == (int32_t)i;
+  keep = (mutual && j < i) ? 0u : 1u;      // the higher of a merging pair leaves the list
+  fresh = (mutual && i < j) ? 1u : 0u;     // the lower becomes the new node
+}
+
+// Per tile: how many clusters stay and how many nodes are made.
+__global__ void __launch_bounds__(kPlocBlock) k_ploc_count(const int32_t* __restrict__ nn,
+                                                           const PlocState* __restrict__ ps, uint32_t* tile_sums) {
+  __shared__ uint32_t s_k[kPlocBlock / 32], s_f[kPlocBlock / 32];
+  const int64_t m = ps->m;
+  const int64_t t0 = (int64_t)blockIdx.x * kPlocTile;
+  if (t0 >= m) return;
+  uint32_t k = 0, f = 0;
+  for (int r = 0; r < kPlocPer; ++r) {
+    const int64_t i = t0 + (int64_t)threadIdx.x * kPlocPer + r;
+    if (i < m) {
+      uint32_t a, b;
+      ploc_flags(nn, i, a, b);
+      k += a;
+      f += b;
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    k += __shfl_xor_sync(0xffffffffu, k, o);
+    f += __shfl_xor_sync(0xffffffffu, f, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    s_k[threadIdx.x >> 5] = k;
+    s_f[threadIdx.x >> 5] = f;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t a = 0, b = 0;
+    for (int w = 0; w < kPlocBlock / 32; ++w) {
+      a += s_k[w];
+      b += s_f[w];
+    }
+    tile_sums[2 * blockIdx.x] = a;
+    tile_sums[2 * blockIdx.x + 1] = b;
+  }
+}
+
+// Exclusive scan of the tile sums (in place), in one block; totals to ps.
+__global__ void __launch_bounds__(1024) k_ploc_scan_tiles(uint32_t* tile_sums, PlocState* ps) {
+  __shared__ uint32_t s_k[1024], s_f[1024];
+  const int64_t m = ps->m;
+  const int64_t tiles = (m + kPlocTile - 1) / kPlocTile;
+  uint32_t carry_k = 0, carry_f = 0;
+  for (int64_t c0 = 0; c0 < tiles; c0 += 1024) {
+    const int64_t t = c0 + threadIdx.x;
+    const uint32_t vk = t < tiles ? tile_sums[2 * t] : 0u, vf = t < tiles ? tile_sums[2 * t + 1] : 0u;
+    s_k[threadIdx.x] = vk;
+    s_f[threadIdx.x] = vf;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {  // Hillis-Steele inclusive scan
+      const uint32_t ak = threadIdx.x >= o ? s_k[threadIdx.x - o] : 0u;
+      const uint32_t af = threadIdx.x >= o ? s_f[threadIdx.x - o] : 0u;
+      __syncthreads();
+      s_k[threadIdx.x] += ak;
+      s_f[threadIdx.x] += af;
+      __syncthreads();
+    }
+    if (t < tiles) {
+      tile_sums[2 * t] = carry_k + s_k[threadIdx.x] - vk;
+      tile_sums[2 * t + 1] = carry_f + s_f[threadIdx.x] - vf;
+    }
+    carry_k += s_k[1023];
+    carry_f += s_f[1023];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    ps->m_next = carry_k;
+    ps->created = carry_f;
+  }
+}
+
+// Compaction in order plus the new nodes: position i of the tile goes to
+// (tile offset + stays before it in the tile); a merging pair's node gets id
+// (n - 2) - (nodes made before it).
+__global__ void __launch_bounds__(kPlocBlock) k_ploc_scatter(TreeArrays T, const int32_t* __restrict__ cl_in,
+                                                             int32_t* cl_out, const int32_t* __restrict__ nn,
+                                                             const PlocState* __restrict__ ps,
+                                                             const uint32_t* __restrict__ tile_off, int64_t n,
+                                                             int32_t* child_bin, uint32_t* leaf_parent,
+                                                             uint32_t* inode_parent, int2* irange, float4* ilo,
+                                                             float4* ihi) {
+  __shared__ uint32_t s_k[kPlocBlock / 32], s_f[kPlocBlock / 32];
+  const int64_t m = ps->m;
+  const int64_t t0 = (int64_t)blockIdx.x * kPlocTile;
+  if (t0 >= m) return;
+  uint32_t kf[kPlocPer], ff[kPlocPer];
+  uint32_t k = 0, f = 0;
+#pragma unroll
+  for (int r = 0; r < kPlocPer; ++r) {
+    const int64_t i = t0 + (int64_t)threadIdx.x * kPlocPer + r;
+    kf[r] = ff[r] = 0u;
+    if (i < m) ploc_flags(nn, i, kf[r], ff[r]);
+    k += kf[r];
+    f += ff[r];
+  }
+  // exclusive scan over the block (warp scan, then the warp totals)
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t ik = k, iff = f;
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t a = __shfl_up_sync(0xffffffffu, ik, o), b = __shfl_up_sync(0xffffffffu, iff, o);
+    if (lane >= o) {
+      ik += a;
+      iff += b;
+    }
+  }
+  if (lane == 31) {
+    s_k[warp] = ik;
+    s_f[warp] = iff;
+  }
+  __syncthreads();
+  uint32_t wk = 0, wf = 0;
+  for (int w = 0; w < warp; ++w) {
+    wk += s_k[w];
+    wf += s_f[w];
+  }
+  uint32_t pk = tile_off[2 * blockIdx.x] + wk + ik - k;
+  uint32_t pf = tile_off[2 * blockIdx.x + 1] + wf + iff - f;
+  const uint32_t base = ps->base;
+#pragma unroll
+  for (int r = 0; r < kPlocPer; ++r) {
+    const int64_t i = t0 + (int64_t)threadIdx.x * kPlocPer + r;
+    if (i >= m || !kf[r]) continue;
+    const int32_t c = cl_in[i];
+    if (ff[r]) {
+      const int32_t c1 = cl_in[nn[i]];
+      const int32_t id = (int32_t)((n - 2) - (int64_t)(base + pf));
+      ++pf;
+      child_bin[2 * id] = c;
+      child_bin[2 * id + 1] = c1;
+      if (c < 0) leaf_parent[~c] = (uint32_t)id; else inode_parent[c] = (uint32_t)id;
+      if (c1 < 0) leaf_parent[~c1] = (uint32_t)id; else inode_parent[c1] = (uint32_t)id;
+      float4 lo0, hi0, lo1, hi1;
+      code_box(T, c, lo0, hi0);
+      code_box(T, c1, lo1, hi1);
+      ilo[id] = make_float4(fminf(lo0.x, lo1.x), fminf(lo0.y, lo1.y), fminf(lo0.z, lo1.z), 0.f);
+      ihi[id] = make_float4(fmaxf(hi0.x, hi1.x), fmaxf(hi0.y, hi1.y), fmaxf(hi0.z, hi1.z), 0.f);
+      const int32_t n0 = c < 0 ? 1 : T.irange[c].y + 1, n1 = c1 < 0 ? 1 : T.irange[c1].y + 1;
+      irange[id] = make_int2(0, n0 + n1 - 1);
+      cl_out[pk++] = id;
+    } else {
+      cl_out[pk++] = c;
+    }
+  }
+}
+
+__global__ void k_ploc_advance(PlocState* ps) {
+  ps->m = ps->m_next;
+  ps->base += ps->created;
+}
+
+static void launch_binary_refit(char* base, const BvhLayout& L, cudaStream_t st);
+
+// Builds the binary tree by PLOC; synchronises the stream once per round to
+// read the cluster count.  Returns false when the round limit is reached.
+static cudaError_t launch_ploc(char* base, const BvhLayout& L, cudaStream_t st) {
+  const int64_t n = L.n;
+  TreeArrays T = tree_arrays(base, L);
+  int32_t* cl[2] = {(int32_t*)(base + L.front0), (int32_t*)(base + L.front1)};
+  int32_t* nn = (int32_t*)(base + L.keys1);
+  uint32_t* tiles = (uint32_t*)(base + L.hist);
+  PlocState* ps = (PlocState*)(base + L.levels);
+  int32_t* child_bin = (int32_t*)(base + L.child_bin);
+  uint32_t* leaf_parent = (uint32_t*)(base + L.leaf_parent);
+  uint32_t* inode_parent = (uint32_t*)(base + L.inode_parent);
+  int2* irange = (int2*)(base + L.irange);
+  float4* ilo = (float4*)(base + L.ibox_lo);
+  float4* ihi = (float4*)(base + L.ibox_hi);
+  EAGPT_LAUNCH(st, "k_ploc_init", k_ploc_init<<<blocks_for(n, 256), 256, 0, st>>>(cl[0], n, ps, inode_parent));
+  int64_t m = n;
+  int cur = 0;
+  for (int round = 0; m > 1; ++round) {
+    if (round >= kPlocMaxRounds) return cudaErrorUnknown;
+    EAGPT_LAUNCH(st, "k_ploc_nn", k_ploc_nn<<<blocks_for(m, kPlocBlock), kPlocBlock, 0, st>>>(T, cl[cur], ps, nn));
+    const unsigned nt = blocks_for(m, kPlocTile);
+    EAGPT_LAUNCH(st, "k_ploc_count", k_ploc_count<<<nt, kPlocBlock, 0, st>>>(nn, ps, tiles));
+    EAGPT_LAUNCH(st, "k_ploc_scan_tiles", k_ploc_scan_tiles<<<1, 1024, 0, st>>>(tiles, ps));
+    EAGPT_LAUNCH(st, "k_ploc_scatter",
+                 k_ploc_scatter<<<nt, kPlocBlock, 0, st>>>(T, cl[cur], cl[cur ^ 1], nn, ps, tiles, n, child_bin,
+                                                           leaf_parent, inode_parent, irange, ilo, ihi));
+    EAGPT_LAUNCH(st, "k_ploc_advance", k_ploc_advance<<<1, 1, 0, st>>>(ps));
+    uint32_t mh = 0;
+    cudaError_t e = cudaMemcpyAsync(&mh, &ps->m, sizeof(uint32_t), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return e;
+    if ((int64_t)mh >= m) return cudaErrorUnknown;  // no progress: impossible by construction
+    m = mh;
+    cur ^= 1;
+  }
+  return cudaGetLastError();
+}
+
 static void launch_binary_refit(char* base, const BvhLayout& L, cudaStream_t st) {
   BvhHeader* hdr = (BvhHeader*)(base + L.header);
   cudaMemsetAsync(&hdr->area_sum, 0, sizeof(double), st);
@@ -382,10 +680,15 @@ cudaError_t launch_tree(const uint32_t* sorted_keys, char* base, const BvhLayout
                                                nodes, src4, levels, hdr));
     return cudaGetLastError();
   }
-  EAGPT_LAUNCH(st, "k_hierarchy",
-               k_hierarchy<<<blocks_for(n - 1, 256), 256, 0, st>>>(
-                   sorted_keys, n, (uint32_t*)(base + L.leaf_parent), (uint32_t*)(base + L.inode_parent),
-                   (int32_t*)(base + L.child_bin), (int2*)(base + L.irange)));
+  if (kUsePloc) {
+    const cudaError_t e = launch_ploc(base, L, st);
+    if (e != cudaSuccess) return e;
+  } else {
+    EAGPT_LAUNCH(st, "k_hierarchy",
+                 k_hierarchy<<<blocks_for(n - 1, 256), 256, 0, st>>>(
+                     sorted_keys, n, (uint32_t*)(base + L.leaf_parent), (uint32_t*)(base + L.inode_parent),
+                     (int32_t*)(base + L.child_bin), (int2*)(base + L.irange)));
+  }
   launch_binary_refit(base, L, st);
   int2* fr[2] = {(int2*)(base + L.front0), (int2*)(base + L.front1)};
   EAGPT_LAUNCH(st, "k_collapse_init", k_collapse_init<<<1, 128, 0, st>>>(levels, fr[0]));
