@@ -372,10 +372,13 @@ static TreeArrays tree_arrays(char* base, const BvhLayout& L) {
 // reads when every leaf holds one surfel.
 // --------------------------------------------------------------------------
 #ifndef EAGPT_PLOC
-#define EAGPT_PLOC 1
+#define EAGPT_PLOC 0
+#endif
+#ifndef EAGPT_PLOC_RADIUS
+#define EAGPT_PLOC_RADIUS 16
 #endif
 constexpr bool kUsePloc = EAGPT_PLOC != 0 && kLeafMax == 1;
-constexpr int kPlocRadius = 16;
+constexpr int kPlocRadius = EAGPT_PLOC_RADIUS;
 constexpr int kPlocBlock = 256;
 constexpr int kPlocPer = 4;                          // positions per thread in count / scatter
 constexpr int kPlocTile = kPlocBlock * kPlocPer;     // positions per tile
@@ -696,10 +699,19 @@ cudaError_t launch_tree(const uint32_t* sorted_keys, char* base, const BvhLayout
   // the frontier of a level never exceeds the node count; a grid of a few
   // blocks per SM strides over it
   const unsigned grid = (unsigned)(4 * device_sms());
+  // levels are launched in groups of 8; after each group the next frontier's
+  // size is read back, and the remaining (empty) levels are skipped
   for (int lv = 0; lv < kMaxCollapseLevels; ++lv) {
     EAGPT_LAUNCH(st, "k_collapse",
                  k_collapse<kBvhWidth><<<grid, 256, 0, st>>>(T, nodes, src4, fr[lv & 1], fr[(lv + 1) & 1], levels, lv,
                                                  L.n_inodes));
+    if ((lv & 7) == 7 && lv + 1 < kMaxCollapseLevels) {
+      uint32_t next = 1;
+      cudaError_t e = cudaMemcpyAsync(&next, levels + lv + 1, sizeof(uint32_t), cudaMemcpyDeviceToHost, st);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+      if (e != cudaSuccess) return e;
+      if (next == 0) break;
+    }
   }
   EAGPT_LAUNCH(st, "k_collapse_check", k_collapse_check<<<1, 32, 0, st>>>(levels));
   return cudaGetLastError();

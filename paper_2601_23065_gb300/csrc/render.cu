@@ -36,6 +36,11 @@ EAGPT_DEFINE_ERROR_READER(take_errors_render)
 #endif
 constexpr bool kSortRays = EAGPT_SORT_RAYS != 0;
 
+// Blend sums of the bounce kernel in shared memory instead of registers.
+#ifndef EAGPT_SMEM_BLEND
+#define EAGPT_SMEM_BLEND 1
+#endif
+
 __global__ void k_ray_keys(const Ray* __restrict__ q, const uint32_t* __restrict__ count_ptr, int64_t cap,
                            const uint32_t* __restrict__ bounds_bits, uint32_t* keys, uint32_t* vals) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -190,6 +195,9 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_bounce(BvhView bvh, Cons
                                                    const Ray* __restrict__ q_in, Ray* q_out, uint32_t* counters,
                                                    float4* slots, int64_t* stats, const uint32_t* __restrict__ perm) {
   __shared__ uint32_t s_stack[kStackSize * kBlock];
+#if EAGPT_SMEM_BLEND
+  __shared__ float s_blend[11 * kBlock];
+#endif
   const int lane = threadIdx.x & 31;
   const uint32_t count = counters[2 * k];
   const int mode = kind == 1 ? 1 : 0;
@@ -205,12 +213,28 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_bounce(BvhView bvh, Cons
     Ray nr;
     if (idx < count) {
       ++traced;
-      const Ray r = q_in[perm ? perm[idx] : idx];
+      const uint32_t qi = perm ? perm[idx] : idx;
+#if EAGPT_SMEM_BLEND
+      // origin and direction stay in registers for the traversal; pixel,
+      // sample, throughput and tag are read again after it (volatile loads,
+      // so the first read is not kept alive across the trace)
+      const float4 ra = q_in[qi].a, rb = q_in[qi].b;
+      const float3 O = f3(ra), w = f3(rb);
+      SmemBlendVisitor vis(bvh.shade, C, mode, s_blend + threadIdx.x, kBlock);
+      trace_segment<kK, kCount>(bvh, C, O, w, 0.f, s_stack + threadIdx.x, kBlock, vis, cnt);
+      const SegRec s = finish(vis.get());
+      Ray r;
+      r.a = make_float4(O.x, O.y, O.z, __ldcv(&q_in[qi].a.w));
+      r.b = make_float4(w.x, w.y, w.z, __ldcv(&q_in[qi].b.w));
+      r.c = __ldcv(&q_in[qi].c);
+#else
+      const Ray r = q_in[qi];
       const float3 O = f3(r.a), w = f3(r.b);
-      const uint32_t pixel = __float_as_uint(r.a.w), sample = __float_as_uint(r.b.w);
       BlendVisitor vis(bvh.shade, C, w, mode);
       trace_segment<kK, kCount>(bvh, C, O, w, 0.f, s_stack + threadIdx.x, kBlock, vis, cnt);
       const SegRec s = finish(vis.b);
+#endif
+      const uint32_t pixel = __float_as_uint(r.a.w), sample = __float_as_uint(r.b.w);
       float3 contrib;
       take = shade_bounce(kind, k, max_bounces, rr_start, seed, C, r, s, contrib, nr);
       if (!take) slots[(int64_t)(sample - (uint32_t)s0) * npix + pixel] = make_float4(contrib.x, contrib.y, contrib.z, 0.f);

@@ -73,6 +73,10 @@ __device__ __forceinline__ bool key_less(float ta, uint32_t ia, float tb, uint32
   return ta < tb || (ta == tb && ia < ib);
 }
 
+#ifndef EAGPT_FAST_SLAB
+#define EAGPT_FAST_SLAB 0
+#endif
+
 // Counters of the work one segment did (enabled by the kCount template flag).
 struct TraceCounters {
   uint32_t nodes, tests, blended, rounds, max_stack;
@@ -120,12 +124,38 @@ __device__ __forceinline__ void leaf_step(const BvhView& bvh, const Consts& C, f
 __device__ __forceinline__ bool node_step(const BvhView& bvh, uint32_t node, float3 O, float3 inv, float t_last,
                                           float tmax, uint32_t* stack, int stride, int& sp, uint32_t& next) {
   const Node4* np = bvh.nodes + node;
-  const float4 lx = __ldg(&np->lox), ly = __ldg(&np->loy), lz = __ldg(&np->loz);
-  const float4 hx = __ldg(&np->hix), hy = __ldg(&np->hiy), hz = __ldg(&np->hiz);
   const uint4 ch = __ldg(&np->child);
   const float inf = __int_as_float(0x7f800000);
   float e[4];
   uint32_t c[4] = {ch.x, ch.y, ch.z, ch.w};
+#if EAGPT_FAST_SLAB
+  // Per axis the plane the ray enters first is the low one when the
+  // direction is positive: load the near and far planes directly (the SoA
+  // node keeps lo at byte 16 a and hi at 48 + 16 a) and form t = p inv - O inv
+  // with one FMA, so no per-child min/max is needed.  The rounding of O inv
+  // is a few ulps of |O|, well inside the boxes' 1e-5 relative inflation.
+  {
+    const char* base = (const char*)np;
+    const int sx = inv.x < 0.f ? 48 : 0, sy = inv.y < 0.f ? 48 : 0, sz = inv.z < 0.f ? 48 : 0;
+    const float4 nx = __ldg((const float4*)(base + sx)), fx = __ldg((const float4*)(base + 48 - sx));
+    const float4 ny = __ldg((const float4*)(base + 16 + sy)), fy = __ldg((const float4*)(base + 64 - sy));
+    const float4 nz = __ldg((const float4*)(base + 32 + sz)), fz = __ldg((const float4*)(base + 80 - sz));
+    const float ox = O.x * inv.x, oy = O.y * inv.y, oz = O.z * inv.z;
+    const float nxa[4] = {nx.x, nx.y, nx.z, nx.w}, nya[4] = {ny.x, ny.y, ny.z, ny.w};
+    const float nza[4] = {nz.x, nz.y, nz.z, nz.w}, fxa[4] = {fx.x, fx.y, fx.z, fx.w};
+    const float fya[4] = {fy.x, fy.y, fy.z, fy.w}, fza[4] = {fz.x, fz.y, fz.z, fz.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const float t0 = fmaxf(fmaxf(__fmaf_rn(nxa[k], inv.x, -ox), __fmaf_rn(nya[k], inv.y, -oy)),
+                             fmaxf(__fmaf_rn(nza[k], inv.z, -oz), t_last));
+      const float t1 = fminf(fminf(__fmaf_rn(fxa[k], inv.x, -ox), __fmaf_rn(fya[k], inv.y, -oy)),
+                             fminf(__fmaf_rn(fza[k], inv.z, -oz), tmax));
+      e[k] = (t0 <= t1 && c[k] != kEmptyChild) ? t0 : inf;
+    }
+  }
+#else
+  const float4 lx = __ldg(&np->lox), ly = __ldg(&np->loy), lz = __ldg(&np->loz);
+  const float4 hx = __ldg(&np->hix), hy = __ldg(&np->hiy), hz = __ldg(&np->hiz);
   {
     const float lxa[4] = {lx.x, lx.y, lx.z, lx.w}, lya[4] = {ly.x, ly.y, ly.z, ly.w};
     const float lza[4] = {lz.x, lz.y, lz.z, lz.w}, hxa[4] = {hx.x, hx.y, hx.z, hx.w};
@@ -138,6 +168,7 @@ __device__ __forceinline__ bool node_step(const BvhView& bvh, uint32_t node, flo
       e[k] = (h && c[k] != kEmptyChild) ? te : inf;
     }
   }
+#endif
   // front-to-back order: sorting network on (entry, link)
 #define EAGPT_CSWAP(i, j)                         \
   if (e[j] < e[i]) {                              \
@@ -435,20 +466,72 @@ struct BlendVisitor {
     b.T = 1.f;
     b.n_hits = 0;
   }
+  // explicit roundings (one FMA per sum), shared with SmemBlendVisitor, so
+  // that every kernel that blends produces the same bits
   __device__ __forceinline__ bool operator()(const TraceRec& R, uint32_t j, const HitGeom& h) {
     const ShadeRec* sp = shade + j;
     const float4 s0 = __ldg(&sp->s0), s1 = __ldg(&sp->s1);
-    const float wgt = b.T * h.alpha;
+    const float wgt = __fmul_rn(b.T, h.alpha);
     const float sgn = h.d > 0.f ? -wgt : wgt;  // normal facing the ray origin
     const float re = (mode == 1 && !(s0.w > C.tau_E)) ? 0.f : wgt;
-    b.N = b.N + sgn * f3(R.r1);
-    b.D += wgt * h.t;
-    b.R = b.R + re * make_float3(s1.x, s1.y, s1.z);
-    b.E += wgt * s0.w;
-    b.P = b.P + wgt * make_float3(s0.x, s0.y, s0.z);
-    b.T *= (1.f - h.alpha);
+    b.N = make_float3(__fmaf_rn(sgn, R.r1.x, b.N.x), __fmaf_rn(sgn, R.r1.y, b.N.y), __fmaf_rn(sgn, R.r1.z, b.N.z));
+    b.D = __fmaf_rn(wgt, h.t, b.D);
+    b.R = make_float3(__fmaf_rn(re, s1.x, b.R.x), __fmaf_rn(re, s1.y, b.R.y), __fmaf_rn(re, s1.z, b.R.z));
+    b.E = __fmaf_rn(wgt, s0.w, b.E);
+    b.P = make_float3(__fmaf_rn(wgt, s0.x, b.P.x), __fmaf_rn(wgt, s0.y, b.P.y), __fmaf_rn(wgt, s0.z, b.P.z));
+    b.T = __fmul_rn(b.T, __fsub_rn(1.f, h.alpha));
     ++b.n_hits;
     return b.T < C.T_min;
+  }
+};
+
+// The same blend with the running sums (all but T) in this thread's slot of
+// a shared-memory array, s[k * stride] for k = 0..10 (N xyz, R xyz, P xyz, D,
+// E): during a multi-round traversal they stay out of the register file.
+struct SmemBlendVisitor {
+  const ShadeRec* shade;
+  Consts C;
+  int mode;
+  float* s;
+  int stride;
+  float T;
+  uint32_t n_hits;
+  __device__ __forceinline__ SmemBlendVisitor(const ShadeRec* sh, const Consts& c, int m, float* slot, int str)
+      : shade(sh), C(c), mode(m), s(slot), stride(str), T(1.f), n_hits(0) {
+#pragma unroll
+    for (int k = 0; k < 11; ++k) s[k * stride] = 0.f;
+  }
+  __device__ __forceinline__ bool operator()(const TraceRec& R, uint32_t j, const HitGeom& h) {
+    const ShadeRec* sp = shade + j;
+    const float4 s0 = __ldg(&sp->s0), s1 = __ldg(&sp->s1);
+    const float wgt = __fmul_rn(T, h.alpha);
+    const float sgn = h.d > 0.f ? -wgt : wgt;
+    const float re = (mode == 1 && !(s0.w > C.tau_E)) ? 0.f : wgt;
+    s[0 * stride] = __fmaf_rn(sgn, R.r1.x, s[0 * stride]);
+    s[1 * stride] = __fmaf_rn(sgn, R.r1.y, s[1 * stride]);
+    s[2 * stride] = __fmaf_rn(sgn, R.r1.z, s[2 * stride]);
+    s[3 * stride] = __fmaf_rn(re, s1.x, s[3 * stride]);
+    s[4 * stride] = __fmaf_rn(re, s1.y, s[4 * stride]);
+    s[5 * stride] = __fmaf_rn(re, s1.z, s[5 * stride]);
+    s[6 * stride] = __fmaf_rn(wgt, s0.x, s[6 * stride]);
+    s[7 * stride] = __fmaf_rn(wgt, s0.y, s[7 * stride]);
+    s[8 * stride] = __fmaf_rn(wgt, s0.z, s[8 * stride]);
+    s[9 * stride] = __fmaf_rn(wgt, h.t, s[9 * stride]);
+    s[10 * stride] = __fmaf_rn(wgt, s0.w, s[10 * stride]);
+    T = __fmul_rn(T, __fsub_rn(1.f, h.alpha));
+    ++n_hits;
+    return T < C.T_min;
+  }
+  __device__ __forceinline__ Blend get() const {
+    Blend b;
+    b.N = make_float3(s[0], s[stride], s[2 * stride]);
+    b.R = make_float3(s[3 * stride], s[4 * stride], s[5 * stride]);
+    b.P = make_float3(s[6 * stride], s[7 * stride], s[8 * stride]);
+    b.D = s[9 * stride];
+    b.E = s[10 * stride];
+    b.T = T;
+    b.n_hits = n_hits;
+    return b;
   }
 };
 
