@@ -594,6 +594,8 @@ def main():
     cnt2 = r.path_traced(ds, api.BVH(ds), cam, wl.spp, wl.max_bounces, rr_start=wl.rr_start, seed=seed_base,
                          want_stats=True)["stats"].cpu().numpy()
     blended, nodes, tests, rounds = int(cnt2[3]), int(cnt2[4]), int(cnt2[5]), int(cnt2[6])
+    # lane work of the bounce batches against 32 x their slowest lane
+    balance = int(cnt2[12]) / max(1, int(cnt2[13]))
     # per-segment algorithmic bytes: 48 B ray read + 48 B ray/slot write +
     # 128 B per BVH4 node visit + 64 B per surfel test + 32 B per blended
     # shade record
@@ -611,7 +613,8 @@ def main():
                 "share_of_kernel_time": bounce[1] / total_kernel_ms if total_kernel_ms else None,
                 "per_secondary_segment": {"nodes": nodes / max(1, sec_segs), "tests": tests / max(1, sec_segs),
                                           "blended": blended / max(1, sec_segs),
-                                          "rounds": rounds / max(1, sec_segs)}}
+                                          "rounds": rounds / max(1, sec_segs),
+                                          "warp_balance": balance}}
 
     # end to end through the public API with host buffers
     pinned = {k: torch.from_numpy(getattr(host_scene, k)).pin_memory() for k in api.FIELDS}

@@ -165,7 +165,10 @@ eagpt_status eagpt_render_single_bounce(const eagpt_scene* scene, const eagpt_bv
  *   [0] primary segments  [1] secondary segments  [2] paths started
  *   [3..6]  secondary segments: blended hits, BVH nodes visited, surfel
  *           tests, traversal rounds
- *   [8..11] the same for the primary segments. */
+ *   [7]     deepest traversal stack of a secondary segment (maximum)
+ *   [8..11] the same as [3..6] for the primary segments
+ *   [12], [13] secondary batches of 32 rays: the lanes' work (nodes +
+ *           tests) and 32 x the work of each batch's slowest lane. */
 eagpt_status eagpt_render_path_traced(const eagpt_scene* scene, const eagpt_bvh* bvh,
                                       const eagpt_camera* cam, const eagpt_params* params, int32_t spp,
                                       int32_t max_bounces, int32_t rr_start_bounce, uint64_t seed,

@@ -23,7 +23,7 @@
 namespace eagpt {
 
 #ifndef EAGPT_KBUF
-#define EAGPT_KBUF 16
+#define EAGPT_KBUF 12
 #endif
 constexpr int kK = EAGPT_KBUF;  // k-buffer size (hits collected per traversal round)
 
@@ -211,6 +211,7 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_bounce(BvhView bvh, Cons
     const uint32_t idx = base + lane;
     bool take = false;
     Ray nr;
+    const uint32_t work0 = cnt.nodes + cnt.tests;
     if (idx < count) {
       ++traced;
       const uint32_t qi = perm ? perm[idx] : idx;
@@ -238,6 +239,104 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_bounce(BvhView bvh, Cons
       float3 contrib;
       take = shade_bounce(kind, k, max_bounces, rr_start, seed, C, r, s, contrib, nr);
       if (!take) slots[(int64_t)(sample - (uint32_t)s0) * npix + pixel] = make_float4(contrib.x, contrib.y, contrib.z, 0.f);
+    }
+    __syncwarp();
+    if (kCount) {
+      // balance of the batch: the lanes' work against 32 x the slowest lane's
+      const uint32_t wr = cnt.nodes + cnt.tests - work0;
+      uint32_t mx = wr;
+      for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      add_stats(stats, 12, wr);
+      add_stats(stats, 13, lane == 0 ? 32u * mx : 0u);
+    }
+    const uint32_t at = warp_append(take, &counters[2 * (k + 1)]);
+    if (take) q_out[at] = nr;
+  }
+  if (kCount) {
+    add_stats(stats, 1, traced);
+    add_stats(stats, 3, cnt.blended);
+    add_stats(stats, 4, cnt.nodes);
+    add_stats(stats, 5, cnt.tests);
+    add_stats(stats, 6, cnt.rounds);
+    uint32_t m = cnt.max_stack;
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0 && m) atomicMax((unsigned long long*)(stats + 7), (unsigned long long)m);
+  }
+}
+
+// The bounce kernel with per-lane refill: a lane whose segment is finished
+// takes the next queued ray at once (one atomic per warp for all the lanes
+// that want one) instead of waiting for the slowest ray of a 32-ray batch.
+// Traversal runs in chunks of kRefillSteps node/leaf steps; between chunks
+// the lanes whose round is complete blend it, and finished segments are shaded
+// and their continuation appended (warp-ballot compaction, as in k_bounce).
+#ifndef EAGPT_REFILL
+#define EAGPT_REFILL 0
+#endif
+#ifndef EAGPT_REFILL_STEPS
+#define EAGPT_REFILL_STEPS 32
+#endif
+constexpr int kRefillSteps = EAGPT_REFILL_STEPS;
+
+template <bool kCount>
+__global__ void __launch_bounds__(kBlock, kMinBlocks) k_bounce_r(BvhView bvh, Consts C, int kind, int k, int max_bounces,
+                                                     int rr_start, uint64_t seed, int64_t npix, int s0,
+                                                     const Ray* __restrict__ q_in, Ray* q_out, uint32_t* counters,
+                                                     float4* slots, int64_t* stats, const uint32_t* __restrict__ perm) {
+  __shared__ uint32_t s_stack[kStackSize * kBlock];
+  __shared__ float s_blend[11 * kBlock];
+  const int lane = threadIdx.x & 31;
+  const uint32_t count = counters[2 * k];
+  const int mode = kind == 1 ? 1 : 0;
+  TraceCounters cnt{0, 0, 0, 0, 0};
+  uint32_t traced = 0;
+  RayTrace<kK> rt;
+  SmemBlendVisitor vis(bvh.shade, C, mode, s_blend + threadIdx.x, kBlock);
+  uint32_t qi = 0;
+  bool active = false, exhausted = false;
+  for (;;) {
+    const bool want = !active && !exhausted;
+    const uint32_t wmask = __ballot_sync(0xffffffffu, want);
+    if (wmask) {
+      const int leader = __ffs(wmask) - 1;
+      uint32_t base = 0;
+      if (lane == leader) base = atomicAdd(&counters[2 * k + 1], (uint32_t)__popc(wmask));
+      base = __shfl_sync(0xffffffffu, base, leader);
+      if (want) {
+        const uint32_t idx = base + (uint32_t)__popc(wmask & ((1u << lane) - 1u));
+        if (idx < count) {
+          qi = perm ? perm[idx] : idx;
+          ray_begin(rt, f3(q_in[qi].a), f3(q_in[qi].b));
+          round_begin(rt, bvh);
+          vis.reset();
+          active = true;
+          ++traced;
+          if (kCount) ++cnt.rounds;
+        } else {
+          exhausted = true;
+        }
+      }
+    }
+    if (!__any_sync(0xffffffffu, active)) break;
+    bool take = false;
+    Ray nr;
+    if (active && round_steps<kK, kCount>(rt, bvh, C, s_stack + threadIdx.x, kBlock, kRefillSteps, cnt)) {
+      if (round_blend<kK, kCount>(rt, bvh, C, vis, cnt)) {
+        const SegRec s = finish(vis.get());
+        Ray r;
+        r.a = make_float4(rt.O.x, rt.O.y, rt.O.z, __ldcv(&q_in[qi].a.w));
+        r.b = make_float4(rt.w.x, rt.w.y, rt.w.z, __ldcv(&q_in[qi].b.w));
+        r.c = __ldcv(&q_in[qi].c);
+        const uint32_t pixel = __float_as_uint(r.a.w), sample = __float_as_uint(r.b.w);
+        float3 contrib;
+        take = shade_bounce(kind, k, max_bounces, rr_start, seed, C, r, s, contrib, nr);
+        if (!take)
+          slots[(int64_t)(sample - (uint32_t)s0) * npix + pixel] = make_float4(contrib.x, contrib.y, contrib.z, 0.f);
+        active = false;
+      } else {
+        round_begin(rt, bvh);
+        if (kCount) ++cnt.rounds;
+      }
     }
     __syncwarp();
     const uint32_t at = warp_append(take, &counters[2 * (k + 1)]);
@@ -403,7 +502,8 @@ static cudaError_t render_impl(const RenderArgs& a, cudaStream_t st, int* launch
   EAGPT_LAUNCH(st, "k_primary", k_primary<kCount><<<nblocks(npix), kBlock, 0, st>>>(a.bvh, a.C, a.cam, mode, npix, prim, a.out_aux, a.out_stats));
   ++nl;
   static int bounce_grid[2] = {0, 0};
-  if (!bounce_grid[kCount]) bounce_grid[kCount] = persistent_blocks(k_bounce<kCount>);
+  if (!bounce_grid[kCount])
+    bounce_grid[kCount] = EAGPT_REFILL ? persistent_blocks(k_bounce_r<kCount>) : persistent_blocks(k_bounce<kCount>);
   for (int s0 = 0; s0 < a.spp; s0 += batch) {
     const int nb = a.spp - s0 < batch ? a.spp - s0 : batch;
     cudaMemsetAsync(counters, 0, kCounterWords * sizeof(uint32_t), st);
@@ -421,7 +521,12 @@ static cudaError_t render_impl(const RenderArgs& a, cudaStream_t st, int* launch
         launch_sort_pairs(k0, v0, k1, v1, (uint32_t*)(ws + L.shist), cap, st);
         perm = v0;
       }
-      EAGPT_LAUNCH(st, "k_bounce", k_bounce<kCount><<<bounce_grid[kCount], kBlock, 0, st>>>(a.bvh, a.C, a.kind, k, B, a.rr_start, a.seed, npix,
+      if (EAGPT_REFILL)
+        EAGPT_LAUNCH(st, "k_bounce", k_bounce_r<kCount><<<bounce_grid[kCount], kBlock, 0, st>>>(a.bvh, a.C, a.kind, k, B, a.rr_start, a.seed, npix,
+                                                                  s0, q[(k - 1) & 1], q[k & 1], counters, slots,
+                                                                  a.out_stats, perm));
+      else
+        EAGPT_LAUNCH(st, "k_bounce", k_bounce<kCount><<<bounce_grid[kCount], kBlock, 0, st>>>(a.bvh, a.C, a.kind, k, B, a.rr_start, a.seed, npix,
                                                                 s0, q[(k - 1) & 1], q[k & 1], counters, slots,
                                                                 a.out_stats, perm));
       ++nl;

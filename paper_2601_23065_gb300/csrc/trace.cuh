@@ -74,7 +74,7 @@ __device__ __forceinline__ bool key_less(float ta, uint32_t ia, float tb, uint32
 }
 
 #ifndef EAGPT_FAST_SLAB
-#define EAGPT_FAST_SLAB 0
+#define EAGPT_FAST_SLAB 1
 #endif
 
 // Counters of the work one segment did (enabled by the kCount template flag).
@@ -451,6 +451,99 @@ __device__ __forceinline__ void trace_segment(const BvhView& bvh, const Consts& 
   }
 }
 
+// Resumable form of trace_segment for a loop that refills lanes with new
+// rays as soon as theirs finish: the same rounds, split into bounded chunks
+// of traversal steps.
+template <int K>
+struct RayTrace {
+  float3 O, w, inv;
+  float t_last;
+  uint32_t j_last;
+  float kt[K];
+  uint32_t kj[K];
+  int count, sp;
+  uint32_t cur;
+};
+
+template <int K>
+__device__ __forceinline__ void ray_begin(RayTrace<K>& r, float3 O, float3 w) {
+  const float big = 1e30f;
+  r.O = O;
+  r.w = w;
+  r.inv = make_float3(fabsf(w.x) > 1e-30f ? 1.0f / w.x : copysignf(big, w.x),
+                      fabsf(w.y) > 1e-30f ? 1.0f / w.y : copysignf(big, w.y),
+                      fabsf(w.z) > 1e-30f ? 1.0f / w.z : copysignf(big, w.z));
+  r.t_last = 0.f;
+  r.j_last = 0xFFFFFFFFu;
+}
+
+template <int K>
+__device__ __forceinline__ void round_begin(RayTrace<K>& r, const BvhView& bvh) {
+#pragma unroll
+  for (int i = 0; i < K; ++i) {
+    r.kt[i] = __int_as_float(0x7f800000);
+    r.kj[i] = 0xFFFFFFFFu;
+  }
+  r.count = 0;
+  r.sp = 0;
+  r.cur = bvh.n > 0 ? bvh.root : kEmptyChild;
+}
+
+// At most `steps` node or leaf steps of the current round; true once the
+// round's walk is complete.  A stack overflow (recorded as a device error)
+// ends the walk.
+template <int K, bool kCount>
+__device__ __forceinline__ bool round_steps(RayTrace<K>& r, const BvhView& bvh, const Consts& C, uint32_t* stack,
+                                            int stride, int steps, TraceCounters& cnt) {
+  for (int s = 0; s < steps && r.cur != kEmptyChild; ++s) {
+    if (r.cur & kLeafBit) {
+      leaf_step<K, kCount>(bvh, C, r.O, r.w, r.cur, r.t_last, r.j_last, r.kt, r.kj, r.count, cnt);
+      r.cur = pop(stack, stride, r.sp);
+    } else {
+      if (kCount) ++cnt.nodes;
+      const float tmax = r.count == K ? r.kt[K - 1] : __int_as_float(0x7f800000);
+      uint32_t next;
+      const bool ok = kBvh8 ? node_step8(bvh, r.cur, r.O, r.inv, r.t_last, tmax, stack, stride, r.sp, next)
+                            : node_step(bvh, r.cur, r.O, r.inv, r.t_last, tmax, stack, stride, r.sp, next);
+      if (!ok) {
+        r.cur = kEmptyChild;
+        break;
+      }
+      if (kCount && (uint32_t)r.sp > cnt.max_stack) cnt.max_stack = (uint32_t)r.sp;
+      r.cur = next != kEmptyChild ? next : pop(stack, stride, r.sp);
+    }
+  }
+  return r.cur == kEmptyChild;
+}
+
+// Blends the round's hits in order (as trace_segment does); true when the
+// segment is finished, otherwise the next round starts after the last key.
+template <int K, bool kCount, class Visitor>
+__device__ __forceinline__ bool round_blend(RayTrace<K>& r, const BvhView& bvh, const Consts& C, Visitor& vis,
+                                            TraceCounters& cnt) {
+  bool stop = false;
+#pragma unroll
+  for (int i = 0; i < K; ++i) {
+    if (i < r.count && !stop) {
+      const uint32_t j = r.kj[i];
+      const TraceRec* rp = bvh.trace + j;
+      TraceRec R;
+      R.r0 = __ldg(&rp->r0);
+      R.r1 = __ldg(&rp->r1);
+      R.r2 = __ldg(&rp->r2);
+      R.r3 = __ldg(&rp->r3);
+      HitGeom h;
+      intersect(R, r.O, r.w, C, h);
+      if (kCount) ++cnt.blended;
+      stop = vis(R, j, h);
+    }
+  }
+  if (stop || r.count < K) return true;
+  r.t_last = r.kt[K - 1];
+  r.j_last = r.kj[K - 1];
+  return false;
+}
+
 // The front-to-back blend of Eq. 2-3.  mode 1 drops the radiance of
 // non-emitters (path tracing, Sec. 3.4).
 struct BlendVisitor {
@@ -498,8 +591,13 @@ struct SmemBlendVisitor {
   uint32_t n_hits;
   __device__ __forceinline__ SmemBlendVisitor(const ShadeRec* sh, const Consts& c, int m, float* slot, int str)
       : shade(sh), C(c), mode(m), s(slot), stride(str), T(1.f), n_hits(0) {
+    reset();
+  }
+  __device__ __forceinline__ void reset() {
 #pragma unroll
     for (int k = 0; k < 11; ++k) s[k * stride] = 0.f;
+    T = 1.f;
+    n_hits = 0;
   }
   __device__ __forceinline__ bool operator()(const TraceRec& R, uint32_t j, const HitGeom& h) {
     const ShadeRec* sp = shade + j;
