@@ -614,7 +614,8 @@ def main():
                 "per_secondary_segment": {"nodes": nodes / max(1, sec_segs), "tests": tests / max(1, sec_segs),
                                           "blended": blended / max(1, sec_segs),
                                           "rounds": rounds / max(1, sec_segs),
-                                          "warp_balance": balance}}
+                                          "warp_balance": balance},
+                "max_stack": int(cnt2[7])}
 
     # end to end through the public API with host buffers
     pinned = {k: torch.from_numpy(getattr(host_scene, k)).pin_memory() for k in api.FIELDS}

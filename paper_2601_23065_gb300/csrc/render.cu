@@ -271,10 +271,10 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_bounce(BvhView bvh, Cons
 // the lanes whose round is complete blend it, and finished segments are shaded
 // and their continuation appended (warp-ballot compaction, as in k_bounce).
 #ifndef EAGPT_REFILL
-#define EAGPT_REFILL 0
+#define EAGPT_REFILL 1
 #endif
 #ifndef EAGPT_REFILL_STEPS
-#define EAGPT_REFILL_STEPS 32
+#define EAGPT_REFILL_STEPS 64
 #endif
 constexpr int kRefillSteps = EAGPT_REFILL_STEPS;
 
