@@ -485,6 +485,93 @@ def run_fit(args):
     print(json.dumps(line), flush=True)
 
 
+def run_diff(args):
+    """The differentiable single-bounce workload (1M surfels, 800x800,
+    16 spp): one step = LBVH build + single-bounce forward (Eq. 6) + the
+    hand-written adjoint for L = sum w . image with w ~ U[-1, 1] (seed 11),
+    gradients for every surfel parameter.  Segments counted: the forward's
+    primary and secondary segments, and the adjoint's re-traces (primary
+    records once, every secondary segment twice: values then adjoint, every
+    hit primary twice)."""
+    import numpy as np
+    import torch
+
+    from paper_2601_23065_gb300 import api, build, capi
+    from paper_2601_23065_gb300 import scenes as S
+
+    build.build()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    L = capi.lib()
+    wl = S.workload("diff")
+    spp = args.spp or wl.spp
+    host = wl.scene_fn()
+    cam = wl.camera
+    ds = api.DeviceScene.from_host(host, device=dev)
+    r = api.Renderer(device=dev)
+    w = torch.from_numpy(np.random.default_rng(11).uniform(-1, 1, (cam.height, cam.width, 3)).astype(np.float32)).to(dev)
+    grads = {k: torch.zeros_like(ds.t[k]) for k in api.GRAD_FIELDS}
+    need = L.eagpt_render_backward_workspace_bytes(ctypes.byref(api.camera(cam)), spp)
+    bws = torch.empty(need, dtype=torch.uint8, device=dev)
+
+    def step(seed):
+        bvh = api.BVH(ds)
+        img = r.single_bounce(ds, bvh, cam, spp, seed=seed)["rgb"]
+        for g in grads.values():
+            g.zero_()
+        api.single_bounce_backward(ds, bvh, cam, spp, seed, w, grads=grads, workspace=bws)
+        return img
+
+    # the same rays as a path-traced render with one bounce and no roulette
+    st = r.path_traced(ds, api.BVH(ds), cam, spp, 1, rr_start=1 << 20, seed=3, want_stats=True)["stats"].cpu().numpy()
+    prim, sec = int(st[0]), int(st[1])
+    hit_prim = int(st[2] // max(1, spp))
+    fwd_segs = prim + sec
+    bwd_segs = prim + 2 * sec + 2 * hit_prim
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    for _ in range(max(3, args.warmup)):
+        step(3)
+    torch.cuda.synchronize(dev)
+    clocks = ClockSampler(0)
+    clocks.start()
+    launches0 = L.eagpt_launch_count()
+    capi.check(L.eagpt_profile_begin())
+    times = []
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        step(3)
+        b.record()
+        b.synchronize()
+        times.append(a.elapsed_time(b))
+    prof = capi.profile_end()
+    launches = L.eagpt_launch_count() - launches0
+    clk = clocks.stop()
+    api.sync_status()
+    ms = sum(times) / len(times)
+    segs = fwd_segs + bwd_segs
+    value = segs / (ms * 1e-3)
+    total_kernel_ms = sum(v[1] for v in prof.values())
+    kname = max(prof.items(), key=lambda kv: kv[1][1])[0]
+    peak, peak_kind = load_peaks()
+    line = {"metric": METRIC + " (single-bounce forward + adjoint)", "value": value, "unit": METRIC, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": wl.name, "surfels": host.n, "width": cam.width, "height": cam.height, "spp": spp,
+                       "forward_segments": fwd_segs, "adjoint_segments": bwd_segs,
+                       "step": "LBVH build + single-bounce forward + adjoint (all parameters)",
+                       "l2": "flushed between steps (512 MB write)"},
+            "roofline": {"bound": "hbm", "kernel": kname, "achieved": None, "peak": peak, "unit": "GB/s",
+                         "frac": None, "traffic": None,
+                         "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
+                         "share_of_kernel_time": prof[kname][1] / total_kernel_ms if total_kernel_ms else None},
+            "cpu_baseline": None, "gpu_launches": int(launches), "clocks": clk,
+            "kernels": {k: {"launches": v[0], "ms": v[1]} for k, v in sorted(prof.items())}}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
@@ -493,6 +580,9 @@ def main():
         return
     if args.workload in ("stage1", "bake") and args.impl == "native":
         run_fit(args)
+        return
+    if args.workload == "diff" and args.impl == "native":
+        run_diff(args)
         return
     if args.impl == "reference":
         if world > 1:

@@ -43,7 +43,7 @@ constexpr int kSrvMaxActive = 64;
 constexpr int kSrvMaxBounces = 60;
 constexpr int kSrvCounterWords = 2 * (kSrvMaxBounces + 2) + 8;
 #ifndef EAGPT_SERVE_KBUF
-#define EAGPT_SERVE_KBUF 16
+#define EAGPT_SERVE_KBUF 12
 #endif
 constexpr int kSrvK = EAGPT_SERVE_KBUF;
 
@@ -91,34 +91,70 @@ __global__ void __launch_bounds__(kBlock) k_srv_generate(const ReqDev* __restric
   if (take) q_out[at] = r;
 }
 
-__global__ void __launch_bounds__(kBlock) k_srv_bounce(BvhView v0, BvhView v1, const ReqDev* __restrict__ reqs,
-                                                       Consts C, int k, const Ray* __restrict__ q_in, Ray* q_out,
-                                                       uint32_t* counters) {
+// One bounce of every queued path of every admitted request, with the
+// per-lane refill of the single-request bounce kernel: a lane whose segment
+// is finished takes the next queued ray at once; traversal runs in chunks of
+// kSrvSteps node/leaf steps.  Each ray traces the BVH version of its request.
+constexpr int kSrvSteps = 64;
+
+__global__ void __launch_bounds__(kBlock, kMinBlocks) k_srv_bounce(BvhView v0, BvhView v1,
+                                                                   const ReqDev* __restrict__ reqs, Consts C, int k,
+                                                                   const Ray* __restrict__ q_in, Ray* q_out,
+                                                                   uint32_t* counters) {
   __shared__ uint32_t s_stack[kStackSize * kBlock];
+  __shared__ float s_blend[11 * kBlock];
   const int lane = threadIdx.x & 31;
   const uint32_t count = counters[2 * k];
   TraceCounters cnt{0, 0, 0, 0, 0};
+  RayTrace<kSrvK> rt;
+  SmemBlendVisitor vis(v0.shade, C, 1, s_blend + threadIdx.x, kBlock);
+  uint32_t qi = 0, rq = 0;
+  bool active = false, exhausted = false;
   for (;;) {
-    uint32_t base = 0;
-    if (lane == 0) base = atomicAdd(&counters[2 * k + 1], 32u);
-    base = __shfl_sync(0xffffffffu, base, 0);
-    if (base >= count) break;
-    const uint32_t idx = base + lane;
+    const bool want = !active && !exhausted;
+    const uint32_t wmask = __ballot_sync(0xffffffffu, want);
+    if (wmask) {
+      const int leader = __ffs(wmask) - 1;
+      uint32_t base = 0;
+      if (lane == leader) base = atomicAdd(&counters[2 * k + 1], (uint32_t)__popc(wmask));
+      base = __shfl_sync(0xffffffffu, base, leader);
+      if (want) {
+        const uint32_t idx = base + (uint32_t)__popc(wmask & ((1u << lane) - 1u));
+        if (idx < count) {
+          qi = idx;
+          rq = __float_as_uint(q_in[qi].c.w);
+          const BvhView& bvh = reqs[rq].version ? v1 : v0;
+          ray_begin(rt, f3(q_in[qi].a), f3(q_in[qi].b));
+          round_begin(rt, bvh);
+          vis.shade = bvh.shade;
+          vis.reset();
+          active = true;
+        } else {
+          exhausted = true;
+        }
+      }
+    }
+    if (!__any_sync(0xffffffffu, active)) break;
     bool take = false;
     Ray nr;
-    if (idx < count) {
-      const Ray r = q_in[idx];
-      const ReqDev& R = reqs[__float_as_uint(r.c.w)];
+    if (active) {
+      const ReqDev& R = reqs[rq];
       const BvhView& bvh = R.version ? v1 : v0;
-      const float3 O = f3(r.a), w = f3(r.b);
-      const uint32_t pixel = __float_as_uint(r.a.w), sample = __float_as_uint(r.b.w);
-      BlendVisitor vis(bvh.shade, C, w, 1);
-      trace_segment<kSrvK, false>(bvh, C, O, w, 0.f, s_stack + threadIdx.x, kBlock, vis, cnt);
-      const SegRec s = finish(vis.b);
-      float3 contrib;
-      take = shade_bounce(1, k, R.max_bounces, R.rr_start, R.seed, C, r, s, contrib, nr);
-      if (!take)
-        R.slots[(int64_t)(sample - (uint32_t)R.s0) * R.npix + pixel] = make_float4(contrib.x, contrib.y, contrib.z, 0.f);
+      if (round_steps<kSrvK, false>(rt, bvh, C, s_stack + threadIdx.x, kBlock, kSrvSteps, cnt)) {
+        if (round_blend<kSrvK, false>(rt, bvh, C, vis, cnt)) {
+          const SegRec s = finish(vis.get());
+          const Ray r = q_in[qi];
+          const uint32_t pixel = __float_as_uint(r.a.w), sample = __float_as_uint(r.b.w);
+          float3 contrib;
+          take = shade_bounce(1, k, R.max_bounces, R.rr_start, R.seed, C, r, s, contrib, nr);
+          if (!take)
+            R.slots[(int64_t)(sample - (uint32_t)R.s0) * R.npix + pixel] =
+                make_float4(contrib.x, contrib.y, contrib.z, 0.f);
+          active = false;
+        } else {
+          round_begin(rt, bvh);
+        }
+      }
     }
     __syncwarp();
     const uint32_t at = warp_append(take, &counters[2 * (k + 1)]);

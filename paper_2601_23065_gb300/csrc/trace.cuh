@@ -216,6 +216,27 @@ __device__ __forceinline__ bool node_step8(const BvhView& bvh, uint32_t node, fl
   uint32_t c[8] = {u1.x, u1.y, u1.z, u1.w, u2.x, u2.y, u2.z, u2.w};
   const uint32_t qlx[2] = {u3.x, u3.y}, qly[2] = {u3.z, u3.w}, qlz[2] = {u4.x, u4.y};
   const uint32_t qhx[2] = {u4.z, u4.w}, qhy[2] = {u5.x, u5.y}, qhz[2] = {u5.z, u5.w};
+#if EAGPT_FAST_SLAB
+  // near/far planes by direction sign, decoded exactly as the builder checked
+  // them (fma(q, quantum, origin)), then one FMA per plane as in node_step
+  const bool px = inv.x >= 0.f, py = inv.y >= 0.f, pz = inv.z >= 0.f;
+  const uint32_t nqx[2] = {px ? qlx[0] : qhx[0], px ? qlx[1] : qhx[1]}, fqx[2] = {px ? qhx[0] : qlx[0], px ? qhx[1] : qlx[1]};
+  const uint32_t nqy[2] = {py ? qly[0] : qhy[0], py ? qly[1] : qhy[1]}, fqy[2] = {py ? qhy[0] : qly[0], py ? qhy[1] : qly[1]};
+  const uint32_t nqz[2] = {pz ? qlz[0] : qhz[0], pz ? qlz[1] : qhz[1]}, fqz[2] = {pz ? qhz[0] : qlz[0], pz ? qhz[1] : qlz[1]};
+  const float oix = O.x * inv.x, oiy = O.y * inv.y, oiz = O.z * inv.z;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const int w = k >> 2, sh = 8 * (k & 3);
+    const float nx = __fmaf_rn((float)((nqx[w] >> sh) & 0xFFu), sx, ox), fx = __fmaf_rn((float)((fqx[w] >> sh) & 0xFFu), sx, ox);
+    const float ny = __fmaf_rn((float)((nqy[w] >> sh) & 0xFFu), sy, oy), fy = __fmaf_rn((float)((fqy[w] >> sh) & 0xFFu), sy, oy);
+    const float nz = __fmaf_rn((float)((nqz[w] >> sh) & 0xFFu), sz, oz), fz = __fmaf_rn((float)((fqz[w] >> sh) & 0xFFu), sz, oz);
+    const float t0 = fmaxf(fmaxf(__fmaf_rn(nx, inv.x, -oix), __fmaf_rn(ny, inv.y, -oiy)),
+                           fmaxf(__fmaf_rn(nz, inv.z, -oiz), t_last));
+    const float t1 = fminf(fminf(__fmaf_rn(fx, inv.x, -oix), __fmaf_rn(fy, inv.y, -oiy)),
+                           fminf(__fmaf_rn(fz, inv.z, -oiz), tmax));
+    e[k] = (t0 <= t1 && c[k] != kEmptyChild) ? t0 : inf;
+  }
+#else
 #pragma unroll
   for (int k = 0; k < 8; ++k) {
     const int w = k >> 2, sh = 8 * (k & 3);
@@ -229,6 +250,7 @@ __device__ __forceinline__ bool node_step8(const BvhView& bvh, uint32_t node, fl
     const bool h = box_hit(lo, hi, O, inv, t_last, tmax, te);
     e[k] = (h && c[k] != kEmptyChild) ? te : inf;
   }
+#endif
 #define EAGPT_CSWAP(i, j)                         \
   if (e[j] < e[i]) {                              \
     const float tf = e[i];                        \
