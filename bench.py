@@ -50,6 +50,28 @@ def parse():
     return ap.parse_args()
 
 
+def rank_seed(rank: int) -> int:
+    """Render seed of a rank: every rank draws its own samples (independent
+    paths), so N ranks together render N times one rank's work."""
+    return 1000003 * rank
+
+
+def max_over_ranks(t_local: float, world: int, device=None) -> float:
+    """The step time of the whole job: the slowest rank's (all-reduce MAX)."""
+    if world <= 1:
+        return t_local
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([t_local], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world: int, units_per_rank_step: int, steps: int, t_max: float) -> float:
+    """Whole-job throughput: every rank's units over the slowest rank's time."""
+    return world * units_per_rank_step * steps / t_max
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -614,7 +636,7 @@ def main():
         wl.spp = args.spp
     host_scene = wl.scene_fn()
     cam = wl.camera
-    seed_base = 1000003 * rank  # each rank renders its own samples
+    seed_base = rank_seed(rank)  # each rank renders its own samples
     ds = api.DeviceScene.from_host(host_scene, device=dev)
     r = api.Renderer(device=dev)
     stream = torch.cuda.current_stream(dev)
@@ -667,13 +689,8 @@ def main():
 
     ms = sum(times) / len(times)
     t_local = sum(times) / 1e3
-    if world > 1:
-        t = torch.tensor([t_local], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_max = float(t.item())
-    else:
-        t_max = t_local
-    value = world * segs_per_step * args.steps / t_max
+    t_max = max_over_ranks(t_local, world, dev)
+    value = job_value(world, segs_per_step, args.steps, t_max)
 
     # roofline of the dominant kernel (the fused trace/shade/compact bounce)
     kern = max(prof.items(), key=lambda kv: kv[1][1])

@@ -230,6 +230,30 @@ eagpt_status eagpt_apply_edit(eagpt_scene_mut* scene, eagpt_bvh* bvh, const eagp
                               eagpt_stream_t stream);
 
 /* ------------------------------------------------------------------------
+ * Inserting and deleting surfels (the teaser's insert / import and delete
+ * edits).  The surfel count changes, so the BVH is rebuilt in place into its
+ * storage (this synchronises `stream`); scene->version and
+ * bvh->scene_version are incremented.  No paper passage fixes an algorithm:
+ * the result is defined as the edited list of surfels.
+ *
+ * eagpt_delete_surfels(): removes the surfels listed in idx (device int32,
+ *   count entries; duplicates allowed) and keeps the others in their order
+ *   at the front of the arrays; scene->n becomes the number kept.  Indices
+ *   outside [0, n) are skipped and reported by eagpt_sync_status().
+ *   scratch: device, eagpt_delete_scratch_bytes(n) bytes, 256-byte aligned.
+ * eagpt_insert_surfels(): appends the src->n surfels of src (device arrays)
+ *   after the scene's n; the scene arrays must hold `capacity` >= n + src->n
+ *   surfels and bvh->bytes >= eagpt_bvh_bytes(n + src->n), else
+ *   EAGPT_ERR_OUT_OF_MEMORY and nothing changes.
+ * ------------------------------------------------------------------------ */
+size_t eagpt_delete_scratch_bytes(int64_t n);
+eagpt_status eagpt_delete_surfels(eagpt_scene_mut* scene, eagpt_bvh* bvh, const eagpt_params* params,
+                                  const int32_t* idx, int64_t count, void* scratch, size_t scratch_bytes,
+                                  eagpt_stream_t stream);
+eagpt_status eagpt_insert_surfels(eagpt_scene_mut* scene, int64_t capacity, const eagpt_scene* src, eagpt_bvh* bvh,
+                                  const eagpt_params* params, eagpt_stream_t stream);
+
+/* ------------------------------------------------------------------------
  * Serving: a persistent request loop over one resident scene (the paper's
  * edit-then-path-trace use, Sec. 3.4, served to many clients).
  *

@@ -484,6 +484,50 @@ def apply_edit(scene: DeviceScene, bvh: BVH, op: str, idx: torch.Tensor, value=(
     return bool(rebuilt.value)
 
 
+def delete_surfels(scene: DeviceScene, bvh: BVH, idx: torch.Tensor, stream=None) -> int:
+    """Removes the listed surfels, keeping the others in order
+    (eagpt_delete_surfels); the scene's tensors become views of their first n
+    rows and the BVH is rebuilt.  Returns the new surfel count."""
+    L = capi.lib()
+    dev = scene.t["pos"].device
+    idx = idx.to(device=dev, dtype=torch.int32).contiguous()
+    scratch = torch.empty(max(L.eagpt_delete_scratch_bytes(scene.n), 256), dtype=torch.uint8, device=dev)
+    sm = scene.c()
+    capi.check(L.eagpt_delete_surfels(ctypes.byref(sm), ctypes.byref(bvh.handle), ctypes.byref(bvh.params),
+                                      _ptr(idx), idx.numel(), _ptr(scratch), scratch.numel(), _stream(stream)))
+    scene.n, scene.version = int(sm.n), int(sm.version)
+    scene.t = {k: v[:scene.n] for k, v in scene.t.items()}
+    return scene.n
+
+
+def insert_surfels(scene: DeviceScene, bvh: BVH, src: DeviceScene, stream=None) -> int:
+    """Appends the surfels of ``src`` (eagpt_insert_surfels) and rebuilds the
+    BVH; the scene's tensors and the BVH storage are reallocated first when
+    they are too small.  Returns the new surfel count."""
+    L = capi.lib()
+    n, m = scene.n, src.n
+    cap = n + m
+    for k in FIELDS:
+        t = scene.t[k]
+        if t.untyped_storage().nbytes() // 4 < cap * SHAPES[k] or t.storage_offset() != 0:
+            grown = torch.empty((cap,) + tuple(t.shape[1:]), dtype=torch.float32, device=t.device)
+            grown[:n].copy_(t[:n])
+            scene.t[k] = grown
+        else:
+            scene.t[k] = t.as_strided((cap,) + tuple(t.shape[1:]), t.stride())
+    need = L.eagpt_bvh_bytes(cap)
+    if bvh.storage.numel() < need:
+        bvh.storage = torch.empty(need, dtype=torch.uint8, device=bvh.storage.device)
+        bvh.handle.storage = bvh.storage.data_ptr()
+        bvh.handle.bytes = bvh.storage.numel()
+    sm = scene.c()
+    srcc = src.c()
+    capi.check(L.eagpt_insert_surfels(ctypes.byref(sm), cap, ctypes.byref(srcc), ctypes.byref(bvh.handle),
+                                      ctypes.byref(bvh.params), _stream(stream)))
+    scene.n, scene.version = int(sm.n), int(sm.version)
+    return scene.n
+
+
 class Server:
     """Continuous-batching request loop (eagpt_server_*): renders and edits
     are submitted from any thread; the library's own thread batches them."""

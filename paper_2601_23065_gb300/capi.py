@@ -146,6 +146,9 @@ SIGNATURES = {
     "eagpt_fit_workspace_bytes": (c_sz, [P(FitConfig), c_vp, c_i32, c_i64]),
     "eagpt_fit": (c_i32, [P(FitConfig), P(Scene), P(Bvh), P(Params), c_vp, c_vp, c_i32, c_vp, c_i64, c_i32,
                           c_vp, c_vp, c_vp, c_vp, c_sz, c_vp]),
+    "eagpt_delete_scratch_bytes": (c_sz, [c_i64]),
+    "eagpt_delete_surfels": (c_i32, [P(Scene), P(Bvh), P(Params), c_vp, c_i64, c_vp, c_sz, c_vp]),
+    "eagpt_insert_surfels": (c_i32, [P(Scene), c_i64, P(Scene), P(Bvh), P(Params), c_vp]),
     "eagpt_sync_status": (c_i32, [c_vp]),
     "eagpt_launch_count": (c_i64, []),
     "eagpt_profile_begin": (c_i32, []),

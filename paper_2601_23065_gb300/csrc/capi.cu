@@ -696,3 +696,67 @@ eagpt_status eagpt_fit(const eagpt_fit_config* cfg, eagpt_scene_mut* scene, eagp
 }
 
 }  // extern "C"
+
+// --------------------------------------------------------------------------
+// insert / delete surfels (the scene's surfel count changes: full rebuild)
+// --------------------------------------------------------------------------
+extern "C" {
+
+size_t eagpt_delete_scratch_bytes(int64_t n) { return n < 0 ? 0 : delete_scratch_bytes(n); }
+
+eagpt_status eagpt_delete_surfels(eagpt_scene_mut* scene, eagpt_bvh* bvh, const eagpt_params* params,
+                                  const int32_t* idx, int64_t count, void* scratch, size_t scratch_bytes,
+                                  eagpt_stream_t stream) {
+  eagpt_status s;
+  if (!scene) return fail(EAGPT_ERR_INVALID_ARGUMENT, "scene is NULL%s");
+  eagpt_scene cs;
+  std::memcpy(&cs, scene, sizeof(cs));
+  if ((s = check_scene(&cs)) != EAGPT_OK) return s;
+  if ((s = check_params(params)) != EAGPT_OK) return s;
+  if ((s = check_bvh(bvh, &cs, params)) != EAGPT_OK) return s;
+  if (count < 0 || (count > 0 && !idx)) return fail(EAGPT_ERR_INVALID_ARGUMENT, "bad idx/count%s");
+  if (!scratch || !aligned(scratch, 256) || scratch_bytes < delete_scratch_bytes(cs.n))
+    return fail(EAGPT_ERR_OUT_OF_MEMORY, "delete scratch too small or misaligned%s");
+  int64_t m = 0;
+  cudaError_t e = launch_delete(*scene, idx, count, scratch, &m, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "delete launch");
+  scene->n = m;
+  scene->version += 1;
+  std::memcpy(&cs, scene, sizeof(cs));
+  return eagpt_build_bvh(&cs, params, bvh->storage, bvh->bytes, bvh, stream);
+}
+
+eagpt_status eagpt_insert_surfels(eagpt_scene_mut* scene, int64_t capacity, const eagpt_scene* src, eagpt_bvh* bvh,
+                                  const eagpt_params* params, eagpt_stream_t stream) {
+  eagpt_status s;
+  if (!scene) return fail(EAGPT_ERR_INVALID_ARGUMENT, "scene is NULL%s");
+  eagpt_scene cs;
+  std::memcpy(&cs, scene, sizeof(cs));
+  if ((s = check_scene(&cs)) != EAGPT_OK) return s;
+  if ((s = check_scene(src)) != EAGPT_OK) return s;
+  if ((s = check_params(params)) != EAGPT_OK) return s;
+  if ((s = check_bvh(bvh, &cs, params)) != EAGPT_OK) return s;
+  const int64_t m = src->n, n = cs.n;
+  if (n + m > capacity) return fail(EAGPT_ERR_OUT_OF_MEMORY, "the scene arrays hold %s%lld surfels", "", capacity);
+  if (n + m > kMaxSurfels) return fail(EAGPT_ERR_INVALID_ARGUMENT, "too many surfels%s");
+  if (n + m > 0 && bvh_layout(n + m).total > bvh->bytes)
+    return fail(EAGPT_ERR_OUT_OF_MEMORY, "bvh storage too small: need %s%lld bytes", "",
+                (long long)bvh_layout(n + m).total);
+  cudaStream_t st = (cudaStream_t)stream;
+  float* dst[7] = {scene->pos, scene->quat, scene->scale, scene->opacity, scene->albedo, scene->radiance,
+                   scene->emissive};
+  const float* from[7] = {src->pos, src->quat, src->scale, src->opacity, src->albedo, src->radiance, src->emissive};
+  const int comps[7] = {3, 4, 2, 1, 3, 3, 1};
+  for (int f = 0; f < 7 && m > 0; ++f) {
+    if (!dst[f]) return fail(EAGPT_ERR_INVALID_ARGUMENT, "scene arrays are required%s");
+    cudaError_t e = cudaMemcpyAsync(dst[f] + n * comps[f], from[f], (size_t)m * comps[f] * sizeof(float),
+                                    cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(e, "insert copy");
+  }
+  scene->n = n + m;
+  scene->version += 1;
+  std::memcpy(&cs, scene, sizeof(cs));
+  return eagpt_build_bvh(&cs, params, bvh->storage, bvh->bytes, bvh, stream);
+}
+
+}  // extern "C"

@@ -211,3 +211,121 @@ cudaError_t launch_edit(const eagpt_scene_mut& sc, const eagpt_edit& e, cudaStre
 }
 
 }  // namespace eagpt
+
+namespace eagpt {
+
+// --------------------------------------------------------------------------
+// Deletion: the listed surfels leave the scene and the others keep their
+// order.  keep[i] = 0 for listed i; the kept positions are counted per
+// block, scanned, and written as an ordered gather map; every field is then
+// gathered into a scratch array and copied back over the front of its array.
+// --------------------------------------------------------------------------
+__global__ void k_del_init(uint32_t* keep, int64_t n) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) keep[i] = 1u;
+}
+
+__global__ void k_del_mark(uint32_t* keep, int64_t n, const int32_t* __restrict__ idx, int64_t count) {
+  const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k >= count) return;
+  const int32_t i = idx[k];
+  if (i < 0 || i >= n) {
+    raise_error(kErrBadIndex);  // skipped and reported
+    return;
+  }
+  keep[i] = 0u;
+}
+
+__global__ void __launch_bounds__(kSelBlock) k_del_count(const uint32_t* __restrict__ keep, int64_t n,
+                                                         uint32_t* block_counts) {
+  __shared__ uint32_t warp_tot[kSelBlock / 32];
+  const int64_t i = blockIdx.x * (int64_t)kSelBlock + threadIdx.x;
+  const uint32_t b = __ballot_sync(0xffffffffu, i < n && keep[i]);
+  if ((threadIdx.x & 31) == 0) warp_tot[threadIdx.x >> 5] = __popc(b);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t t = 0;
+    for (int w = 0; w < kSelBlock / 32; ++w) t += warp_tot[w];
+    block_counts[blockIdx.x] = t;
+  }
+}
+
+__global__ void __launch_bounds__(kSelBlock) k_del_map(const uint32_t* __restrict__ keep, int64_t n,
+                                                       const uint32_t* __restrict__ block_offsets, int32_t* map) {
+  __shared__ uint32_t warp_off[kSelBlock / 32];
+  const int64_t i = blockIdx.x * (int64_t)kSelBlock + threadIdx.x;
+  const bool in = i < n && keep[i];
+  const uint32_t b = __ballot_sync(0xffffffffu, in);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) warp_off[warp] = __popc(b);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t run = 0;
+    for (int w = 0; w < kSelBlock / 32; ++w) {
+      const uint32_t c = warp_off[w];
+      warp_off[w] = run;
+      run += c;
+    }
+  }
+  __syncthreads();
+  if (in) map[(int64_t)block_offsets[blockIdx.x] + warp_off[warp] + __popc(b & ((1u << lane) - 1u))] = (int32_t)i;
+}
+
+__global__ void k_del_gather(const float* __restrict__ src, float* dst, const int32_t* __restrict__ map,
+                             int64_t m, int comps) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= m * comps) return;
+  const int64_t d = t / comps;
+  const int c = (int)(t - d * comps);
+  dst[t] = src[(int64_t)map[d] * comps + c];
+}
+
+size_t delete_scratch_bytes(int64_t n) {
+  const size_t nn = (size_t)(n > 0 ? n : 1);
+  const size_t blocks = (nn + kSelBlock - 1) / kSelBlock + 1;
+  return align256(nn * 4) + align256(blocks * 4) + align256(nn * 4) + align256(nn * 16) + 256;
+}
+
+// Deletes the listed surfels (in place); returns the new count in *out_n
+// (synchronises the stream to read it).
+cudaError_t launch_delete(const eagpt_scene_mut& sc, const int32_t* idx, int64_t count, void* scratch,
+                          int64_t* out_n, cudaStream_t st) {
+  const int64_t n = sc.n;
+  const size_t nn = (size_t)(n > 0 ? n : 1);
+  const int64_t blocks = (n + kSelBlock - 1) / kSelBlock;
+  char* s = (char*)scratch;
+  uint32_t* keep = (uint32_t*)s;
+  s += align256(nn * 4);
+  uint32_t* bc = (uint32_t*)s;
+  s += align256(((nn + kSelBlock - 1) / kSelBlock + 1) * 4);
+  int32_t* map = (int32_t*)s;
+  s += align256(nn * 4);
+  float* tmp = (float*)s;
+  s += align256(nn * 16);
+  int64_t* dcount = (int64_t*)s;
+  if (n == 0) {
+    *out_n = 0;
+    return cudaSuccess;
+  }
+  EAGPT_LAUNCH(st, "k_del_init", k_del_init<<<nb(n, 256), 256, 0, st>>>(keep, n));
+  if (count > 0) EAGPT_LAUNCH(st, "k_del_mark", k_del_mark<<<nb(count, 256), 256, 0, st>>>(keep, n, idx, count));
+  EAGPT_LAUNCH(st, "k_del_count", k_del_count<<<(unsigned)blocks, kSelBlock, 0, st>>>(keep, n, bc));
+  EAGPT_LAUNCH(st, "k_select_scan", k_select_scan<<<1, 1024, 0, st>>>(bc, blocks, dcount));
+  EAGPT_LAUNCH(st, "k_del_map", k_del_map<<<(unsigned)blocks, kSelBlock, 0, st>>>(keep, n, bc, map));
+  int64_t m = 0;
+  cudaError_t e = cudaMemcpyAsync(&m, dcount, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return e;
+  float* fields[7] = {sc.pos, sc.quat, sc.scale, sc.opacity, sc.albedo, sc.radiance, sc.emissive};
+  const int comps[7] = {3, 4, 2, 1, 3, 3, 1};
+  for (int f = 0; f < 7 && m > 0; ++f) {
+    EAGPT_LAUNCH(st, "k_del_gather",
+                 k_del_gather<<<nb(m * comps[f], 256), 256, 0, st>>>(fields[f], tmp, map, m, comps[f]));
+    e = cudaMemcpyAsync(fields[f], tmp, (size_t)m * comps[f] * sizeof(float), cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) return e;
+  }
+  *out_n = m;
+  return cudaGetLastError();
+}
+
+}  // namespace eagpt

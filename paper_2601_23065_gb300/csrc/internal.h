@@ -87,6 +87,9 @@ cudaError_t launch_select(const eagpt_scene& sc, int shape, const float* v, int3
                           int64_t* out_count, uint32_t* scratch_blocks, cudaStream_t st);
 size_t select_scratch_bytes(int64_t n);
 cudaError_t launch_edit(const eagpt_scene_mut& sc, const eagpt_edit& e, cudaStream_t st);
+size_t delete_scratch_bytes(int64_t n);
+cudaError_t launch_delete(const eagpt_scene_mut& sc, const int32_t* idx, int64_t count, void* scratch,
+                          int64_t* out_n, cudaStream_t st);
 
 // capi.cu: argument checks + render launch shared by the render entry points;
 // set_error records the thread-local message of eagpt_last_error()
