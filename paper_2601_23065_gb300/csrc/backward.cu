@@ -24,7 +24,14 @@ namespace eagpt {
 
 EAGPT_DEFINE_ERROR_READER(take_errors_backward)
 
-constexpr int kKb = 16;
+#ifndef EAGPT_BWD_KBUF
+#define EAGPT_BWD_KBUF 12
+#endif
+#ifndef EAGPT_BWD_MIN_BLOCKS
+#define EAGPT_BWD_MIN_BLOCKS 4
+#endif
+constexpr int kKb = EAGPT_BWD_KBUF;             // k-buffer of the adjoint's traversals
+constexpr int kBwdMinBlocks = EAGPT_BWD_MIN_BLOCKS;  // resident blocks per SM of the secondary adjoint
 
 struct __align__(16) PrimRecB {
   float4 a, b, c;  // same layout as the forward's primary record
@@ -36,6 +43,30 @@ struct RawVisitor {
   __device__ __forceinline__ RawVisitor(const ShadeRec* s, const Consts& c, float3 w, int m) : blend(s, c, w, m) {}
   __device__ __forceinline__ bool operator()(const TraceRec& R, uint32_t j, const HitGeom& h) {
     return blend(R, j, h);
+  }
+};
+
+// First pass when only the blended radiance R is differentiated (the
+// secondary segment of Eq. 6, the 0-bounce image): R and T with the forward's
+// exact arithmetic (same stopping decisions), nothing else.
+struct RBlendVisitor {
+  const ShadeRec* shade;
+  Consts C;
+  int mode;
+  float3 R;
+  float T;
+  uint32_t n_hits;
+  __device__ __forceinline__ RBlendVisitor(const ShadeRec* s, const Consts& c, int m)
+      : shade(s), C(c), mode(m), R(make_float3(0.f, 0.f, 0.f)), T(1.f), n_hits(0) {}
+  __device__ __forceinline__ bool operator()(const TraceRec&, uint32_t j, const HitGeom& h) {
+    const ShadeRec* sp = shade + j;
+    const float4 s1 = __ldg(&sp->s1);
+    const float wgt = __fmul_rn(T, h.alpha);
+    const float re = (mode == 1 && !(__ldg(&sp->s0.w) > C.tau_E)) ? 0.f : wgt;
+    R = make_float3(__fmaf_rn(re, s1.x, R.x), __fmaf_rn(re, s1.y, R.y), __fmaf_rn(re, s1.z, R.z));
+    T = __fmul_rn(T, __fsub_rn(1.f, h.alpha));
+    ++n_hits;
+    return T < C.T_min;
   }
 };
 
@@ -56,7 +87,8 @@ __device__ __forceinline__ float4 quat_adjoint(float4 q, float3 a, float3 b, flo
 // Front-to-back adjoint of one segment (second pass).  gN, gD, gR, gP, gA
 // are the adjoints of the raw blended sums N, D, R, P and of A = 1 - T_n;
 // V holds the raw sums of the first pass.
-struct AdjointVisitor {
+template <bool kOnlyR>
+struct AdjointVisitorT {
   const ShadeRec* shade;
   eagpt_scene sc;
   eagpt_scene_grad gr;
@@ -82,22 +114,26 @@ struct AdjointVisitor {
     const float3 vR = remit * make_float3(s1.x, s1.y, s1.z);
     const float3 vP = make_float3(s0.x, s0.y, s0.z);
     // running sums including this hit
-    run.N = run.N + wgt * vN;
+    if (!kOnlyR) {
+      run.N = run.N + wgt * vN;
+      run.P = run.P + wgt * vP;
+      run.D += wgt * h.t;
+    }
     run.R = run.R + wgt * vR;
-    run.P = run.P + wgt * vP;
-    run.D += wgt * h.t;
     run.T = Tp * (1.f - a);
     const float inv1a = 1.f / (1.f - a);
     // dL/dalpha: T_{i-1} v_i - S_i / (1 - alpha_i), S_i = V - V_{<=i}
-    float da = gA * V.T * inv1a;
-    da += dot3(gN, Tp * vN - inv1a * (V.N - run.N));
-    da += dot3(gR, Tp * vR - inv1a * (V.R - run.R));
-    da += dot3(gP, Tp * vP - inv1a * (V.P - run.P));
-    da += gD * (Tp * h.t - inv1a * (V.D - run.D));
-    // albedo, radiance
-    atomicAdd(&gr.albedo[3 * id + 0], wgt * gP.x);
-    atomicAdd(&gr.albedo[3 * id + 1], wgt * gP.y);
-    atomicAdd(&gr.albedo[3 * id + 2], wgt * gP.z);
+    float da = dot3(gR, Tp * vR - inv1a * (V.R - run.R));
+    if (!kOnlyR) {
+      da += gA * V.T * inv1a;
+      da += dot3(gN, Tp * vN - inv1a * (V.N - run.N));
+      da += dot3(gP, Tp * vP - inv1a * (V.P - run.P));
+      da += gD * (Tp * h.t - inv1a * (V.D - run.D));
+      // albedo
+      atomicAdd(&gr.albedo[3 * id + 0], wgt * gP.x);
+      atomicAdd(&gr.albedo[3 * id + 1], wgt * gP.y);
+      atomicAdd(&gr.albedo[3 * id + 2], wgt * gP.z);
+    }
     if (remit != 0.f) {
       atomicAdd(&gr.radiance[3 * id + 0], wgt * gR.x);
       atomicAdd(&gr.radiance[3 * id + 1], wgt * gR.y);
@@ -123,8 +159,8 @@ struct AdjointVisitor {
     const float3 dtu = (du / su) * Dx, dtv = (dv / sv) * Dx;
     atomicAdd(&gr.scale[2 * id + 0], -du * h.u / su);
     atomicAdd(&gr.scale[2 * id + 1], -dv * h.v / sv);
-    float3 dn = (wgt * sgn) * gN;
-    const float dt = wgt * gD + dot3(dDx, w);
+    float3 dn = kOnlyR ? make_float3(0.f, 0.f, 0.f) : (wgt * sgn) * gN;
+    const float dt = kOnlyR ? dot3(dDx, w) : wgt * gD + dot3(dDx, w);
     // Dx = O - p + t w
     dO = dO + dDx;
     dw = dw + h.t * dDx;
@@ -147,6 +183,8 @@ struct AdjointVisitor {
     return run.T < C.T_min;
   }
 };
+
+using AdjointVisitor = AdjointVisitorT<false>;
 
 __device__ __forceinline__ void init_blend(Blend& b) {
   b.N = b.R = b.P = make_float3(0.f, 0.f, 0.f);
@@ -177,7 +215,7 @@ __device__ __forceinline__ float3 cosine_direction_adjoint(float3 n, float u0, f
   return l0 * g1 + l1 * g2 + l2 * dw;
 }
 
-__global__ void __launch_bounds__(kBlock) k_bwd_secondary(BvhView bvh, Consts C, eagpt_camera cam, eagpt_scene sc,
+__global__ void __launch_bounds__(kBlock, kBwdMinBlocks) k_bwd_secondary(BvhView bvh, Consts C, eagpt_camera cam, eagpt_scene sc,
                                                           eagpt_scene_grad gr, const PrimRecB* __restrict__ prim,
                                                           const float* __restrict__ dL, int spp, uint64_t seed,
                                                           int64_t npix, int s0, int batch, float4* per_sample) {
@@ -198,13 +236,14 @@ __global__ void __launch_bounds__(kBlock) k_bwd_secondary(BvhView bvh, Consts C,
     const float3 O2 = X + C.bounce_offset * Nn;
     const float3 w2 = cosine_direction(Nn, u.x, u.y);
     TraceCounters cnt{0, 0, 0, 0, 0};
-    RawVisitor v1(bvh.shade, C, w2, 0);
+    // the secondary segment enters the pixel only through its R (Eq. 6)
+    RBlendVisitor v1(bvh.shade, C, 0);
     trace_segment<kKb, false>(bvh, C, O2, w2, 0.f, s_stack + threadIdx.x, kBlock, v1, cnt);
     const float invS = 1.f / (float)spp;
     const float3 g = make_float3(dL[3 * pixel], dL[3 * pixel + 1], dL[3 * pixel + 2]);
     const float3 P1 = make_float3(p.c.x, p.c.y, p.c.z);
-    if (v1.blend.b.n_hits > 0) {
-      AdjointVisitor av;
+    if (v1.n_hits > 0) {
+      AdjointVisitorT<true> av;
       av.shade = bvh.shade;
       av.sc = sc;
       av.gr = gr;
@@ -215,14 +254,16 @@ __global__ void __launch_bounds__(kBlock) k_bwd_secondary(BvhView bvh, Consts C,
       av.gN = av.gP = make_float3(0.f, 0.f, 0.f);
       av.gR = invS * mul3(g, P1);
       av.gD = av.gA = 0.f;
-      av.V = v1.blend.b;
+      init_blend(av.V);
+      av.V.R = v1.R;
+      av.V.T = v1.T;
       init_blend(av.run);
       av.dO = av.dw = make_float3(0.f, 0.f, 0.f);
       trace_segment<kKb, false>(bvh, C, O2, w2, 0.f, s_stack + threadIdx.x, kBlock, av, cnt);
       // O2 = O + D~1 w + offset N~1 ; w2 = basis(N~1) l
       const float gDn = dot3(av.dO, w);
       const float3 gNn = C.bounce_offset * av.dO + cosine_direction_adjoint(Nn, u.x, u.y, av.dw);
-      const float3 gP1 = invS * mul3(g, v1.blend.b.R);
+      const float3 gP1 = invS * mul3(g, v1.R);
       outA = make_float4(gNn.x, gNn.y, gNn.z, gDn);
       outB = make_float4(gP1.x, gP1.y, gP1.z, 0.f);
     }
@@ -378,10 +419,10 @@ __global__ void __launch_bounds__(kBlock) k_radiance_bwd(BvhView bvh, Consts C, 
   float3 O, w;
   camera_ray(cam, (uint32_t)i, O, w);
   TraceCounters cnt{0, 0, 0, 0, 0};
-  RawVisitor v1(bvh.shade, C, w, 0);
+  RBlendVisitor v1(bvh.shade, C, 0);
   trace_segment<kKb, false>(bvh, C, O, w, 0.f, s_stack + threadIdx.x, kBlock, v1, cnt);
-  if (v1.blend.b.n_hits == 0) return;
-  AdjointVisitor av;
+  if (v1.n_hits == 0) return;
+  AdjointVisitorT<true> av;
   av.shade = bvh.shade;
   av.sc = sc;
   av.gr = gr;
@@ -389,7 +430,9 @@ __global__ void __launch_bounds__(kBlock) k_radiance_bwd(BvhView bvh, Consts C, 
   av.O = O;
   av.w = w;
   av.mode = 0;
-  av.V = v1.blend.b;
+  init_blend(av.V);
+  av.V.R = v1.R;
+  av.V.T = v1.T;
   init_blend(av.run);
   av.dO = av.dw = make_float3(0.f, 0.f, 0.f);
   av.gN = av.gP = make_float3(0.f, 0.f, 0.f);
