@@ -137,11 +137,17 @@ class ClockSampler:
 
 
 # --------------------------------------------------------------------------
+# the sources that define the bounce kernel (its traffic summary is valid
+# while these are unchanged)
+BOUNCE_SOURCES = ("render.cu", "trace.cuh", "wave.cuh", "common.cuh")
+
+
 def source_digest() -> str:
     h = hashlib.sha256()
-    for p in sorted(glob.glob(os.path.join(ROOT, "paper_2601_23065_gb300", "csrc", "*"))):
-        with open(p, "rb") as f:
+    for name in BOUNCE_SOURCES:
+        with open(os.path.join(ROOT, "paper_2601_23065_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
+    h.update(os.environ.get("EAGPT_NVCC_FLAGS", "").encode())
     return h.hexdigest()[:16]
 
 
@@ -155,8 +161,10 @@ def load_peaks():
 
 
 def load_traffic(workload: str):
-    """Per-launch DRAM bytes of the dominant kernel from the committed ncu
-    summary, if it was taken on the current kernel sources."""
+    """DRAM bytes per secondary segment of the bounce kernel from the
+    committed ncu summary (dram__bytes_read.sum + dram__bytes_write.sum of one
+    captured launch / its segments), if it was taken on the current kernel
+    sources; None otherwise."""
     p = os.path.join(ROOT, "profiles", f"k_bounce_{workload}_traffic.json")
     try:
         with open(p) as f:
@@ -165,7 +173,7 @@ def load_traffic(workload: str):
         return None
     if d.get("source_digest") != source_digest():
         return None
-    return d.get("dram_bytes_per_launch")
+    return d.get("dram_bytes_per_segment")
 
 
 def cpu_baseline(wl, scene, seconds: float):
@@ -712,7 +720,10 @@ def main():
     alg_bytes_bounce_launch = (96 * sec_segs + NODE_BYTES * nodes + 64 * tests + 32 * blended) / max(
         1.0, bounce_launches_per_step)
     achieved = alg_bytes_bounce_launch / (bounce_ms_per_launch * 1e-3) / 1e9 if bounce_ms_per_launch else None
-    traffic = load_traffic(args.workload)
+    per_seg_dram = load_traffic(args.workload)
+    # DRAM traffic of the bounce launches is the ray queues and slots, in
+    # proportion to the segments: scaled from the captured launch
+    traffic = per_seg_dram * sec_segs / max(1.0, bounce_launches_per_step) if per_seg_dram else None
     roofline = {"bound": "hbm", "kernel": "k_bounce", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": (achieved / peak) if achieved else None, "traffic": traffic,
                 "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback",

@@ -28,7 +28,7 @@ EAGPT_DEFINE_ERROR_READER(take_errors_backward)
 #define EAGPT_BWD_KBUF 12
 #endif
 #ifndef EAGPT_BWD_MIN_BLOCKS
-#define EAGPT_BWD_MIN_BLOCKS 4
+#define EAGPT_BWD_MIN_BLOCKS 5
 #endif
 constexpr int kKb = EAGPT_BWD_KBUF;             // k-buffer of the adjoint's traversals
 constexpr int kBwdMinBlocks = EAGPT_BWD_MIN_BLOCKS;  // resident blocks per SM of the secondary adjoint
