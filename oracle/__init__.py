@@ -24,6 +24,7 @@ _lib = None
 FLAGS = {
     "support": 1 << 0, "tlo": 1 << 1, "amin": 1 << 2, "amax": 1 << 3, "order": 1 << 4,
     "tstop": 1 << 5, "emit": 1 << 6, "rr": 1 << 7, "onb": 1 << 8, "graze": 1 << 9, "cond": 1 << 10,
+    "hemi": 1 << 11,
 }
 FP32_EPS = 2.0 ** -24
 
@@ -54,7 +55,7 @@ class _Params(ctypes.Structure):
     _fields_ = [("tau_E", ctypes.c_double), ("T_min", ctypes.c_double), ("alpha_min", ctypes.c_double),
                 ("alpha_max", ctypes.c_double), ("support_sigma", ctypes.c_double),
                 ("bounce_offset", ctypes.c_double), ("emitters_reflect", ctypes.c_int32),
-                ("fp32_eps", ctypes.c_double), ("cond_tol", ctypes.c_double)]
+                ("fp32_eps", ctypes.c_double), ("cond_tol", ctypes.c_double), ("mis", ctypes.c_int32)]
 
 
 class _Segment(ctypes.Structure):
@@ -82,6 +83,8 @@ def _load():
                                        P(d), P(d), P(u32), P(i64), i32]
             lib.ora_single_bounce_grad.argtypes = [P(_Scene), P(_Camera), P(_Params), i32, u64, P(i32), i64,
                                                    P(d), P(d), P(u32), i32]
+            lib.ora_light_pdf.argtypes = [P(_Scene), P(_Params), P(d), P(d), P(d)]
+            lib.ora_light_pdf.restype = i32
             lib.ora_radiance_grad.argtypes = [P(_Scene), P(_Camera), P(_Params), P(i32), i64, P(d), P(d), P(u32),
                                               i32]
             for f in ("ora_trace_segment", "ora_trace_rays", "ora_primary", "ora_render",
@@ -107,15 +110,16 @@ class Params:
     stated readings of constants the paper does not give."""
 
     def __init__(self, tau_E=0.1, T_min=1e-3, alpha_min=1.0 / 255.0, alpha_max=0.99, support_sigma=3.0,
-                 bounce_offset=1e-3, emitters_reflect=False, fp32_eps=FP32_EPS, cond_tol=2.5e-5):
+                 bounce_offset=1e-3, emitters_reflect=False, fp32_eps=FP32_EPS, cond_tol=2.5e-5, mis=False):
         self.tau_E, self.T_min, self.alpha_min, self.alpha_max = tau_E, T_min, alpha_min, alpha_max
         self.support_sigma, self.bounce_offset = support_sigma, bounce_offset
         self.emitters_reflect, self.fp32_eps, self.cond_tol = emitters_reflect, fp32_eps, cond_tol
+        self.mis = mis
 
     def _c(self):
         return _Params(self.tau_E, self.T_min, self.alpha_min, self.alpha_max, self.support_sigma,
                        self.bounce_offset, 1 if self.emitters_reflect else 0, self.fp32_eps,
-                       self.cond_tol if self.fp32_eps > 0 else 0.0)
+                       self.cond_tol if self.fp32_eps > 0 else 0.0, 1 if self.mis else 0)
 
 
 class OracleScene:
@@ -271,6 +275,23 @@ def radiance_grad(scene, camera, pixels, dL_drgb, params=None, n_threads=None):
     if rc:
         raise RuntimeError("oracle radiance grad failed")
     return grad, fl
+
+
+def light_pdf(scene, origin, direction, params=None):
+    """Solid-angle density of the emitter-sampling strategy (mis) at origin
+    for a unit direction, summed over every emitter crossed (no occlusion);
+    returns (pdf, number of emitters crossed)."""
+    lib = _load()
+    sc = _oscene(scene)
+    prm = (params or Params(mis=True))._c()
+    O = np.ascontiguousarray(origin, np.float64)
+    w = np.ascontiguousarray(direction, np.float64)
+    out = np.zeros(1)
+    n = lib.ora_light_pdf(ctypes.byref(sc._c), ctypes.byref(prm), _ptr(O, ctypes.c_double),
+                          _ptr(w, ctypes.c_double), _ptr(out, ctypes.c_double))
+    if n < 0:
+        raise RuntimeError("oracle light_pdf failed")
+    return float(out[0]), int(n)
 
 
 def grad_split(grad):

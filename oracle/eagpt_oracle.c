@@ -67,6 +67,14 @@ void ora_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t ou
 /* Uniform in [0,1) from the top 24 bits (exactly representable in FP32). */
 static double u24(uint32_t x) { return (double)(x >> 8) * (1.0 / 16777216.0); }
 
+static void draws_w(uint64_t seed, int64_t pixel, int32_t sample, int32_t bounce, uint32_t word, double u[4]) {
+  uint32_t ctr[4] = {(uint32_t)pixel, (uint32_t)sample, (uint32_t)bounce, word};
+  uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+  uint32_t o[4];
+  ora_philox4x32_10(ctr, key, o);
+  for (int i = 0; i < 4; ++i) u[i] = u24(o[i]);
+}
+
 static void draws(uint64_t seed, int64_t pixel, int32_t sample, int32_t bounce, double u[4]) {
   uint32_t ctr[4] = {(uint32_t)pixel, (uint32_t)sample, (uint32_t)bounce, 0u};
   uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
@@ -512,6 +520,133 @@ int ora_primary(const ora_scene* sc, const ora_camera* cam, const ora_params* pr
 }
 
 /* ------------------------------------------------------------------------ */
+/* emitter sampling with multiple importance sampling (path tracing, mis = 1)
+ *
+ * The paper names emitter importance sampling with MIS as future work
+ * (Sec. 6 and the appendix on sampling); this is one exact form of it.  The
+ * blended radiance of a segment is a sum of per-surfel terms, R = sum_i w_i
+ * r~_i (Eq. 2, w_i = T_{i-1} alpha_i), and each emitter term of the
+ * one-bounce integral is estimated by two strategies combined with the power
+ * heuristic: the cosine-sampled continuation (pdf p_B = cos / pi) and
+ * sampling a point on that emitter surfel (pdf p_L,i = q_i g_i(u, v) t^2 /
+ * |w . n_i| in solid angle, q_i the selection probability and g_i the
+ * truncated Gaussian density on the surfel plane).  Both pdfs are local to
+ * the hit, so no other surfel is involved.                                  */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+  int64_t n_e;   /* emitters with a positive weight                       */
+  int64_t* idx;  /* surfel index of the k-th emitter, ascending           */
+  double* cdf;   /* running sum of the weights in that order              */
+  double total;
+  double* q;     /* per surfel: selection probability (0: not an emitter) */
+  double norm;   /* 2 pi (1 - exp(-S^2 / 2)): the truncated Gaussian's mass */
+} emitters;
+
+/* selection weight: mean radiance x opacity x scale area (e_i > tau_E) */
+static double emitter_weight(const surfel64* g, const ora_params* prm) {
+  if (!(g->e > prm->tau_E)) return 0.0;
+  double m = (g->r[0] + g->r[1]) + g->r[2];
+  m = m / 3.0;
+  return ((m * g->sigma) * g->su) * g->sv;
+}
+
+static int build_emitters(const world* W, emitters* em) {
+  memset(em, 0, sizeof(*em));
+  const ora_params* prm = W->prm;
+  em->norm = 2.0 * ORA_PI * (1.0 - exp(-0.5 * prm->support_sigma * prm->support_sigma));
+  em->idx = (int64_t*)malloc(sizeof(int64_t) * (size_t)(W->n > 0 ? W->n : 1));
+  em->cdf = (double*)malloc(sizeof(double) * (size_t)(W->n > 0 ? W->n : 1));
+  em->q = (double*)calloc((size_t)(W->n > 0 ? W->n : 1), sizeof(double));
+  if (!em->idx || !em->cdf || !em->q) return -1;
+  double run = 0.0;
+  for (int64_t i = 0; i < W->n; ++i) {
+    double w = emitter_weight(&W->s[i], prm);
+    if (w > 0.0) {
+      run += w;
+      em->idx[em->n_e] = i;
+      em->cdf[em->n_e] = run;
+      ++em->n_e;
+    }
+  }
+  em->total = run;
+  for (int64_t k = 0; k < em->n_e; ++k) {
+    const int64_t i = em->idx[k];
+    em->q[i] = emitter_weight(&W->s[i], prm) / run;
+  }
+  return 0;
+}
+
+static void free_emitters(emitters* em) {
+  free(em->idx);
+  free(em->cdf);
+  free(em->q);
+}
+
+/* the k-th emitter for a draw u in [0, 1): smallest k with cdf_k > u total */
+static int64_t select_emitter(const emitters* em, double u) {
+  const double x = u * em->total;
+  int64_t lo = 0, hi = em->n_e - 1;
+  while (lo < hi) {
+    int64_t mid = (lo + hi) / 2;
+    if (em->cdf[mid] > x) hi = mid;
+    else lo = mid + 1;
+  }
+  return em->idx[lo];
+}
+
+/* a point of the emitter's support disc with the truncated standard 2D
+ * Gaussian density: radius by the inverse of its CDF, uniform angle */
+static void emitter_point(const surfel64* g, double S2, double u1, double u2, double y[3]) {
+  double rho = sqrt(-2.0 * log(1.0 - u1 * (1.0 - exp(-0.5 * S2))));
+  double phi = 2.0 * ORA_PI * u2;
+  double a = rho * cos(phi), b = rho * sin(phi);
+  for (int k = 0; k < 3; ++k) y[k] = g->p[k] + a * g->su * g->tu[k] + b * g->sv * g->tv[k];
+}
+
+/* solid-angle density of the emitter strategy for a hit of surfel g */
+static double light_pdf_hit(const emitters* em, const surfel64* g, double qsel, const hit64* h) {
+  return qsel * exp(-0.5 * h->q) / (em->norm * g->su * g->sv) * h->t * h->t / fabs(h->d);
+}
+
+int ora_light_pdf(const ora_scene* sc, const ora_params* prm, const double O[3], const double w[3],
+                  double* out_pdf) {
+  surfel64* s = load_surfels(sc);
+  if (!s) return -1;
+  world W = {s, sc->n, prm};
+  emitters em;
+  if (build_emitters(&W, &em)) {
+    free(s);
+    free_emitters(&em);
+    return -1;
+  }
+  const double S2 = prm->support_sigma * prm->support_sigma;
+  double sum = 0.0;
+  int count = 0;
+  for (int64_t i = 0; i < sc->n; ++i) {
+    if (!(em.q[i] > 0.0)) continue;
+    const surfel64* g = &s[i];
+    double d = dot3(w, g->n);
+    if (fabs(d) < 1e-12) continue;
+    double pO[3] = {g->p[0] - O[0], g->p[1] - O[1], g->p[2] - O[2]};
+    double t = dot3(pO, g->n) / d;
+    if (!(t > 0.0)) continue;
+    double dx[3] = {-pO[0] + t * w[0], -pO[1] + t * w[1], -pO[2] + t * w[2]};
+    double u = dot3(dx, g->tu) / g->su, v = dot3(dx, g->tv) / g->sv;
+    hit64 h;
+    h.q = u * u + v * v;
+    if (h.q > S2) continue;
+    h.t = t;
+    h.d = d;
+    sum += light_pdf_hit(&em, g, em.q[i], &h);
+    ++count;
+  }
+  *out_pdf = sum;
+  free_emitters(&em);
+  free(s);
+  return count;
+}
+
+/* ------------------------------------------------------------------------ */
 /* rendering (Eq. 6 and Eq. 8)                                               */
 /* ------------------------------------------------------------------------ */
 typedef struct {
@@ -523,6 +658,7 @@ typedef struct {
   double* out_samples;
   uint32_t* out_sample_flags;
   int64_t* out_segments;
+  const emitters* em; /* emitter sampling (path tracing with mis), else NULL */
 } render_ctx;
 
 /* Perturbs a ray at FP32 rounding scale for the conditioning estimate:
@@ -589,6 +725,41 @@ static int path_sample(job* jb, const render_ctx* c, hitbuf* b, int64_t pix, int
     double w2[3], O2[3];
     ora_cosine_direction(Nn, u[0], u[1], w2);
     for (int j = 0; j < 3; ++j) O2[j] = X[j] + prm->bounce_offset * Nn[j];
+    const emitters* em = c->em;
+    if (em && em->n_e > 0) {
+      /* emitter sample from this vertex: draws (pixel, sample, k, 1) */
+      double v4[4], y[3], wl[3], Ol[3] = {O2[0], O2[1], O2[2]};
+      draws_w(c->seed, pix, s, k, 1u, v4);
+      const int64_t it = select_emitter(em, v4[0]);
+      const surfel64* gt = &jb->W.s[it];
+      emitter_point(gt, prm->support_sigma * prm->support_sigma, v4[1], v4[2], y);
+      double dl[3] = {y[0] - O2[0], y[1] - O2[1], y[2] - O2[2]};
+      const double dist = norm3(dl);
+      for (int j = 0; j < 3; ++j) wl[j] = dl[j] / dist;
+      const double cosx = dot3(wl, Nn);
+      if (eps > 0 && fabs(cosx) <= FLAG_K * (eN + ERR_C * eps * (1.0 + amax3(O2) / dist))) *sflags |= ORA_FLAG_HEMI;
+      if (cosx > 0.0) {
+        if (run > 0) jitter_ray(Ol, wl, c->seed, pix, s, k + (1 << 20), run, 2.0 * eps);
+        ora_segment g3;
+        if (segment(&jb->W, Ol, wl, 0.0, 1, ERR_C * eps * amax3(Ol), ERR_C * eps, b, &g3)) return -1;
+        ++*segments;
+        *sflags |= g3.flags;
+        if (g3.n_hits > 0 && g3.E > prm->tau_E) {
+          double T = 1.0;
+          for (int64_t h = 0; h < b->n; ++h) {
+            const hit64* hh = &b->h[h];
+            if (hh->idx == it) {
+              const double wi = T * hh->alpha;
+              const double pl = light_pdf_hit(em, gt, em->q[it], hh), pb = cosx / ORA_PI;
+              const double f = wi * pb * pl / (pl * pl + pb * pb);
+              for (int j = 0; j < 3; ++j) contrib[j] += beta[j] * gt->r[j] * f;
+              break;
+            }
+            T *= 1.0 - hh->alpha;
+          }
+        }
+      }
+    }
     if (run > 0) jitter_ray(O2, w2, c->seed, pix, s, k, run, 2.0 * eps);
     ora_segment g2;
     /* margins at this segment's own FP32 rounding scale */
@@ -603,8 +774,25 @@ static int path_sample(job* jb, const render_ctx* c, hitbuf* b, int64_t pix, int
       for (int j = 0; j < 3; ++j) contrib[j] = beta[j] * g2.R[j];
       return 0;
     } else if (g2.E > prm->tau_E) {
-      /* Eq. 8: first emissive vertex within the bounce limit */
-      for (int j = 0; j < 3; ++j) contrib[j] = beta[j] * g2.R[j];
+      /* Eq. 8: first emissive vertex within the bounce limit; with emitter
+       * sampling each emitter term carries its power-heuristic weight */
+      if (em && em->n_e > 0) {
+        const double pb = dot3(w2, Nn) / ORA_PI;
+        double T = 1.0;
+        for (int64_t h = 0; h < b->n; ++h) {
+          const hit64* hh = &b->h[h];
+          const surfel64* g = &jb->W.s[hh->idx];
+          const double wk = T * hh->alpha;
+          if (em->q[hh->idx] > 0.0) {
+            const double pl = light_pdf_hit(em, g, em->q[hh->idx], hh);
+            const double f = wk * pb * pb / (pb * pb + pl * pl);
+            for (int j = 0; j < 3; ++j) contrib[j] += beta[j] * g->r[j] * f;
+          }
+          T *= 1.0 - hh->alpha;
+        }
+      } else {
+        for (int j = 0; j < 3; ++j) contrib[j] = beta[j] * g2.R[j];
+      }
       return 0;
     }
     if (k == B) return 0; /* bounce limit exceeded: discarded (or done) */
@@ -703,7 +891,7 @@ int ora_render(const ora_scene* sc, const ora_camera* cam, const ora_params* prm
   surfel64* s = load_surfels(sc);
   if (!s) return -1;
   render_ctx c = {cam, kind, spp, max_bounces, rr_start, seed, pixels, out_rgb, out_samples, out_sample_flags,
-                  out_segments};
+                  out_segments, NULL};
   job jb;
   jb.W.s = s;
   jb.W.n = sc->n;
@@ -711,7 +899,18 @@ int ora_render(const ora_scene* sc, const ora_camera* cam, const ora_params* prm
   jb.fn = render_item;
   jb.n_items = n_pix;
   jb.ctx = &c;
+  emitters em;
+  memset(&em, 0, sizeof(em));
+  if (prm->mis && kind == 1) {
+    if (prm->emitters_reflect || build_emitters(&jb.W, &em)) {
+      free_emitters(&em);
+      free(s);
+      return -1;
+    }
+    c.em = &em;
+  }
   int rc = run_job(&jb, n_threads);
+  free_emitters(&em);
   free(s);
   return rc;
 }

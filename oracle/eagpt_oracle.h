@@ -42,6 +42,8 @@ typedef struct {
                             0 disables flagging                              */
   double cond_tol;       /* flag a sample whose estimated FP32 relative error
                             exceeds cond_tol (ORA_FLAG_COND); 0 disables     */
+  int32_t mis;           /* 1: path tracing with emitter sampling and
+                            multiple importance sampling (see ora_render)   */
 } ora_params;
 
 /* near-boundary flag bits (a decision the FP32 path may take differently) */
@@ -57,6 +59,8 @@ enum {
   ORA_FLAG_ONB = 1u << 8,      /* normal z near 0 (basis branch)            */
   ORA_FLAG_GRAZE = 1u << 9,    /* ray nearly parallel to a surfel plane     */
   ORA_FLAG_COND = 1u << 10,    /* sample ill-conditioned in FP32            */
+  ORA_FLAG_HEMI = 1u << 11,    /* emitter-sample direction near the tangent
+                                  plane of its vertex                       */
 };
 
 /* Result of one traced segment (Eq. 2-3). */
@@ -91,6 +95,14 @@ int ora_trace_segment(const ora_scene* sc, const ora_params* prm, const double O
 int ora_trace_rays(const ora_scene* sc, const ora_params* prm, const double* rays, int64_t n_rays,
                    int32_t mode, double* out_rec, int32_t* out_nhits, uint32_t* out_flags,
                    int32_t* hit_idx, int32_t max_hits, int32_t n_threads);
+
+/* Emitter sampling (path tracing with mis = 1): the solid-angle density at
+ * origin O of sampling direction w by the emitter-sampling strategy, summed
+ * over every emitter surfel whose plane the ray O + t w (t > 0) crosses
+ * inside its support, with no occlusion: sum_i q_i g_i(u, v) t^2 / |w . n_i|.
+ * Returns the number of emitter surfels crossed (-1 on error). */
+int ora_light_pdf(const ora_scene* sc, const ora_params* prm, const double O[3], const double w[3],
+                  double* out_pdf);
 
 /* Primary record of listed pixels: 12 doubles per pixel as in ora_trace_rays.
  * mode as in ora_trace_segment. */
