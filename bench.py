@@ -41,7 +41,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--workload", default="medium",
-                    choices=["tiny", "medium", "diff", "large", "serving", "stage1", "bake"])
+                    choices=["tiny", "medium", "diff", "large", "serving", "stage1", "bake", "mis"])
     ap.add_argument("--views", type=int, default=8, help="stage1/bake: training views")
     ap.add_argument("--requests", type=int, default=16, help="serving: requests in the stream")
     ap.add_argument("--spp", type=int, default=None, help="override samples per pixel")
@@ -602,6 +602,67 @@ def run_diff(args):
     print(json.dumps(line), flush=True)
 
 
+def run_mis(args):
+    """Emitter sampling with MIS against plain path tracing on the medium room
+    (200k surfels, 512x512, 4 bounces, RR from 2; 16 spp unless --spp): path
+    segments/s of each (emitter samples are segments too), the per-pixel
+    variance of each estimated from two renders with different seeds
+    (E[(a - b)^2] / 2, averaged over pixels and channels), and the
+    efficiency ratio (variance x time of plain) / (variance x time of MIS)."""
+    import torch
+
+    from paper_2601_23065_gb300 import api, build, capi
+    from paper_2601_23065_gb300 import scenes as S
+
+    build.build()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    L = capi.lib()
+    wl = S.workload("medium")
+    spp = args.spp or 16
+    host = wl.scene_fn()
+    cam = wl.camera
+    ds = api.DeviceScene.from_host(host, device=dev)
+    bvh = api.BVH(ds)
+    r = api.Renderer(device=dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    res = {}
+    for name, prm in (("plain", api.params()), ("mis", api.params(flags=capi.FLAG_EMITTER_SAMPLING))):
+        st = r.path_traced(ds, bvh, cam, spp, wl.max_bounces, rr_start=wl.rr_start, seed=1, prm=prm,
+                           want_stats=True)["stats"].cpu().numpy()
+        segs = int(st[0]) + int(st[1])
+        for _ in range(max(3, args.warmup)):
+            r.path_traced(ds, bvh, cam, spp, wl.max_bounces, rr_start=wl.rr_start, seed=1, prm=prm)
+        torch.cuda.synchronize(dev)
+        times, imgs = [], []
+        for k in range(max(2, args.steps)):
+            flush.fill_(float(k))
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record()
+            out = r.path_traced(ds, bvh, cam, spp, wl.max_bounces, rr_start=wl.rr_start, seed=1 + 7919 * k, prm=prm)
+            b.record()
+            b.synchronize()
+            times.append(a.elapsed_time(b))
+            if k < 2:
+                imgs.append(out["rgb"].double().clone())
+        api.sync_status()
+        ms = sum(times) / len(times)
+        var = float(((imgs[0] - imgs[1]) ** 2).mean() / 2.0)
+        res[name] = {"ms_per_render": ms, "segments_per_render": segs, "segments_per_s": segs / (ms * 1e-3),
+                     "variance": var, "mean": float(imgs[0].mean())}
+    eff = (res["plain"]["variance"] * res["plain"]["ms_per_render"]) / max(
+        1e-300, res["mis"]["variance"] * res["mis"]["ms_per_render"])
+    line = {"metric": "path segments/s (emitter sampling + MIS)", "value": res["mis"]["segments_per_s"],
+            "unit": "path segments/s", "n_gpus": 1, "steps": max(2, args.steps), "warmup": max(3, args.warmup),
+            "ms_per_step": res["mis"]["ms_per_render"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"medium room 200k surfels 512x512 {spp}spp 4 bounces RR>=2, emitter sampling + MIS",
+                       "l2": "flushed between renders (512 MB write)"},
+            "plain": res["plain"], "mis": res["mis"], "efficiency_vs_plain": eff}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
@@ -613,6 +674,9 @@ def main():
         return
     if args.workload == "diff" and args.impl == "native":
         run_diff(args)
+        return
+    if args.workload == "mis" and args.impl == "native":
+        run_mis(args)
         return
     if args.impl == "reference":
         if world > 1:

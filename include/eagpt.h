@@ -94,8 +94,27 @@ typedef struct {
   float alpha_max;      /* alpha = min(sigma * g, alpha_max) (0.99)           */
   float support_sigma;  /* Gaussian support u^2 + v^2 <= support^2 (3)        */
   float bounce_offset;  /* new origin X + offset * N~ (1e-3 scene units)      */
-  int32_t reserved;     /* must be 0                                          */
+  int32_t flags;        /* EAGPT_FLAG_* bits; others must be 0 (default 0)    */
 } eagpt_params;
+
+/* flags of eagpt_params */
+enum {
+  /* Path tracing (Eq. 8) with emitter sampling and multiple importance
+   * sampling (the variance reduction the paper names as future work).  At
+   * every reflection vertex one emitter surfel i (e_i > tau_E) is chosen with
+   * probability q_i proportional to mean(r_i) sigma_i s_u,i s_v,i (FP64
+   * cumulative sums in surfel-index order), a point of its support disc is
+   * drawn from the truncated Gaussian (radius by inverse CDF, uniform angle)
+   * and the segment towards it is traced.  The blended radiance is a sum of
+   * per-surfel terms w_i r_i (Eq. 2); each emitter term is estimated by both
+   * the cosine-sampled continuation (pdf p_B = cos / pi) and the emitter
+   * sample (pdf p_L = q_i g_i(u, v) t^2 / |w . n_i|), combined with the power
+   * heuristic.  The expectation is that of Eq. 8.  Draws: the emitter sample
+   * of reflection k uses Philox counter (pixel, sample, k, 1): u0 selects the
+   * emitter, u1 the radius, u2 the angle.  Single-bounce renders and the
+   * serving loop ignore / reject it. */
+  EAGPT_FLAG_EMITTER_SAMPLING = 1
+};
 
 void eagpt_default_params(eagpt_params* out);
 
@@ -131,6 +150,8 @@ eagpt_status eagpt_build_bvh(const eagpt_scene* scene, const eagpt_params* param
  * at least eagpt_render_workspace_min_bytes() works (samples are then done
  * in several passes, with identical results).  256-byte aligned, device.
  * ------------------------------------------------------------------------ */
+/* kind for the workspace queries: 0 single bounce, 1 path tracing, 2 path
+ * tracing with EAGPT_FLAG_EMITTER_SAMPLING (32 more bytes per queued ray). */
 size_t eagpt_render_workspace_bytes(const eagpt_camera* cam, int32_t spp, int32_t kind);
 size_t eagpt_render_workspace_min_bytes(const eagpt_camera* cam, int32_t spp, int32_t kind);
 

@@ -120,10 +120,12 @@ class Renderer:
     def path_traced(self, scene: DeviceScene, bvh: BVH, cam: HostCamera, spp: int, max_bounces: int,
                     rr_start: int = 2, seed: int = 0, prm: Optional[capi.Params] = None, want_aux=False,
                     want_samples=False, want_stats=False, out: Optional[torch.Tensor] = None, stream=None):
-        """Eq. 8 render; returns dict(rgb (H,W,3)[, aux (H,W,12)][, samples (H,W,spp,3)][, stats])."""
+        """Eq. 8 render; returns dict(rgb (H,W,3)[, aux (H,W,12)][, samples (H,W,spp,3)][, stats]).
+        With ``prm.flags`` containing capi.FLAG_EMITTER_SAMPLING the path
+        tracer samples emitters at every reflection (MIS)."""
         c = camera(cam)
         prm = prm or bvh.params
-        ws = self._workspace(c, spp, 1)
+        ws = self._workspace(c, spp, 2 if prm.flags & capi.FLAG_EMITTER_SAMPLING else 1)
         H, W = cam.height, cam.width
         rgb = out if out is not None else torch.empty((H, W, 3), dtype=torch.float32, device=self.device)
         aux = torch.empty((H, W, 12), dtype=torch.float32, device=self.device) if want_aux else None

@@ -55,7 +55,7 @@ class Camera(ctypes.Structure):
 
 class Params(ctypes.Structure):
     _fields_ = [("tau_E", c_f), ("T_min", c_f), ("alpha_min", c_f), ("alpha_max", c_f),
-                ("support_sigma", c_f), ("bounce_offset", c_f), ("reserved", c_i32)]
+                ("support_sigma", c_f), ("bounce_offset", c_f), ("flags", c_i32)]
 
 
 class Bvh(ctypes.Structure):
@@ -97,6 +97,8 @@ class FitConfig(ctypes.Structure):
     _fields_ = [("field", c_i32), ("spp", c_i32), ("seed", c_u64), ("peak", c_f), ("lambda_c", c_f),
                 ("adam", Adam)]
 
+
+FLAG_EMITTER_SAMPLING = 1
 
 REQ_STATES = {0: "queued", 1: "running", 2: "done", 3: "failed", 4: "cancelled", 5: "timed_out"}
 

@@ -10,6 +10,8 @@
 //      into the 4-wide BVH that the renderer traverses
 #include <cuda_runtime.h>
 
+#include <cmath>
+
 #include "common.cuh"
 #include "internal.h"
 
@@ -206,6 +208,130 @@ __global__ void k_records(eagpt_scene sc, Consts C, const uint32_t* __restrict__
 // --------------------------------------------------------------------------
 static inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
+// --------------------------------------------------------------------------
+// Emitter table of the emitter-sampling path tracer: the emitters (e > tau_E
+// and a positive weight) in surfel-index order with their record indices,
+// FP64 running sums of the weights mean(r) sigma s_u s_v (summed by one
+// thread in that order, so the sums are exactly those of a sequential FP64
+// loop), and in each emitter's shade record (s1.w) the density factor
+// q_i / (2 pi (1 - exp(-S^2 / 2)) s_u s_v) of its emitter samples.
+// --------------------------------------------------------------------------
+constexpr int kEmBlock = 256;
+
+__device__ __forceinline__ double emitter_weight(const eagpt_scene& sc, const Consts& C, int64_t i) {
+  if (!(sc.emissive[i] > C.tau_E)) return 0.0;
+  double m = __dadd_rn(__dadd_rn((double)sc.radiance[3 * i], (double)sc.radiance[3 * i + 1]),
+                       (double)sc.radiance[3 * i + 2]);
+  m = __ddiv_rn(m, 3.0);
+  return __dmul_rn(__dmul_rn(__dmul_rn(m, (double)sc.opacity[i]), (double)sc.scale[2 * i]),
+                   (double)sc.scale[2 * i + 1]);
+}
+
+__global__ void __launch_bounds__(kEmBlock) k_em_count(eagpt_scene sc, Consts C, uint32_t* block_counts) {
+  __shared__ uint32_t warp_tot[kEmBlock / 32];
+  const int64_t i = blockIdx.x * (int64_t)kEmBlock + threadIdx.x;
+  const uint32_t b = __ballot_sync(0xffffffffu, i < sc.n && emitter_weight(sc, C, i) > 0.0);
+  if ((threadIdx.x & 31) == 0) warp_tot[threadIdx.x >> 5] = __popc(b);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t t = 0;
+    for (int w = 0; w < kEmBlock / 32; ++w) t += warp_tot[w];
+    block_counts[blockIdx.x] = t;
+  }
+}
+
+// exclusive scan of the block counts in one block of 1024 threads
+__global__ void __launch_bounds__(1024) k_em_scan(uint32_t* block_counts, int64_t nb) {
+  __shared__ uint32_t part[1024];
+  const int64_t per = (nb + 1023) / 1024;
+  const int64_t b = threadIdx.x * per, e = b + per < nb ? b + per : nb;
+  uint32_t s = 0;
+  for (int64_t k = b; k < e; ++k) s += block_counts[k];
+  part[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = 1; o < 1024; o <<= 1) {
+    const uint32_t v = threadIdx.x >= o ? part[threadIdx.x - o] : 0u;
+    __syncthreads();
+    part[threadIdx.x] += v;
+    __syncthreads();
+  }
+  uint32_t run = threadIdx.x ? part[threadIdx.x - 1] : 0u;
+  for (int64_t k = b; k < e; ++k) {
+    const uint32_t v = block_counts[k];
+    block_counts[k] = run;
+    run += v;
+  }
+  if (threadIdx.x == 1023) block_counts[nb] = part[1023];  // total
+}
+
+__global__ void __launch_bounds__(kEmBlock) k_em_write(eagpt_scene sc, Consts C, const uint32_t* __restrict__ offs,
+                                                       const uint32_t* __restrict__ inv_idx, uint32_t* em_idx,
+                                                       double* em_w) {
+  __shared__ uint32_t warp_off[kEmBlock / 32];
+  const int64_t i = blockIdx.x * (int64_t)kEmBlock + threadIdx.x;
+  const double w = i < sc.n ? emitter_weight(sc, C, i) : 0.0;
+  const bool in = w > 0.0;
+  const uint32_t b = __ballot_sync(0xffffffffu, in);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) warp_off[warp] = __popc(b);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t run = 0;
+    for (int k = 0; k < kEmBlock / 32; ++k) {
+      const uint32_t c = warp_off[k];
+      warp_off[k] = run;
+      run += c;
+    }
+  }
+  __syncthreads();
+  if (in) {
+    const uint32_t at = offs[blockIdx.x] + warp_off[warp] + __popc(b & ((1u << lane) - 1u));
+    em_idx[at] = inv_idx[i];
+    em_w[at] = w;
+  }
+}
+
+// one thread: the running sums (in place) and each emitter's density factor
+__global__ void k_em_finalize(const uint32_t* __restrict__ total_count, const uint32_t* __restrict__ em_idx,
+                              double* em_cdf, const uint32_t* __restrict__ sorted_idx, const float* __restrict__ scale,
+                              ShadeRec* shade, BvhHeader* hdr, double norm) {
+  const uint32_t ne = *total_count;
+  double total = 0.0;
+  for (uint32_t k = 0; k < ne; ++k) total = __dadd_rn(total, em_cdf[k]);
+  double run = 0.0;
+  for (uint32_t k = 0; k < ne; ++k) {
+    const double w = em_cdf[k];
+    run = __dadd_rn(run, w);
+    em_cdf[k] = run;
+    const uint32_t j = em_idx[k];
+    const uint32_t i = sorted_idx[j];
+    const double c = __ddiv_rn(__ddiv_rn(w, total),
+                               __dmul_rn(__dmul_rn(norm, (double)scale[2 * (int64_t)i]), (double)scale[2 * (int64_t)i + 1]));
+    shade[j].s1.w = (float)c;
+  }
+  hdr->em_total = total;
+  hdr->em_count = ne;
+}
+
+static cudaError_t launch_emitters(const eagpt_scene& sc, const Consts& C, char* base, const BvhLayout& L,
+                                   cudaStream_t st) {
+  const int64_t n = sc.n;
+  const int64_t nb = (n + kEmBlock - 1) / kEmBlock;
+  uint32_t* counts = (uint32_t*)(base + L.hist);  // free after the sort
+  EAGPT_LAUNCH(st, "k_em_count", k_em_count<<<(unsigned)nb, kEmBlock, 0, st>>>(sc, C, counts));
+  EAGPT_LAUNCH(st, "k_em_scan", k_em_scan<<<1, 1024, 0, st>>>(counts, nb));
+  EAGPT_LAUNCH(st, "k_em_write", k_em_write<<<(unsigned)nb, kEmBlock, 0, st>>>(sc, C, counts,
+                                                (const uint32_t*)(base + L.inv_idx), (uint32_t*)(base + L.em_idx),
+                                                (double*)(base + L.em_cdf)));
+  const double S2 = (double)C.support2;
+  const double norm = 2.0 * 3.14159265358979323846 * (1.0 - std::exp(-0.5 * S2));
+  EAGPT_LAUNCH(st, "k_em_finalize", k_em_finalize<<<1, 1, 0, st>>>(counts + nb, (const uint32_t*)(base + L.em_idx),
+                                                    (double*)(base + L.em_cdf), (const uint32_t*)(base + L.sorted_idx),
+                                                    sc.scale, (ShadeRec*)(base + L.shade),
+                                                    (BvhHeader*)(base + L.header), norm));
+  return cudaGetLastError();
+}
+
 cudaError_t launch_build(const eagpt_scene& sc, const Consts& C, char* base, const BvhLayout& L, cudaStream_t st,
                          int* launches) {
   const int64_t n = sc.n;
@@ -244,7 +370,9 @@ cudaError_t launch_build(const eagpt_scene& sc, const Consts& C, char* base, con
   ++nl;
   cudaError_t e = launch_tree(k0, base, L, st);
   if (e != cudaSuccess) return e;
-  if (launches) *launches += nl;
+  e = launch_emitters(sc, C, base, L, st);
+  if (e != cudaSuccess) return e;
+  if (launches) *launches += nl + 4;
   return cudaGetLastError();
 }
 
@@ -255,7 +383,12 @@ cudaError_t launch_records_update(const eagpt_scene& sc, const Consts& C, char* 
                                                   (TraceRec*)(base + L.trace), (ShadeRec*)(base + L.shade),
                                                   (float4*)(base + L.prim_lo), (float4*)(base + L.prim_hi),
                                                   (uint32_t*)(base + L.inv_idx), L.n, 0));
-  return cudaGetLastError();
+  return launch_emitters(sc, C, base, L, st);
+}
+
+cudaError_t launch_emitter_table(const eagpt_scene& sc, const Consts& C, char* base, const BvhLayout& L,
+                                 cudaStream_t st) {
+  return sc.n > 0 ? launch_emitters(sc, C, base, L, st) : cudaSuccess;
 }
 
 }  // namespace eagpt

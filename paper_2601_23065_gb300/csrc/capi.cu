@@ -41,7 +41,8 @@ eagpt_status check_params(const eagpt_params* p) {
   if (!(p->bounce_offset >= 0.f && std::isfinite(p->bounce_offset)))
     return fail(EAGPT_ERR_INVALID_ARGUMENT, "bounce_offset must be >= 0%s");
   if (!std::isfinite(p->tau_E)) return fail(EAGPT_ERR_INVALID_ARGUMENT, "tau_E must be finite%s");
-  if (p->reserved != 0) return fail(EAGPT_ERR_INVALID_ARGUMENT, "params.reserved must be 0%s");
+  if (p->flags & ~(int32_t)EAGPT_FLAG_EMITTER_SAMPLING)
+    return fail(EAGPT_ERR_INVALID_ARGUMENT, "params.flags has unknown bits%s");
   return EAGPT_OK;
 }
 
@@ -98,6 +99,9 @@ BvhView make_view(const eagpt_bvh& b) {
     v.nodes8 = (const Node8*)(base + L.nodes);
     v.root = 0;  // node 0: Karras root, or the single node of a small scene
     v.bounds_bits = (const uint32_t*)(base + L.header);
+    v.hdr = (const BvhHeader*)(base + L.header);
+    v.em_idx = (const uint32_t*)(base + L.em_idx);
+    v.em_cdf = (const double*)(base + L.em_cdf);
   }
   return v;
 }
@@ -114,7 +118,7 @@ void eagpt_default_params(eagpt_params* p) {
   p->alpha_max = 0.99f;
   p->support_sigma = 3.0f;
   p->bounce_offset = 1e-3f;
-  p->reserved = 0;
+  p->flags = 0;
 }
 
 const char* eagpt_last_error(void) { return g_msg.c_str(); }
@@ -160,20 +164,18 @@ eagpt_status eagpt_build_bvh(const eagpt_scene* scene, const eagpt_params* param
 }
 
 size_t eagpt_render_workspace_bytes(const eagpt_camera* cam, int32_t spp, int32_t kind) {
-  (void)kind;
-  if (!cam || cam->width <= 0 || cam->height <= 0 || spp <= 0) return 0;
+  if (!cam || cam->width <= 0 || cam->height <= 0 || spp <= 0 || kind < 0 || kind > 2) return 0;
   const int64_t npix = (int64_t)cam->width * cam->height;
   // one pass over all samples, capped at 2^27 paths per pass (~8.6 GB)
   int64_t batch = spp;
   const int64_t cap = (int64_t)1 << 27;
   if (npix * batch > cap) batch = cap / npix > 0 ? cap / npix : 1;
-  return render_layout(npix, spp, (int)batch).total;
+  return render_layout(npix, spp, (int)batch, kind == 2).total;
 }
 
 size_t eagpt_render_workspace_min_bytes(const eagpt_camera* cam, int32_t spp, int32_t kind) {
-  (void)kind;
-  if (!cam || cam->width <= 0 || cam->height <= 0 || spp <= 0) return 0;
-  return render_layout((int64_t)cam->width * cam->height, spp, 1).total;
+  if (!cam || cam->width <= 0 || cam->height <= 0 || spp <= 0 || kind < 0 || kind > 2) return 0;
+  return render_layout((int64_t)cam->width * cam->height, spp, 1, kind == 2).total;
 }
 
 }  // extern "C"
@@ -203,9 +205,10 @@ static eagpt_status render_common(const eagpt_scene* scene, const eagpt_bvh* bvh
   if (!out_rgb) return fail(EAGPT_ERR_INVALID_ARGUMENT, "out_rgb is NULL%s");
   if (!ws || !aligned(ws, 256)) return fail(EAGPT_ERR_INVALID_ARGUMENT, "workspace must be non-NULL and 256-byte aligned%s");
   const int64_t npix = (int64_t)cam->width * cam->height;
-  if (choose_batch_spp(npix, spp, ws_bytes) < 1)
+  const bool mis = kind == 1 && (params->flags & EAGPT_FLAG_EMITTER_SAMPLING);
+  if (choose_batch_spp(npix, spp, ws_bytes, mis) < 1)
     return fail(EAGPT_ERR_OUT_OF_MEMORY, "workspace too small: need at least %s%lld bytes", "",
-                (long long)render_layout(npix, spp, 1).total);
+                (long long)render_layout(npix, spp, 1, mis).total);
   RenderArgs a{};
   a.bvh = make_view(*bvh);
   a.C = make_consts(*params);
@@ -688,6 +691,11 @@ eagpt_status eagpt_fit(const eagpt_fit_config* cfg, eagpt_scene_mut* scene, eagp
     if (e == cudaSuccess) e = launch_shade_adjoint(view, C, cam, dL, li, grad, st);
     if (e == cudaSuccess)
       e = launch_adam(field_ptr, grad, m, v, np, cfg->adam, t, 1, mirror, inv_idx, mirror_field, st);
+  }
+  // new radiance changes the emitters' sampling weights
+  if (e == cudaSuccess && cfg->field == 1) {
+    std::memcpy(&cs, scene, sizeof(cs));
+    e = launch_emitter_table(cs, C, (char*)bvh->storage, BL, st);
   }
   if (e != cudaSuccess) return cuda_fail(e, "fit launch");
   scene->version += 1;

@@ -93,7 +93,7 @@ constexpr int kMaxCollapseLevels = 96;  // BVH levels built top-down
 struct BvhLayout {
   size_t header, trace, shade, nodes, prim_lo, prim_hi, ibox_lo, ibox_hi, leaf_parent, inode_parent,
       sorted_idx, inv_idx, keys0, keys1, vals0, vals1, hist, visit, child_bin, irange, src4, front0, front1,
-      levels, total;
+      levels, em_idx, em_cdf, total;
   int64_t n, n_inodes, n_tiles;
 };
 
@@ -103,7 +103,9 @@ struct BvhHeader {
   uint32_t root;            // root node index (0) or encoded leaf
   uint32_t pad0;
   double area_sum;          // sum of node surface areas after the last refit
-  uint32_t pad[8];
+  double em_total;          // emitter table: sum of the selection weights
+  uint32_t em_count;        // emitters with a positive weight
+  uint32_t pad[5];
 };
 
 constexpr int kSortTileItems = 4096;  // keys per radix-sort tile (256 x 16)
@@ -147,6 +149,8 @@ inline BvhLayout bvh_layout(int64_t n) {
   L.front0 = take((size_t)L.n_inodes * 8);
   L.front1 = take((size_t)L.n_inodes * 8);
   L.levels = take((size_t)(kMaxCollapseLevels + 2) * 4);
+  L.em_idx = take(nn * 4);   // record index of the k-th emitter, in surfel-index order
+  L.em_cdf = take(nn * 8);   // running sums of the emitter weights (FP64)
   L.total = o;
   return L;
 }
@@ -160,11 +164,15 @@ struct BvhView {
   uint32_t root;  // node index, or an encoded leaf when n <= kLeafMax
   int64_t n;
   const uint32_t* bounds_bits;  // scene centroid bounds (BvhHeader), ordered-int encoded
+  const BvhHeader* hdr;         // the header (emitter count and total)
+  const uint32_t* em_idx;       // emitter table: record index per emitter
+  const double* em_cdf;         // emitter table: running weight sums
 };
 
 // Method constants as passed to kernels.
 struct Consts {
   float tau_E, T_min, alpha_min, alpha_max, support2, bounce_offset;
+  int flags;
 };
 
 inline Consts make_consts(const eagpt_params& p) {
@@ -175,6 +183,7 @@ inline Consts make_consts(const eagpt_params& p) {
   c.alpha_max = p.alpha_max;
   c.support2 = p.support_sigma * p.support_sigma;
   c.bounce_offset = p.bounce_offset;
+  c.flags = p.flags;
   return c;
 }
 
@@ -239,6 +248,15 @@ __device__ __forceinline__ float u24(uint32_t x) { return (float)(x >> 8) * (1.0
 
 __device__ __forceinline__ float4 draws(uint64_t seed, uint32_t pixel, uint32_t sample, uint32_t bounce) {
   const uint4 o = philox4x32_10(make_uint4(pixel, sample, bounce, 0u),
+                                make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
+  return make_float4(u24(o.x), u24(o.y), u24(o.z), u24(o.w));
+}
+
+// The same stream with counter word 3 = word (word 1: the emitter sample of
+// reflection `bounce`).
+__device__ __forceinline__ float4 draws_w(uint64_t seed, uint32_t pixel, uint32_t sample, uint32_t bounce,
+                                          uint32_t word) {
+  const uint4 o = philox4x32_10(make_uint4(pixel, sample, bounce, word),
                                 make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
   return make_float4(u24(o.x), u24(o.y), u24(o.z), u24(o.w));
 }

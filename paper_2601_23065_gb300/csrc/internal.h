@@ -18,6 +18,9 @@ void launch_sort_pairs(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, u
 cudaError_t launch_tree(const uint32_t* sorted_keys, char* base, const BvhLayout& L, cudaStream_t st);
 cudaError_t launch_records_update(const eagpt_scene& sc, const Consts& C, char* base, const BvhLayout& L,
                                   cudaStream_t st);
+// the emitter table (emitter sampling) from the scene's current radiance and emission
+cudaError_t launch_emitter_table(const eagpt_scene& sc, const Consts& C, char* base, const BvhLayout& L,
+                                 cudaStream_t st);
 
 // render.cu
 struct RenderArgs {
@@ -37,13 +40,14 @@ struct RenderArgs {
 };
 
 struct RenderLayout {
-  size_t prim, acc, slots, q0, q1, counters, sk0, sk1, sv0, sv1, shist, total;
+  size_t prim, acc, slots, q0, q1, counters, e0, e1, sk0, sk1, sv0, sv1, shist, total;
   int64_t npix, batch_paths;
   int batch_spp;
 };
 
-RenderLayout render_layout(int64_t npix, int spp, int batch_spp);
-int choose_batch_spp(int64_t npix, int spp, size_t ws_bytes);
+// mis: path tracing with emitter sampling (side queues of RayExt)
+RenderLayout render_layout(int64_t npix, int spp, int batch_spp, bool mis = false);
+int choose_batch_spp(int64_t npix, int spp, size_t ws_bytes, bool mis = false);
 cudaError_t launch_render(const RenderArgs& a, cudaStream_t st, int* launches);
 cudaError_t launch_trace_rays(const BvhView& bvh, const Consts& C, int mode, const float* rays, int64_t n_rays,
                               float* out_rec, int32_t* out_hits, int max_hits, int32_t* out_nhits, cudaStream_t st);

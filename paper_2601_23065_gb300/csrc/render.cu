@@ -67,7 +67,7 @@ __global__ void k_ray_keys(const Ray* __restrict__ q, const uint32_t* __restrict
 constexpr int kMaxBounces = 60;
 constexpr int kCounterWords = 2 * (kMaxBounces + 2) + 8;
 
-RenderLayout render_layout(int64_t npix, int spp, int batch_spp) {
+RenderLayout render_layout(int64_t npix, int spp, int batch_spp, bool mis) {
   RenderLayout L{};
   L.npix = npix;
   L.batch_spp = batch_spp;
@@ -84,6 +84,10 @@ RenderLayout render_layout(int64_t npix, int spp, int batch_spp) {
   L.q0 = take((size_t)L.batch_paths * sizeof(Ray));
   L.q1 = take((size_t)L.batch_paths * sizeof(Ray));
   L.counters = take(kCounterWords * sizeof(uint32_t));
+  if (mis) {
+    L.e0 = take((size_t)L.batch_paths * sizeof(RayExt));
+    L.e1 = take((size_t)L.batch_paths * sizeof(RayExt));
+  }
   if (kSortRays) {
     L.sk0 = take((size_t)L.batch_paths * 4);
     L.sk1 = take((size_t)L.batch_paths * 4);
@@ -96,12 +100,12 @@ RenderLayout render_layout(int64_t npix, int spp, int batch_spp) {
   return L;
 }
 
-int choose_batch_spp(int64_t npix, int spp, size_t ws_bytes) {
+int choose_batch_spp(int64_t npix, int spp, size_t ws_bytes, bool mis) {
   int lo = 1, hi = spp;
-  if (render_layout(npix, spp, 1).total > ws_bytes) return 0;
+  if (render_layout(npix, spp, 1, mis).total > ws_bytes) return 0;
   while (lo < hi) {  // largest batch that fits
     const int mid = lo + (hi - lo + 1) / 2;
-    if (render_layout(npix, spp, mid).total <= ws_bytes) lo = mid;
+    if (render_layout(npix, spp, mid, mis).total <= ws_bytes) lo = mid;
     else hi = mid - 1;
   }
   return lo;
@@ -165,7 +169,7 @@ template <bool kCount>
 __global__ void __launch_bounds__(kBlock) k_generate(const PrimRec* __restrict__ prim, Consts C, eagpt_camera cam,
                                                      int kind, int max_bounces, int rr_start, uint64_t seed, int64_t npix,
                                                      int s0, int batch, Ray* q_out, uint32_t* counters, float4* slots,
-                                                     int64_t* stats) {
+                                                     int64_t* stats, RayExt* e_out) {
   const int64_t t = blockIdx.x * (int64_t)kBlock + threadIdx.x;
   const int64_t total = npix * (int64_t)batch;
   bool take = false;
@@ -184,7 +188,19 @@ __global__ void __launch_bounds__(kBlock) k_generate(const PrimRec* __restrict__
     }
   }
   const uint32_t at = warp_append(take, &counters[2 * 1]);
-  if (take) q_out[at] = r;
+  if (take) {
+    q_out[at] = r;
+    if (e_out) {
+      // the first reflection leaves the primary vertex: its normal, the
+      // cosine pdf of the direction, nothing gathered yet
+      const PrimRec p = prim[t % npix];
+      const float3 Nn = make_float3(p.a.x, p.a.y, p.a.z);
+      RayExt x;
+      x.n = make_float4(Nn.x, Nn.y, Nn.z, dot3(f3(r.b), Nn) * 0.318309886183790672f);
+      x.l = make_float4(0.f, 0.f, 0.f, 0.f);
+      e_out[at] = x;
+    }
+  }
   if (kCount) add_stats(stats, 2, started ? 1u : 0u);
 }
 
@@ -354,6 +370,143 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_bounce_r(BvhView bvh, Co
   }
 }
 
+// Path tracing with emitter sampling: every queued ray first traces its
+// emitter sample (the segment from its origin towards a point on a sampled
+// emitter, Philox (pixel, sample, k, 1)), adds that estimate to the path's
+// gathered radiance, then traces its own continuation with power-heuristic
+// weights on emitter hits, and shades it (shade_bounce_mis).  Per-lane
+// refill and chunked traversal as in k_bounce_r.
+template <bool kCount>
+__global__ void __launch_bounds__(kBlock, kMinBlocks) k_bounce_mis(BvhView bvh, Consts C, int k, int max_bounces,
+                                                       int rr_start, uint64_t seed, int64_t npix, int s0,
+                                                       const Ray* __restrict__ q_in, Ray* q_out,
+                                                       const RayExt* __restrict__ e_in, RayExt* e_out,
+                                                       uint32_t* counters, float4* slots, int64_t* stats) {
+  __shared__ uint32_t s_stack[kStackSize * kBlock];
+  __shared__ float s_blend[11 * kBlock];
+  __shared__ float s_gath[3 * kBlock];  // radiance gathered by the emitter samples
+  const int lane = threadIdx.x & 31;
+  float* gath = s_gath + threadIdx.x;
+  const uint32_t count = counters[2 * k];
+  TraceCounters cnt{0, 0, 0, 0, 0};
+  uint32_t traced = 0;
+  RayTrace<kK> rt;
+  SmemBlendVisitorT<true> vis(bvh.shade, C, 1, s_blend + threadIdx.x, kBlock);
+  NeeVisitor nee;
+  nee.shade = bvh.shade;
+  nee.C = C;
+  nee.reset(0xFFFFFFFFu);
+  uint32_t qi = 0;
+  float cosx = 0.f;
+  int phase = 0;  // 0: emitter-sample segment, 1: continuation
+  bool active = false, exhausted = false;
+  for (;;) {
+    const bool want = !active && !exhausted;
+    const uint32_t wmask = __ballot_sync(0xffffffffu, want);
+    if (wmask) {
+      const int leader = __ffs(wmask) - 1;
+      uint32_t base = 0;
+      if (lane == leader) base = atomicAdd(&counters[2 * k + 1], (uint32_t)__popc(wmask));
+      base = __shfl_sync(0xffffffffu, base, leader);
+      if (want) {
+        const uint32_t idx = base + (uint32_t)__popc(wmask & ((1u << lane) - 1u));
+        if (idx < count) {
+          qi = idx;
+          const float4 ra = q_in[qi].a, rb = q_in[qi].b;
+          const float4 xn = e_in[qi].n, xl = e_in[qi].l;
+          gath[0] = xl.x;
+          gath[kBlock] = xl.y;
+          gath[2 * kBlock] = xl.z;
+          uint32_t jt;
+          float3 wl;
+          if (sample_emitter(bvh, C, seed, __float_as_uint(ra.w), __float_as_uint(rb.w), (uint32_t)k, f3(ra), f3(xn),
+                             jt, wl, cosx)) {
+            phase = 0;
+            nee.reset(jt);
+            ray_begin(rt, f3(ra), wl);
+          } else {
+            phase = 1;
+            vis.pb2 = xn.w * xn.w;
+            vis.reset();
+            ray_begin(rt, f3(ra), f3(rb));
+          }
+          round_begin(rt, bvh);
+          active = true;
+          ++traced;
+          if (kCount) ++cnt.rounds;
+        } else {
+          exhausted = true;
+        }
+      }
+    }
+    if (!__any_sync(0xffffffffu, active)) break;
+    bool take = false;
+    Ray nr;
+    RayExt nx;
+    if (active && round_steps<kK, kCount>(rt, bvh, C, s_stack + threadIdx.x, kBlock, kRefillSteps, cnt)) {
+      if (phase == 0) {
+        if (round_blend<kK, kCount>(rt, bvh, C, nee, cnt)) {
+          // the emitter sample's estimate: beta r_i w_i p_B p_L / (p_L^2 + p_B^2)
+          if (nee.found && nee.E > C.tau_E) {
+            const float pb = cosx * 0.318309886183790672f;
+            const float f = nee.wt * pb * nee.pl / (nee.pl * nee.pl + pb * pb);
+            const float4 beta = __ldcv(&q_in[qi].c);
+            const float4 ri = __ldg(&bvh.shade[nee.jt].s1);
+            gath[0] += beta.x * ri.x * f;
+            gath[kBlock] += beta.y * ri.y * f;
+            gath[2 * kBlock] += beta.z * ri.z * f;
+          }
+          phase = 1;
+          const float4 xn = e_in[qi].n;
+          vis.pb2 = xn.w * xn.w;
+          vis.reset();
+          ray_begin(rt, f3(q_in[qi].a), f3(q_in[qi].b));
+          round_begin(rt, bvh);
+          ++traced;
+          if (kCount) ++cnt.rounds;
+        } else {
+          round_begin(rt, bvh);
+          if (kCount) ++cnt.rounds;
+        }
+      } else if (round_blend<kK, kCount>(rt, bvh, C, vis, cnt)) {
+        const SegRec sg = finish(vis.get());
+        Ray r;
+        r.a = make_float4(rt.O.x, rt.O.y, rt.O.z, __ldcv(&q_in[qi].a.w));
+        r.b = make_float4(rt.w.x, rt.w.y, rt.w.z, __ldcv(&q_in[qi].b.w));
+        r.c = __ldcv(&q_in[qi].c);
+        RayExt x;
+        x.n = e_in[qi].n;
+        x.l = make_float4(gath[0], gath[kBlock], gath[2 * kBlock], 0.f);
+        const uint32_t pixel = __float_as_uint(r.a.w), sample = __float_as_uint(r.b.w);
+        float3 contrib;
+        take = shade_bounce_mis(k, max_bounces, rr_start, seed, C, r, x, sg, contrib, nr, nx);
+        if (!take)
+          slots[(int64_t)(sample - (uint32_t)s0) * npix + pixel] = make_float4(contrib.x, contrib.y, contrib.z, 0.f);
+        active = false;
+      } else {
+        round_begin(rt, bvh);
+        if (kCount) ++cnt.rounds;
+      }
+    }
+    __syncwarp();
+    const uint32_t at = warp_append(take, &counters[2 * (k + 1)]);
+    if (take) {
+      q_out[at] = nr;
+      e_out[at] = nx;
+    }
+  }
+  if (kCount) {
+    add_stats(stats, 1, traced);
+    add_stats(stats, 3, cnt.blended);
+    add_stats(stats, 4, cnt.nodes);
+    add_stats(stats, 5, cnt.tests);
+    add_stats(stats, 6, cnt.rounds);
+    uint32_t m = cnt.max_stack;
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0 && m) atomicMax((unsigned long long*)(stats + 7), (unsigned long long)m);
+  }
+}
+
 // Per pixel: add the batch's samples in order; on the last batch write the
 // mean.  Emitter pixels show R (Eq. 4), missed pixels 0.  With out_li (the
 // incident-radiance variant of the single-bounce render) the slots hold the
@@ -488,9 +641,11 @@ static inline unsigned nblocks(int64_t n) { return (unsigned)((n + kBlock - 1) /
 template <bool kCount>
 static cudaError_t render_impl(const RenderArgs& a, cudaStream_t st, int* launches) {
   const int64_t npix = (int64_t)a.cam.width * a.cam.height;
-  const int batch = choose_batch_spp(npix, a.spp, a.ws_bytes);
-  const RenderLayout L = render_layout(npix, a.spp, batch);
+  const bool mis = a.kind == 1 && (a.C.flags & EAGPT_FLAG_EMITTER_SAMPLING);
+  const int batch = choose_batch_spp(npix, a.spp, a.ws_bytes, mis);
+  const RenderLayout L = render_layout(npix, a.spp, batch, mis);
   char* ws = (char*)a.ws;
+  RayExt* ex[2] = {mis ? (RayExt*)(ws + L.e0) : nullptr, mis ? (RayExt*)(ws + L.e1) : nullptr};
   PrimRec* prim = (PrimRec*)(ws + L.prim);
   float4* acc = (float4*)(ws + L.acc);
   float4* slots = (float4*)(ws + L.slots);
@@ -501,14 +656,15 @@ static cudaError_t render_impl(const RenderArgs& a, cudaStream_t st, int* launch
   int nl = 0;
   EAGPT_LAUNCH(st, "k_primary", k_primary<kCount><<<nblocks(npix), kBlock, 0, st>>>(a.bvh, a.C, a.cam, mode, npix, prim, a.out_aux, a.out_stats));
   ++nl;
-  static int bounce_grid[2] = {0, 0};
+  static int bounce_grid[2] = {0, 0}, mis_grid[2] = {0, 0};
   if (!bounce_grid[kCount])
     bounce_grid[kCount] = EAGPT_REFILL ? persistent_blocks(k_bounce_r<kCount>) : persistent_blocks(k_bounce<kCount>);
+  if (mis && !mis_grid[kCount]) mis_grid[kCount] = persistent_blocks(k_bounce_mis<kCount>);
   for (int s0 = 0; s0 < a.spp; s0 += batch) {
     const int nb = a.spp - s0 < batch ? a.spp - s0 : batch;
     cudaMemsetAsync(counters, 0, kCounterWords * sizeof(uint32_t), st);
     EAGPT_LAUNCH(st, "k_generate", k_generate<kCount><<<nblocks(npix * nb), kBlock, 0, st>>>(prim, a.C, a.cam, a.kind, B, a.rr_start, a.seed, npix,
-                                                              s0, nb, q[0], counters, slots, a.out_stats));
+                                                              s0, nb, q[0], counters, slots, a.out_stats, ex[0]));
     ++nl;
     for (int k = 1; k <= B; ++k) {
       const uint32_t* perm = nullptr;
@@ -521,7 +677,11 @@ static cudaError_t render_impl(const RenderArgs& a, cudaStream_t st, int* launch
         launch_sort_pairs(k0, v0, k1, v1, (uint32_t*)(ws + L.shist), cap, st);
         perm = v0;
       }
-      if (EAGPT_REFILL)
+      if (mis)
+        EAGPT_LAUNCH(st, "k_bounce", k_bounce_mis<kCount><<<mis_grid[kCount], kBlock, 0, st>>>(a.bvh, a.C, k, B, a.rr_start, a.seed, npix, s0,
+                                                                   q[(k - 1) & 1], q[k & 1], ex[(k - 1) & 1], ex[k & 1],
+                                                                   counters, slots, a.out_stats));
+      else if (EAGPT_REFILL)
         EAGPT_LAUNCH(st, "k_bounce", k_bounce_r<kCount><<<bounce_grid[kCount], kBlock, 0, st>>>(a.bvh, a.C, a.kind, k, B, a.rr_start, a.seed, npix,
                                                                   s0, q[(k - 1) & 1], q[k & 1], counters, slots,
                                                                   a.out_stats, perm));

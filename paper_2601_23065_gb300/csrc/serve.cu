@@ -555,6 +555,8 @@ size_t eagpt_server_arena_bytes(int64_t n, int64_t queue_paths) {
 eagpt_status eagpt_server_create(const eagpt_scene_mut* scene, const eagpt_bvh* bvh, const eagpt_params* params,
                                  const eagpt_server_config* cfg, eagpt_server* out) {
   if (!scene || !bvh || !params || !cfg || !out) return set_error(EAGPT_ERR_INVALID_ARGUMENT, "null argument");
+  if (params->flags & EAGPT_FLAG_EMITTER_SAMPLING)
+    return set_error(EAGPT_ERR_NOT_SUPPORTED, "the serving loop renders without emitter sampling");
   if (cfg->max_active < 1 || cfg->max_active > kSrvMaxActive)
     return set_error(EAGPT_ERR_INVALID_ARGUMENT, "max_active must be in [1, 64]");
   if (cfg->queue_paths < 1) return set_error(EAGPT_ERR_INVALID_ARGUMENT, "queue_paths must be positive");

@@ -603,7 +603,12 @@ struct BlendVisitor {
 // The same blend with the running sums (all but T) in this thread's slot of
 // a shared-memory array, s[k * stride] for k = 0..10 (N xyz, R xyz, P xyz, D,
 // E): during a multi-round traversal they stay out of the register file.
-struct SmemBlendVisitor {
+// kMis: the continuation segment of the emitter-sampling path tracer; each
+// emitter hit's radiance term is weighted by the power heuristic
+// p_B^2 / (p_B^2 + p_L^2), p_L = c g(u, v) t^2 / |w . n| with c the emitter's
+// density factor kept in its shade record (s1.w, 0 for non-emitters).
+template <bool kMis>
+struct SmemBlendVisitorT {
   const ShadeRec* shade;
   Consts C;
   int mode;
@@ -611,8 +616,9 @@ struct SmemBlendVisitor {
   int stride;
   float T;
   uint32_t n_hits;
-  __device__ __forceinline__ SmemBlendVisitor(const ShadeRec* sh, const Consts& c, int m, float* slot, int str)
-      : shade(sh), C(c), mode(m), s(slot), stride(str), T(1.f), n_hits(0) {
+  float pb2;  // kMis: p_B^2 of the segment's direction
+  __device__ __forceinline__ SmemBlendVisitorT(const ShadeRec* sh, const Consts& c, int m, float* slot, int str)
+      : shade(sh), C(c), mode(m), s(slot), stride(str), T(1.f), n_hits(0), pb2(0.f) {
     reset();
   }
   __device__ __forceinline__ void reset() {
@@ -626,7 +632,11 @@ struct SmemBlendVisitor {
     const float4 s0 = __ldg(&sp->s0), s1 = __ldg(&sp->s1);
     const float wgt = __fmul_rn(T, h.alpha);
     const float sgn = h.d > 0.f ? -wgt : wgt;
-    const float re = (mode == 1 && !(s0.w > C.tau_E)) ? 0.f : wgt;
+    float re = (mode == 1 && !(s0.w > C.tau_E)) ? 0.f : wgt;
+    if (kMis && re != 0.f) {
+      const float pl = s1.w * expf(-0.5f * (h.u * h.u + h.v * h.v)) * (h.t * h.t) / fabsf(h.d);
+      re = re * (pb2 / (pb2 + pl * pl));
+    }
     s[0 * stride] = __fmaf_rn(sgn, R.r1.x, s[0 * stride]);
     s[1 * stride] = __fmaf_rn(sgn, R.r1.y, s[1 * stride]);
     s[2 * stride] = __fmaf_rn(sgn, R.r1.z, s[2 * stride]);
@@ -652,6 +662,38 @@ struct SmemBlendVisitor {
     b.T = T;
     b.n_hits = n_hits;
     return b;
+  }
+};
+using SmemBlendVisitor = SmemBlendVisitorT<false>;
+
+// The emitter-sample segment: the blend's E and T (same arithmetic and
+// stopping rule as the other visitors) and, when the target emitter record jt
+// is blended, its weight w = T_{i-1} alpha and its light pdf.
+struct NeeVisitor {
+  const ShadeRec* shade;
+  Consts C;
+  uint32_t jt;
+  float T, E, wt, pl;
+  bool found;
+  __device__ __forceinline__ void reset(uint32_t target) {
+    jt = target;
+    T = 1.f;
+    E = 0.f;
+    wt = 0.f;
+    pl = 0.f;
+    found = false;
+  }
+  __device__ __forceinline__ bool operator()(const TraceRec&, uint32_t j, const HitGeom& h) {
+    const ShadeRec* sp = shade + j;
+    const float wgt = __fmul_rn(T, h.alpha);
+    E = __fmaf_rn(wgt, __ldg(&sp->s0.w), E);
+    if (j == jt) {
+      found = true;
+      wt = wgt;
+      pl = __ldg(&sp->s1.w) * expf(-0.5f * (h.u * h.u + h.v * h.v)) * (h.t * h.t) / fabsf(h.d);
+    }
+    T = __fmul_rn(T, __fsub_rn(1.f, h.alpha));
+    return T < C.T_min;
   }
 };
 

@@ -14,6 +14,14 @@ struct __align__(16) Ray {
   float4 c;  // throughput, request id (bits; 0 outside the serving loop)
 };
 
+// Side record of a queued ray when emitter sampling is on (same queue
+// index): the normal of the vertex the ray leaves, the cosine-sampling pdf of
+// its direction, and the radiance the path's emitter samples gathered so far.
+struct __align__(16) RayExt {
+  float4 n;  // N~ of the origin vertex, p_B = (w . N~) / pi
+  float4 l;  // accumulated radiance, unused
+};
+
 struct __align__(16) PrimRec {
   float4 a;  // N~, D~
   float4 b;  // R, E
@@ -87,6 +95,78 @@ __device__ __forceinline__ bool shade_bounce(int kind, int k, int max_bounces, i
   nr.a = make_float4(O2.x, O2.y, O2.z, r.a.w);
   nr.b = make_float4(w2.x, w2.y, w2.z, r.b.w);
   nr.c = make_float4(beta.x, beta.y, beta.z, r.c.w);
+  return true;
+}
+
+// Emitter sample of the reflection at origin O2 with normal Nn (draws
+// (pixel, sample, k, 1)): an emitter chosen by the FP64 running weight sums, a
+// point of its support disc from the truncated Gaussian; returns false when
+// there is no emitter or the direction is below the tangent plane.
+__device__ __forceinline__ bool sample_emitter(const BvhView& bvh, const Consts& C, uint64_t seed, uint32_t pixel,
+                                               uint32_t sample, uint32_t k, float3 O2, float3 Nn, uint32_t& jt,
+                                               float3& wl, float& cosx) {
+  const uint32_t ne = bvh.hdr->em_count;
+  if (ne == 0) return false;
+  const float4 u = draws_w(seed, pixel, sample, k, 1u);
+  const double x = (double)u.x * bvh.hdr->em_total;  // u.x is exact in FP64
+  uint32_t lo = 0, hi = ne - 1;
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (bvh.em_cdf[mid] > x) hi = mid;
+    else lo = mid + 1;
+  }
+  jt = bvh.em_idx[lo];
+  const TraceRec* R = bvh.trace + jt;
+  const float4 r0 = __ldg(&R->r0), r2 = __ldg(&R->r2), r3 = __ldg(&R->r3);
+  // r2 = t_u / s_u and r3 = t_v / s_v: s_u t_u = r2 / |r2|^2
+  const float ia = 1.f / (r2.x * r2.x + r2.y * r2.y + r2.z * r2.z);
+  const float ib = 1.f / (r3.x * r3.x + r3.y * r3.y + r3.z * r3.z);
+  const float rho = sqrtf(-2.f * logf(1.f - u.y * (1.f - expf(-0.5f * C.support2))));
+  float sn, cs;
+  sincospif(2.f * u.z, &sn, &cs);
+  const float a = rho * cs * ia, b = rho * sn * ib;
+  const float3 y = make_float3(r0.x + a * r2.x + b * r3.x, r0.y + a * r2.y + b * r3.y, r0.z + a * r2.z + b * r3.z);
+  const float3 d = y - O2;
+  const float inv = rsqrtf(dot3(d, d));
+  wl = inv * d;
+  cosx = dot3(wl, Nn);
+  return cosx > 0.f;
+}
+
+// Shading after the continuation segment of bounce k with emitter sampling:
+// as shade_bounce for path tracing, but every way the path ends returns the
+// radiance its emitter samples gathered (ext.l) plus, at an emissive vertex,
+// the weighted R of the segment; a continuation carries the normal, its
+// direction's p_B and that radiance in next.
+__device__ __forceinline__ bool shade_bounce_mis(int k, int max_bounces, int rr_start, uint64_t seed,
+                                                 const Consts& C, const Ray& r, const RayExt& ext, const SegRec& s,
+                                                 float3& contrib, Ray& nr, RayExt& next) {
+  const float3 O = f3(r.a), w = f3(r.b);
+  const uint32_t pixel = __float_as_uint(r.a.w), sample = __float_as_uint(r.b.w);
+  float3 beta = f3(r.c);
+  const float3 L = f3(ext.l);
+  contrib = L;
+  if (!s.hit) return false;
+  if (s.E > C.tau_E) {
+    contrib = L + mul3(beta, s.R);  // s.R carries the power-heuristic weights
+    return false;
+  }
+  if (k >= max_bounces) return false;
+  beta = mul3(beta, s.P);
+  const float4 u = draws(seed, pixel, sample, (uint32_t)(k + 1));
+  if (k + 1 >= rr_start) {
+    const float q = fminf(1.f, fmaxf(beta.x, fmaxf(beta.y, beta.z)));
+    if (!(u.z < q)) return false;
+    beta = (1.f / q) * beta;
+  }
+  const float3 X = O + s.Dn * w;
+  const float3 O2 = X + C.bounce_offset * s.Nn;
+  const float3 w2 = cosine_direction(s.Nn, u.x, u.y);
+  nr.a = make_float4(O2.x, O2.y, O2.z, r.a.w);
+  nr.b = make_float4(w2.x, w2.y, w2.z, r.b.w);
+  nr.c = make_float4(beta.x, beta.y, beta.z, r.c.w);
+  next.n = make_float4(s.Nn.x, s.Nn.y, s.Nn.z, dot3(w2, s.Nn) * 0.318309886183790672f);
+  next.l = make_float4(L.x, L.y, L.z, 0.f);
   return true;
 }
 

@@ -38,7 +38,7 @@ def test_signatures_cover_header(lib):
 def test_defaults_and_sizes(lib):
     from paper_2601_23065_gb300 import capi
     p = capi.default_params()
-    assert abs(p.tau_E - 0.1) < 1e-7 and p.support_sigma == 3.0 and p.reserved == 0
+    assert abs(p.tau_E - 0.1) < 1e-7 and p.support_sigma == 3.0 and p.flags == 0
     assert lib.eagpt_bvh_bytes(0) > 0
     assert lib.eagpt_bvh_bytes(1000) > 1000 * 64
     assert lib.eagpt_bvh_bytes(-1) == 0
@@ -64,7 +64,7 @@ def test_host_argument_checks(lib):
     sc.n = 0
     assert lib.eagpt_build_bvh(ctypes.byref(sc), ctypes.byref(bad), None, 0, ctypes.byref(out), None) == 1
     bad = capi.default_params()
-    bad.reserved = 1
+    bad.flags = 2
     assert lib.eagpt_build_bvh(ctypes.byref(sc), ctypes.byref(bad), None, 0, ctypes.byref(out), None) == 1
     # stale BVH: version mismatch is refused before anything is launched
     cam = capi.Camera(8, 8, 4.0, 4.0, 4.0, 4.0)
