@@ -739,7 +739,10 @@ static int path_sample(job* jb, const render_ctx* c, hitbuf* b, int64_t pix, int
       const double cosx = dot3(wl, Nn);
       if (eps > 0 && fabs(cosx) <= FLAG_K * (eN + ERR_C * eps * (1.0 + amax3(O2) / dist))) *sflags |= ORA_FLAG_HEMI;
       if (cosx > 0.0) {
-        if (run > 0) jitter_ray(Ol, wl, c->seed, pix, s, k + (1 << 20), run, 2.0 * eps);
+        /* the FP32 emitter point comes from three transcendental evaluations
+         * (log, sqrt, sincos): its rays are perturbed at four times the scale
+         * of the other rays in the conditioning runs */
+        if (run > 0) jitter_ray(Ol, wl, c->seed, pix, s, k + (1 << 20), run, 8.0 * eps);
         ora_segment g3;
         if (segment(&jb->W, Ol, wl, 0.0, 1, ERR_C * eps * amax3(Ol), ERR_C * eps, b, &g3)) return -1;
         ++*segments;
