@@ -384,7 +384,7 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_bounce_mis(BvhView bvh, 
                                                        uint32_t* counters, float4* slots, int64_t* stats) {
   __shared__ uint32_t s_stack[kStackSize * kBlock];
   __shared__ float s_blend[11 * kBlock];
-  __shared__ float s_gath[3 * kBlock];  // radiance gathered by the emitter samples
+  __shared__ float s_gath[4 * kBlock];  // radiance gathered by the emitter samples, cos at the vertex
   const int lane = threadIdx.x & 31;
   float* gath = s_gath + threadIdx.x;
   const uint32_t count = counters[2 * k];
@@ -392,12 +392,13 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_bounce_mis(BvhView bvh, 
   uint32_t traced = 0;
   RayTrace<kK> rt;
   SmemBlendVisitorT<true> vis(bvh.shade, C, 1, s_blend + threadIdx.x, kBlock);
-  NeeVisitor nee;
+  // the emitter segment's state shares the blend slot (the phases never overlap)
+  NeeVisitorSM nee;
   nee.shade = bvh.shade;
   nee.C = C;
-  nee.reset(0xFFFFFFFFu);
+  nee.s = s_blend + threadIdx.x;
+  nee.stride = kBlock;
   uint32_t qi = 0;
-  float cosx = 0.f;
   int phase = 0;  // 0: emitter-sample segment, 1: continuation
   bool active = false, exhausted = false;
   for (;;) {
@@ -419,8 +420,10 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_bounce_mis(BvhView bvh, 
           gath[2 * kBlock] = xl.z;
           uint32_t jt;
           float3 wl;
+          float cosx;
           if (sample_emitter(bvh, C, seed, __float_as_uint(ra.w), __float_as_uint(rb.w), (uint32_t)k, f3(ra), f3(xn),
                              jt, wl, cosx)) {
+            gath[3 * kBlock] = cosx;
             phase = 0;
             nee.reset(jt);
             ray_begin(rt, f3(ra), wl);
@@ -447,11 +450,12 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_bounce_mis(BvhView bvh, 
       if (phase == 0) {
         if (round_blend<kK, kCount>(rt, bvh, C, nee, cnt)) {
           // the emitter sample's estimate: beta r_i w_i p_B p_L / (p_L^2 + p_B^2)
-          if (nee.found && nee.E > C.tau_E) {
-            const float pb = cosx * 0.318309886183790672f;
-            const float f = nee.wt * pb * nee.pl / (nee.pl * nee.pl + pb * pb);
+          if (nee.found() && nee.E() > C.tau_E) {
+            const float pb = gath[3 * kBlock] * 0.318309886183790672f;
+            const float pl = nee.pl();
+            const float f = nee.wt() * pb * pl / (pl * pl + pb * pb);
             const float4 beta = __ldcv(&q_in[qi].c);
-            const float4 ri = __ldg(&bvh.shade[nee.jt].s1);
+            const float4 ri = __ldg(&bvh.shade[nee.target()].s1);
             gath[0] += beta.x * ri.x * f;
             gath[kBlock] += beta.y * ri.y * f;
             gath[2 * kBlock] += beta.z * ri.z * f;

@@ -666,6 +666,42 @@ struct SmemBlendVisitorT {
 };
 using SmemBlendVisitor = SmemBlendVisitorT<false>;
 
+// NeeVisitor with its state (E, target weight, light pdf, found flag, target
+// record) in a per-thread shared-memory slot s[k * stride], k = 0..4, and only
+// T in a register.
+struct NeeVisitorSM {
+  const ShadeRec* shade;
+  Consts C;
+  float* s;
+  int stride;
+  float T;
+  __device__ __forceinline__ void reset(uint32_t target) {
+    T = 1.f;
+    s[0] = 0.f;
+    s[stride] = 0.f;
+    s[2 * stride] = 0.f;
+    s[3 * stride] = 0.f;
+    s[4 * stride] = __uint_as_float(target);
+  }
+  __device__ __forceinline__ float E() const { return s[0]; }
+  __device__ __forceinline__ float wt() const { return s[stride]; }
+  __device__ __forceinline__ float pl() const { return s[2 * stride]; }
+  __device__ __forceinline__ bool found() const { return s[3 * stride] != 0.f; }
+  __device__ __forceinline__ uint32_t target() const { return __float_as_uint(s[4 * stride]); }
+  __device__ __forceinline__ bool operator()(const TraceRec&, uint32_t j, const HitGeom& h) {
+    const ShadeRec* sp = shade + j;
+    const float wgt = __fmul_rn(T, h.alpha);
+    s[0] = __fmaf_rn(wgt, __ldg(&sp->s0.w), s[0]);
+    if (j == target()) {
+      s[stride] = wgt;
+      s[2 * stride] = __ldg(&sp->s1.w) * expf(-0.5f * (h.u * h.u + h.v * h.v)) * (h.t * h.t) / fabsf(h.d);
+      s[3 * stride] = 1.f;
+    }
+    T = __fmul_rn(T, __fsub_rn(1.f, h.alpha));
+    return T < C.T_min;
+  }
+};
+
 // The emitter-sample segment: the blend's E and T (same arithmetic and
 // stopping rule as the other visitors) and, when the target emitter record jt
 // is blended, its weight w = T_{i-1} alpha and its light pdf.

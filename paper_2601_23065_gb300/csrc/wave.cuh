@@ -121,7 +121,8 @@ __device__ __forceinline__ bool sample_emitter(const BvhView& bvh, const Consts&
   // r2 = t_u / s_u and r3 = t_v / s_v: s_u t_u = r2 / |r2|^2
   const float ia = 1.f / (r2.x * r2.x + r2.y * r2.y + r2.z * r2.z);
   const float ib = 1.f / (r3.x * r3.x + r3.y * r3.y + r3.z * r3.z);
-  const float rho = sqrtf(-2.f * logf(1.f - u.y * (1.f - expf(-0.5f * C.support2))));
+  // log1p keeps the relative accuracy of log(1 - x) for small x (small u1)
+  const float rho = sqrtf(-2.f * log1pf(-u.y * (1.f - expf(-0.5f * C.support2))));
   float sn, cs;
   sincospif(2.f * u.z, &sn, &cs);
   const float a = rho * cs * ia, b = rho * sn * ib;
