@@ -207,7 +207,18 @@ typedef struct {
   const surfel64* s;
   int64_t n;
   const ora_params* prm;
+  uint32_t ajit; /* conditioning run r > 0: every sigma g is perturbed by a
+                    reproducible relative +-4 FP32 ulps (its FP32 rounding) */
 } world;
+
+/* uniform in [-1, 1) from (surfel, run): splitmix64 finaliser */
+static double ajit_draw(int64_t idx, uint32_t run) {
+  uint64_t z = (uint64_t)idx * 0x9E3779B97F4A7C15ull + (uint64_t)run * 0xD1B54A32D192ED03ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  z ^= z >> 31;
+  return (double)(z >> 11) * (2.0 / 9007199254740992.0) - 1.0;
+}
 
 /* Collects every blended hit of the segment in order (after the stop) into
  * b, fills seg, returns 0.  mode 1 masks the radiance of non-emitters.
@@ -249,6 +260,7 @@ static int segment(const world* W, const double O[3], const double w[3], double 
     double du = ep / (fabs(d) * smin);
     double dq = 2.0 * sqrt(2.0 * (q > S2 ? q : S2)) * du + ERR_C * eps * S2;
     double sg = g->sigma * exp(-0.5 * q);
+    if (W->ajit) sg *= 1.0 + 4.0 * eps * ajit_draw(i, W->ajit);
     double rel_a = sqrt(2.0 * q) * du + ERR_C * eps;
     int in_support = q <= S2;
     int near_support = eps > 0 && fabs(q - S2) <= FLAG_K * dq;
@@ -726,6 +738,15 @@ static int path_sample(job* jb, const render_ctx* c, hitbuf* b, int64_t pix, int
     ora_cosine_direction(Nn, u[0], u[1], w2);
     for (int j = 0; j < 3; ++j) O2[j] = X[j] + prm->bounce_offset * Nn[j];
     const emitters* em = c->em;
+    /* the normal the MIS pdfs use: with emitter sampling the blended normal
+     * enters the sample directly (p_B = cos / pi, the emitter sample's cos),
+     * so the conditioning runs also perturb it by its propagated FP32 error
+     * estimate */
+    double Nm[3] = {Nn[0], Nn[1], Nn[2]};
+    if (em && em->n_e > 0 && run > 0) {
+      double Oz[3] = {0, 0, 0};
+      jitter_ray(Oz, Nm, c->seed, pix, s, k + (2 << 20), run, eN + ERR_C * eps);
+    }
     if (em && em->n_e > 0) {
       /* emitter sample from this vertex: draws (pixel, sample, k, 1) */
       double v4[4], y[3], wl[3], Ol[3] = {O2[0], O2[1], O2[2]};
@@ -736,7 +757,7 @@ static int path_sample(job* jb, const render_ctx* c, hitbuf* b, int64_t pix, int
       double dl[3] = {y[0] - O2[0], y[1] - O2[1], y[2] - O2[2]};
       const double dist = norm3(dl);
       for (int j = 0; j < 3; ++j) wl[j] = dl[j] / dist;
-      const double cosx = dot3(wl, Nn);
+      const double cosx = dot3(wl, Nm);
       if (eps > 0 && fabs(cosx) <= FLAG_K * (eN + ERR_C * eps * (1.0 + amax3(O2) / dist))) *sflags |= ORA_FLAG_HEMI;
       if (cosx > 0.0) {
         /* the FP32 emitter point comes from three transcendental evaluations
@@ -780,7 +801,7 @@ static int path_sample(job* jb, const render_ctx* c, hitbuf* b, int64_t pix, int
       /* Eq. 8: first emissive vertex within the bounce limit; with emitter
        * sampling each emitter term carries its power-heuristic weight */
       if (em && em->n_e > 0) {
-        const double pb = dot3(w2, Nn) / ORA_PI;
+        const double pb = dot3(w2, Nm) / ORA_PI;
         double T = 1.0;
         for (int64_t h = 0; h < b->n; ++h) {
           const hit64* hh = &b->h[h];
@@ -838,11 +859,14 @@ static int render_item(job* jb, int64_t i, hitbuf* b) {
   }
   ora_segment gj[2];
   double wj[2][3];
+  job jr[2];
   for (int r = 0; r < n_runs; ++r) {
+    jr[r] = *jb;
+    jr[r].W.ajit = (uint32_t)(r + 1);
     double Oj[3] = {O[0], O[1], O[2]};
     for (int k = 0; k < 3; ++k) wj[r][k] = w[k];
     jitter_ray(Oj, wj[r], c->seed, pix, -1, 0, r + 1, 2.0 * eps);
-    if (segment(&jb->W, O, wj[r], 0.0, seg_mode, 0.0, ERR_C * eps, b, &gj[r])) {
+    if (segment(&jr[r].W, O, wj[r], 0.0, seg_mode, 0.0, ERR_C * eps, b, &gj[r])) {
       free(dev);
       return -1;
     }
@@ -858,7 +882,7 @@ static int render_item(job* jb, int64_t i, hitbuf* b) {
       double cj[3];
       uint32_t fj = 0;
       int64_t sj = 0;
-      if (path_sample(jb, c, b, pix, s, O, wj[r], &gj[r], r + 1, cj, &fj, &sj)) {
+      if (path_sample(&jr[r], c, b, pix, s, O, wj[r], &gj[r], r + 1, cj, &fj, &sj)) {
         free(dev);
         return -1;
       }

@@ -45,7 +45,7 @@ __device__ __forceinline__ bool intersect(const TraceRec& R, float3 O, float3 w,
   const float u = dot3_rn(x, a), v = dot3_rn(x, b);
   const float q = __fmaf_rn(u, u, __fmul_rn(v, v));
   if (!(q <= C.support2)) return false;
-  const float sg = __fmul_rn(R.r0.w, __expf(-0.5f * q));
+  const float sg = __fmul_rn(R.r0.w, expf(-0.5f * q));  // expf: within 2 ulps
   const float alpha = fminf(sg, C.alpha_max);
   if (!(alpha >= C.alpha_min)) return false;
   h.t = t;
