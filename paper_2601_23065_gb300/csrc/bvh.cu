@@ -291,26 +291,62 @@ __global__ void __launch_bounds__(kEmBlock) k_em_write(eagpt_scene sc, Consts C,
   }
 }
 
-// one thread: the running sums (in place) and each emitter's density factor
-__global__ void k_em_finalize(const uint32_t* __restrict__ total_count, const uint32_t* __restrict__ em_idx,
-                              double* em_cdf, const uint32_t* __restrict__ sorted_idx, const float* __restrict__ scale,
-                              ShadeRec* shade, BvhHeader* hdr, double norm) {
+// The running sums (in place) and each emitter's density factor, in one block:
+// the weights are staged in shared memory chunk by chunk (coalesced loads) and
+// one thread adds them in emitter order, so the sums are exactly those of a
+// sequential FP64 loop; the density factors are then written in parallel.
+constexpr int kEmChunk = 4096;
+
+__global__ void __launch_bounds__(1024) k_em_finalize(const uint32_t* __restrict__ total_count,
+                                                      const uint32_t* __restrict__ em_idx, double* em_cdf,
+                                                      const uint32_t* __restrict__ sorted_idx,
+                                                      const float* __restrict__ scale, ShadeRec* shade, BvhHeader* hdr,
+                                                      double norm) {
+  __shared__ double s_w[kEmChunk];
+  __shared__ double s_total;
   const uint32_t ne = *total_count;
-  double total = 0.0;
-  for (uint32_t k = 0; k < ne; ++k) total = __dadd_rn(total, em_cdf[k]);
-  double run = 0.0;
-  for (uint32_t k = 0; k < ne; ++k) {
-    const double w = em_cdf[k];
-    run = __dadd_rn(run, w);
-    em_cdf[k] = run;
-    const uint32_t j = em_idx[k];
-    const uint32_t i = sorted_idx[j];
-    const double c = __ddiv_rn(__ddiv_rn(w, total),
-                               __dmul_rn(__dmul_rn(norm, (double)scale[2 * (int64_t)i]), (double)scale[2 * (int64_t)i + 1]));
-    shade[j].s1.w = (float)c;
+  if (threadIdx.x == 0) s_total = 0.0;
+  // pass 1: the total, in emitter order
+  for (uint32_t c0 = 0; c0 < ne; c0 += kEmChunk) {
+    const uint32_t m = ne - c0 < (uint32_t)kEmChunk ? ne - c0 : (uint32_t)kEmChunk;
+    __syncthreads();
+    for (uint32_t k = threadIdx.x; k < m; k += blockDim.x) s_w[k] = em_cdf[c0 + k];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = s_total;
+      for (uint32_t k = 0; k < m; ++k) t = __dadd_rn(t, s_w[k]);
+      s_total = t;
+    }
   }
-  hdr->em_total = total;
-  hdr->em_count = ne;
+  __syncthreads();
+  const double total = s_total;
+  // pass 2: running sums (one thread) and density factors (all threads)
+  double run = 0.0;
+  for (uint32_t c0 = 0; c0 < ne; c0 += kEmChunk) {
+    const uint32_t m = ne - c0 < (uint32_t)kEmChunk ? ne - c0 : (uint32_t)kEmChunk;
+    __syncthreads();
+    for (uint32_t k = threadIdx.x; k < m; k += blockDim.x) {
+      const double w = em_cdf[c0 + k];
+      s_w[k] = w;
+      const uint32_t j = em_idx[c0 + k];
+      const uint32_t i = sorted_idx[j];
+      const double c = __ddiv_rn(__ddiv_rn(w, total), __dmul_rn(__dmul_rn(norm, (double)scale[2 * (int64_t)i]),
+                                                                 (double)scale[2 * (int64_t)i + 1]));
+      shade[j].s1.w = (float)c;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0)
+      for (uint32_t k = 0; k < m; ++k) {
+        run = __dadd_rn(run, s_w[k]);
+        s_w[k] = run;
+      }
+    __syncthreads();
+    for (uint32_t k = threadIdx.x; k < m; k += blockDim.x) em_cdf[c0 + k] = s_w[k];
+  }
+  if (threadIdx.x == 0) {
+    hdr->em_total = total;
+    hdr->em_count = ne;
+  }
 }
 
 static cudaError_t launch_emitters(const eagpt_scene& sc, const Consts& C, char* base, const BvhLayout& L,
@@ -325,7 +361,7 @@ static cudaError_t launch_emitters(const eagpt_scene& sc, const Consts& C, char*
                                                 (double*)(base + L.em_cdf)));
   const double S2 = (double)C.support2;
   const double norm = 2.0 * 3.14159265358979323846 * (1.0 - std::exp(-0.5 * S2));
-  EAGPT_LAUNCH(st, "k_em_finalize", k_em_finalize<<<1, 1, 0, st>>>(counts + nb, (const uint32_t*)(base + L.em_idx),
+  EAGPT_LAUNCH(st, "k_em_finalize", k_em_finalize<<<1, 1024, 0, st>>>(counts + nb, (const uint32_t*)(base + L.em_idx),
                                                     (double*)(base + L.em_cdf), (const uint32_t*)(base + L.sorted_idx),
                                                     sc.scale, (ShadeRec*)(base + L.shade),
                                                     (BvhHeader*)(base + L.header), norm));
