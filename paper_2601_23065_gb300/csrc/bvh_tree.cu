@@ -198,7 +198,56 @@ __device__ __forceinline__ Node8 make_node8(const float4* lo, const float4* hi, 
   return n;
 }
 
-// One level of the top-down collapse.  Frontier entries are (binary node,
+// Quantised BVH4 node (see Node4q): the same quantisation as make_node8 for
+// four children (origin = union lo, quantum 2^e per axis with extent /
+// quantum <= 254, bounds rounded outward and checked against the exact
+// decode fma(q, 2^e, origin) the traversal uses).
+__device__ __forceinline__ Node4q make_node4q(const float4* lo, const float4* hi, const uint32_t* link, int nc) {
+  float o[3] = {3e38f, 3e38f, 3e38f}, top[3] = {-3e38f, -3e38f, -3e38f};
+  for (int k = 0; k < nc; ++k) {
+    const float l[3] = {lo[k].x, lo[k].y, lo[k].z}, h[3] = {hi[k].x, hi[k].y, hi[k].z};
+    for (int a = 0; a < 3; ++a) {
+      o[a] = fminf(o[a], l[a]);
+      top[a] = fmaxf(top[a], h[a]);
+    }
+  }
+  uint32_t eb[3];
+  float s[3];
+  for (int a = 0; a < 3; ++a) {
+    int e = -100;
+    const float x = (top[a] - o[a]) / 254.0f;
+    if (x > 0.f) {
+      frexpf(x, &e);  // x <= 2^e
+      e = max(-100, min(100, e));
+    }
+    eb[a] = (uint32_t)(e + 127);
+    s[a] = __int_as_float((int)(eb[a] << 23));
+  }
+  uint32_t qlo[3] = {0, 0, 0}, qhi[3] = {0, 0, 0};
+  for (int k = 0; k < nc; ++k) {
+    const float l[3] = {lo[k].x, lo[k].y, lo[k].z}, h[3] = {hi[k].x, hi[k].y, hi[k].z};
+    for (int a = 0; a < 3; ++a) {
+      int ql = (int)floorf((l[a] - o[a]) / s[a]);
+      ql = max(0, min(255, ql));
+      while (ql > 0 && __fmaf_rn((float)ql, s[a], o[a]) > l[a]) --ql;
+      int qh = (int)ceilf((h[a] - o[a]) / s[a]);
+      qh = max(0, min(255, qh));
+      while (qh < 255 && __fmaf_rn((float)qh, s[a], o[a]) < h[a]) ++qh;
+      qlo[a] |= (uint32_t)ql << (8 * k);
+      qhi[a] |= (uint32_t)qh << (8 * k);
+    }
+  }
+  Node4q n;
+  n.u0 = make_uint4(__float_as_uint(o[0]), __float_as_uint(o[1]), __float_as_uint(o[2]),
+                    eb[0] | (eb[1] << 8) | (eb[2] << 16));
+  n.u1 = make_uint4(nc > 0 ? link[0] : kEmptyChild, nc > 1 ? link[1] : kEmptyChild, nc > 2 ? link[2] : kEmptyChild,
+                    nc > 3 ? link[3] : kEmptyChild);
+  n.u2 = make_uint4(qlo[0], qlo[1], qlo[2], 0u);
+  n.u3 = make_uint4(qhi[0], qhi[1], qhi[2], 0u);
+  return n;
+}
+
+// One level of the top-down collapse.// One level of the top-down collapse.  Frontier entries are (binary node,
 // BVH node).  levels[lv] holds this level's frontier size, levels[lv + 1]
 // collects the next one; levels[kMaxCollapseLevels + 1] counts BVH nodes.
 template <int W>
@@ -254,6 +303,8 @@ __global__ void k_collapse(TreeArrays T, void* nodes_out, int32_t* src4, const i
     }
     if (W == 8) {
       ((Node8*)nodes_out)[e.y] = make_node8(blo, bhi, link, nc);
+    } else if (kQ4) {
+      ((Node4q*)nodes_out)[e.y] = make_node4q(blo, bhi, link, nc);
     } else {
       Node4 nd;
       nd.lox = nd.loy = nd.loz = make_float4(1e30f, 1e30f, 1e30f, 1e30f);
@@ -302,6 +353,19 @@ __global__ void k_bvh_boxes(TreeArrays T, void* nodes_out, const int32_t* __rest
         nc = k + 1;
       }
       nodes[i] = make_node8(lo, hi, link, nc);
+    } else if (kQ4) {
+      Node4q* nodes = (Node4q*)nodes_out;
+      const Node4q old = nodes[i];
+      const uint32_t link[4] = {old.u1.x, old.u1.y, old.u1.z, old.u1.w};
+      float4 lo[4], hi[4];
+      int nc = 0;
+      for (int k = 0; k < 4; ++k) {
+        const int32_t c = src4[8 * i + k];
+        if (c == INT32_MIN) break;
+        code_box(T, c, lo[k], hi[k]);
+        nc = k + 1;
+      }
+      nodes[i] = make_node4q(lo, hi, link, nc);
     } else {
       Node4* nodes = (Node4*)nodes_out;
       Node4 nd = nodes[i];
@@ -326,7 +390,9 @@ __global__ void k_small_root(int64_t n, const float4* __restrict__ plo, const fl
     hi = make_float4(fmaxf(hi.x, phi[j].x), fmaxf(hi.y, phi[j].y), fmaxf(hi.z, phi[j].z), 0.f);
   }
   const uint32_t leaf = kLeafBit | ((uint32_t)(n - 1) << kLeafCountShift);
-  if (kBvh8) {
+  if (kQ4) {
+    ((Node4q*)nodes_out)[0] = make_node4q(&lo, &hi, &leaf, 1);
+  } else if (kBvh8) {
     ((Node8*)nodes_out)[0] = make_node8(&lo, &hi, &leaf, 1);
   } else {
     Node4 nd;

@@ -97,6 +97,7 @@ BvhView make_view(const eagpt_bvh& b) {
     v.shade = (const ShadeRec*)(base + L.shade);
     v.nodes = (const Node4*)(base + L.nodes);
     v.nodes8 = (const Node8*)(base + L.nodes);
+    v.nodes4q = (const Node4q*)(base + L.nodes);
     v.root = 0;  // node 0: Karras root, or the single node of a small scene
     v.bounds_bits = (const uint32_t*)(base + L.header);
     v.hdr = (const BvhHeader*)(base + L.header);

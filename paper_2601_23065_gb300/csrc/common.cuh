@@ -66,6 +66,18 @@ struct __align__(128) Node4 {
   uint4 pad;
 };
 
+// Quantised BVH4 node, 64 B (four 16-byte loads): per axis the children's
+// bounds as 8-bit multiples q of a power of two 2^e above the node's origin,
+// decoded as fma(q, 2^e, origin), rounded outward and checked against that
+// exact decode when built.
+//   u0 = (origin.x, origin.y, origin.z, exps)  exps bytes 0..2: biased e per axis
+//   u1 = child links 0..3
+//   u2 = (qlo.x, qlo.y, qlo.z, 0), byte k of a word = child k
+//   u3 = (qhi.x, qhi.y, qhi.z, 0)
+struct __align__(64) Node4q {
+  uint4 u0, u1, u2, u3;
+};
+
 // BVH8 node, 96 B (six 16-byte loads): eight child links and eight child
 // boxes quantised to 8 bits per bound relative to the node's box.
 //   u0 = (origin.x, origin.y, origin.z, exps)  exps bytes 0..2: biased
@@ -84,6 +96,11 @@ struct __align__(16) Node8 {
 #define EAGPT_BVH8 0
 #endif
 constexpr bool kBvh8 = EAGPT_BVH8 != 0;
+// quantised 64-byte BVH4 nodes instead of 128-byte ones
+#ifndef EAGPT_QNODE4
+#define EAGPT_QNODE4 0
+#endif
+constexpr bool kQ4 = EAGPT_QNODE4 != 0 && !kBvh8;
 constexpr int kBvhWidth = kBvh8 ? 8 : 4;
 
 constexpr int kMaxCollapseLevels = 96;  // BVH levels built top-down
@@ -161,6 +178,7 @@ struct BvhView {
   const ShadeRec* shade;
   const Node4* nodes;    // BVH4 nodes (kBvh8 == false)
   const Node8* nodes8;   // BVH8 nodes (kBvh8 == true), same storage
+  const Node4q* nodes4q; // quantised BVH4 nodes (kQ4 == true), same storage
   uint32_t root;  // node index, or an encoded leaf when n <= kLeafMax
   int64_t n;
   const uint32_t* bounds_bits;  // scene centroid bounds (BvhHeader), ordered-int encoded

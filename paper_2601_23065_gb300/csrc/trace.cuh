@@ -123,10 +123,39 @@ __device__ __forceinline__ void leaf_step(const BvhView& bvh, const Consts& C, f
 // nearest, or kEmptyChild when none is hit.  Returns false on stack overflow.
 __device__ __forceinline__ bool node_step(const BvhView& bvh, uint32_t node, float3 O, float3 inv, float t_last,
                                           float tmax, uint32_t* stack, int stride, int& sp, uint32_t& next) {
-  const Node4* np = bvh.nodes + node;
-  const uint4 ch = __ldg(&np->child);
   const float inf = __int_as_float(0x7f800000);
   float e[4];
+#if EAGPT_QNODE4
+  // quantised node: near/far planes by direction sign, decoded exactly as the
+  // builder checked them, one FMA per plane
+  const Node4q* qp = bvh.nodes4q + node;
+  const uint4 u0 = __ldg(&qp->u0), ch = __ldg(&qp->u1), u2 = __ldg(&qp->u2), u3 = __ldg(&qp->u3);
+  uint32_t c[4] = {ch.x, ch.y, ch.z, ch.w};
+  {
+    const float ox = __uint_as_float(u0.x), oy = __uint_as_float(u0.y), oz = __uint_as_float(u0.z);
+    const float sx = __uint_as_float((u0.w & 0xFFu) << 23), sy = __uint_as_float(((u0.w >> 8) & 0xFFu) << 23);
+    const float sz = __uint_as_float(((u0.w >> 16) & 0xFFu) << 23);
+    const bool px = inv.x >= 0.f, py = inv.y >= 0.f, pz = inv.z >= 0.f;
+    const uint32_t nqx = px ? u2.x : u3.x, fqx = px ? u3.x : u2.x;
+    const uint32_t nqy = py ? u2.y : u3.y, fqy = py ? u3.y : u2.y;
+    const uint32_t nqz = pz ? u2.z : u3.z, fqz = pz ? u3.z : u2.z;
+    const float oix = O.x * inv.x, oiy = O.y * inv.y, oiz = O.z * inv.z;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int sh = 8 * k;
+      const float nx = __fmaf_rn((float)((nqx >> sh) & 0xFFu), sx, ox), fx = __fmaf_rn((float)((fqx >> sh) & 0xFFu), sx, ox);
+      const float ny = __fmaf_rn((float)((nqy >> sh) & 0xFFu), sy, oy), fy = __fmaf_rn((float)((fqy >> sh) & 0xFFu), sy, oy);
+      const float nz = __fmaf_rn((float)((nqz >> sh) & 0xFFu), sz, oz), fz = __fmaf_rn((float)((fqz >> sh) & 0xFFu), sz, oz);
+      const float t0 = fmaxf(fmaxf(__fmaf_rn(nx, inv.x, -oix), __fmaf_rn(ny, inv.y, -oiy)),
+                             fmaxf(__fmaf_rn(nz, inv.z, -oiz), t_last));
+      const float t1 = fminf(fminf(__fmaf_rn(fx, inv.x, -oix), __fmaf_rn(fy, inv.y, -oiy)),
+                             fminf(__fmaf_rn(fz, inv.z, -oiz), tmax));
+      e[k] = (t0 <= t1 && c[k] != kEmptyChild) ? t0 : inf;
+    }
+  }
+#else
+  const Node4* np = bvh.nodes + node;
+  const uint4 ch = __ldg(&np->child);
   uint32_t c[4] = {ch.x, ch.y, ch.z, ch.w};
 #if EAGPT_FAST_SLAB
   // Per axis the plane the ray enters first is the low one when the
@@ -169,6 +198,7 @@ __device__ __forceinline__ bool node_step(const BvhView& bvh, uint32_t node, flo
     }
   }
 #endif
+#endif  // EAGPT_QNODE4
   // front-to-back order: sorting network on (entry, link)
 #define EAGPT_CSWAP(i, j)                         \
   if (e[j] < e[i]) {                              \
