@@ -211,13 +211,25 @@ typedef struct {
                     reproducible relative +-4 FP32 ulps (its FP32 rounding) */
 } world;
 
-/* uniform in [-1, 1) from (surfel, run): splitmix64 finaliser */
-static double ajit_draw(int64_t idx, uint32_t run) {
-  uint64_t z = (uint64_t)idx * 0x9E3779B97F4A7C15ull + (uint64_t)run * 0xD1B54A32D192ED03ull;
+/* splitmix64 finaliser (Steele, Lea, Flood: "Fast splittable pseudorandom
+ * number generators", OOPSLA 2014) */
+static uint64_t mix64(uint64_t z) {
   z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
   z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-  z ^= z >> 31;
+  return z ^ (z >> 31);
+}
+
+/* uniform in [-1, 1) from (surfel, run) */
+static double ajit_draw(int64_t idx, uint32_t run) {
+  const uint64_t z = mix64((uint64_t)idx * 0x9E3779B97F4A7C15ull + (uint64_t)run * 0xD1B54A32D192ED03ull);
   return (double)(z >> 11) * (2.0 / 9007199254740992.0) - 1.0;
+}
+
+/* the discrete outcome of a traced segment: its blended surfels in order */
+static uint64_t hits_signature(const hitbuf* b) {
+  uint64_t h = mix64(0x9E3779B97F4A7C15ull ^ (uint64_t)b->n);
+  for (int64_t k = 0; k < b->n; ++k) h = mix64(h ^ (uint64_t)b->h[k].idx);
+  return h;
 }
 
 /* Collects every blended hit of the segment in order (after the stop) into
@@ -697,10 +709,12 @@ static void jitter_ray(double O[3], double w[3], uint64_t seed, int64_t pix, int
 
 /* One sample's path from the pixel's primary segment g1 (Eq. 6 for kind 0,
  * Eq. 8 for kind 1).  run > 0 perturbs every secondary ray (conditioning
- * estimate); run 0 is the exact evaluation and also collects the flags. */
+ * estimate); run 0 is the exact evaluation and also collects the flags.
+ * *psig accumulates the path's discrete outcome: each traced segment's
+ * blended surfels and each bounce entered. */
 static int path_sample(job* jb, const render_ctx* c, hitbuf* b, int64_t pix, int32_t s, const double O[3],
                        const double w[3], const ora_segment* g1, int32_t run, double contrib[3], uint32_t* sflags,
-                       int64_t* segments) {
+                       int64_t* segments, uint64_t* psig) {
   const ora_params* prm = jb->W.prm;
   const double eps = prm->fp32_eps;
   const int pt = c->kind == 1;
@@ -734,6 +748,7 @@ static int path_sample(job* jb, const render_ctx* c, hitbuf* b, int64_t pix, int
       for (int j = 0; j < 3; ++j) beta[j] /= q;
     }
     if (eps > 0 && fabs(Nn[2]) <= FLAG_K * eN) *sflags |= ORA_FLAG_ONB;
+    *psig = mix64(*psig ^ (0x100u + (uint32_t)k));
     double w2[3], O2[3];
     ora_cosine_direction(Nn, u[0], u[1], w2);
     for (int j = 0; j < 3; ++j) O2[j] = X[j] + prm->bounce_offset * Nn[j];
@@ -766,6 +781,7 @@ static int path_sample(job* jb, const render_ctx* c, hitbuf* b, int64_t pix, int
         if (run > 0) jitter_ray(Ol, wl, c->seed, pix, s, k + (1 << 20), run, 8.0 * eps);
         ora_segment g3;
         if (segment(&jb->W, Ol, wl, 0.0, 1, ERR_C * eps * amax3(Ol), ERR_C * eps, b, &g3)) return -1;
+        *psig = mix64(*psig ^ hits_signature(b));
         ++*segments;
         *sflags |= g3.flags;
         if (g3.n_hits > 0 && g3.E > prm->tau_E) {
@@ -788,6 +804,7 @@ static int path_sample(job* jb, const render_ctx* c, hitbuf* b, int64_t pix, int
     ora_segment g2;
     /* margins at this segment's own FP32 rounding scale */
     if (segment(&jb->W, O2, w2, 0.0, seg_mode, ERR_C * eps * amax3(O2), ERR_C * eps, b, &g2)) return -1;
+    *psig = mix64(*psig ^ hits_signature(b));
     ++*segments;
     *sflags |= g2.flags;
     if (g2.n_hits == 0) return 0; /* miss: no light */
@@ -841,6 +858,7 @@ static int render_item(job* jb, int64_t i, hitbuf* b) {
   primary_ray(c->cam, pix, O, w);
   ora_segment g1;
   if (segment(&jb->W, O, w, 0.0, seg_mode, 0.0, ERR_C * eps, b, &g1)) return -1;
+  const uint64_t sig1 = hits_signature(b);
   int64_t segments = 1;
   double acc[3] = {0, 0, 0};
   /* conditioning runs: the whole sample (primary direction included) is
@@ -859,6 +877,7 @@ static int render_item(job* jb, int64_t i, hitbuf* b) {
   }
   ora_segment gj[2];
   double wj[2][3];
+  uint64_t sigj[2];
   job jr[2];
   for (int r = 0; r < n_runs; ++r) {
     jr[r] = *jb;
@@ -868,28 +887,38 @@ static int render_item(job* jb, int64_t i, hitbuf* b) {
     jitter_ray(Oj, wj[r], c->seed, pix, -1, 0, r + 1, 2.0 * eps);
     if (segment(&jr[r].W, O, wj[r], 0.0, seg_mode, 0.0, ERR_C * eps, b, &gj[r])) {
       free(dev);
+      free(mag);
       return -1;
     }
+    sigj[r] = hits_signature(b);
   }
   for (int32_t s = 0; s < c->spp; ++s) {
     uint32_t sflags = g1.flags;
     double contrib[3];
-    if (path_sample(jb, c, b, pix, s, O, w, &g1, 0, contrib, &sflags, &segments)) {
+    uint64_t sig0 = sig1;
+    if (path_sample(jb, c, b, pix, s, O, w, &g1, 0, contrib, &sflags, &segments, &sig0)) {
       free(dev);
+      free(mag);
       return -1;
     }
     for (int r = 0; r < n_runs; ++r) {
       double cj[3];
       uint32_t fj = 0;
       int64_t sj = 0;
-      if (path_sample(&jr[r], c, b, pix, s, O, wj[r], &gj[r], r + 1, cj, &fj, &sj)) {
+      uint64_t sigr = sigj[r];
+      if (path_sample(&jr[r], c, b, pix, s, O, wj[r], &gj[r], r + 1, cj, &fj, &sj, &sigr)) {
         free(dev);
+        free(mag);
         return -1;
       }
       for (int k = 0; k < 3; ++k) {
         double d = fabs(cj[k] - contrib[k]);
         if (d > dev[s]) dev[s] = d;
       }
+      /* a discrete outcome along the path (a blended surfel, a bounce) that
+       * FP32-scale perturbations change makes the sample ill-conditioned even
+       * when this run's value happens to agree */
+      if (sigr != sig0) dev[s] = INFINITY;
     }
     for (int k = 0; k < 3; ++k) acc[k] += contrib[k];
     if (mag) mag[s] = amax3(contrib);
@@ -901,7 +930,8 @@ static int render_item(job* jb, int64_t i, hitbuf* b) {
   if (n_runs && c->out_sample_flags) {
     /* a sample is ill-conditioned when FP32-scale perturbations move it by
      * more than cond_tol of its own value (radiance is non-negative, so a
-     * mean of unflagged samples keeps that relative bound) */
+     * mean of unflagged samples keeps that relative bound) or change a
+     * discrete outcome along its path */
     for (int32_t s = 0; s < c->spp; ++s)
       if (dev[s] > prm->cond_tol * mag[s]) c->out_sample_flags[i * c->spp + s] |= ORA_FLAG_COND;
   }
