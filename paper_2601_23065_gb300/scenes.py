@@ -16,7 +16,13 @@ scenes with 500k, Eyeful e- scenes with 1M, Sec. 4.1-4.2):
 * interior surfels: uniform in the box shrunk by 5 %, uniformly random
   orientation (Shoemake's uniform quaternion);
 * scales log-uniform in [0.005, 0.05] m, opacity U[0.5, 1], albedo RGB
-  U[0.1, 0.8];
+  U[0.1, 0.8]; in rooms whose wall surfels are denser than the medium room's
+  (200k surfels in 5x4x3 m: 1,558 per m^2), every scale is multiplied by
+  sqrt(medium density / density), so that a point of a wall is covered by as
+  many surfels as in the medium room and the interior stays as transparent: a
+  finer reconstruction of the same surfaces, not a denser fog (with the fixed
+  scale law, the 6M-surfel layout's primary rays stop 0.14 m from the camera
+  and no path reaches an emitter);
 * emitters e = 1 with radiance RGB U[1, 10]; non-emitters e = 0 with a
   radiance cache RGB U[0, 0.5].
 
@@ -31,6 +37,15 @@ import math
 import numpy as np
 
 WALL_FRACTION = 3000.0 / 4096.0  # wall : interior = 3000 : 1096 in every room
+# wall surfels per m^2 of the medium room (200k surfels, 5 x 4 x 3 m box)
+REF_WALL_DENSITY = round(200_000 * WALL_FRACTION) / 94.0
+
+
+def scale_factor(n_wall: int, wall_area: float) -> float:
+    """Factor on the scale law for a room with n_wall wall surfels over
+    wall_area m^2: sqrt(REF_WALL_DENSITY / density), never above 1."""
+    density = n_wall / wall_area
+    return 1.0 if density <= REF_WALL_DENSITY else math.sqrt(REF_WALL_DENSITY / density)
 
 
 @dataclasses.dataclass
@@ -198,8 +213,8 @@ def _wall_surfels(rng, m, lo, hi, faces=_FACES, holes=None):
     return np.concatenate(pos), np.concatenate(quat), np.concatenate(face)
 
 
-def _common_attributes(rng, n):
-    scale = np.exp(rng.uniform(math.log(0.005), math.log(0.05), (n, 2)))
+def _common_attributes(rng, n, scale_f=1.0):
+    scale = np.exp(rng.uniform(math.log(0.005), math.log(0.05), (n, 2))) * scale_f
     opacity = rng.uniform(0.5, 1.0, n)
     albedo = rng.uniform(0.1, 0.8, (n, 3))
     radiance = rng.uniform(0.0, 0.5, (n, 3))   # radiance cache of non-emitters
@@ -238,7 +253,8 @@ def box_room(n: int, lo, hi, seed: int, emitter_mode: str, emitter_frac: float,
     iquat = _uniform_quats(rng, n_int)
     pos = np.concatenate([wpos, ipos])
     quat = np.concatenate([wquat, iquat])
-    scale, opacity, albedo, radiance, emissive = _common_attributes(rng, n)
+    area = sum(_face_area(lo, hi, ax) for ax, _s in _FACES)
+    scale, opacity, albedo, radiance, emissive = _common_attributes(rng, n, scale_factor(n_wall, area))
     n_emit = int(round(n * emitter_frac))
     if emitter_mode == "uniform":
         idx = rng.choice(n, n_emit, replace=False)
@@ -339,7 +355,7 @@ def three_room_layout(n: int, seed: int, emitter_frac: float = 0.005) -> SurfelS
         iquat.append(_uniform_quats(rng, k))
     all_pos = np.concatenate([wpos] + ipos)
     all_quat = np.concatenate([wquat] + iquat)
-    scale, opacity, albedo, radiance, emissive = _common_attributes(rng, n)
+    scale, opacity, albedo, radiance, emissive = _common_attributes(rng, n, scale_factor(n_wall, total_area))
     n_emit = int(round(n * emitter_frac))
     idx = []
     for ri, (lo, hi) in enumerate(rooms):

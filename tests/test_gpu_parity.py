@@ -202,3 +202,26 @@ def test_medium_room_full_size_sampled_pixels(eg):
     assert np.array_equal(lit_ref[clean], lit_gpu[clean])
     assert (lit_ref & clean).sum() >= 5, (lit_ref & clean).sum()
     assert ok.mean() >= 0.99, st
+
+
+@pytest.mark.slow
+def test_large_layout_sampled_pixels(eg):
+    """Three-room layout at full size (6M surfels, 1920x1080, 5 bounces,
+    roulette from bounce 2) at 4 spp: the Philox keys make these the first
+    4 samples of the full-spp render.  The oracle computes 96 random pixels
+    (seed 7) one by one; the GPU image must carry light (the layout is not
+    an opaque fog) and agree with the oracle on which unflagged samples are
+    lit."""
+    wl = S.workload("large")
+    rng = np.random.default_rng(7)
+    npix = wl.camera.width * wl.camera.height
+    pix = rng.choice(npix, 96, replace=False)
+    ok, st, out, ref = _parity(eg, wl.scene_fn(), wl.camera, "pt", 4, wl.max_bounces, wl.rr_start, 0, pixels=pix)
+    print(st)
+    g_all = out["samples"].cpu().numpy().reshape(npix, 4, 3)
+    assert (np.abs(g_all).max(-1) > 0).mean() > 1e-3
+    clean = ref["sample_flags"] == 0
+    lit_ref = np.abs(ref["samples"]).max(-1) > 0
+    lit_gpu = np.abs(g_all[pix]).max(-1) > 0
+    assert np.array_equal(lit_ref[clean], lit_gpu[clean])
+    assert ok.all(), st
