@@ -450,7 +450,7 @@ def run_fit(args):
     prim, sec = int(st[0]), int(st[1])
     p_blend, p_nodes, p_tests = int(st[8]), int(st[9]), int(st[10])
     s_blend, s_nodes, s_tests = int(st[3]), int(st[4]), int(st[5])
-    fit.run(max(3, args.warmup))
+    warm_losses = fit.run(max(3, args.warmup)).cpu().tolist()
     torch.cuda.synchronize(dev)
     clocks = ClockSampler(0)
     clocks.start()
@@ -501,6 +501,7 @@ def run_fit(args):
                        "surfels": host.n, "views": len(cams), "pixels_per_step": npix, "spp": spp,
                        "segments_per_step": segs, "segments_per_s": segs * value,
                        "loss_first_last": [losses[0], losses[-1]],
+                       "loss_at_start": warm_losses[0],
                        "l2": "steps in one native loop; scene and BVH (~0.5 GB) exceed the L2"},
             "roofline": {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak if achieved else None, "traffic": None,
