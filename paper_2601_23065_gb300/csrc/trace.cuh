@@ -118,6 +118,22 @@ __device__ __forceinline__ void leaf_step(const BvhView& bvh, const Consts& C, f
   }
 }
 
+// L2 prefetch of the children a node step pushes (EAGPT_PREFETCH): when the
+// frame's working set exceeds the L2, a popped child's node or surfel record
+// otherwise comes from DRAM on the traversal's dependent chain.
+#ifndef EAGPT_PREFETCH
+#define EAGPT_PREFETCH 0
+#endif
+__device__ __forceinline__ void prefetch_child(const BvhView& bvh, uint32_t c) {
+  const void* p = (c & kLeafBit) ? (const void*)(bvh.trace + (c & kLeafStartMask))
+#if EAGPT_QNODE4
+                                 : (const void*)(bvh.nodes4q + c);
+#else
+                                 : (const void*)(bvh.nodes + c);
+#endif
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
 // One BVH4 node: slab-test the four child boxes against [t_last, tmax],
 // push the hit children but the nearest (farthest first) and return the
 // nearest, or kEmptyChild when none is hit.  Returns false on stack overflow.
@@ -226,6 +242,11 @@ __device__ __forceinline__ bool node_step(const BvhView& bvh, uint32_t node, flo
     if (e[2] != inf) stack[(sp++) * stride] = c[2];
     if (e[1] != inf) stack[(sp++) * stride] = c[1];
     next = c[0];
+    if (EAGPT_PREFETCH) {
+      if (e[1] != inf) prefetch_child(bvh, c[1]);
+      if (e[2] != inf) prefetch_child(bvh, c[2]);
+      if (e[3] != inf) prefetch_child(bvh, c[3]);
+    }
   }
   return true;
 }
