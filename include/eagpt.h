@@ -278,13 +278,17 @@ eagpt_status eagpt_insert_surfels(eagpt_scene_mut* scene, int64_t capacity, cons
  * Serving: a persistent request loop over one resident scene (the paper's
  * edit-then-path-trace use, Sec. 3.4, served to many clients).
  *
- * A host thread runs waves: each wave takes the next slice of samples of
- * every admitted render, puts all their paths into one shared wavefront
- * queue (rays carry a request id) and runs the path-tracing kernels once over
- * it (continuous batching).  Submitted renders are admitted before the next
- * wave, in submission order, when one of max_active request slots and enough
- * arena memory (primary records, sums and one slice of per-sample values of
- * the request) are free.  A request's image equals, bit for bit, what
+ * A host thread runs waves: each wave takes the next samples of the admitted
+ * renders, puts all their paths into one shared wavefront queue of
+ * queue_paths paths (rays carry a request id) and runs the path-tracing
+ * kernels once over it (continuous batching).  The queue is filled shortest
+ * remaining work first (pixels x samples left x bounces): one sample per
+ * request while it fits, the longest-admitted request always included, then
+ * the rest of the queue in the same order, so small requests do not wait on
+ * large ones and no request starves.  Submitted renders are admitted before
+ * the next wave, in submission order, when one of max_active request slots
+ * and arena memory for the request's primary records and sums (64 bytes per
+ * pixel) are free.  A request's image equals, bit for bit, what
  * eagpt_render_path_traced() renders with the same arguments: it does not
  * depend on the other requests in the mix.
  * Edits apply in submission order: renders submitted earlier finish on the

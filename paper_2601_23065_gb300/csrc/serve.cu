@@ -265,7 +265,7 @@ struct Req {
   int version = 0;
   uint64_t scene_version = 0;
   int64_t npix = 0;
-  int s_next = 0, batch_cap = 1;
+  int s_next = 0;
   size_t off = 0, bytes = 0;
   int32_t rebuilt = 0;
 };
@@ -282,6 +282,7 @@ struct Server {
   char* base = nullptr;
   cudaStream_t stream = nullptr;
   Ray* q[2] = {nullptr, nullptr};
+  float4* slots = nullptr;  // per-sample values of one wave, queue_cap of them
   uint32_t* counters = nullptr;
   ReqDev* table = nullptr;
   int64_t queue_cap = 0;
@@ -308,23 +309,12 @@ static size_t scene_bytes(int64_t n) { return align256((size_t)(n > 0 ? n : 1) *
 
 bool Server::admit_locked(Req& r) {
   const int64_t npix = (int64_t)r.rr.cam.width * r.rr.cam.height;
-  // paths per wave of this request: its share of the queue, at least one
-  // sample per pixel
-  int64_t share = queue_cap / std::max<int64_t>(1, cfg.max_active);
-  int64_t cap = std::max<int64_t>(1, share / std::max<int64_t>(1, npix));
-  cap = std::min<int64_t>(cap, r.rr.spp);
-  int64_t in_use = 0;
-  for (uint64_t id : active) in_use += reqs[id].npix * reqs[id].batch_cap;
-  if (in_use + npix * cap > queue_cap) {
-    cap = std::min<int64_t>(cap, (queue_cap - in_use) / std::max<int64_t>(1, npix));
-    if (cap < 1) return false;
-  }
-  const size_t bytes = align256((size_t)npix * sizeof(PrimRec)) + align256((size_t)npix * sizeof(float4)) +
-                       align256((size_t)npix * cap * sizeof(float4));
+  // the request's own memory: primary records and running sums; its
+  // per-sample values of a wave live in the shared wave buffer
+  const size_t bytes = align256((size_t)npix * sizeof(PrimRec)) + align256((size_t)npix * sizeof(float4));
   size_t off = 0;
   if (!arena.alloc(bytes, &off)) return false;
   r.npix = npix;
-  r.batch_cap = (int)cap;
   r.off = off;
   r.bytes = bytes;
   r.version = current;
@@ -402,13 +392,61 @@ bool Server::apply_edit_locked(Req& r, std::unique_lock<std::mutex>& lk) {
   return true;
 }
 
+// Samples of each active render in the next wave.  The queue is filled
+// shortest remaining work first (pixels x samples left x bounces), which keeps
+// small requests from waiting on large ones; one sample per request first,
+// in that order while it fits, with the longest-admitted request always
+// first, so that every request progresses and none starves; then the rest
+// of the queue in the same order.  The batches only change which wave a
+// sample is traced in: every image still sums its samples in sample order.
+static std::vector<int> plan_wave(const std::vector<const Req*>& act, int64_t queue_cap) {
+  const size_t n = act.size();
+  std::vector<size_t> order(n);
+  for (size_t k = 0; k < n; ++k) order[k] = k;
+  auto work = [&](size_t k) {
+    const Req& r = *act[k];
+    return (double)r.npix * (double)(r.rr.spp - r.s_next) * (double)std::max(1, r.rr.max_bounces);
+  };
+  std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) { return work(a) < work(b); });
+  size_t oldest = 0;
+  for (size_t k = 1; k < n; ++k)
+    if (act[k]->t_admit < act[oldest]->t_admit) oldest = k;
+  if (n) {
+    order.erase(std::find(order.begin(), order.end(), oldest));
+    order.insert(order.begin(), oldest);
+  }
+  std::vector<int> batch(n, 0);
+  int64_t left = queue_cap;
+  for (size_t k : order) {
+    const Req& r = *act[k];
+    if (r.s_next < r.rr.spp && r.npix <= left) {
+      batch[k] = 1;
+      left -= r.npix;
+    }
+  }
+  for (size_t k : order) {
+    const Req& r = *act[k];
+    if (!batch[k]) continue;
+    const int64_t more = std::min<int64_t>(r.rr.spp - r.s_next - batch[k], left / std::max<int64_t>(1, r.npix));
+    batch[k] += (int)more;
+    left -= more * r.npix;
+  }
+  return batch;
+}
+
 void Server::wave(std::unique_lock<std::mutex>& lk) {
   std::vector<ReqDev> tab;
+  std::vector<uint64_t> in_wave;
   tab.reserve(active.size());
   int64_t paths = 0, pixels = 0;
   int maxB = 0;
-  for (uint64_t id : active) {
-    Req& r = reqs[id];
+  std::vector<const Req*> act;
+  for (uint64_t id : active) act.push_back(&reqs[id]);
+  const std::vector<int> plan = plan_wave(act, queue_cap);
+  for (size_t k = 0; k < active.size(); ++k) {
+    if (plan[k] == 0) continue;
+    Req& r = reqs[active[k]];
+    in_wave.push_back(r.id);
     ReqDev d{};
     d.cam = r.rr.cam;
     d.seed = r.rr.seed;
@@ -417,13 +455,13 @@ void Server::wave(std::unique_lock<std::mutex>& lk) {
     d.pix_off = pixels;
     d.prim = (PrimRec*)(base + r.off);
     d.acc = (float4*)(base + r.off + align256((size_t)r.npix * sizeof(PrimRec)));
-    d.slots = (float4*)((char*)d.acc + align256((size_t)r.npix * sizeof(float4)));
+    d.slots = slots + paths;
     d.out_rgb = r.rr.out_rgb;
     d.spp = r.rr.spp;
     d.max_bounces = r.rr.max_bounces;
     d.rr_start = r.rr.rr_start_bounce;
     d.s0 = r.s_next;
-    d.batch = std::min(r.batch_cap, r.rr.spp - r.s_next);
+    d.batch = plan[k];
     d.version = r.version;
     d.first = r.s_next == 0;
     d.last = r.s_next + d.batch >= r.rr.spp;
@@ -473,10 +511,10 @@ void Server::wave(std::unique_lock<std::mutex>& lk) {
   stats.segments += segs;
   stats.paths += paths;
   const double t = now_s();
+  for (size_t k = 0; k < in_wave.size(); ++k) reqs[in_wave[k]].s_next += tab[k].batch;
   std::vector<uint64_t> ids = active;
-  for (size_t k = 0; k < ids.size(); ++k) {
-    Req& r = reqs[ids[k]];
-    r.s_next += tab[k].batch;
+  for (uint64_t id : ids) {
+    Req& r = reqs[id];
     if (r.state == EAGPT_REQ_RUNNING && r.s_next >= r.rr.spp) finish_locked(r, EAGPT_REQ_DONE);
     else if (r.state == EAGPT_REQ_RUNNING && r.deadline > 0 && t > r.deadline) finish_locked(r, EAGPT_REQ_TIMED_OUT);
   }
@@ -545,11 +583,12 @@ extern "C" {
 
 size_t eagpt_server_arena_bytes(int64_t n, int64_t queue_paths) {
   if (n < 0 || queue_paths <= 0) return 0;
-  // second scene version + its BVH, two ray queues, counters, request table,
-  // and as much again as the queues for per-request buffers
+  // second scene version + its BVH, two ray queues, the wave's per-sample
+  // values, counters, request table, and primary records and sums for as
+  // many pixels as the queue holds paths
   return scene_bytes(n) + align256(bvh_layout(n).total) + 2 * align256((size_t)queue_paths * sizeof(Ray)) +
-         align256(kSrvCounterWords * 4) + align256(kSrvMaxActive * sizeof(ReqDev)) +
-         (size_t)queue_paths * (sizeof(float4) * 2 + sizeof(PrimRec));
+         align256((size_t)queue_paths * sizeof(float4)) + align256(kSrvCounterWords * 4) +
+         align256(kSrvMaxActive * sizeof(ReqDev)) + (size_t)queue_paths * (sizeof(float4) + sizeof(PrimRec));
 }
 
 eagpt_status eagpt_server_create(const eagpt_scene_mut* scene, const eagpt_bvh* bvh, const eagpt_params* params,
@@ -566,7 +605,8 @@ eagpt_status eagpt_server_create(const eagpt_scene_mut* scene, const eagpt_bvh* 
     return set_error(EAGPT_ERR_STALE_BVH, "bvh does not match the scene");
   const int64_t n = scene->n;
   const size_t fixed = scene_bytes(n) + align256(bvh_layout(n).total) +
-                       2 * align256((size_t)cfg->queue_paths * sizeof(Ray)) + align256(kSrvCounterWords * 4) +
+                       2 * align256((size_t)cfg->queue_paths * sizeof(Ray)) +
+                       align256((size_t)cfg->queue_paths * sizeof(float4)) + align256(kSrvCounterWords * 4) +
                        align256(kSrvMaxActive * sizeof(ReqDev));
   if (cfg->arena_bytes < fixed + 4096)
     return set_error(EAGPT_ERR_OUT_OF_MEMORY, "arena too small for the second scene version and the queues");
@@ -599,6 +639,7 @@ eagpt_status eagpt_server_create(const eagpt_scene_mut* scene, const eagpt_bvh* 
   S.bvh[1].storage = S.base + take(S.bvh[1].bytes);
   S.q[0] = (Ray*)(S.base + take((size_t)cfg->queue_paths * sizeof(Ray)));
   S.q[1] = (Ray*)(S.base + take((size_t)cfg->queue_paths * sizeof(Ray)));
+  S.slots = (float4*)(S.base + take((size_t)cfg->queue_paths * sizeof(float4)));
   S.counters = (uint32_t*)(S.base + take(kSrvCounterWords * 4));
   S.table = (ReqDev*)(S.base + take(kSrvMaxActive * sizeof(ReqDev)));
   S.queue_cap = cfg->queue_paths;
