@@ -284,8 +284,8 @@ eagpt_status eagpt_insert_surfels(eagpt_scene_mut* scene, int64_t capacity, cons
  * kernels once over it (continuous batching).  The queue is filled shortest
  * remaining work first (pixels x samples left x bounces): one sample per
  * request while it fits, the longest-admitted request always included, then
- * the rest of the queue in the same order, so small requests do not wait on
- * large ones and no request starves.  Submitted renders are admitted before
+ * the rest of the queue in shortest-remaining-work order, so small requests
+ * do not wait on large ones and no request starves.  Submitted renders are admitted before
  * the next wave, in submission order, when one of max_active request slots
  * and arena memory for the request's primary records and sums (64 bytes per
  * pixel) are free.  A request's image equals, bit for bit, what

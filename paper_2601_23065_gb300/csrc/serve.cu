@@ -394,11 +394,12 @@ bool Server::apply_edit_locked(Req& r, std::unique_lock<std::mutex>& lk) {
 
 // Samples of each active render in the next wave.  The queue is filled
 // shortest remaining work first (pixels x samples left x bounces), which keeps
-// small requests from waiting on large ones; one sample per request first,
-// in that order while it fits, with the longest-admitted request always
-// first, so that every request progresses and none starves; then the rest
-// of the queue in the same order.  The batches only change which wave a
-// sample is traced in: every image still sums its samples in sample order.
+// small requests from waiting on large ones: one sample per request first,
+// in that order while it fits but with the longest-admitted request ahead of
+// all, so that it always progresses and no request starves; then the rest of
+// the queue in shortest-remaining-work order.  The batches only change which
+// wave a sample is traced in: every image still sums its samples in sample
+// order.
 static std::vector<int> plan_wave(const std::vector<const Req*>& act, int64_t queue_cap) {
   const size_t n = act.size();
   std::vector<size_t> order(n);
@@ -408,16 +409,17 @@ static std::vector<int> plan_wave(const std::vector<const Req*>& act, int64_t qu
     return (double)r.npix * (double)(r.rr.spp - r.s_next) * (double)std::max(1, r.rr.max_bounces);
   };
   std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) { return work(a) < work(b); });
+  std::vector<size_t> first = order;
   size_t oldest = 0;
   for (size_t k = 1; k < n; ++k)
     if (act[k]->t_admit < act[oldest]->t_admit) oldest = k;
   if (n) {
-    order.erase(std::find(order.begin(), order.end(), oldest));
-    order.insert(order.begin(), oldest);
+    first.erase(std::find(first.begin(), first.end(), oldest));
+    first.insert(first.begin(), oldest);
   }
   std::vector<int> batch(n, 0);
   int64_t left = queue_cap;
-  for (size_t k : order) {
+  for (size_t k : first) {
     const Req& r = *act[k];
     if (r.s_next < r.rr.spp && r.npix <= left) {
       batch[k] = 1;
