@@ -554,6 +554,7 @@ def run_diff(args):
     # the same rays as a path-traced render with one bounce and no roulette
     st = r.path_traced(ds, api.BVH(ds), cam, spp, 1, rr_start=1 << 20, seed=3, want_stats=True)["stats"].cpu().numpy()
     prim, sec = int(st[0]), int(st[1])
+    s_blend, s_nodes, s_tests = int(st[3]), int(st[4]), int(st[5])
     hit_prim = int(st[2] // max(1, spp))
     fwd_segs = prim + sec
     bwd_segs = prim + 2 * sec + 2 * hit_prim
@@ -585,6 +586,13 @@ def run_diff(args):
     total_kernel_ms = sum(v[1] for v in prof.values())
     kname = max(prof.items(), key=lambda kv: kv[1][1])[0]
     peak, peak_kind = load_peaks()
+    achieved = None
+    if kname == "k_bwd_secondary":
+        # per secondary segment: the primary record it is rebuilt from (48 B),
+        # two traversals (values, then the adjoint) and 16 gradient atomics
+        # (64 B) per blended hit
+        step_bytes = 48 * sec + 2 * (NODE_BYTES * s_nodes + 64 * s_tests + 32 * s_blend) + 64 * s_blend
+        achieved = step_bytes / (prof[kname][1] / args.steps * 1e-3) / 1e9
     line = {"metric": METRIC + " (single-bounce forward + adjoint)", "value": value, "unit": METRIC, "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -592,8 +600,8 @@ def run_diff(args):
                        "forward_segments": fwd_segs, "adjoint_segments": bwd_segs,
                        "step": "LBVH build + single-bounce forward + adjoint (all parameters)",
                        "l2": "flushed between steps (512 MB write)"},
-            "roofline": {"bound": "hbm", "kernel": kname, "achieved": None, "peak": peak, "unit": "GB/s",
-                         "frac": None, "traffic": None,
+            "roofline": {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak if achieved else None, "traffic": None,
                          "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
                          "share_of_kernel_time": prof[kname][1] / total_kernel_ms if total_kernel_ms else None},
             "cpu_baseline": None, "gpu_launches": int(launches), "clocks": clk,
