@@ -405,6 +405,42 @@ eagpt_status eagpt_render_path_traced_noalloc(const eagpt_scene* scene, const ea
  * FP32 atomics: the summation order of the gradients is not deterministic. */
 size_t eagpt_render_backward_workspace_bytes(const eagpt_camera* cam, int32_t spp);
 size_t eagpt_render_backward_workspace_min_bytes(const eagpt_camera* cam, int32_t spp);
+
+/* Forward-to-adjoint sample cache (Eq. 6 and its adjoint).  The adjoint of
+ * the single-bounce render needs, for every sample, the blended radiance R
+ * and transmittance T of its secondary segment (the suffix sums of the
+ * front-to-back adjoint of Eq. 2 are R - R_<=i); without a cache it re-traces
+ * each secondary segment once for them before the adjoint pass.  The cached
+ * forward stores them, and the cached adjoint reads them instead of tracing:
+ * one traversal per secondary segment fewer, for 16 bytes per sample of
+ * device memory.
+ *   sample_cache device, eagpt_single_bounce_cache_bytes() bytes, 16-byte
+ *                aligned: float4 (R, T) per (sample, pixel), sample-major
+ *                (index sample * W * H + pixel); entries of pixels whose
+ *                primary segment misses or is emissive are not written.
+ * eagpt_render_single_bounce_cached() renders exactly the image
+ * eagpt_render_single_bounce() renders (same kernels and arithmetic; no aux
+ * or sample output) and fills the cache.  Its R and T are the bits the
+ * adjoint's own trace would produce, so
+ * eagpt_render_single_bounce_backward_cached(), given the cache of a
+ * forward with the same scene, BVH, camera, params, spp and seed, adds the
+ * same gradients as eagpt_render_single_bounce_backward() (up to the
+ * nondeterministic order of the FP32 atomics).  A cache from other
+ * arguments, or a scene edited in between, gives wrong gradients; nothing
+ * checks it.  Workspaces as for the uncached calls.  The forward returns
+ * EAGPT_ERR_NOT_SUPPORTED when the library was built without the per-lane
+ * refill bounce kernel. */
+size_t eagpt_single_bounce_cache_bytes(const eagpt_camera* cam, int32_t spp);
+eagpt_status eagpt_render_single_bounce_cached(const eagpt_scene* scene, const eagpt_bvh* bvh,
+                                               const eagpt_camera* cam, const eagpt_params* params, int32_t spp,
+                                               uint64_t seed, float* out_rgb, float* sample_cache, void* workspace,
+                                               size_t workspace_bytes, eagpt_stream_t stream);
+eagpt_status eagpt_render_single_bounce_backward_cached(const eagpt_scene* scene, const eagpt_bvh* bvh,
+                                                        const eagpt_camera* cam, const eagpt_params* params,
+                                                        int32_t spp, uint64_t seed, const float* dL_drgb,
+                                                        const float* sample_cache, const eagpt_scene_grad* grads,
+                                                        void* workspace, size_t workspace_bytes,
+                                                        eagpt_stream_t stream);
 eagpt_status eagpt_render_single_bounce_backward(const eagpt_scene* scene, const eagpt_bvh* bvh,
                                                  const eagpt_camera* cam, const eagpt_params* params,
                                                  int32_t spp, uint64_t seed, const float* dL_drgb,

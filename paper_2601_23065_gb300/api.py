@@ -146,13 +146,28 @@ class Renderer:
         return r
 
     def single_bounce(self, scene: DeviceScene, bvh: BVH, cam: HostCamera, spp: int, seed: int = 0,
-                      prm: Optional[capi.Params] = None, want_aux=False, want_samples=False, stream=None):
-        """Eq. 6 render; returns dict(rgb[, aux][, samples])."""
+                      prm: Optional[capi.Params] = None, want_aux=False, want_samples=False, want_cache=False,
+                      stream=None):
+        """Eq. 6 render; returns dict(rgb[, aux][, samples][, cache]).  With
+        ``want_cache`` the render also keeps each sample's secondary R and T
+        (16 bytes per sample) for single_bounce_backward(cache=...), which
+        then skips one traversal per secondary segment."""
         c = camera(cam)
         prm = prm or bvh.params
         ws = self._workspace(c, spp, 0)
         H, W = cam.height, cam.width
         rgb = torch.empty((H, W, 3), dtype=torch.float32, device=self.device)
+        if want_cache:
+            if want_aux or want_samples:
+                raise ValueError("the cached render writes no aux or sample output")
+            L = capi.lib()
+            cache = torch.empty(L.eagpt_single_bounce_cache_bytes(ctypes.byref(c), spp) // 4, dtype=torch.float32,
+                                device=self.device)
+            sc = scene.c()
+            capi.check(L.eagpt_render_single_bounce_cached(
+                ctypes.byref(sc), ctypes.byref(bvh.c()), ctypes.byref(c), ctypes.byref(prm), int(spp),
+                ctypes.c_uint64(int(seed)), _ptr(rgb), _ptr(cache), _ptr(ws), ws.numel(), _stream(stream)))
+            return {"rgb": rgb, "cache": cache}
         aux = torch.empty((H, W, 12), dtype=torch.float32, device=self.device) if want_aux else None
         smp = torch.empty((H, W, spp, 3), dtype=torch.float32, device=self.device) if want_samples else None
         sc = scene.c()
@@ -194,9 +209,11 @@ def sync_status(stream=None) -> None:
 
 def single_bounce_backward(scene: DeviceScene, bvh: BVH, cam: HostCamera, spp: int, seed: int, dL_drgb: torch.Tensor,
                            grads: Optional[dict] = None, prm: Optional[capi.Params] = None, stream=None,
-                           workspace: Optional[torch.Tensor] = None) -> dict:
+                           workspace: Optional[torch.Tensor] = None, cache: Optional[torch.Tensor] = None) -> dict:
     """Adjoint of the single-bounce render: accumulates dL/dtheta for
-    L = sum(dL_drgb * image) into ``grads`` (created zeroed if None)."""
+    L = sum(dL_drgb * image) into ``grads`` (created zeroed if None).
+    ``cache``: the per-sample cache of a single_bounce(want_cache=True) render
+    with the same scene, BVH, camera, spp, seed and params."""
     dev = scene.t["pos"].device
     if grads is None:
         grads = {k: torch.zeros_like(scene.t[k]) for k in GRAD_FIELDS}
@@ -212,6 +229,12 @@ def single_bounce_backward(scene: DeviceScene, bvh: BVH, cam: HostCamera, spp: i
         need, dtype=torch.uint8, device=dev)
     dL = dL_drgb.contiguous().to(torch.float32)
     sc = scene.c()
+    if cache is not None:
+        capi.check(L.eagpt_render_single_bounce_backward_cached(
+            ctypes.byref(sc), ctypes.byref(bvh.c()), ctypes.byref(c), ctypes.byref(prm), int(spp),
+            ctypes.c_uint64(int(seed)), _ptr(dL), _ptr(cache), ctypes.byref(g), _ptr(ws), ws.numel(),
+            _stream(stream)))
+        return grads
     capi.check(L.eagpt_render_single_bounce_backward(ctypes.byref(sc), ctypes.byref(bvh.c()), ctypes.byref(c),
                                                      ctypes.byref(prm), int(spp), ctypes.c_uint64(int(seed)),
                                                      _ptr(dL), ctypes.byref(g), _ptr(ws), ws.numel(),
@@ -230,14 +253,14 @@ class _SingleBounceFn(torch.autograd.Function):
                           "albedo": albedo.detach().contiguous(), "radiance": radiance.detach().contiguous(),
                           "emissive": emissive.detach().contiguous()})
         bvh = BVH(ds, prm)
-        out = renderer.single_bounce(ds, bvh, cam, spp, seed=seed, prm=prm)
-        ctx.state = (ds, bvh, cam, spp, seed, prm)
+        out = renderer.single_bounce(ds, bvh, cam, spp, seed=seed, prm=prm, want_cache=True)
+        ctx.state = (ds, bvh, cam, spp, seed, prm, out["cache"])
         return out["rgb"]
 
     @staticmethod
     def backward(ctx, grad_rgb):
-        ds, bvh, cam, spp, seed, prm = ctx.state
-        g = single_bounce_backward(ds, bvh, cam, spp, seed, grad_rgb, prm=prm)
+        ds, bvh, cam, spp, seed, prm, cache = ctx.state
+        g = single_bounce_backward(ds, bvh, cam, spp, seed, grad_rgb, prm=prm, cache=cache)
         return (g["pos"], g["quat"], g["scale"], g["opacity"], g["albedo"], g["radiance"], None, None, None, None,
                 None, None)
 

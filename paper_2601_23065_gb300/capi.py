@@ -136,6 +136,11 @@ SIGNATURES = {
     "eagpt_render_backward_workspace_min_bytes": (c_sz, [P(Camera), c_i32]),
     "eagpt_render_single_bounce_backward": (c_i32, [P(Scene), P(Bvh), P(Camera), P(Params), c_i32, c_u64, c_vp,
                                                     P(SceneGrad), c_vp, c_sz, c_vp]),
+    "eagpt_single_bounce_cache_bytes": (c_sz, [P(Camera), c_i32]),
+    "eagpt_render_single_bounce_cached": (c_i32, [P(Scene), P(Bvh), P(Camera), P(Params), c_i32, c_u64, c_vp, c_vp,
+                                                  c_vp, c_sz, c_vp]),
+    "eagpt_render_single_bounce_backward_cached": (c_i32, [P(Scene), P(Bvh), P(Camera), P(Params), c_i32, c_u64,
+                                                           c_vp, c_vp, P(SceneGrad), c_vp, c_sz, c_vp]),
     "eagpt_render_radiance": (c_i32, [P(Scene), P(Bvh), P(Camera), P(Params), c_vp, c_vp, c_vp]),
     "eagpt_render_radiance_backward": (c_i32, [P(Scene), P(Bvh), P(Camera), P(Params), c_vp, P(SceneGrad), c_vp]),
     "eagpt_render_single_bounce_incident": (c_i32, [P(Scene), P(Bvh), P(Camera), P(Params), c_i32, c_u64, c_vp,

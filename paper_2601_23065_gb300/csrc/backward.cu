@@ -215,10 +215,16 @@ __device__ __forceinline__ float3 cosine_direction_adjoint(float3 n, float u0, f
   return l0 * g1 + l1 * g2 + l2 * dw;
 }
 
+// kCached: the forward stored each sample's secondary R and T (sample-major,
+// written by the single-bounce render from the same bit-identical blend), so
+// the values pass is read instead of traced; T < 1 exactly when the segment
+// blended a hit (alpha >= alpha_min > 0).
+template <bool kCached>
 __global__ void __launch_bounds__(kBlock, kBwdMinBlocks) k_bwd_secondary(BvhView bvh, Consts C, eagpt_camera cam, eagpt_scene sc,
                                                           eagpt_scene_grad gr, const PrimRecB* __restrict__ prim,
                                                           const float* __restrict__ dL, int spp, uint64_t seed,
-                                                          int64_t npix, int s0, int batch, float4* per_sample) {
+                                                          int64_t npix, int s0, int batch, float4* per_sample,
+                                                          const float4* __restrict__ sb_cache) {
   __shared__ uint32_t s_stack[kStackSize * kBlock];
   const int64_t t = blockIdx.x * (int64_t)kBlock + threadIdx.x;
   if (t >= npix * (int64_t)batch) return;
@@ -238,7 +244,14 @@ __global__ void __launch_bounds__(kBlock, kBwdMinBlocks) k_bwd_secondary(BvhView
     TraceCounters cnt{0, 0, 0, 0, 0};
     // the secondary segment enters the pixel only through its R (Eq. 6)
     RBlendVisitor v1(bvh.shade, C, 0);
-    trace_segment<kKb, false>(bvh, C, O2, w2, 0.f, s_stack + threadIdx.x, kBlock, v1, cnt);
+    if (kCached) {
+      const float4 c = sb_cache[(int64_t)sample * npix + pixel];
+      v1.R = make_float3(c.x, c.y, c.z);
+      v1.T = c.w;
+      v1.n_hits = c.w < 1.f ? 1u : 0u;
+    } else {
+      trace_segment<kKb, false>(bvh, C, O2, w2, 0.f, s_stack + threadIdx.x, kBlock, v1, cnt);
+    }
     const float invS = 1.f / (float)spp;
     const float3 g = make_float3(dL[3 * pixel], dL[3 * pixel + 1], dL[3 * pixel + 2]);
     const float3 P1 = make_float3(p.c.x, p.c.y, p.c.z);
@@ -383,7 +396,7 @@ static inline unsigned nb(int64_t n) { return (unsigned)((n + kBlock - 1) / kBlo
 
 cudaError_t launch_backward(const BvhView& bvh, const Consts& C, const eagpt_camera& cam, const eagpt_scene& sc,
                             const eagpt_scene_grad& gr, int spp, uint64_t seed, const float* dL, void* ws,
-                            size_t ws_bytes, cudaStream_t st) {
+                            size_t ws_bytes, cudaStream_t st, const float4* sb_cache) {
   const int64_t npix = (int64_t)cam.width * cam.height;
   const int batch = backward_choose_batch(npix, spp, ws_bytes);
   const BwdLayout L = bwd_layout(npix, batch);
@@ -395,9 +408,14 @@ cudaError_t launch_backward(const BvhView& bvh, const Consts& C, const eagpt_cam
   if (e != cudaSuccess) return e;
   for (int s0 = 0; s0 < spp; s0 += batch) {
     const int n = spp - s0 < batch ? spp - s0 : batch;
-    EAGPT_LAUNCH(st, "k_bwd_secondary",
-                 k_bwd_secondary<<<nb(npix * n), kBlock, 0, st>>>(bvh, C, cam, sc, gr, prim, dL, spp, seed, npix, s0,
-                                                                  n, per));
+    if (sb_cache)
+      EAGPT_LAUNCH(st, "k_bwd_secondary",
+                   k_bwd_secondary<true><<<nb(npix * n), kBlock, 0, st>>>(bvh, C, cam, sc, gr, prim, dL, spp, seed, npix,
+                                                                          s0, n, per, sb_cache));
+    else
+      EAGPT_LAUNCH(st, "k_bwd_secondary",
+                   k_bwd_secondary<false><<<nb(npix * n), kBlock, 0, st>>>(bvh, C, cam, sc, gr, prim, dL, spp, seed,
+                                                                           npix, s0, n, per, nullptr));
     EAGPT_LAUNCH(st, "k_bwd_reduce", k_bwd_reduce<<<nb(npix), kBlock, 0, st>>>(npix, n, s0 == 0, per, acc));
   }
   EAGPT_LAUNCH(st, "k_bwd_primary",

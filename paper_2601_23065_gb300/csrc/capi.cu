@@ -194,7 +194,7 @@ static eagpt_status render_common(const eagpt_scene* scene, const eagpt_bvh* bvh
                                   const eagpt_params* params, int kind, int32_t spp, int32_t max_bounces,
                                   int32_t rr_start, uint64_t seed, float* out_rgb, float* out_aux, float* out_samples,
                                   int64_t* out_stats, void* ws, size_t ws_bytes, eagpt_stream_t stream,
-                                  float* out_li = nullptr) {
+                                  float* out_li = nullptr, float4* sb_cache = nullptr) {
   eagpt_status s;
   if ((s = check_scene(scene)) != EAGPT_OK) return s;
   if ((s = check_params(params)) != EAGPT_OK) return s;
@@ -226,6 +226,7 @@ static eagpt_status render_common(const eagpt_scene* scene, const eagpt_bvh* bvh
   a.out_stats = out_stats;
   a.ws = ws;
   a.ws_bytes = ws_bytes;
+  a.sb_cache = sb_cache;
   cudaError_t e = launch_render(a, (cudaStream_t)stream, nullptr);
   if (e != cudaSuccess) return cuda_fail(e, "render launch");
   return EAGPT_OK;
@@ -285,10 +286,10 @@ size_t eagpt_render_backward_workspace_min_bytes(const eagpt_camera* cam, int32_
   return backward_workspace_bytes((int64_t)cam->width * cam->height, spp, 1);
 }
 
-eagpt_status eagpt_render_single_bounce_backward(const eagpt_scene* scene, const eagpt_bvh* bvh,
-                                                 const eagpt_camera* cam, const eagpt_params* params, int32_t spp,
-                                                 uint64_t seed, const float* dL_drgb, const eagpt_scene_grad* grads,
-                                                 void* ws, size_t ws_bytes, eagpt_stream_t stream) {
+static eagpt_status backward_common(const eagpt_scene* scene, const eagpt_bvh* bvh, const eagpt_camera* cam,
+                                    const eagpt_params* params, int32_t spp, uint64_t seed, const float* dL_drgb,
+                                    const eagpt_scene_grad* grads, void* ws, size_t ws_bytes, eagpt_stream_t stream,
+                                    const float4* sb_cache) {
   eagpt_status s;
   if ((s = check_scene(scene)) != EAGPT_OK) return s;
   if ((s = check_params(params)) != EAGPT_OK) return s;
@@ -307,9 +308,43 @@ eagpt_status eagpt_render_single_bounce_backward(const eagpt_scene* scene, const
                 (long long)backward_workspace_bytes(npix, spp, 1));
   if (scene->n == 0) return EAGPT_OK;
   cudaError_t e = launch_backward(make_view(*bvh), make_consts(*params), *cam, *scene, *grads, spp, seed, dL_drgb, ws,
-                                  ws_bytes, (cudaStream_t)stream);
+                                  ws_bytes, (cudaStream_t)stream, sb_cache);
   if (e != cudaSuccess) return cuda_fail(e, "backward launch");
   return EAGPT_OK;
+}
+
+eagpt_status eagpt_render_single_bounce_backward(const eagpt_scene* scene, const eagpt_bvh* bvh,
+                                                 const eagpt_camera* cam, const eagpt_params* params, int32_t spp,
+                                                 uint64_t seed, const float* dL_drgb, const eagpt_scene_grad* grads,
+                                                 void* ws, size_t ws_bytes, eagpt_stream_t stream) {
+  return backward_common(scene, bvh, cam, params, spp, seed, dL_drgb, grads, ws, ws_bytes, stream, nullptr);
+}
+
+size_t eagpt_single_bounce_cache_bytes(const eagpt_camera* cam, int32_t spp) {
+  if (!cam || cam->width <= 0 || cam->height <= 0 || spp <= 0) return 0;
+  return (size_t)cam->width * cam->height * (size_t)spp * sizeof(float4);
+}
+
+eagpt_status eagpt_render_single_bounce_cached(const eagpt_scene* scene, const eagpt_bvh* bvh,
+                                               const eagpt_camera* cam, const eagpt_params* params, int32_t spp,
+                                               uint64_t seed, float* out_rgb, float* sample_cache, void* ws,
+                                               size_t ws_bytes, eagpt_stream_t stream) {
+  if (!render_has_refill()) return fail(EAGPT_ERR_NOT_SUPPORTED, "the sample cache needs the refill bounce kernel%s");
+  if (!sample_cache || !aligned(sample_cache, 16))
+    return fail(EAGPT_ERR_INVALID_ARGUMENT, "sample_cache must be non-NULL and 16-byte aligned%s");
+  return render_common(scene, bvh, cam, params, 0, spp, 1, 0, seed, out_rgb, nullptr, nullptr, nullptr, ws, ws_bytes,
+                       stream, nullptr, (float4*)sample_cache);
+}
+
+eagpt_status eagpt_render_single_bounce_backward_cached(const eagpt_scene* scene, const eagpt_bvh* bvh,
+                                                        const eagpt_camera* cam, const eagpt_params* params,
+                                                        int32_t spp, uint64_t seed, const float* dL_drgb,
+                                                        const float* sample_cache, const eagpt_scene_grad* grads,
+                                                        void* ws, size_t ws_bytes, eagpt_stream_t stream) {
+  if (!sample_cache || !aligned(sample_cache, 16))
+    return fail(EAGPT_ERR_INVALID_ARGUMENT, "sample_cache must be non-NULL and 16-byte aligned%s");
+  return backward_common(scene, bvh, cam, params, spp, seed, dL_drgb, grads, ws, ws_bytes, stream,
+                         (const float4*)sample_cache);
 }
 
 eagpt_status eagpt_render_radiance(const eagpt_scene* scene, const eagpt_bvh* bvh, const eagpt_camera* cam,

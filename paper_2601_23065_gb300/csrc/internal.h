@@ -37,6 +37,7 @@ struct RenderArgs {
   int64_t* out_stats;
   void* ws;
   size_t ws_bytes;
+  float4* sb_cache;  // single bounce: per-sample secondary (R, T), sample-major, or NULL
 };
 
 struct RenderLayout {
@@ -49,6 +50,7 @@ struct RenderLayout {
 RenderLayout render_layout(int64_t npix, int spp, int batch_spp, bool mis = false);
 int choose_batch_spp(int64_t npix, int spp, size_t ws_bytes, bool mis = false);
 cudaError_t launch_render(const RenderArgs& a, cudaStream_t st, int* launches);
+bool render_has_refill();  // the bounce kernel is the per-lane refill form
 cudaError_t launch_trace_rays(const BvhView& bvh, const Consts& C, int mode, const float* rays, int64_t n_rays,
                               float* out_rec, int32_t* out_hits, int max_hits, int32_t* out_nhits, cudaStream_t st);
 
@@ -66,7 +68,7 @@ size_t backward_workspace_bytes(int64_t npix, int spp, int batch);
 int backward_choose_batch(int64_t npix, int spp, size_t ws_bytes);
 cudaError_t launch_backward(const BvhView& bvh, const Consts& C, const eagpt_camera& cam, const eagpt_scene& sc,
                             const eagpt_scene_grad& gr, int spp, uint64_t seed, const float* dL, void* ws,
-                            size_t ws_bytes, cudaStream_t st);
+                            size_t ws_bytes, cudaStream_t st, const float4* sb_cache = nullptr);
 
 // optim.cu
 int64_t pq_partials(int64_t n);

@@ -293,12 +293,14 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_bounce(BvhView bvh, Cons
 #define EAGPT_REFILL_STEPS 64
 #endif
 constexpr int kRefillSteps = EAGPT_REFILL_STEPS;
+bool render_has_refill() { return EAGPT_REFILL != 0; }
 
-template <bool kCount>
+template <bool kCount, bool kCache = false>
 __global__ void __launch_bounds__(kBlock, kMinBlocks) k_bounce_r(BvhView bvh, Consts C, int kind, int k, int max_bounces,
                                                      int rr_start, uint64_t seed, int64_t npix, int s0,
                                                      const Ray* __restrict__ q_in, Ray* q_out, uint32_t* counters,
-                                                     float4* slots, int64_t* stats, const uint32_t* __restrict__ perm) {
+                                                     float4* slots, int64_t* stats, const uint32_t* __restrict__ perm,
+                                                     float4* sb_cache) {
   __shared__ uint32_t s_stack[kStackSize * kBlock];
   __shared__ float s_blend[11 * kBlock];
   const int lane = threadIdx.x & 31;
@@ -338,12 +340,16 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_bounce_r(BvhView bvh, Co
     Ray nr;
     if (active && round_steps<kK, kCount>(rt, bvh, C, s_stack + threadIdx.x, kBlock, kRefillSteps, cnt)) {
       if (round_blend<kK, kCount>(rt, bvh, C, vis, cnt)) {
-        const SegRec s = finish(vis.get());
+        const Blend bl = vis.get();
+        const SegRec s = finish(bl);
+        const float4 rt_cache = make_float4(bl.R.x, bl.R.y, bl.R.z, bl.T);
         Ray r;
         r.a = make_float4(rt.O.x, rt.O.y, rt.O.z, __ldcv(&q_in[qi].a.w));
         r.b = make_float4(rt.w.x, rt.w.y, rt.w.z, __ldcv(&q_in[qi].b.w));
         r.c = __ldcv(&q_in[qi].c);
         const uint32_t pixel = __float_as_uint(r.a.w), sample = __float_as_uint(r.b.w);
+        // single bounce: the secondary segment's R and T for the adjoint
+        if (kCache) sb_cache[(int64_t)sample * npix + pixel] = rt_cache;
         float3 contrib;
         take = shade_bounce(kind, k, max_bounces, rr_start, seed, C, r, s, contrib, nr);
         if (!take)
@@ -660,9 +666,11 @@ static cudaError_t render_impl(const RenderArgs& a, cudaStream_t st, int* launch
   int nl = 0;
   EAGPT_LAUNCH(st, "k_primary", k_primary<kCount><<<nblocks(npix), kBlock, 0, st>>>(a.bvh, a.C, a.cam, mode, npix, prim, a.out_aux, a.out_stats));
   ++nl;
-  static int bounce_grid[2] = {0, 0}, mis_grid[2] = {0, 0};
+  static int bounce_grid[2] = {0, 0}, mis_grid[2] = {0, 0}, cache_grid[2] = {0, 0};
   if (!bounce_grid[kCount])
     bounce_grid[kCount] = EAGPT_REFILL ? persistent_blocks(k_bounce_r<kCount>) : persistent_blocks(k_bounce<kCount>);
+  const bool cache = EAGPT_REFILL && a.kind == 0 && a.sb_cache;
+  if (cache && !cache_grid[kCount]) cache_grid[kCount] = persistent_blocks(k_bounce_r<kCount, true>);
   if (mis && !mis_grid[kCount]) mis_grid[kCount] = persistent_blocks(k_bounce_mis<kCount>);
   for (int s0 = 0; s0 < a.spp; s0 += batch) {
     const int nb = a.spp - s0 < batch ? a.spp - s0 : batch;
@@ -685,10 +693,14 @@ static cudaError_t render_impl(const RenderArgs& a, cudaStream_t st, int* launch
         EAGPT_LAUNCH(st, "k_bounce", k_bounce_mis<kCount><<<mis_grid[kCount], kBlock, 0, st>>>(a.bvh, a.C, k, B, a.rr_start, a.seed, npix, s0,
                                                                    q[(k - 1) & 1], q[k & 1], ex[(k - 1) & 1], ex[k & 1],
                                                                    counters, slots, a.out_stats));
+      else if (cache)
+        EAGPT_LAUNCH(st, "k_bounce", k_bounce_r<kCount, true><<<cache_grid[kCount], kBlock, 0, st>>>(a.bvh, a.C, a.kind, k, B, a.rr_start, a.seed, npix,
+                                                                        s0, q[(k - 1) & 1], q[k & 1], counters, slots,
+                                                                        a.out_stats, perm, a.sb_cache));
       else if (EAGPT_REFILL)
         EAGPT_LAUNCH(st, "k_bounce", k_bounce_r<kCount><<<bounce_grid[kCount], kBlock, 0, st>>>(a.bvh, a.C, a.kind, k, B, a.rr_start, a.seed, npix,
                                                                   s0, q[(k - 1) & 1], q[k & 1], counters, slots,
-                                                                  a.out_stats, perm));
+                                                                  a.out_stats, perm, nullptr));
       else
         EAGPT_LAUNCH(st, "k_bounce", k_bounce<kCount><<<bounce_grid[kCount], kBlock, 0, st>>>(a.bvh, a.C, a.kind, k, B, a.rr_start, a.seed, npix,
                                                                 s0, q[(k - 1) & 1], q[k & 1], counters, slots,

@@ -39,13 +39,23 @@ def _weights(scene, cam, pixels, spp, seed, wseed):
     return w, int(bad.sum())
 
 
-def _compare(api, scene, cam, pixels, spp, seed, wseed, tol=1e-3):
+def _compare(api, scene, cam, pixels, spp, seed, wseed, tol=1e-3, cached=False):
     import torch
     w, n_bad = _weights(scene, cam, pixels, spp, seed, wseed)
     ds = api.DeviceScene.from_host(scene)
     bvh = api.BVH(ds)
     dL = torch.from_numpy(w.reshape(cam.height, cam.width, 3).astype(np.float32)).cuda()
-    g = api.single_bounce_backward(ds, bvh, cam, spp, seed, dL)
+    cache = None
+    if cached:
+        # the forward keeps each sample's secondary R and T; the adjoint
+        # reads them instead of re-tracing
+        r = api.Renderer()
+        fwd = r.single_bounce(ds, bvh, cam, spp, seed=seed, want_cache=True)
+        plain = r.single_bounce(ds, bvh, cam, spp, seed=seed)["rgb"]
+        api.sync_status()
+        assert torch.equal(fwd["rgb"], plain)
+        cache = fwd["cache"]
+    g = api.single_bounce_backward(ds, bvh, cam, spp, seed, dL, cache=cache)
     api.sync_status()
     ref, _ = O.single_bounce_grad(scene, cam, np.asarray(pixels, np.int32), w[pixels], spp, seed=seed)
     errs = {}
@@ -66,11 +76,20 @@ def test_gradients_small_scene(api):
     _compare(api, sc, cam, np.arange(120), 6, 3, 5)
 
 
-def test_gradients_tiny_room_crop(api):
+@pytest.mark.parametrize("cached", [False, True])
+def test_gradients_tiny_room_crop(api, cached):
     wl = S.workload("tiny")
     cam = wl.camera
     crop = np.array([(y * cam.width + x) for y in range(24, 40) for x in range(20, 36)])
-    _compare(api, wl.scene_fn(), cam, crop, 4, 0, 11)
+    _compare(api, wl.scene_fn(), cam, crop, 4, 0, 11, cached=cached)
+
+
+def test_cached_adjoint_small_scene_ragged(api):
+    """Sample cache on a scene with misses and emissive primaries (whose
+    cache entries stay unwritten), an odd image size and 5 samples."""
+    sc = S.random_small_scene(8, 31, spread=0.25, emit_frac=0.25)
+    cam = S.look_at_camera(13, 9, 60.0, (0.0, 0.0, 0.0), (1.0, 0.0, 0.0), (0, 0, 1))
+    _compare(api, sc, cam, np.arange(13 * 9), 5, 7, 3, cached=True)
 
 
 def test_autograd_function(api):
