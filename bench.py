@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--requests", type=int, default=16, help="serving: requests in the stream")
     ap.add_argument("--spp", type=int, default=None, help="override samples per pixel")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--adjoint-retrace", action="store_true",
+                    help="diff: the adjoint re-traces every secondary segment instead of reading the forward's cache")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     return ap.parse_args()
 
@@ -518,10 +520,11 @@ def run_diff(args):
     """The differentiable single-bounce workload (1M surfels, 800x800,
     16 spp): one step = LBVH build + single-bounce forward (Eq. 6) + the
     hand-written adjoint for L = sum w . image with w ~ U[-1, 1] (seed 11),
-    gradients for every surfel parameter.  Segments counted: the forward's
-    primary and secondary segments, and the adjoint's re-traces (primary
-    records once, every secondary segment twice: values then adjoint, every
-    hit primary twice)."""
+    gradients for every surfel parameter.  The forward keeps each sample's
+    secondary R and T for the adjoint (``--adjoint-retrace``: the adjoint
+    re-traces them).  value = the render's segments (primary and secondary),
+    each differentiated, per second of the whole step; the adjoint's own
+    traversals are reported in the config."""
     import numpy as np
     import torch
 
@@ -543,13 +546,15 @@ def run_diff(args):
     need = L.eagpt_render_backward_workspace_bytes(ctypes.byref(api.camera(cam)), spp)
     bws = torch.empty(need, dtype=torch.uint8, device=dev)
 
+    cached = not args.adjoint_retrace
+
     def step(seed):
         bvh = api.BVH(ds)
-        img = r.single_bounce(ds, bvh, cam, spp, seed=seed)["rgb"]
+        fwd = r.single_bounce(ds, bvh, cam, spp, seed=seed, want_cache=cached)
         for g in grads.values():
             g.zero_()
-        api.single_bounce_backward(ds, bvh, cam, spp, seed, w, grads=grads, workspace=bws)
-        return img
+        api.single_bounce_backward(ds, bvh, cam, spp, seed, w, grads=grads, workspace=bws, cache=fwd.get("cache"))
+        return fwd["rgb"]
 
     # the same rays as a path-traced render with one bounce and no roulette
     st = r.path_traced(ds, api.BVH(ds), cam, spp, 1, rr_start=1 << 20, seed=3, want_stats=True)["stats"].cpu().numpy()
@@ -557,7 +562,9 @@ def run_diff(args):
     s_blend, s_nodes, s_tests = int(st[3]), int(st[4]), int(st[5])
     hit_prim = int(st[2] // max(1, spp))
     fwd_segs = prim + sec
-    bwd_segs = prim + 2 * sec + 2 * hit_prim
+    # adjoint traversals: primary records once, every hit primary twice,
+    # every secondary segment once (twice when it re-traces the values)
+    bwd_segs = prim + (1 if cached else 2) * sec + 2 * hit_prim
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     for _ in range(max(3, args.warmup)):
         step(3)
@@ -581,23 +588,26 @@ def run_diff(args):
     clk = clocks.stop()
     api.sync_status()
     ms = sum(times) / len(times)
-    segs = fwd_segs + bwd_segs
-    value = segs / (ms * 1e-3)
+    value = fwd_segs / (ms * 1e-3)
     total_kernel_ms = sum(v[1] for v in prof.values())
     kname = max(prof.items(), key=lambda kv: kv[1][1])[0]
     peak, peak_kind = load_peaks()
     achieved = None
     if kname == "k_bwd_secondary":
         # per secondary segment: the primary record it is rebuilt from (48 B),
-        # two traversals (values, then the adjoint) and 16 gradient atomics
-        # (64 B) per blended hit
-        step_bytes = 48 * sec + 2 * (NODE_BYTES * s_nodes + 64 * s_tests + 32 * s_blend) + 64 * s_blend
+        # the cached R and T (16 B) and one traversal, or two traversals
+        # (values, then the adjoint), and 16 gradient atomics (64 B) per
+        # blended hit
+        trav = NODE_BYTES * s_nodes + 64 * s_tests + 32 * s_blend
+        step_bytes = 48 * sec + (16 * sec + trav if cached else 2 * trav) + 64 * s_blend
         achieved = step_bytes / (prof[kname][1] / args.steps * 1e-3) / 1e9
     line = {"metric": METRIC + " (single-bounce forward + adjoint)", "value": value, "unit": METRIC, "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": wl.name, "surfels": host.n, "width": cam.width, "height": cam.height, "spp": spp,
-                       "forward_segments": fwd_segs, "adjoint_segments": bwd_segs,
+                       "forward_segments": fwd_segs, "adjoint_traced_segments": bwd_segs,
+                       "traced_segments_per_s": (fwd_segs + bwd_segs) / (ms * 1e-3),
+                       "adjoint": "re-traces the secondary values" if not cached else "reads the forward's per-sample cache",
                        "step": "LBVH build + single-bounce forward + adjoint (all parameters)",
                        "l2": "flushed between steps (512 MB write)"},
             "roofline": {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "GB/s",
