@@ -124,6 +124,10 @@ __device__ __forceinline__ void leaf_step(const BvhView& bvh, const Consts& C, f
 #ifndef EAGPT_PREFETCH
 #define EAGPT_PREFETCH 0
 #endif
+// BVH4 nodes read with 256-bit loads (four per node instead of seven 128-bit)
+#ifndef EAGPT_V8NODE
+#define EAGPT_V8NODE 0
+#endif
 __device__ __forceinline__ void prefetch_child(const BvhView& bvh, uint32_t c) {
   const void* p = (c & kLeafBit) ? (const void*)(bvh.trace + (c & kLeafStartMask))
 #if EAGPT_QNODE4
@@ -166,6 +170,34 @@ __device__ __forceinline__ bool node_step(const BvhView& bvh, uint32_t node, flo
                              fmaxf(__fmaf_rn(nz, inv.z, -oiz), t_last));
       const float t1 = fminf(fminf(__fmaf_rn(fx, inv.x, -oix), __fmaf_rn(fy, inv.y, -oiy)),
                              fminf(__fmaf_rn(fz, inv.z, -oiz), tmax));
+      e[k] = (t0 <= t1 && c[k] != kEmptyChild) ? t0 : inf;
+    }
+  }
+#elif EAGPT_V8NODE
+  // the whole 128-byte node in four 32-byte loads (rows: lo x, y | lo z, hi x
+  // | hi y, z | links, pad), near and far planes picked in registers by the
+  // direction's signs, then the same one-FMA plane distances as below
+  const float* nb = (const float*)(bvh.nodes + node);
+  float v[32];
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+    asm("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+        : "=f"(v[8 * r]), "=f"(v[8 * r + 1]), "=f"(v[8 * r + 2]), "=f"(v[8 * r + 3]), "=f"(v[8 * r + 4]),
+          "=f"(v[8 * r + 5]), "=f"(v[8 * r + 6]), "=f"(v[8 * r + 7])
+        : "l"(nb + 8 * r));
+  uint32_t c[4] = {__float_as_uint(v[24]), __float_as_uint(v[25]), __float_as_uint(v[26]), __float_as_uint(v[27])};
+  {
+    const bool px = !(inv.x < 0.f), py = !(inv.y < 0.f), pz = !(inv.z < 0.f);
+    const float ox = O.x * inv.x, oy = O.y * inv.y, oz = O.z * inv.z;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const float nx = px ? v[k] : v[12 + k], fx = px ? v[12 + k] : v[k];
+      const float ny = py ? v[4 + k] : v[16 + k], fy = py ? v[16 + k] : v[4 + k];
+      const float nz = pz ? v[8 + k] : v[20 + k], fz = pz ? v[20 + k] : v[8 + k];
+      const float t0 = fmaxf(fmaxf(__fmaf_rn(nx, inv.x, -ox), __fmaf_rn(ny, inv.y, -oy)),
+                             fmaxf(__fmaf_rn(nz, inv.z, -oz), t_last));
+      const float t1 = fminf(fminf(__fmaf_rn(fx, inv.x, -ox), __fmaf_rn(fy, inv.y, -oy)),
+                             fminf(__fmaf_rn(fz, inv.z, -oz), tmax));
       e[k] = (t0 <= t1 && c[k] != kEmptyChild) ? t0 : inf;
     }
   }
