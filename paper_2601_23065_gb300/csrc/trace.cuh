@@ -23,6 +23,42 @@
 
 namespace eagpt {
 
+#ifndef EAGPT_V8REC
+#define EAGPT_V8REC 0
+#endif
+
+// 32 bytes in one 256-bit read-only load (p 32-byte aligned)
+__device__ __forceinline__ void ld_v8(const void* p, float4& a, float4& b) {
+  asm("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+      : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w), "=f"(b.x), "=f"(b.y), "=f"(b.z), "=f"(b.w)
+      : "l"(p));
+}
+
+// A surfel's trace record (EAGPT_V8REC: two 256-bit loads instead of four).
+__device__ __forceinline__ TraceRec load_trace(const TraceRec* rp) {
+  TraceRec R;
+#if EAGPT_V8REC
+  ld_v8(rp, R.r0, R.r1);
+  ld_v8((const char*)rp + 32, R.r2, R.r3);
+#else
+  R.r0 = __ldg(&rp->r0);
+  R.r1 = __ldg(&rp->r1);
+  R.r2 = __ldg(&rp->r2);
+  R.r3 = __ldg(&rp->r3);
+#endif
+  return R;
+}
+
+// A surfel's shade record.
+__device__ __forceinline__ void load_shade(const ShadeRec* sp, float4& s0, float4& s1) {
+#if EAGPT_V8REC
+  ld_v8(sp, s0, s1);
+#else
+  s0 = __ldg(&sp->s0);
+  s1 = __ldg(&sp->s1);
+#endif
+}
+
 __device__ __forceinline__ float dot3_rn(float3 a, float3 b) {
   return __fmaf_rn(a.z, b.z, __fmaf_rn(a.y, b.y, __fmul_rn(a.x, b.x)));
 }
@@ -92,11 +128,7 @@ __device__ __forceinline__ void leaf_step(const BvhView& bvh, const Consts& C, f
   const uint32_t cnum = ((leaf >> kLeafCountShift) & 3u) + 1u;
   for (uint32_t j = start; j < start + cnum; ++j) {
     const TraceRec* rp = bvh.trace + j;
-    TraceRec R;
-    R.r0 = __ldg(&rp->r0);
-    R.r1 = __ldg(&rp->r1);
-    R.r2 = __ldg(&rp->r2);
-    R.r3 = __ldg(&rp->r3);
+    const TraceRec R = load_trace(rp);
     if (kCount) ++cnt.tests;
     HitGeom h;
     if (!intersect(R, O, w, C, h)) continue;
@@ -539,11 +571,7 @@ __device__ __forceinline__ void trace_segment(const BvhView& bvh, const Consts& 
       if (i < count && !stop) {
         const uint32_t j = kj[i];
         const TraceRec* rp = bvh.trace + j;
-        TraceRec R;
-        R.r0 = __ldg(&rp->r0);
-        R.r1 = __ldg(&rp->r1);
-        R.r2 = __ldg(&rp->r2);
-        R.r3 = __ldg(&rp->r3);
+        const TraceRec R = load_trace(rp);
         HitGeom h;
         intersect(R, O, w, C, h);  // bit-identical to the collection pass
         if (kCount) ++cnt.blended;
@@ -632,11 +660,7 @@ __device__ __forceinline__ bool round_blend(RayTrace<K>& r, const BvhView& bvh, 
     if (i < r.count && !stop) {
       const uint32_t j = r.kj[i];
       const TraceRec* rp = bvh.trace + j;
-      TraceRec R;
-      R.r0 = __ldg(&rp->r0);
-      R.r1 = __ldg(&rp->r1);
-      R.r2 = __ldg(&rp->r2);
-      R.r3 = __ldg(&rp->r3);
+      const TraceRec R = load_trace(rp);
       HitGeom h;
       intersect(R, r.O, r.w, C, h);
       if (kCount) ++cnt.blended;
@@ -668,7 +692,8 @@ struct BlendVisitor {
   // that every kernel that blends produces the same bits
   __device__ __forceinline__ bool operator()(const TraceRec& R, uint32_t j, const HitGeom& h) {
     const ShadeRec* sp = shade + j;
-    const float4 s0 = __ldg(&sp->s0), s1 = __ldg(&sp->s1);
+    float4 s0, s1;
+    load_shade(sp, s0, s1);
     const float wgt = __fmul_rn(b.T, h.alpha);
     const float sgn = h.d > 0.f ? -wgt : wgt;  // normal facing the ray origin
     const float re = (mode == 1 && !(s0.w > C.tau_E)) ? 0.f : wgt;
@@ -712,7 +737,8 @@ struct SmemBlendVisitorT {
   }
   __device__ __forceinline__ bool operator()(const TraceRec& R, uint32_t j, const HitGeom& h) {
     const ShadeRec* sp = shade + j;
-    const float4 s0 = __ldg(&sp->s0), s1 = __ldg(&sp->s1);
+    float4 s0, s1;
+    load_shade(sp, s0, s1);
     const float wgt = __fmul_rn(T, h.alpha);
     const float sgn = h.d > 0.f ? -wgt : wgt;
     float re = (mode == 1 && !(s0.w > C.tau_E)) ? 0.f : wgt;
