@@ -27,9 +27,24 @@ namespace eagpt {
 #define EAGPT_V8REC 1
 #endif
 
-// 32 bytes in one 256-bit read-only load (p 32-byte aligned)
+// the 256-bit load's form (cache operator and hint): 0 read-only (.nc),
+// 1 plain, 2 .ca, 3 read-only with an L1 evict-last hint
+#ifndef EAGPT_V8_KIND
+#define EAGPT_V8_KIND 0
+#endif
+#if EAGPT_V8_KIND == 1
+#define EAGPT_LD_V8 "ld.global.v8.f32"
+#elif EAGPT_V8_KIND == 2
+#define EAGPT_LD_V8 "ld.global.ca.v8.f32"
+#elif EAGPT_V8_KIND == 3
+#define EAGPT_LD_V8 "ld.global.nc.L1::evict_last.v8.f32"
+#else
+#define EAGPT_LD_V8 "ld.global.nc.v8.f32"
+#endif
+
+// 32 bytes in one 256-bit load of read-only data (p 32-byte aligned)
 __device__ __forceinline__ void ld_v8(const void* p, float4& a, float4& b) {
-  asm("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+  asm(EAGPT_LD_V8 " {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
       : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w), "=f"(b.x), "=f"(b.y), "=f"(b.z), "=f"(b.w)
       : "l"(p));
 }
@@ -214,7 +229,7 @@ __device__ __forceinline__ bool node_step(const BvhView& bvh, uint32_t node, flo
   float v[32];
 #pragma unroll
   for (int r = 0; r < 4; ++r)
-    asm("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+    asm(EAGPT_LD_V8 " {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
         : "=f"(v[8 * r]), "=f"(v[8 * r + 1]), "=f"(v[8 * r + 2]), "=f"(v[8 * r + 3]), "=f"(v[8 * r + 4]),
           "=f"(v[8 * r + 5]), "=f"(v[8 * r + 6]), "=f"(v[8 * r + 7])
         : "l"(nb + 8 * r));
