@@ -285,6 +285,113 @@ __global__ void __launch_bounds__(kBlock, kBwdMinBlocks) k_bwd_secondary(BvhView
   per_sample[2 * t + 1] = outB;
 }
 
+// The cached adjoint of the secondary segments as a persistent kernel with
+// per-lane refill (as the forward bounce kernel): a lane whose sample is done
+// takes the next one, and traversal runs in chunks of kBwdSteps node or leaf
+// steps, so lanes of a warp do not idle while one traces a long segment.
+// Per sample it computes what k_bwd_secondary<true> computes, in the same
+// order of blended hits.
+#ifndef EAGPT_BWD_REFILL
+#define EAGPT_BWD_REFILL 1
+#endif
+constexpr int kBwdSteps = 64;
+
+__global__ void __launch_bounds__(kBlock, kBwdMinBlocks) k_bwd_secondary_r(BvhView bvh, Consts C, eagpt_camera cam, eagpt_scene sc,
+                                                            eagpt_scene_grad gr, const PrimRecB* __restrict__ prim,
+                                                            const float* __restrict__ dL, int spp, uint64_t seed,
+                                                            int64_t npix, int s0, int batch, float4* per_sample,
+                                                            const float4* __restrict__ sb_cache, uint32_t* counter) {
+  __shared__ uint32_t s_stack[kStackSize * kBlock];
+  const int lane = threadIdx.x & 31;
+  const int64_t total = npix * (int64_t)batch;
+  const float invS = 1.f / (float)spp;
+  TraceCounters cnt{0, 0, 0, 0, 0};
+  RayTrace<kKb> rt;
+  AdjointVisitorT<true> av;
+  av.shade = bvh.shade;
+  av.sc = sc;
+  av.gr = gr;
+  av.C = C;
+  av.mode = 0;
+  int64_t t = 0;
+  bool active = false, exhausted = false;
+  for (;;) {
+    const bool want = !active && !exhausted;
+    const uint32_t wmask = __ballot_sync(0xffffffffu, want);
+    if (wmask) {
+      const int leader = __ffs(wmask) - 1;
+      uint32_t base = 0;
+      if (lane == leader) base = atomicAdd(counter, (uint32_t)__popc(wmask));
+      base = __shfl_sync(0xffffffffu, base, leader);
+      if (want) {
+        const int64_t idx = (int64_t)base + __popc(wmask & ((1u << lane) - 1u));
+        if (idx < total) {
+          t = idx;
+          const int64_t pixel = t % npix;
+          const int sl = (int)(t / npix);
+          const PrimRecB p = prim[pixel];
+          if (p.c.w >= 0.f && !(p.b.w > C.tau_E)) {
+            const uint32_t sample = (uint32_t)(s0 + sl);
+            const float4 c = sb_cache[(int64_t)sample * npix + pixel];
+            if (c.w < 1.f) {  // the secondary segment blended a hit
+              const float4 u = draws(seed, (uint32_t)pixel, sample, 1u);
+              float3 O, w;
+              camera_ray(cam, (uint32_t)pixel, O, w);
+              const float3 Nn = make_float3(p.a.x, p.a.y, p.a.z);
+              const float3 O2 = (O + p.a.w * w) + C.bounce_offset * Nn;
+              const float3 w2 = cosine_direction(Nn, u.x, u.y);
+              const float3 g = make_float3(dL[3 * pixel], dL[3 * pixel + 1], dL[3 * pixel + 2]);
+              av.O = O2;
+              av.w = w2;
+              av.gN = av.gP = make_float3(0.f, 0.f, 0.f);
+              av.gR = invS * mul3(g, make_float3(p.c.x, p.c.y, p.c.z));
+              av.gD = av.gA = 0.f;
+              init_blend(av.V);
+              av.V.R = make_float3(c.x, c.y, c.z);
+              av.V.T = c.w;
+              init_blend(av.run);
+              av.dO = av.dw = make_float3(0.f, 0.f, 0.f);
+              ray_begin(rt, O2, w2);
+              round_begin(rt, bvh);
+              active = true;
+            }
+          }
+          if (!active) {
+            per_sample[2 * t] = make_float4(0.f, 0.f, 0.f, 0.f);
+            per_sample[2 * t + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
+          }
+        } else {
+          exhausted = true;
+        }
+      }
+    }
+    if (!__any_sync(0xffffffffu, active)) break;
+    if (active && round_steps<kKb, false>(rt, bvh, C, s_stack + threadIdx.x, kBlock, kBwdSteps, cnt)) {
+      if (round_blend<kKb, false>(rt, bvh, C, av, cnt)) {
+        // O2 = O + D~1 w + offset N~1 ; w2 = basis(N~1) l  (the sample's
+        // primary data are re-read here rather than kept across the trace)
+        const int64_t pixel = t % npix;
+        const uint32_t sample = (uint32_t)(s0 + (int)(t / npix));
+        const PrimRecB p = prim[pixel];
+        const float4 u = draws(seed, (uint32_t)pixel, sample, 1u);
+        float3 O, w;
+        camera_ray(cam, (uint32_t)pixel, O, w);
+        const float3 Nn = make_float3(p.a.x, p.a.y, p.a.z);
+        const float4 c = sb_cache[(int64_t)sample * npix + pixel];
+        const float3 g = make_float3(dL[3 * pixel], dL[3 * pixel + 1], dL[3 * pixel + 2]);
+        const float gDn = dot3(av.dO, w);
+        const float3 gNn = C.bounce_offset * av.dO + cosine_direction_adjoint(Nn, u.x, u.y, av.dw);
+        const float3 gP1 = invS * mul3(g, make_float3(c.x, c.y, c.z));
+        per_sample[2 * t] = make_float4(gNn.x, gNn.y, gNn.z, gDn);
+        per_sample[2 * t + 1] = make_float4(gP1.x, gP1.y, gP1.z, 0.f);
+        active = false;
+      } else {
+        round_begin(rt, bvh);
+      }
+    }
+  }
+}
+
 __global__ void k_bwd_reduce(int64_t npix, int batch, int first, const float4* __restrict__ per_sample, float4* acc) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= npix) return;
@@ -356,7 +463,7 @@ __global__ void __launch_bounds__(kBlock) k_bwd_primary(BvhView bvh, Consts C, e
 
 // --------------------------------------------------------------------------
 struct BwdLayout {
-  size_t prim, acc, per_sample, total;
+  size_t prim, acc, per_sample, counter, total;
   int batch;
 };
 
@@ -371,6 +478,7 @@ static BwdLayout bwd_layout(int64_t npix, int batch) {
   L.prim = take((size_t)npix * sizeof(PrimRecB));
   L.acc = take((size_t)npix * 2 * sizeof(float4));
   L.per_sample = take((size_t)npix * batch * 2 * sizeof(float4));
+  L.counter = take(sizeof(uint32_t));  // work counter of the refill kernel
   L.total = o;
   L.batch = batch;
   return L;
@@ -408,7 +516,19 @@ cudaError_t launch_backward(const BvhView& bvh, const Consts& C, const eagpt_cam
   if (e != cudaSuccess) return e;
   for (int s0 = 0; s0 < spp; s0 += batch) {
     const int n = spp - s0 < batch ? spp - s0 : batch;
-    if (sb_cache)
+    if (sb_cache && EAGPT_BWD_REFILL) {
+      static int grid = 0;
+      if (!grid) {
+        int per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bwd_secondary_r, kBlock, 0);
+        grid = (per_sm > 0 ? per_sm : 1) * device_sms();
+      }
+      uint32_t* counter = (uint32_t*)(base + L.counter);
+      cudaMemsetAsync(counter, 0, sizeof(uint32_t), st);
+      EAGPT_LAUNCH(st, "k_bwd_secondary",
+                   k_bwd_secondary_r<<<grid, kBlock, 0, st>>>(bvh, C, cam, sc, gr, prim, dL, spp, seed, npix, s0, n, per,
+                                                              sb_cache, counter));
+    } else if (sb_cache)
       EAGPT_LAUNCH(st, "k_bwd_secondary",
                    k_bwd_secondary<true><<<nb(npix * n), kBlock, 0, st>>>(bvh, C, cam, sc, gr, prim, dL, spp, seed, npix,
                                                                           s0, n, per, sb_cache));
