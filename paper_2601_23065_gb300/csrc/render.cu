@@ -35,6 +35,10 @@ EAGPT_DEFINE_ERROR_READER(take_errors_render)
 #define EAGPT_SORT_RAYS 0
 #endif
 constexpr bool kSortRays = EAGPT_SORT_RAYS != 0;
+#ifndef EAGPT_MIS_SPLIT
+#define EAGPT_MIS_SPLIT 0
+#endif
+constexpr bool kMisSplit = EAGPT_MIS_SPLIT != 0;
 
 // Blend sums of the bounce kernel in shared memory instead of registers.
 #ifndef EAGPT_SMEM_BLEND
@@ -65,7 +69,10 @@ __global__ void k_ray_keys(const Ray* __restrict__ q, const uint32_t* __restrict
 
 // counters block: per bounce k, [2k] = rays queued for bounce k, [2k+1] = fetch
 constexpr int kMaxBounces = 60;
-constexpr int kCounterWords = 2 * (kMaxBounces + 2) + 8;
+// per bounce k: queue length (2k) and fetch index (2k + 1); then the fetch
+// indices of the emitter-sample pass (kNeeFetch + k)
+constexpr int kNeeFetch = 2 * (kMaxBounces + 2) + 8;
+constexpr int kCounterWords = kNeeFetch + kMaxBounces + 2;
 
 RenderLayout render_layout(int64_t npix, int spp, int batch_spp, bool mis) {
   RenderLayout L{};
@@ -376,6 +383,17 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_bounce_r(BvhView bvh, Co
   }
 }
 
+// The emitter sample's estimate added to the radiance L gathered at a vertex
+// (Sec. 3.4 path tracing with emitter sampling): beta r_i w_i p_B p_L /
+// (p_L^2 + p_B^2), p_B = cos / pi, with explicit roundings so that every
+// kernel that gathers gives the same bits.
+__device__ __forceinline__ float3 nee_gather(float3 L, float4 beta, float4 ri, float wt, float cosx, float pl) {
+  const float pb = __fmul_rn(cosx, 0.318309886183790672f);
+  const float f = __fdiv_rn(__fmul_rn(__fmul_rn(wt, pb), pl), __fmaf_rn(pl, pl, __fmul_rn(pb, pb)));
+  return make_float3(__fmaf_rn(__fmul_rn(beta.x, ri.x), f, L.x), __fmaf_rn(__fmul_rn(beta.y, ri.y), f, L.y),
+                     __fmaf_rn(__fmul_rn(beta.z, ri.z), f, L.z));
+}
+
 // Path tracing with emitter sampling: every queued ray first traces its
 // emitter sample (the segment from its origin towards a point on a sampled
 // emitter, Philox (pixel, sample, k, 1)), adds that estimate to the path's
@@ -457,14 +475,13 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_bounce_mis(BvhView bvh, 
         if (round_blend<kK, kCount>(rt, bvh, C, nee, cnt)) {
           // the emitter sample's estimate: beta r_i w_i p_B p_L / (p_L^2 + p_B^2)
           if (nee.found() && nee.E() > C.tau_E) {
-            const float pb = gath[3 * kBlock] * 0.318309886183790672f;
-            const float pl = nee.pl();
-            const float f = nee.wt() * pb * pl / (pl * pl + pb * pb);
             const float4 beta = __ldcv(&q_in[qi].c);
             const float4 ri = __ldg(&bvh.shade[nee.target()].s1);
-            gath[0] += beta.x * ri.x * f;
-            gath[kBlock] += beta.y * ri.y * f;
-            gath[2 * kBlock] += beta.z * ri.z * f;
+            const float3 L = nee_gather(make_float3(gath[0], gath[kBlock], gath[2 * kBlock]), beta, ri, nee.wt(),
+                                        gath[3 * kBlock], nee.pl());
+            gath[0] = L.x;
+            gath[kBlock] = L.y;
+            gath[2 * kBlock] = L.z;
           }
           phase = 1;
           const float4 xn = e_in[qi].n;
@@ -515,6 +532,170 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_bounce_mis(BvhView bvh, 
     for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
     if ((threadIdx.x & 31) == 0 && m) atomicMax((unsigned long long*)(stats + 7), (unsigned long long)m);
   }
+}
+
+// Counting variant's totals of one kernel (segments traced, blended hits,
+// node steps, tests, rounds, deepest stack).
+__device__ __forceinline__ void flush_counts(int64_t* stats, uint32_t traced, const TraceCounters& cnt) {
+  add_stats(stats, 1, traced);
+  add_stats(stats, 3, cnt.blended);
+  add_stats(stats, 4, cnt.nodes);
+  add_stats(stats, 5, cnt.tests);
+  add_stats(stats, 6, cnt.rounds);
+  uint32_t m = cnt.max_stack;
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0 && m) atomicMax((unsigned long long*)(stats + 7), (unsigned long long)m);
+}
+
+// Emitter sampling split in two passes per bounce, each with one visitor's
+// state (EAGPT_MIS_SPLIT): k_nee traces every queued ray's emitter sample and
+// adds its estimate to the ray's gathered radiance (RayExt l, in place);
+// k_cont_mis then traces the continuations with power-heuristic weights and
+// shades them.  Per segment the arithmetic is k_bounce_mis's.
+template <bool kCount>
+__global__ void __launch_bounds__(kBlock, kMinBlocks) k_nee(BvhView bvh, Consts C, int k, uint64_t seed,
+                                                const Ray* __restrict__ q_in, RayExt* e_io, uint32_t* counters,
+                                                int64_t* stats) {
+  __shared__ uint32_t s_stack[kStackSize * kBlock];
+  __shared__ float s_nee[6 * kBlock];  // the visitor's state (5 words) and cos at the vertex
+  const int lane = threadIdx.x & 31;
+  const uint32_t count = counters[2 * k];
+  float* cosp = s_nee + 5 * kBlock + threadIdx.x;
+  TraceCounters cnt{0, 0, 0, 0, 0};
+  uint32_t traced = 0;
+  RayTrace<kK> rt;
+  NeeVisitorSM nee;
+  nee.shade = bvh.shade;
+  nee.C = C;
+  nee.s = s_nee + threadIdx.x;
+  nee.stride = kBlock;
+  uint32_t qi = 0;
+  bool active = false, exhausted = false;
+  for (;;) {
+    const bool want = !active && !exhausted;
+    const uint32_t wmask = __ballot_sync(0xffffffffu, want);
+    if (wmask) {
+      const int leader = __ffs(wmask) - 1;
+      uint32_t base = 0;
+      if (lane == leader) base = atomicAdd(&counters[kNeeFetch + k], (uint32_t)__popc(wmask));
+      base = __shfl_sync(0xffffffffu, base, leader);
+      if (want) {
+        const uint32_t idx = base + (uint32_t)__popc(wmask & ((1u << lane) - 1u));
+        if (idx < count) {
+          qi = idx;
+          const float4 ra = q_in[qi].a, rb = q_in[qi].b;
+          uint32_t jt;
+          float3 wl;
+          float cosx;
+          if (sample_emitter(bvh, C, seed, __float_as_uint(ra.w), __float_as_uint(rb.w), (uint32_t)k, f3(ra),
+                             f3(e_io[qi].n), jt, wl, cosx)) {
+            *cosp = cosx;
+            nee.reset(jt);
+            ray_begin(rt, f3(ra), wl);
+            round_begin(rt, bvh);
+            active = true;
+            ++traced;
+            if (kCount) ++cnt.rounds;
+          }
+        } else {
+          exhausted = true;
+        }
+      }
+    }
+    if (!__any_sync(0xffffffffu, active)) break;
+    if (active && round_steps<kK, kCount>(rt, bvh, C, s_stack + threadIdx.x, kBlock, kRefillSteps, cnt)) {
+      if (round_blend<kK, kCount>(rt, bvh, C, nee, cnt)) {
+        if (nee.found() && nee.E() > C.tau_E) {
+          const float4 beta = __ldg(&q_in[qi].c);
+          const float4 ri = __ldg(&bvh.shade[nee.target()].s1);
+          const float4 l = e_io[qi].l;
+          const float3 L = nee_gather(f3(l), beta, ri, nee.wt(), *cosp, nee.pl());
+          e_io[qi].l = make_float4(L.x, L.y, L.z, l.w);
+        }
+        active = false;
+      } else {
+        round_begin(rt, bvh);
+        if (kCount) ++cnt.rounds;
+      }
+    }
+  }
+  if (kCount) flush_counts(stats, traced, cnt);
+}
+
+template <bool kCount>
+__global__ void __launch_bounds__(kBlock, kMinBlocks) k_cont_mis(BvhView bvh, Consts C, int k, int max_bounces,
+                                                     int rr_start, uint64_t seed, int64_t npix, int s0,
+                                                     const Ray* __restrict__ q_in, Ray* q_out,
+                                                     const RayExt* __restrict__ e_in, RayExt* e_out,
+                                                     uint32_t* counters, float4* slots, int64_t* stats) {
+  __shared__ uint32_t s_stack[kStackSize * kBlock];
+  __shared__ float s_blend[11 * kBlock];
+  const int lane = threadIdx.x & 31;
+  const uint32_t count = counters[2 * k];
+  TraceCounters cnt{0, 0, 0, 0, 0};
+  uint32_t traced = 0;
+  RayTrace<kK> rt;
+  SmemBlendVisitorT<true> vis(bvh.shade, C, 1, s_blend + threadIdx.x, kBlock);
+  uint32_t qi = 0;
+  bool active = false, exhausted = false;
+  for (;;) {
+    const bool want = !active && !exhausted;
+    const uint32_t wmask = __ballot_sync(0xffffffffu, want);
+    if (wmask) {
+      const int leader = __ffs(wmask) - 1;
+      uint32_t base = 0;
+      if (lane == leader) base = atomicAdd(&counters[2 * k + 1], (uint32_t)__popc(wmask));
+      base = __shfl_sync(0xffffffffu, base, leader);
+      if (want) {
+        const uint32_t idx = base + (uint32_t)__popc(wmask & ((1u << lane) - 1u));
+        if (idx < count) {
+          qi = idx;
+          const float pbw = e_in[qi].n.w;
+          vis.pb2 = pbw * pbw;
+          vis.reset();
+          ray_begin(rt, f3(q_in[qi].a), f3(q_in[qi].b));
+          round_begin(rt, bvh);
+          active = true;
+          ++traced;
+          if (kCount) ++cnt.rounds;
+        } else {
+          exhausted = true;
+        }
+      }
+    }
+    if (!__any_sync(0xffffffffu, active)) break;
+    bool take = false;
+    Ray nr;
+    RayExt nx;
+    if (active && round_steps<kK, kCount>(rt, bvh, C, s_stack + threadIdx.x, kBlock, kRefillSteps, cnt)) {
+      if (round_blend<kK, kCount>(rt, bvh, C, vis, cnt)) {
+        const SegRec sg = finish(vis.get());
+        Ray r;
+        r.a = make_float4(rt.O.x, rt.O.y, rt.O.z, __ldg(&q_in[qi].a.w));
+        r.b = make_float4(rt.w.x, rt.w.y, rt.w.z, __ldg(&q_in[qi].b.w));
+        r.c = __ldg(&q_in[qi].c);
+        RayExt x;
+        x.n = e_in[qi].n;
+        x.l = e_in[qi].l;
+        const uint32_t pixel = __float_as_uint(r.a.w), sample = __float_as_uint(r.b.w);
+        float3 contrib;
+        take = shade_bounce_mis(k, max_bounces, rr_start, seed, C, r, x, sg, contrib, nr, nx);
+        if (!take)
+          slots[(int64_t)(sample - (uint32_t)s0) * npix + pixel] = make_float4(contrib.x, contrib.y, contrib.z, 0.f);
+        active = false;
+      } else {
+        round_begin(rt, bvh);
+        if (kCount) ++cnt.rounds;
+      }
+    }
+    __syncwarp();
+    const uint32_t at = warp_append(take, &counters[2 * (k + 1)]);
+    if (take) {
+      q_out[at] = nr;
+      e_out[at] = nx;
+    }
+  }
+  if (kCount) flush_counts(stats, traced, cnt);
 }
 
 // Per pixel: add the batch's samples in order; on the last batch write the
@@ -671,7 +852,10 @@ static cudaError_t render_impl(const RenderArgs& a, cudaStream_t st, int* launch
     bounce_grid[kCount] = EAGPT_REFILL ? persistent_blocks(k_bounce_r<kCount>) : persistent_blocks(k_bounce<kCount>);
   const bool cache = EAGPT_REFILL && a.kind == 0 && a.sb_cache;
   if (cache && !cache_grid[kCount]) cache_grid[kCount] = persistent_blocks(k_bounce_r<kCount, true>);
-  if (mis && !mis_grid[kCount]) mis_grid[kCount] = persistent_blocks(k_bounce_mis<kCount>);
+  static int nee_grid[2] = {0, 0};
+  if (mis && !mis_grid[kCount])
+    mis_grid[kCount] = kMisSplit ? persistent_blocks(k_cont_mis<kCount>) : persistent_blocks(k_bounce_mis<kCount>);
+  if (mis && kMisSplit && !nee_grid[kCount]) nee_grid[kCount] = persistent_blocks(k_nee<kCount>);
   for (int s0 = 0; s0 < a.spp; s0 += batch) {
     const int nb = a.spp - s0 < batch ? a.spp - s0 : batch;
     cudaMemsetAsync(counters, 0, kCounterWords * sizeof(uint32_t), st);
@@ -689,7 +873,16 @@ static cudaError_t render_impl(const RenderArgs& a, cudaStream_t st, int* launch
         launch_sort_pairs(k0, v0, k1, v1, (uint32_t*)(ws + L.shist), cap, st);
         perm = v0;
       }
-      if (mis)
+      if (mis && kMisSplit) {
+        EAGPT_LAUNCH(st, "k_bounce", k_nee<kCount><<<nee_grid[kCount], kBlock, 0, st>>>(a.bvh, a.C, k, a.seed, q[(k - 1) & 1],
+                                                                                      ex[(k - 1) & 1], counters,
+                                                                                      a.out_stats));
+        ++nl;
+        EAGPT_LAUNCH(st, "k_bounce", k_cont_mis<kCount><<<mis_grid[kCount], kBlock, 0, st>>>(a.bvh, a.C, k, B, a.rr_start, a.seed, npix,
+                                                                                           s0, q[(k - 1) & 1], q[k & 1],
+                                                                                           ex[(k - 1) & 1], ex[k & 1],
+                                                                                           counters, slots, a.out_stats));
+      } else if (mis)
         EAGPT_LAUNCH(st, "k_bounce", k_bounce_mis<kCount><<<mis_grid[kCount], kBlock, 0, st>>>(a.bvh, a.C, k, B, a.rr_start, a.seed, npix, s0,
                                                                    q[(k - 1) & 1], q[k & 1], ex[(k - 1) & 1], ex[k & 1],
                                                                    counters, slots, a.out_stats));
