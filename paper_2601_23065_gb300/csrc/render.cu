@@ -36,7 +36,7 @@ EAGPT_DEFINE_ERROR_READER(take_errors_render)
 #endif
 constexpr bool kSortRays = EAGPT_SORT_RAYS != 0;
 #ifndef EAGPT_MIS_SPLIT
-#define EAGPT_MIS_SPLIT 0
+#define EAGPT_MIS_SPLIT 1
 #endif
 constexpr bool kMisSplit = EAGPT_MIS_SPLIT != 0;
 
