@@ -39,6 +39,10 @@ constexpr bool kSortRays = EAGPT_SORT_RAYS != 0;
 #define EAGPT_MIS_SPLIT 1
 #endif
 constexpr bool kMisSplit = EAGPT_MIS_SPLIT != 0;
+#ifndef EAGPT_PATH_PERSIST
+#define EAGPT_PATH_PERSIST 0
+#endif
+constexpr bool kPathPersist = EAGPT_PATH_PERSIST != 0;
 
 // Blend sums of the bounce kernel in shared memory instead of registers.
 #ifndef EAGPT_SMEM_BLEND
@@ -383,6 +387,108 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_bounce_r(BvhView bvh, Co
   }
 }
 
+// Counting variant's totals of one kernel (segments traced, blended hits,
+// node steps, tests, rounds, deepest stack).
+__device__ __forceinline__ void flush_counts(int64_t* stats, uint32_t traced, const TraceCounters& cnt) {
+  add_stats(stats, 1, traced);
+  add_stats(stats, 3, cnt.blended);
+  add_stats(stats, 4, cnt.nodes);
+  add_stats(stats, 5, cnt.tests);
+  add_stats(stats, 6, cnt.rounds);
+  uint32_t m = cnt.max_stack;
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0 && m) atomicMax((unsigned long long*)(stats + 7), (unsigned long long)m);
+}
+
+// Path tracing with every path kept by one lane from its first bounce to its
+// end (EAGPT_PATH_PERSIST): a lane takes the next first-bounce ray from the
+// generator's queue, traces and shades each of its segments in turn (the
+// throughput, pixel and sample in a shared-memory payload, the bounce index in
+// a register) and writes the path's slot when it ends, so one launch per pass
+// replaces the per-bounce launches and their tails, and no ray goes through a
+// queue between bounces.  Per path the arithmetic is k_bounce_r's.
+template <bool kCount>
+__global__ void __launch_bounds__(kBlock, kMinBlocks) k_path_r(BvhView bvh, Consts C, int kind, int max_bounces,
+                                                   int rr_start, uint64_t seed, int64_t npix, int s0,
+                                                   const Ray* __restrict__ q_in, uint32_t* counters, float4* slots,
+                                                   int64_t* stats) {
+  __shared__ uint32_t s_stack[kStackSize * kBlock];
+  __shared__ float s_blend[11 * kBlock];
+  __shared__ float s_pay[5 * kBlock];  // pixel, sample (bits), throughput
+  const int lane = threadIdx.x & 31;
+  float* pay = s_pay + threadIdx.x;
+  const uint32_t count = counters[2];
+  const int mode = kind == 1 ? 1 : 0;
+  TraceCounters cnt{0, 0, 0, 0, 0};
+  uint32_t traced = 0;
+  RayTrace<kK> rt;
+  SmemBlendVisitor vis(bvh.shade, C, mode, s_blend + threadIdx.x, kBlock);
+  int kb = 1;
+  bool active = false, pending = false, exhausted = false;  // pending: rt holds the next segment's ray
+  for (;;) {
+    const bool want = !active && !pending && !exhausted;
+    const uint32_t wmask = __ballot_sync(0xffffffffu, want);
+    if (wmask) {
+      const int leader = __ffs(wmask) - 1;
+      uint32_t base = 0;
+      if (lane == leader) base = atomicAdd(&counters[3], (uint32_t)__popc(wmask));
+      base = __shfl_sync(0xffffffffu, base, leader);
+      if (want) {
+        const uint32_t idx = base + (uint32_t)__popc(wmask & ((1u << lane) - 1u));
+        if (idx < count) {
+          const Ray r = q_in[idx];
+          pay[0] = r.a.w;
+          pay[kBlock] = r.b.w;
+          pay[2 * kBlock] = r.c.x;
+          pay[3 * kBlock] = r.c.y;
+          pay[4 * kBlock] = r.c.z;
+          kb = 1;
+          ray_begin(rt, f3(r.a), f3(r.b));
+          pending = true;
+        } else {
+          exhausted = true;
+        }
+      }
+    }
+    if (pending) {
+      round_begin(rt, bvh);
+      vis.reset();
+      active = true;
+      pending = false;
+      ++traced;
+      if (kCount) ++cnt.rounds;
+    }
+    if (!__any_sync(0xffffffffu, active)) break;
+    if (active && round_steps<kK, kCount>(rt, bvh, C, s_stack + threadIdx.x, kBlock, kRefillSteps, cnt)) {
+      if (round_blend<kK, kCount>(rt, bvh, C, vis, cnt)) {
+        const SegRec s = finish(vis.get());
+        Ray r;
+        r.a = make_float4(rt.O.x, rt.O.y, rt.O.z, pay[0]);
+        r.b = make_float4(rt.w.x, rt.w.y, rt.w.z, pay[kBlock]);
+        r.c = make_float4(pay[2 * kBlock], pay[3 * kBlock], pay[4 * kBlock], 0.f);
+        float3 contrib;
+        Ray nr;
+        if (shade_bounce(kind, kb, max_bounces, rr_start, seed, C, r, s, contrib, nr)) {
+          pay[2 * kBlock] = nr.c.x;
+          pay[3 * kBlock] = nr.c.y;
+          pay[4 * kBlock] = nr.c.z;
+          ++kb;
+          ray_begin(rt, f3(nr.a), f3(nr.b));
+          pending = true;
+        } else {
+          const uint32_t pixel = __float_as_uint(r.a.w), sample = __float_as_uint(r.b.w);
+          slots[(int64_t)(sample - (uint32_t)s0) * npix + pixel] = make_float4(contrib.x, contrib.y, contrib.z, 0.f);
+        }
+        active = false;
+      } else {
+        round_begin(rt, bvh);
+        if (kCount) ++cnt.rounds;
+      }
+    }
+  }
+  if (kCount) flush_counts(stats, traced, cnt);
+}
+
 // The emitter sample's estimate added to the radiance L gathered at a vertex
 // (Sec. 3.4 path tracing with emitter sampling): beta r_i w_i p_B p_L /
 // (p_L^2 + p_B^2), p_B = cos / pi, with explicit roundings so that every
@@ -534,18 +640,6 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_bounce_mis(BvhView bvh, 
   }
 }
 
-// Counting variant's totals of one kernel (segments traced, blended hits,
-// node steps, tests, rounds, deepest stack).
-__device__ __forceinline__ void flush_counts(int64_t* stats, uint32_t traced, const TraceCounters& cnt) {
-  add_stats(stats, 1, traced);
-  add_stats(stats, 3, cnt.blended);
-  add_stats(stats, 4, cnt.nodes);
-  add_stats(stats, 5, cnt.tests);
-  add_stats(stats, 6, cnt.rounds);
-  uint32_t m = cnt.max_stack;
-  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
-  if ((threadIdx.x & 31) == 0 && m) atomicMax((unsigned long long*)(stats + 7), (unsigned long long)m);
-}
 
 // Emitter sampling split in two passes per bounce, each with one visitor's
 // state (EAGPT_MIS_SPLIT): k_nee traces every queued ray's emitter sample and
@@ -853,6 +947,7 @@ static cudaError_t render_impl(const RenderArgs& a, cudaStream_t st, int* launch
   const bool cache = EAGPT_REFILL && a.kind == 0 && a.sb_cache;
   if (cache && !cache_grid[kCount]) cache_grid[kCount] = persistent_blocks(k_bounce_r<kCount, true>);
   static int nee_grid[2] = {0, 0};
+  static int path_grid[2] = {0, 0};
   if (mis && !mis_grid[kCount])
     mis_grid[kCount] = kMisSplit ? persistent_blocks(k_cont_mis<kCount>) : persistent_blocks(k_bounce_mis<kCount>);
   if (mis && kMisSplit && !nee_grid[kCount]) nee_grid[kCount] = persistent_blocks(k_nee<kCount>);
@@ -862,7 +957,15 @@ static cudaError_t render_impl(const RenderArgs& a, cudaStream_t st, int* launch
     EAGPT_LAUNCH(st, "k_generate", k_generate<kCount><<<nblocks(npix * nb), kBlock, 0, st>>>(prim, a.C, a.cam, a.kind, B, a.rr_start, a.seed, npix,
                                                               s0, nb, q[0], counters, slots, a.out_stats, ex[0]));
     ++nl;
-    for (int k = 1; k <= B; ++k) {
+    const bool persist = kPathPersist && a.kind == 1 && !mis && !kSortRays && EAGPT_REFILL && B >= 2;
+    if (persist) {
+      if (!path_grid[kCount]) path_grid[kCount] = persistent_blocks(k_path_r<kCount>);
+      EAGPT_LAUNCH(st, "k_bounce", k_path_r<kCount><<<path_grid[kCount], kBlock, 0, st>>>(a.bvh, a.C, a.kind, B, a.rr_start, a.seed,
+                                                                                        npix, s0, q[0], counters, slots,
+                                                                                        a.out_stats));
+      ++nl;
+    }
+    for (int k = 1; k <= (persist ? 0 : B); ++k) {
       const uint32_t* perm = nullptr;
       if (kSortRays) {
         uint32_t *k0 = (uint32_t*)(ws + L.sk0), *k1 = (uint32_t*)(ws + L.sk1);
