@@ -107,3 +107,34 @@ def test_timeout_and_cancel(api):
     assert srv.wait(first, 300.0)["state"] == "done"
     srv.close()
     api.sync_status()
+
+
+def test_small_requests_do_not_wait_on_a_large_one(api):
+    """Each wave's queue is filled shortest remaining work first, with one
+    sample per request first: renders submitted just after a large one finish
+    long before it, and the large one still progresses every wave and ends."""
+    import torch
+    sc = S.tiny_room(4096)
+    ds = api.DeviceScene.from_host(sc)
+    bvh = api.BVH(ds)
+    srv = api.Server(ds, bvh, queue_paths=200_000, max_active=8)
+    big_cam = S.look_at_camera(256, 256, 90.0, (0.0, 0.0, 0.0), (1, 0, 0), (0, 0, 1))
+    big = srv.submit_render(big_cam, 64, 5, rr_start=2, seed=9)  # 4.2 M paths: 21 full waves at least
+    small = []
+    for k in range(4):
+        cam = S.look_at_camera(32, 32, 90.0, (0.05 * k, 0.0, 0.0), (0, 1, 0), (0, 0, 1))
+        small.append((srv.submit_render(cam, 8, 2, rr_start=2, seed=20 + k), cam, 20 + k))
+    done_small = []
+    for (rid, out), cam, seed in small:
+        info = srv.wait(rid, timeout_s=120.0)
+        assert info["state"] == "done", info
+        done_small.append(info["t_done"])
+        torch.cuda.synchronize()
+        ref = api.Renderer().path_traced(ds, bvh, cam, 8, 2, rr_start=2, seed=seed)["rgb"]
+        assert torch.equal(out, ref)
+    info = srv.wait(big[0], timeout_s=300.0)
+    assert info["state"] == "done", info
+    assert max(done_small) < info["t_done"]
+    assert srv.stats()["waves"] >= 21
+    srv.close()
+    api.sync_status()
