@@ -43,10 +43,6 @@ constexpr bool kMisSplit = EAGPT_MIS_SPLIT != 0;
 #define EAGPT_PATH_PERSIST 0
 #endif
 constexpr bool kPathPersist = EAGPT_PATH_PERSIST != 0;
-#ifndef EAGPT_PRIM_REFILL
-#define EAGPT_PRIM_REFILL 0
-#endif
-constexpr bool kPrimRefill = EAGPT_PRIM_REFILL != 0;
 
 // Blend sums of the bounce kernel in shared memory instead of registers.
 #ifndef EAGPT_SMEM_BLEND
@@ -81,7 +77,6 @@ constexpr int kMaxBounces = 60;
 // indices of the emitter-sample pass (kNeeFetch + k)
 constexpr int kNeeFetch = 2 * (kMaxBounces + 2) + 8;
 constexpr int kCounterWords = kNeeFetch + kMaxBounces + 2;
-constexpr int kPrimFetch = kCounterWords - 1;  // fetch index of the refill primary kernel
 
 RenderLayout render_layout(int64_t npix, int spp, int batch_spp, bool mis) {
   RenderLayout L{};
@@ -310,74 +305,6 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_bounce(BvhView bvh, Cons
 #endif
 constexpr int kRefillSteps = EAGPT_REFILL_STEPS;
 bool render_has_refill() { return EAGPT_REFILL != 0; }
-
-// The primary segments as a persistent per-lane refill kernel
-// (EAGPT_PRIM_REFILL): a lane whose pixel is done takes the next one, the
-// traversal runs in chunks, the blend sums live in shared memory; the
-// records are k_primary's bit for bit.
-template <bool kCount>
-__global__ void __launch_bounds__(kBlock, kMinBlocks) k_primary_r(BvhView bvh, Consts C, eagpt_camera cam, int mode,
-                                                      int64_t npix, PrimRec* prim, float* aux, uint32_t* fetch,
-                                                      int64_t* stats) {
-  __shared__ uint32_t s_stack[kStackSize * kBlock];
-  __shared__ float s_blend[11 * kBlock];
-  const int lane = threadIdx.x & 31;
-  TraceCounters cnt{0, 0, 0, 0, 0};
-  uint32_t traced = 0;
-  RayTrace<kK> rt;
-  SmemBlendVisitor vis(bvh.shade, C, mode, s_blend + threadIdx.x, kBlock);
-  int64_t i = 0;
-  bool active = false, exhausted = false;
-  for (;;) {
-    const bool want = !active && !exhausted;
-    const uint32_t wmask = __ballot_sync(0xffffffffu, want);
-    if (wmask) {
-      const int leader = __ffs(wmask) - 1;
-      uint32_t base = 0;
-      if (lane == leader) base = atomicAdd(fetch, (uint32_t)__popc(wmask));
-      base = __shfl_sync(0xffffffffu, base, leader);
-      if (want) {
-        const int64_t idx = (int64_t)base + __popc(wmask & ((1u << lane) - 1u));
-        if (idx < npix) {
-          i = idx;
-          float3 O, w;
-          camera_ray(cam, (uint32_t)i, O, w);
-          ray_begin(rt, O, w);
-          round_begin(rt, bvh);
-          vis.reset();
-          active = true;
-          ++traced;
-          if (kCount) ++cnt.rounds;
-        } else {
-          exhausted = true;
-        }
-      }
-    }
-    if (!__any_sync(0xffffffffu, active)) break;
-    if (active && round_steps<kK, kCount>(rt, bvh, C, s_stack + threadIdx.x, kBlock, kRefillSteps, cnt)) {
-      if (round_blend<kK, kCount>(rt, bvh, C, vis, cnt)) {
-        const SegRec s = finish(vis.get());
-        PrimRec p;
-        p.a = make_float4(s.Nn.x, s.Nn.y, s.Nn.z, s.Dn);
-        p.b = make_float4(s.R.x, s.R.y, s.R.z, s.E);
-        p.c = make_float4(s.P.x, s.P.y, s.P.z, s.hit ? s.A : -1.f);  // A < 0 marks a miss
-        prim[i] = p;
-        if (aux) write_aux(aux, i, s);
-        active = false;
-      } else {
-        round_begin(rt, bvh);
-        if (kCount) ++cnt.rounds;
-      }
-    }
-  }
-  if (kCount) {
-    add_stats(stats, 0, traced);
-    add_stats(stats, 8, cnt.blended);
-    add_stats(stats, 9, cnt.nodes);
-    add_stats(stats, 10, cnt.tests);
-    add_stats(stats, 11, cnt.rounds);
-  }
-}
 
 template <bool kCount, bool kCache = false>
 __global__ void __launch_bounds__(kBlock, kMinBlocks) k_bounce_r(BvhView bvh, Consts C, int kind, int k, int max_bounces,
@@ -1012,16 +939,7 @@ static cudaError_t render_impl(const RenderArgs& a, cudaStream_t st, int* launch
   const int mode = a.kind == 1 ? 1 : 0;
   const int B = a.kind == 1 ? a.max_bounces : 1;
   int nl = 0;
-  if (kPrimRefill && EAGPT_REFILL) {
-    static int prim_grid[2] = {0, 0};
-    if (!prim_grid[kCount]) prim_grid[kCount] = persistent_blocks(k_primary_r<kCount>);
-    uint32_t* fetch = counters + kPrimFetch;
-    cudaMemsetAsync(fetch, 0, sizeof(uint32_t), st);
-    EAGPT_LAUNCH(st, "k_primary", k_primary_r<kCount><<<prim_grid[kCount], kBlock, 0, st>>>(a.bvh, a.C, a.cam, mode, npix, prim,
-                                                                                          a.out_aux, fetch, a.out_stats));
-  } else {
-    EAGPT_LAUNCH(st, "k_primary", k_primary<kCount><<<nblocks(npix), kBlock, 0, st>>>(a.bvh, a.C, a.cam, mode, npix, prim, a.out_aux, a.out_stats));
-  }
+  EAGPT_LAUNCH(st, "k_primary", k_primary<kCount><<<nblocks(npix), kBlock, 0, st>>>(a.bvh, a.C, a.cam, mode, npix, prim, a.out_aux, a.out_stats));
   ++nl;
   static int bounce_grid[2] = {0, 0}, mis_grid[2] = {0, 0}, cache_grid[2] = {0, 0};
   if (!bounce_grid[kCount])
