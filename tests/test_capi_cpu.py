@@ -85,3 +85,33 @@ def test_host_argument_checks(lib):
     st = lib.eagpt_render_path_traced(ctypes.byref(sc), ctypes.byref(bvh), ctypes.byref(cam), ctypes.byref(p), 4, 2,
                                       2, 0, rgb, None, None, None, ctypes.c_void_p(256), 16, None)
     assert st == 2  # workspace too small
+
+
+def test_sample_cache_argument_checks(lib):
+    """The forward-to-adjoint cache: its size, and the checks made before
+    any launch (missing or misaligned cache, stale BVH)."""
+    from paper_2601_23065_gb300 import capi
+    cam = capi.Camera(8, 6, 4.0, 4.0, 4.0, 3.0)
+    assert lib.eagpt_single_bounce_cache_bytes(ctypes.byref(cam), 5) == 8 * 6 * 5 * 16
+    assert lib.eagpt_single_bounce_cache_bytes(ctypes.byref(cam), 0) == 0
+    assert lib.eagpt_single_bounce_cache_bytes(None, 4) == 0
+    p = capi.default_params()
+    sc = capi.Scene()
+    sc.n, sc.version = 0, 3
+    bvh = capi.Bvh()
+    bvh.n, bvh.scene_version, bvh.support_sigma = 0, 3, 3.0
+    rgb, ws = ctypes.c_void_p(256), ctypes.c_void_p(512)
+    fwd = lib.eagpt_render_single_bounce_cached
+    assert fwd(ctypes.byref(sc), ctypes.byref(bvh), ctypes.byref(cam), ctypes.byref(p), 4, 0, rgb, None, ws, 1 << 20,
+               None) == 1
+    assert b"sample_cache" in lib.eagpt_last_error()
+    assert fwd(ctypes.byref(sc), ctypes.byref(bvh), ctypes.byref(cam), ctypes.byref(p), 4, 0, rgb, ctypes.c_void_p(8),
+               ws, 1 << 20, None) == 1
+    sc.version = 4  # the BVH was built for version 3
+    assert fwd(ctypes.byref(sc), ctypes.byref(bvh), ctypes.byref(cam), ctypes.byref(p), 4, 0, rgb,
+               ctypes.c_void_p(1024), ws, 1 << 20, None) == 4
+    g = capi.SceneGrad()
+    bwd = lib.eagpt_render_single_bounce_backward_cached
+    assert bwd(ctypes.byref(sc), ctypes.byref(bvh), ctypes.byref(cam), ctypes.byref(p), 4, 0, rgb, None,
+               ctypes.byref(g), ws, 1 << 20, None) == 1
+    assert b"sample_cache" in lib.eagpt_last_error()
