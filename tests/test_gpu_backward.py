@@ -121,3 +121,39 @@ def test_gradients_full_size_diff_workload(api):
     cam = wl.camera
     crop = np.array([(y * cam.width + x) for y in range(392, 408) for x in range(392, 408)])
     _compare(api, sc, cam, crop, wl.spp, 0, 11)
+
+
+def test_cached_adjoint_one_sample_per_pass(api):
+    """The cached adjoint with the smallest workspace (one sample per pass,
+    so every pass starts at a later sample of the cache) adds the same
+    gradients as with a full workspace, up to the order of the atomics."""
+    import ctypes
+    import torch
+    sc = S.tiny_room(4096)
+    cam = S.horizontal_camera(40, 30, hfov=100.0)
+    spp, seed = 6, 4
+    ds = api.DeviceScene.from_host(sc)
+    bvh = api.BVH(ds)
+    fwd = api.Renderer().single_bounce(ds, bvh, cam, spp, seed=seed, want_cache=True)
+    dL = torch.rand((cam.height, cam.width, 3), device="cuda") * 2 - 1
+    full = api.single_bounce_backward(ds, bvh, cam, spp, seed, dL, cache=fwd["cache"])
+    L = api.capi.lib()
+    c = api.camera(cam)
+    need = L.eagpt_render_backward_workspace_min_bytes(ctypes.byref(c), spp)
+    assert need < L.eagpt_render_backward_workspace_bytes(ctypes.byref(c), spp)
+    ws = torch.empty(need, dtype=torch.uint8, device="cuda")
+    grads = {k: torch.zeros_like(ds.t[k]) for k in api.GRAD_FIELDS}
+    g = api.capi.SceneGrad()
+    g.n = ds.n
+    for k in api.GRAD_FIELDS:
+        setattr(g, k, grads[k].data_ptr())
+    sc_c = ds.c()
+    api.capi.check(L.eagpt_render_single_bounce_backward_cached(
+        ctypes.byref(sc_c), ctypes.byref(bvh.c()), ctypes.byref(c), ctypes.byref(bvh.params), spp,
+        ctypes.c_uint64(seed), ctypes.c_void_p(dL.data_ptr()), ctypes.c_void_p(fwd["cache"].data_ptr()),
+        ctypes.byref(g), ctypes.c_void_p(ws.data_ptr()), need, None))
+    api.sync_status()
+    for k in api.GRAD_FIELDS:
+        a, b = grads[k], full[k]
+        assert float(b.abs().max()) > 0, k
+        assert torch.allclose(a, b, rtol=1e-4, atol=1e-6 * float(b.abs().max())), k
