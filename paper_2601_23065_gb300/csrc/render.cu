@@ -26,10 +26,6 @@ namespace eagpt {
 #define EAGPT_KBUF 12
 #endif
 constexpr int kK = EAGPT_KBUF;  // k-buffer size (hits collected per traversal round)
-#ifndef EAGPT_KBUF2
-#define EAGPT_KBUF2 0
-#endif
-constexpr int kK2 = EAGPT_KBUF2;  // second k-buffer tier in shared memory (bounce kernel; 0: none)
 
 EAGPT_DEFINE_ERROR_READER(take_errors_render)
 
@@ -318,13 +314,6 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_bounce_r(BvhView bvh, Co
                                                      float4* sb_cache) {
   __shared__ uint32_t s_stack[kStackSize * kBlock];
   __shared__ float s_blend[11 * kBlock];
-  Tier2 tier{nullptr, nullptr, kBlock};
-  if constexpr (kK2 > 0) {
-    __shared__ float s_t2[(kK2 > 0 ? kK2 : 1) * kBlock];
-    __shared__ uint32_t s_j2[(kK2 > 0 ? kK2 : 1) * kBlock];
-    tier.t = s_t2 + threadIdx.x;
-    tier.j = s_j2 + threadIdx.x;
-  }
   const int lane = threadIdx.x & 31;
   const uint32_t count = counters[2 * k];
   const int mode = kind == 1 ? 1 : 0;
@@ -360,20 +349,8 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_bounce_r(BvhView bvh, Co
     if (!__any_sync(0xffffffffu, active)) break;
     bool take = false;
     Ray nr;
-    bool walked = false;
-    if (active) {
-      if constexpr (kK2 > 0)
-        walked = round_steps2<kK, kK2, kCount>(rt, bvh, C, s_stack + threadIdx.x, kBlock, tier, kRefillSteps, cnt);
-      else
-        walked = round_steps<kK, kCount>(rt, bvh, C, s_stack + threadIdx.x, kBlock, kRefillSteps, cnt);
-    }
-    if (walked) {
-      bool done;
-      if constexpr (kK2 > 0)
-        done = round_blend2<kK, kK2, kCount>(rt, bvh, C, vis, tier, cnt);
-      else
-        done = round_blend<kK, kCount>(rt, bvh, C, vis, cnt);
-      if (done) {
+    if (active && round_steps<kK, kCount>(rt, bvh, C, s_stack + threadIdx.x, kBlock, kRefillSteps, cnt)) {
+      if (round_blend<kK, kCount>(rt, bvh, C, vis, cnt)) {
         const Blend bl = vis.get();
         const SegRec s = finish(bl);
         const float4 rt_cache = make_float4(bl.R.x, bl.R.y, bl.R.z, bl.T);

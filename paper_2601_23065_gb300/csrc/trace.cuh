@@ -612,8 +612,6 @@ struct RayTrace {
   uint32_t kj[K];
   int count, sp;
   uint32_t cur;
-  int count2;   // entries in the shared-memory second tier (two-tier form)
-  float t2max;  // culling bound once both tiers are full
 };
 
 template <int K>
@@ -638,124 +636,6 @@ __device__ __forceinline__ void round_begin(RayTrace<K>& r, const BvhView& bvh) 
   r.count = 0;
   r.sp = 0;
   r.cur = bvh.n > 0 ? bvh.root : kEmptyChild;
-  r.count2 = 0;
-  r.t2max = __int_as_float(0x7f800000);
-}
-
-// Two-tier k-buffer (EAGPT_KBUF2): behind the K nearest hits in registers,
-// the next K2 in this thread's column of shared memory (t2[i * stride],
-// j2[i * stride], sorted by key).  A round collects the K + K2 nearest hits
-// past the last blended key and blends both tiers in order, so a segment needs
-// fewer rounds (each restarting at the root) than with K alone, while the
-// register file holds only K.  Every key in tier 1 is below every key in
-// tier 2; the blended sequence is the same as with one buffer of K + K2.
-struct Tier2 {
-  float* t;
-  uint32_t* j;
-  int stride;
-};
-
-template <int K, int K2, bool kCount>
-__device__ __forceinline__ void leaf_step2(const BvhView& bvh, const Consts& C, float3 O, float3 w, uint32_t leaf,
-                                           float t_last, uint32_t j_last, float (&kt)[K], uint32_t (&kj)[K],
-                                           int& count, int& count2, float& t2max, const Tier2& q,
-                                           TraceCounters& cnt) {
-  const uint32_t start = leaf & kLeafStartMask;
-  const uint32_t cnum = ((leaf >> kLeafCountShift) & 3u) + 1u;
-  for (uint32_t j = start; j < start + cnum; ++j) {
-    const TraceRec R = load_trace(bvh.trace + j);
-    if (kCount) ++cnt.tests;
-    HitGeom h;
-    if (!intersect(R, O, w, C, h)) continue;
-    if (!key_less(t_last, j_last, h.t, j)) continue;  // already blended (or behind)
-    if (count2 == K2 && !key_less(h.t, j, q.t[(K2 - 1) * q.stride], q.j[(K2 - 1) * q.stride])) continue;
-    float ct = h.t;
-    uint32_t cj = j;
-    if (count < K || key_less(ct, cj, kt[K - 1], kj[K - 1])) {
-#pragma unroll
-      for (int i = 0; i < K; ++i) {
-        const bool lt = key_less(ct, cj, kt[i], kj[i]);
-        const float tt = kt[i];
-        const uint32_t tj = kj[i];
-        kt[i] = lt ? ct : tt;
-        kj[i] = lt ? cj : tj;
-        ct = lt ? tt : ct;
-        cj = lt ? tj : cj;
-      }
-      if (count < K) {
-        ++count;
-        continue;
-      }
-    }
-    // (ct, cj): the new hit, or the register entry it displaced; its place in
-    // tier 2 (the last entry drops when the tier is full)
-    int i = count2 < K2 ? count2 : K2 - 1;
-    while (i > 0) {
-      const float pt = q.t[(i - 1) * q.stride];
-      const uint32_t pj = q.j[(i - 1) * q.stride];
-      if (!key_less(ct, cj, pt, pj)) break;
-      q.t[i * q.stride] = pt;
-      q.j[i * q.stride] = pj;
-      --i;
-    }
-    q.t[i * q.stride] = ct;
-    q.j[i * q.stride] = cj;
-    if (count2 < K2) ++count2;
-    if (count2 == K2) t2max = q.t[(K2 - 1) * q.stride];
-  }
-}
-
-template <int K, int K2, bool kCount>
-__device__ __forceinline__ bool round_steps2(RayTrace<K>& r, const BvhView& bvh, const Consts& C, uint32_t* stack,
-                                             int stride, const Tier2& q, int steps, TraceCounters& cnt) {
-  for (int s = 0; s < steps && r.cur != kEmptyChild; ++s) {
-    if (r.cur & kLeafBit) {
-      leaf_step2<K, K2, kCount>(bvh, C, r.O, r.w, r.cur, r.t_last, r.j_last, r.kt, r.kj, r.count, r.count2, r.t2max,
-                                q, cnt);
-      r.cur = pop(stack, stride, r.sp);
-    } else {
-      if (kCount) ++cnt.nodes;
-      uint32_t next;
-      const bool ok = kBvh8 ? node_step8(bvh, r.cur, r.O, r.inv, r.t_last, r.t2max, stack, stride, r.sp, next)
-                            : node_step(bvh, r.cur, r.O, r.inv, r.t_last, r.t2max, stack, stride, r.sp, next);
-      if (!ok) {
-        r.cur = kEmptyChild;
-        break;
-      }
-      if (kCount && (uint32_t)r.sp > cnt.max_stack) cnt.max_stack = (uint32_t)r.sp;
-      r.cur = next != kEmptyChild ? next : pop(stack, stride, r.sp);
-    }
-  }
-  return r.cur == kEmptyChild;
-}
-
-template <int K, int K2, bool kCount, class Visitor>
-__device__ __forceinline__ bool round_blend2(RayTrace<K>& r, const BvhView& bvh, const Consts& C, Visitor& vis,
-                                             const Tier2& q, TraceCounters& cnt) {
-  bool stop = false;
-#pragma unroll
-  for (int i = 0; i < K; ++i) {
-    if (i < r.count && !stop) {
-      const uint32_t j = r.kj[i];
-      const TraceRec R = load_trace(bvh.trace + j);
-      HitGeom h;
-      intersect(R, r.O, r.w, C, h);
-      if (kCount) ++cnt.blended;
-      stop = vis(R, j, h);
-    }
-  }
-  for (int i = 0; i < r.count2 && !stop; ++i) {
-    const uint32_t j = q.j[i * q.stride];
-    const TraceRec R = load_trace(bvh.trace + j);
-    HitGeom h;
-    intersect(R, r.O, r.w, C, h);
-    if (kCount) ++cnt.blended;
-    stop = vis(R, j, h);
-  }
-  if (stop || r.count2 < K2) return true;
-  r.t_last = q.t[(K2 - 1) * q.stride];
-  r.j_last = q.j[(K2 - 1) * q.stride];
-  return false;
 }
 
 // At most `steps` node or leaf steps of the current round; true once the
