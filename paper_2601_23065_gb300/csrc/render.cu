@@ -304,10 +304,6 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_bounce(BvhView bvh, Cons
 #define EAGPT_REFILL_STEPS 64
 #endif
 constexpr int kRefillSteps = EAGPT_REFILL_STEPS;
-#ifndef EAGPT_IDLE_BREAK
-#define EAGPT_IDLE_BREAK 0
-#endif
-constexpr int kIdleBreak = EAGPT_IDLE_BREAK;  // end a traversal chunk once this many lanes wait (0: never)
 bool render_has_refill() { return EAGPT_REFILL != 0; }
 
 template <bool kCount, bool kCache = false>
@@ -353,9 +349,7 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_bounce_r(BvhView bvh, Co
     if (!__any_sync(0xffffffffu, active)) break;
     bool take = false;
     Ray nr;
-    const uint32_t amask = kIdleBreak > 0 ? __ballot_sync(0xffffffffu, active) : 0u;
-    if (active && round_steps<kK, kCount>(rt, bvh, C, s_stack + threadIdx.x, kBlock, kRefillSteps, cnt, amask,
-                                          kIdleBreak)) {
+    if (active && round_steps<kK, kCount>(rt, bvh, C, s_stack + threadIdx.x, kBlock, kRefillSteps, cnt)) {
       if (round_blend<kK, kCount>(rt, bvh, C, vis, cnt)) {
         const Blend bl = vis.get();
         const SegRec s = finish(bl);

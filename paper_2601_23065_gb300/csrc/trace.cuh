@@ -641,24 +641,10 @@ __device__ __forceinline__ void round_begin(RayTrace<K>& r, const BvhView& bvh) 
 // At most `steps` node or leaf steps of the current round; true once the
 // round's walk is complete.  A stack overflow (recorded as a device error)
 // ends the walk.
-//
-// With amask (the warp's lanes that called, all of which must call) and
-// idle_break > 0, the chunk also ends, for all of them together, as soon as
-// idle_break of them have finished their walk: they can blend, shade and
-// take new rays while the others wait less.
 template <int K, bool kCount>
 __device__ __forceinline__ bool round_steps(RayTrace<K>& r, const BvhView& bvh, const Consts& C, uint32_t* stack,
-                                            int stride, int steps, TraceCounters& cnt, uint32_t amask = 0u,
-                                            int idle_break = 0) {
-  const int n_in = __popc(amask);
-  for (int s = 0; s < steps; ++s) {
-    if (idle_break > 0) {
-      const uint32_t walking = __ballot_sync(amask, r.cur != kEmptyChild);
-      if (walking == 0u || n_in - __popc(walking) >= idle_break) break;
-      if (r.cur == kEmptyChild) continue;
-    } else if (r.cur == kEmptyChild) {
-      break;
-    }
+                                            int stride, int steps, TraceCounters& cnt) {
+  for (int s = 0; s < steps && r.cur != kEmptyChild; ++s) {
     if (r.cur & kLeafBit) {
       leaf_step<K, kCount>(bvh, C, r.O, r.w, r.cur, r.t_last, r.j_last, r.kt, r.kj, r.count, cnt);
       r.cur = pop(stack, stride, r.sp);
