@@ -225,3 +225,20 @@ def test_large_layout_sampled_pixels(eg):
     lit_gpu = np.abs(g_all[pix]).max(-1) > 0
     assert np.array_equal(lit_ref[clean], lit_gpu[clean])
     assert ok.all(), st
+
+
+@pytest.mark.slow
+def test_serving_room_full_size_sampled_pixels(eg):
+    """Path tracing in the serving room at full size (3M surfels, 10x8x3 m),
+    a 512x512 view from the room centre, 16 spp, 3 bounces; the oracle
+    computes 48 random pixels (seed 7)."""
+    wl = S.workload("serving")
+    rng = np.random.default_rng(7)
+    pix = rng.choice(wl.camera.width * wl.camera.height, 48, replace=False)
+    ok, st, out, ref = _parity(eg, wl.scene_fn(), wl.camera, "pt", wl.spp, wl.max_bounces, wl.rr_start, 0, pixels=pix)
+    print(st)
+    clean = ref["sample_flags"] == 0
+    lit_ref = np.abs(ref["samples"]).max(-1) > 0
+    g_s = out["samples"].cpu().numpy().reshape(-1, wl.spp, 3)[pix]
+    assert np.array_equal(lit_ref[clean], np.abs(g_s).max(-1)[clean] > 0)
+    assert ok.all(), st
