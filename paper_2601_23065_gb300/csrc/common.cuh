@@ -24,10 +24,7 @@ constexpr int kStackSize = EAGPT_STACK;  // traversal stack entries per ray
 #define EAGPT_MIN_BLOCKS 6
 #endif
 constexpr int kMinBlocks = EAGPT_MIN_BLOCKS;  // resident trace blocks per SM the compiler must allow
-#ifndef EAGPT_BLOCK
-#define EAGPT_BLOCK 128
-#endif
-constexpr int kBlock = EAGPT_BLOCK;  // threads per block of the trace kernels (a multiple of 32)
+constexpr int kBlock = 128;          // threads per block of the trace kernels
 constexpr uint32_t kLeafBit = 0x80000000u;
 constexpr int kLeafCountShift = 29;  // leaf: bit31 | (count-1) << 29 | start
 constexpr uint32_t kLeafStartMask = (1u << kLeafCountShift) - 1u;
