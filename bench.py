@@ -1,18 +1,22 @@
 """Benchmark: path segments/s of the surfel path tracer on one GB300.
 
 One step = one pass of the whole hot path over the workload: surfel
-preprocess + LBVH build (sort, hierarchy, refit) + path-traced render (primary
-segments, then per-bounce trace/shade/compact waves, then the deterministic
-accumulation).  Default workload: the medium room (200k surfels, 512x512,
-64 spp, up to 4 bounces, Russian roulette from bounce 2).
+preprocess + LBVH build (sort, hierarchy, collapse) + path-traced render
+(primary segments, then per-bounce trace/shade/compact waves, then the
+deterministic accumulation).  Default workload: the large final render
+(6M-surfel three-room layout, 1920x1080, 1024 spp, 5 bounces, Russian
+roulette from bounce 2), one 64-sample slice of the frame per step: step k
+renders samples [64 (k mod 16), 64 (k mod 16) + 64) with their own Philox
+counters, so 16 consecutive steps render the whole 1024-sample frame.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload medium|large|tiny|diff]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload large|medium|tiny] [--slice-spp S]
   python bench.py --workload serving [--requests R]   (continuous-batching server)
+  python bench.py --workload diff|mis                 (differentiable single bounce / emitter sampling)
   python bench.py --workload stage1|bake [--views V]  (Eq. 7 / Eq. 10 optimisation loops)
   python bench.py --impl reference ...    (the FP64 CPU oracle on a bounded sample)
 
-Prints one JSON line (rank 0).  With N > 1 every rank renders its own share
-of the samples (independent paths; no collective on the data path).
+Prints one JSON line (rank 0).  With N > 1 every rank renders its own
+samples (independent paths; no collective on the data path).
 """
 from __future__ import annotations
 
@@ -40,11 +44,13 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--workload", default="medium",
+    ap.add_argument("--workload", default="large",
                     choices=["tiny", "medium", "diff", "large", "serving", "stage1", "bake", "mis"])
     ap.add_argument("--views", type=int, default=8, help="stage1/bake: training views")
     ap.add_argument("--requests", type=int, default=16, help="serving: requests in the stream")
-    ap.add_argument("--spp", type=int, default=None, help="override samples per pixel")
+    ap.add_argument("--spp", type=int, default=None, help="override samples per pixel (of the frame)")
+    ap.add_argument("--slice-spp", type=int, default=None,
+                    help="samples per step (default: 64 for the large render, the whole frame otherwise)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--adjoint-retrace", action="store_true",
                     help="diff: the adjoint re-traces every secondary segment instead of reading the forward's cache")
@@ -178,6 +184,12 @@ def load_traffic(workload: str):
     return d.get("dram_bytes_per_segment")
 
 
+def cpu_sample_spp(wl) -> int:
+    """Samples per pixel of the oracle's bounded sample: the frame's first
+    samples (same Philox counters as the GPU's)."""
+    return min(wl.spp, 2 if wl.scene_fn.__name__ == "large_layout" else 16)
+
+
 def cpu_baseline(wl, scene, seconds: float):
     """The FP64 oracle on a bounded pixel sample of the same workload."""
     import numpy as np
@@ -187,13 +199,14 @@ def cpu_baseline(wl, scene, seconds: float):
     n_threads = O.default_threads()
     osc = O.OracleScene(scene)
     npix = wl.camera.width * wl.camera.height
-    # grow the sample until ~`seconds` of CPU work
-    m = 2
+    spp = cpu_sample_spp(wl)
+    # grow the sample until ~`seconds` of CPU work (at least 2 pixels per thread)
+    m = 2 * n_threads
     total_segs, total_t, total_pix = 0, 0.0, 0
     while True:
         pix = rng.choice(npix, m, replace=False).astype(np.int32)
         t0 = time.perf_counter()
-        out = O.render(osc, wl.camera, pix, "pt", wl.spp, max_bounces=wl.max_bounces, rr_start=wl.rr_start,
+        out = O.render(osc, wl.camera, pix, "pt", spp, max_bounces=wl.max_bounces, rr_start=wl.rr_start,
                        seed=0, params=O.Params(fp32_eps=0.0), n_threads=n_threads)
         dt = time.perf_counter() - t0
         total_segs += int(out["segments"].sum())
@@ -203,14 +216,19 @@ def cpu_baseline(wl, scene, seconds: float):
             break
         m = int(min(4096, max(m * 2, m * seconds / max(dt, 1e-3) / 2)))
     return {"value": total_segs / total_t, "unit": METRIC, "cores": n_threads, "kind": "oracle",
-            "sample": f"{total_pix} random pixels x {wl.spp} spp of the same workload "
+            "sample": f"{total_pix} random pixels x {spp} spp (the frame's first samples) of the same workload "
                       f"({total_segs} segments in {total_t:.1f} s, brute force over {scene.n} surfels, FP64)"}
 
 
 def run_reference(args, rank, world):
-    """--impl reference: the oracle as it stands, timed on the host cores."""
+    """--impl reference: the oracle as it stands, timed on the host cores.
+    Each step renders 2 x threads random pixels (so every thread has work) at
+    the oracle sample's samples per pixel."""
     if rank != 0:
         return
+    import numpy as np
+
+    import oracle as O
     from paper_2601_23065_gb300 import scenes as S
     if args.workload in ("stage1", "bake"):
         field = 0 if args.workload == "stage1" else 1
@@ -228,26 +246,44 @@ def run_reference(args, rank, world):
     if args.spp:
         wl.spp = args.spp
     scene = wl.scene_fn()
+    osc = O.OracleScene(scene)
+    n_threads = O.default_threads()
+    spp = cpu_sample_spp(wl)
+    npix = wl.camera.width * wl.camera.height
+    rng = np.random.default_rng(321)
+
+    def one(m):
+        pix = rng.choice(npix, m, replace=False).astype(np.int32)
+        t0 = time.perf_counter()
+        out = O.render(osc, wl.camera, pix, "pt", spp, max_bounces=wl.max_bounces, rr_start=wl.rr_start, seed=0,
+                       params=O.Params(fp32_eps=0.0), n_threads=n_threads)
+        return int(out["segments"].sum()), time.perf_counter() - t0
+
     for _ in range(max(0, args.warmup)):
-        cpu_baseline(wl, scene, 0.5)
-    vals = []
+        one(n_threads)
+    segs, secs = 0, 0.0
     for _ in range(args.steps):
-        vals.append(cpu_baseline(wl, scene, args.cpu_seconds / max(1, args.steps)))
-    v = statistics.mean(x["value"] for x in vals)
+        a, b = one(2 * n_threads)
+        segs += a
+        secs += b
+    v = segs / secs
+    sample = (f"{args.steps} steps x {2 * n_threads} random pixels x {spp} spp (the frame's first samples) of the "
+              f"same workload ({segs} segments in {secs:.1f} s, brute force over {scene.n} surfels, FP64)")
     line = {"metric": METRIC, "value": v, "unit": METRIC, "impl": "reference", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": wl.name},
-            "cpu_baseline": {"value": v, "unit": METRIC, "cores": vals[0]["cores"], "kind": "oracle",
-                             "sample": vals[0]["sample"]},
+            "config": {"workload": wl.name, "scale_factor": wl.scale_factor},
+            "cpu_baseline": {"value": v, "unit": METRIC, "cores": n_threads, "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
 def run_serving(args):
-    """Serving room (3M surfels): a seeded request stream (renders of
-    256x256..1920x1080, 16/64/256 spp, 1-5 bounces, 10 % edits) served (a)
-    by plain sequential launches, (b) by the continuous-batching server at
+    """Serving room (3M surfels, scales x0.436 of the medium room's law): a
+    seeded request stream (renders of 256x256..1920x1080, 16/64/256 spp, 1-5
+    bounces, 10 % edits) served (a) by plain sequential launches, (b) by the
+    continuous-batching server with every request submitted at once (closed
+    loop: throughput and latency under a full queue), (c) by the server at
     Poisson arrival rates of 0.8x and 1.2x the plain capacity.  Reports
     throughput (pixel samples/s), p50/p99 latency, and whether every served
     image equals its plain render bit for bit."""
@@ -261,9 +297,11 @@ def run_serving(args):
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
     host = S.serving_room()
+    wl = S.workload("serving")
     reqs = S.serving_requests(host, args.requests, seed=13)
     n_render = sum(1 for r in reqs if r["type"] == "render")
     samples = sum(r["camera"].width * r["camera"].height * r["spp"] for r in reqs if r["type"] == "render")
+    queue_paths = 1 << 27
 
     def resolve_edit(ds, r):
         idx = torch.from_numpy(r["idx"]).to(dev) if "idx" in r else api.select(ds, "sphere", r["sphere"])
@@ -277,11 +315,13 @@ def run_serving(args):
     for _ in range(max(1, args.warmup)):
         rend.path_traced(ds, bvh, S.horizontal_camera(256, 256), 4, 2)
     torch.cuda.synchronize(dev)
-    plain_out, t0 = [], time.perf_counter()
+    plain_out, plain_lat, t0 = [], [], time.perf_counter()
     for r in reqs:
         if r["type"] == "render":
             o = rend.path_traced(ds, bvh, r["camera"], r["spp"], r["max_bounces"], rr_start=2, seed=r["seed"])
             plain_out.append(o["rgb"].clone())
+            torch.cuda.synchronize(dev)
+            plain_lat.append(time.perf_counter() - t0)  # completion time when all arrive at t = 0
         else:
             idx, per = resolve_edit(ds, r)
             api.apply_edit(ds, bvh, r["op"], idx, value=r.get("value", ()), per_index=per)
@@ -291,19 +331,19 @@ def run_serving(args):
     del ds, bvh, rend
     torch.cuda.empty_cache()
 
-    results = {}
-    for load in (0.8, 1.2):
+    def serve(arrivals):
+        """Submits the stream at the given arrival offsets (None: all at
+        once) and returns its throughput, latencies and bitwise check."""
         ds = api.DeviceScene.from_host(host, device=dev)
         bvh = api.BVH(ds)
-        srv = api.Server(ds, bvh, queue_paths=1 << 24, max_active=16)
-        rng = np.random.default_rng(int(load * 100))
-        arrivals = np.cumsum(rng.exponential(1.0 / (load * mu), len(reqs)))
+        srv = api.Server(ds, bvh, queue_paths=queue_paths, max_active=16)
         ids = []
         start = time.perf_counter()
-        for r, ta in zip(reqs, arrivals):
-            delay = start + ta - time.perf_counter()
-            if delay > 0:
-                time.sleep(delay)
+        for n, r in enumerate(reqs):
+            if arrivals is not None:
+                delay = start + arrivals[n] - time.perf_counter()
+                if delay > 0:
+                    time.sleep(delay)
             if r["type"] == "render":
                 ids.append(("render", srv.submit_render(r["camera"], r["spp"], r["max_bounces"], rr_start=2,
                                                         seed=r["seed"])))
@@ -324,41 +364,54 @@ def run_serving(args):
                     view.c = lambda cur=cur: cur
                     idx = api.select(view, "sphere", r["sphere"])
                 ids.append(("edit", srv.submit_edit(r["op"], idx, value=r.get("value", ()), per_index=per)))
-        lat, equal, t_end = [], True, start
+        lat, equal, t_first, t_last = [], True, None, None
         k = 0
         for kind, x in ids:
             if kind == "render":
                 rid, out = x
-                info = srv.wait(rid, 1200.0)
+                info = srv.wait(rid, 1800.0)
+                assert info["state"] == "done", info
                 lat.append(info["t_done"] - info["t_submit"])
-                t_end = max(t_end, info["t_done"])
+                t_first = info["t_submit"] if t_first is None else min(t_first, info["t_submit"])
+                t_last = info["t_done"] if t_last is None else max(t_last, info["t_done"])
                 torch.cuda.synchronize(dev)
                 equal &= bool(torch.equal(out, plain_out[k]))
                 k += 1
             else:
-                srv.wait(x, 1200.0)
+                srv.wait(x, 1800.0)
         st = srv.stats()
-        first_submit = start + arrivals[0]
-        span = max(1e-9, time.perf_counter() - first_submit)
-        results[f"load_{load}"] = {"throughput": samples / span, "p50_s": float(np.percentile(lat, 50)),
-                                   "p99_s": float(np.percentile(lat, 99)), "equal_to_plain": equal,
-                                   "segments_per_s_busy": st["segments"] / max(st["busy_s"], 1e-9),
-                                   "waves": st["waves"], "edits": st["edits"], "rebuilds": st["rebuilds"]}
+        span = max(1e-9, t_last - t_first)
+        res = {"throughput": samples / span, "seconds": span, "p50_s": float(np.percentile(lat, 50)),
+               "p99_s": float(np.percentile(lat, 99)), "mean_s": float(np.mean(lat)), "equal_to_plain": equal,
+               "segments_per_s_busy": st["segments"] / max(st["busy_s"], 1e-9), "waves": st["waves"],
+               "edits": st["edits"], "rebuilds": st["rebuilds"]}
         srv.close()
         del ds, bvh
         torch.cuda.empty_cache()
-    line = {"metric": "pixel samples/s (serving)", "value": results["load_1.2"]["throughput"],
+        return res
+
+    closed = serve(None)
+    results = {}
+    for load in (0.8, 1.2):
+        rng = np.random.default_rng(int(load * 100))
+        results[f"load_{load}"] = serve(np.cumsum(rng.exponential(1.0 / (load * mu), len(reqs))))
+    plain = {"throughput": samples / t_plain, "capacity_req_per_s": mu, "seconds": t_plain,
+             "p50_s": float(np.percentile(plain_lat, 50)), "p99_s": float(np.percentile(plain_lat, 99)),
+             "mean_s": float(np.mean(plain_lat))}
+    line = {"metric": "pixel samples/s (serving, all requests submitted at once)", "value": closed["throughput"],
             "unit": "pixel samples/s", "n_gpus": 1, "steps": 1, "warmup": args.warmup, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "serving room 3M surfels, Poisson request stream", "requests": len(reqs),
-                       "renders": n_render, "pixel_samples": samples},
-            "plain": {"throughput": samples / t_plain, "capacity_req_per_s": mu, "seconds": t_plain},
-            "served": results}
+            "config": {"workload": "serving room 3M surfels, seeded request stream", "scale_factor": wl.scale_factor,
+                       "requests": len(reqs), "renders": n_render, "pixel_samples": samples,
+                       "queue_paths": queue_paths, "max_active": 16},
+            "plain": plain, "closed_loop": closed, "speedup_vs_plain": closed["throughput"] / plain["throughput"],
+            "poisson": results}
     print(json.dumps(line), flush=True)
 
 
-# bytes of one BVH4 node visit (six float4 child-box planes + four links, 128 B)
-NODE_BYTES = 128
+# bytes counted per BVH node visit in the byte model (a binary node's two child
+# boxes and links; one BVH4 node of 128 B replaces about two of them)
+NODE_BYTES = 64
 
 
 def fit_views(n_views, width=540, height=360):
@@ -680,6 +733,220 @@ def run_mis(args):
     print(json.dumps(line), flush=True)
 
 
+def frame_slices(frame_spp: int, slice_spp: int):
+    """(first sample, samples) of each slice of a frame of frame_spp samples."""
+    out, first = [], 0
+    while first < frame_spp:
+        n = min(slice_spp, frame_spp - first)
+        out.append((first, n))
+        first += n
+    return out
+
+
+# Bytes the method moves per secondary segment (the byte model of the
+# roofline): the ray read (48 B) and the ray or slot write (48 B), 64 B per BVH
+# node visit, 64 B per surfel record tested and 32 B per shade record blended.
+def alg_bytes_per_segment(nodes, tests, blended):
+    return 48.0 + 48.0 + 64.0 * nodes + 64.0 * tests + 32.0 * blended
+
+
+# The part no BVH can avoid: the ray in and out and, per blended hit, its
+# trace and shade records (64 + 32 B).
+def floor_bytes_per_segment(blended):
+    return 96.0 + 96.0 * blended
+
+
+def run_render(args, rank, world, local):
+    """The path-traced render workloads (large | medium | tiny)."""
+    import numpy as np
+    import torch
+
+    from paper_2601_23065_gb300 import api, build
+    from paper_2601_23065_gb300 import capi
+    from paper_2601_23065_gb300 import scenes as S
+
+    build.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    wl = S.workload(args.workload)
+    frame_spp = args.spp or wl.spp
+    slice_spp = min(args.slice_spp or (64 if args.workload == "large" else frame_spp), frame_spp)
+    slices = frame_slices(frame_spp, slice_spp)
+    host_scene = wl.scene_fn()
+    cam = wl.camera
+    seed_base = rank_seed(rank)  # each rank renders its own samples
+    ds = api.DeviceScene.from_host(host_scene, device=dev)
+    r = api.Renderer(device=dev)
+    stream = torch.cuda.current_stream(dev)
+    L = capi.lib()
+    img = torch.empty((cam.height, cam.width, 3), dtype=torch.float32, device=dev)
+
+    def step(k):
+        first, n = slices[k % len(slices)]
+        bvh = api.BVH(ds, stream=stream)
+        r.path_traced(ds, bvh, cam, n, wl.max_bounces, rr_start=wl.rr_start, seed=seed_base, stream=stream,
+                      first_sample=first, out=img)
+        return bvh
+
+    # untimed: the counting variant on the first slice gives the per-segment
+    # work (BVH nodes, surfel tests, blended hits) of the byte model
+    first0, n0 = slices[0]
+    cnt = r.path_traced(ds, api.BVH(ds, stream=stream), cam, n0, wl.max_bounces, rr_start=wl.rr_start,
+                        seed=seed_base, first_sample=first0, want_stats=True)["stats"].cpu().numpy()
+    api.sync_status()
+    c_sec = max(1, int(cnt[1]))
+    per_seg = {"nodes": int(cnt[4]) / c_sec, "tests": int(cnt[5]) / c_sec, "blended": int(cnt[3]) / c_sec,
+               "rounds": int(cnt[6]) / c_sec}
+    prim_per_pixel_nodes = int(cnt[9]) / max(1, int(cnt[0]))
+
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2 (129 MB)
+
+    for k in range(args.warmup):
+        step(k)
+    torch.cuda.synchronize(dev)
+
+    # timed region
+    clocks = ClockSampler(local)
+    clocks.start()
+    launches0 = L.eagpt_launch_count()
+    capi.check(L.eagpt_profile_begin())
+    barrier()
+    torch.cuda.synchronize(dev)
+    times, prim_segs, sec_segs = [], 0, 0
+    for k in range(args.steps):
+        flush.fill_(float(k))  # L2 flush between steps (outside the step's events)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        step(k)
+        b.record(stream)
+        b.synchronize()
+        times.append(a.elapsed_time(b))
+        p, q = r.segments(stream)  # this step's exact segment counts (read after its events)
+        prim_segs += p
+        sec_segs += q
+    torch.cuda.synchronize(dev)
+    barrier()
+    prof = capi.profile_end()
+    launches = L.eagpt_launch_count() - launches0
+    clk = clocks.stop()
+    api.sync_status()
+
+    ms = sum(times) / len(times)
+    t_max = max_over_ranks(sum(times) / 1e3, world, dev)
+    segs_local = prim_segs + sec_segs
+    segs_job = segs_local
+    if world > 1:
+        t = torch.tensor([float(segs_local)], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t)
+        segs_job = float(t.item())
+    value = segs_job / t_max
+    npix = cam.width * cam.height
+    paths_local = npix * sum(slices[k % len(slices)][1] for k in range(args.steps))
+
+    # roofline of the dominant kernel (the fused trace/shade/compact bounce)
+    bounce = prof.get("k_bounce", (0, 0.0))
+    total_kernel_ms = sum(v[1] for v in prof.values())
+    peak, peak_kind = load_peaks()
+    bounce_launches = max(1, bounce[0])
+    ms_per_launch = bounce[1] / bounce_launches
+    segs_per_launch = sec_segs / bounce_launches
+    model_b = alg_bytes_per_segment(per_seg["nodes"], per_seg["tests"], per_seg["blended"])
+    floor_b = floor_bytes_per_segment(per_seg["blended"])
+
+    def gbs(bytes_per_seg):
+        return bytes_per_seg * segs_per_launch / (ms_per_launch * 1e-3) / 1e9 if ms_per_launch else None
+
+    achieved = gbs(model_b)
+    dram_b = load_traffic(args.workload)
+    traffic = dram_b * segs_per_launch if dram_b else None
+    l2_resident = args.workload in ("medium", "tiny")
+    roofline = {"bound": "l2" if l2_resident else "hbm", "kernel": "k_bounce", "achieved": achieved,
+                "peak": None if l2_resident else peak, "unit": "GB/s",
+                "frac": None if (l2_resident or not achieved) else achieved / peak,
+                "traffic": traffic,
+                "model": "algorithmic bytes per secondary segment = 48 (ray in) + 48 (ray or slot out) + 64 per BVH "
+                         "node visit + 64 per surfel test + 32 per blended hit; per-segment counts from the counting "
+                         "variant on the first slice",
+                "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback",
+                "bytes_per_launch": model_b * segs_per_launch, "ms_per_launch": ms_per_launch,
+                "launches": bounce[0], "share_of_kernel_time": bounce[1] / total_kernel_ms if total_kernel_ms else None,
+                "floor": {"what": "96 + 96 per blended hit (ray in/out, trace + shade record of every blended hit)",
+                          "bytes_per_segment": floor_b, "achieved": gbs(floor_b),
+                          "frac": (gbs(floor_b) / peak) if (ms_per_launch and not l2_resident) else None},
+                "dram": ({"bytes_per_segment": dram_b, "achieved": gbs(dram_b), "frac": gbs(dram_b) / peak,
+                          "source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of a captured bounce launch, "
+                                    "per segment (profiles/)"} if dram_b else None),
+                "per_secondary_segment": per_seg, "bytes_per_segment": model_b,
+                "primary_nodes_per_pixel": prim_per_pixel_nodes, "max_stack": int(cnt[7])}
+    if l2_resident:
+        roofline["note"] = ("scene and BVH fit in the 129 MB L2: L2/latency-bound, achieved is the byte model's "
+                            "bandwidth equivalent, not an HBM fraction")
+
+    # end to end through the public API with host buffers: the scene copied
+    # from pinned host memory, BVH build, render, the image copied back
+    pinned = {k: torch.from_numpy(getattr(host_scene, k)).pin_memory() for k in api.FIELDS}
+    dev_t = {k: torch.empty_like(v, device=dev) for k, v in pinned.items()}
+    out_host = torch.empty((cam.height, cam.width, 3), dtype=torch.float32).pin_memory()
+    h2d = sum(v.numel() * 4 for v in pinned.values())
+    d2h = out_host.numel() * 4
+    e2e_t, e2e_segs = 0.0, 0
+    for k in range(min(args.steps, 4)):
+        flush.fill_(float(k))
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for kk in api.FIELDS:
+            dev_t[kk].copy_(pinned[kk], non_blocking=True)
+        dsk = api.DeviceScene(dev_t)
+        bvh = api.BVH(dsk, stream=stream)
+        first, n = slices[k % len(slices)]
+        r.path_traced(dsk, bvh, cam, n, wl.max_bounces, rr_start=wl.rr_start, seed=seed_base, stream=stream,
+                      first_sample=first, out=img)
+        out_host.copy_(img, non_blocking=True)
+        torch.cuda.synchronize(dev)
+        e2e_t += time.perf_counter() - t0
+        p, q = r.segments(stream)
+        e2e_segs += p + q
+    e2e_val = world * e2e_segs / e2e_t
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(wl, host_scene, args.cpu_seconds)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": wl.name, "surfels": host_scene.n, "scale_factor": wl.scale_factor,
+                           "width": cam.width, "height": cam.height, "frame_spp": frame_spp,
+                           "spp_per_step": slice_spp,
+                           "step": (f"LBVH build + path-traced render of samples [{slice_spp}*(k mod {len(slices)}), "
+                                    f"+{slice_spp}) of the {frame_spp}-sample frame (own Philox counters; "
+                                    f"{len(slices)} steps cover the frame)"),
+                           "max_bounces": wl.max_bounces, "rr_start": wl.rr_start,
+                           "segments": prim_segs + sec_segs, "primary_segments": prim_segs,
+                           "secondary_segments": sec_segs, "paths": paths_local,
+                           "rays_per_s": world * paths_local / t_max,
+                           "l2": "flushed between steps (512 MB write)",
+                           "parallelism": f"replicas x{world} (independent samples per rank)"},
+                "roofline": roofline, "cpu_baseline": cpu,
+                "e2e": {"value": e2e_val, "unit": METRIC, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                        "steps": min(args.steps, 4)},
+                "gpu_launches": int(launches), "clocks": clk,
+                "kernels": {k: {"launches": v[0], "ms": v[1]} for k, v in sorted(prof.items())}}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
@@ -701,165 +968,7 @@ def main():
             dist.init_process_group("gloo")
         run_reference(args, rank, world)
         return
-
-    import numpy as np
-    import torch
-
-    from paper_2601_23065_gb300 import api, build
-    from paper_2601_23065_gb300 import capi
-    from paper_2601_23065_gb300 import scenes as S
-
-    build.build()
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=dev)
-
-    def barrier():
-        if world > 1:
-            torch.distributed.barrier()
-
-    wl = S.workload(args.workload)
-    if args.spp:
-        wl.spp = args.spp
-    host_scene = wl.scene_fn()
-    cam = wl.camera
-    seed_base = rank_seed(rank)  # each rank renders its own samples
-    ds = api.DeviceScene.from_host(host_scene, device=dev)
-    r = api.Renderer(device=dev)
-    stream = torch.cuda.current_stream(dev)
-    L = capi.lib()
-
-    def step(seed):
-        bvh = api.BVH(ds, stream=stream)
-        out = r.path_traced(ds, bvh, cam, wl.spp, wl.max_bounces, rr_start=wl.rr_start, seed=seed, stream=stream)
-        return bvh, out
-
-    # untimed: counters of the work one step does (same seeds as timed)
-    bvh0 = api.BVH(ds, stream=stream)
-    cnt = r.path_traced(ds, bvh0, cam, wl.spp, wl.max_bounces, rr_start=wl.rr_start, seed=seed_base,
-                        want_stats=True)["stats"].cpu().numpy()
-    api.sync_status()
-    prim_segs, sec_segs = int(cnt[0]), int(cnt[1])
-    segs_per_step = prim_segs + sec_segs
-    paths = int(cnt[2])
-    del bvh0
-
-    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2 (129 MB)
-
-    for w in range(args.warmup):
-        step(seed_base)
-    torch.cuda.synchronize(dev)
-
-    # timed region
-    clocks = ClockSampler(local)
-    clocks.start()
-    launches0 = L.eagpt_launch_count()
-    capi.check(L.eagpt_profile_begin())
-    barrier()
-    torch.cuda.synchronize(dev)
-    times = []
-    for k in range(args.steps):
-        flush.fill_(float(k))  # L2 flush between steps (outside the step's events)
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        step(seed_base)
-        b.record(stream)
-        b.synchronize()
-        times.append(a.elapsed_time(b))
-    torch.cuda.synchronize(dev)
-    barrier()
-    prof = capi.profile_end()
-    launches = L.eagpt_launch_count() - launches0
-    clk = clocks.stop()
-    api.sync_status()
-
-    ms = sum(times) / len(times)
-    t_local = sum(times) / 1e3
-    t_max = max_over_ranks(t_local, world, dev)
-    value = job_value(world, segs_per_step, args.steps, t_max)
-
-    # roofline of the dominant kernel (the fused trace/shade/compact bounce)
-    kern = max(prof.items(), key=lambda kv: kv[1][1])
-    bounce = prof.get("k_bounce", (0, 0.0))
-    total_kernel_ms = sum(v[1] for v in prof.values())
-    peak, peak_kind = load_peaks()
-    # counters of the secondary segments: blended hits, nodes, surfel tests
-    cnt2 = r.path_traced(ds, api.BVH(ds), cam, wl.spp, wl.max_bounces, rr_start=wl.rr_start, seed=seed_base,
-                         want_stats=True)["stats"].cpu().numpy()
-    blended, nodes, tests, rounds = int(cnt2[3]), int(cnt2[4]), int(cnt2[5]), int(cnt2[6])
-    # lane work of the bounce batches against 32 x their slowest lane
-    balance = int(cnt2[12]) / max(1, int(cnt2[13]))
-    # per-segment algorithmic bytes: 48 B ray read + 48 B ray/slot write +
-    # 128 B per BVH4 node visit + 64 B per surfel test + 32 B per blended
-    # shade record
-    bounce_launches_per_step = bounce[0] / max(1, args.steps)
-    bounce_ms_per_launch = bounce[1] / max(1, bounce[0])
-    # bytes of the bounce launches only (secondary segments)
-    alg_bytes_bounce_launch = (96 * sec_segs + NODE_BYTES * nodes + 64 * tests + 32 * blended) / max(
-        1.0, bounce_launches_per_step)
-    achieved = alg_bytes_bounce_launch / (bounce_ms_per_launch * 1e-3) / 1e9 if bounce_ms_per_launch else None
-    per_seg_dram = load_traffic(args.workload)
-    # DRAM traffic of the bounce launches is the ray queues and slots, in
-    # proportion to the segments: scaled from the captured launch
-    traffic = per_seg_dram * sec_segs / max(1.0, bounce_launches_per_step) if per_seg_dram else None
-    roofline = {"bound": "hbm", "kernel": "k_bounce", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": (achieved / peak) if achieved else None, "traffic": traffic,
-                "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback",
-                "bytes_per_launch": alg_bytes_bounce_launch, "ms_per_launch": bounce_ms_per_launch,
-                "share_of_kernel_time": bounce[1] / total_kernel_ms if total_kernel_ms else None,
-                "per_secondary_segment": {"nodes": nodes / max(1, sec_segs), "tests": tests / max(1, sec_segs),
-                                          "blended": blended / max(1, sec_segs),
-                                          "rounds": rounds / max(1, sec_segs),
-                                          "warp_balance": balance},
-                "max_stack": int(cnt2[7])}
-
-    # end to end through the public API with host buffers
-    pinned = {k: torch.from_numpy(getattr(host_scene, k)).pin_memory() for k in api.FIELDS}
-    dev_t = {k: torch.empty_like(v, device=dev) for k, v in pinned.items()}
-    out_host = torch.empty((cam.height, cam.width, 3), dtype=torch.float32).pin_memory()
-    h2d = sum(v.numel() * 4 for v in pinned.values())
-    d2h = out_host.numel() * 4
-    e2e_times = []
-    for k in range(max(1, args.steps)):
-        flush.fill_(float(k))
-        torch.cuda.synchronize(dev)
-        t0 = time.perf_counter()
-        for kk in api.FIELDS:
-            dev_t[kk].copy_(pinned[kk], non_blocking=True)
-        dsk = api.DeviceScene(dev_t)
-        bvh = api.BVH(dsk, stream=stream)
-        out = r.path_traced(dsk, bvh, cam, wl.spp, wl.max_bounces, rr_start=wl.rr_start, seed=seed_base)
-        out_host.copy_(out["rgb"], non_blocking=True)
-        torch.cuda.synchronize(dev)
-        e2e_times.append(time.perf_counter() - t0)
-    e2e_val = world * segs_per_step / (sum(e2e_times) / len(e2e_times))
-
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(wl, host_scene, args.cpu_seconds)
-
-    if rank == 0:
-        line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
-                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": wl.name, "surfels": host_scene.n, "width": cam.width, "height": cam.height,
-                           "spp": wl.spp, "max_bounces": wl.max_bounces, "rr_start": wl.rr_start,
-                           "segments_per_step": segs_per_step, "primary_segments": prim_segs,
-                           "secondary_segments": sec_segs, "paths_per_step": paths,
-                           "rays_per_s": world * paths * args.steps / t_max,
-                           "step": "LBVH build + path-traced render",
-                           "l2": "flushed between steps (512 MB write)",
-                           "parallelism": f"replicas x{world} (independent samples per rank)"},
-                "roofline": roofline, "cpu_baseline": cpu,
-                "e2e": {"value": e2e_val, "unit": METRIC, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-                "gpu_launches": int(launches), "clocks": clk,
-                "kernels": {k: {"launches": v[0], "ms": v[1]} for k, v in sorted(prof.items())}}
-        print(json.dumps(line), flush=True)
-    if world > 1:
-        torch.distributed.destroy_process_group()
+    run_render(args, rank, world, local)
 
 
 if __name__ == "__main__":

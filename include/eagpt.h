@@ -188,14 +188,41 @@ eagpt_status eagpt_render_single_bounce(const eagpt_scene* scene, const eagpt_bv
  *           tests, traversal rounds
  *   [7]     deepest traversal stack of a secondary segment (maximum)
  *   [8..11] the same as [3..6] for the primary segments
- *   [12], [13] secondary batches of 32 rays: the lanes' work (nodes +
- *           tests) and 32 x the work of each batch's slowest lane. */
+ *   [12..15] unused (0). */
 eagpt_status eagpt_render_path_traced(const eagpt_scene* scene, const eagpt_bvh* bvh,
                                       const eagpt_camera* cam, const eagpt_params* params, int32_t spp,
                                       int32_t max_bounces, int32_t rr_start_bounce, uint64_t seed,
                                       float* out_rgb, float* out_aux, float* out_samples,
                                       int64_t* out_stats, void* workspace, size_t workspace_bytes,
                                       eagpt_stream_t stream);
+
+/* Segments traced by the last render into `workspace` (any of the render
+ * entry points above), kept without the counting variant:
+ *   out_segments[0] primary segments (one per pixel)
+ *   out_segments[1] secondary segments the bounce kernels traced (with
+ *                   emitter sampling: the continuations; emitter-sample
+ *                   segments are counted only by out_stats)
+ * host array of 2.  Synchronises `stream` (a 16-byte device-to-host copy).
+ * Not part of the method; it lets a caller report segments per second. */
+eagpt_status eagpt_render_segments(const void* workspace, int64_t* out_segments, eagpt_stream_t stream);
+
+/* Samples first_sample .. first_sample + spp - 1 of every pixel of the path-
+ * traced render (Eq. 8): the same paths, with the same Philox counters
+ * (pixel, sample, bounce), as those samples of eagpt_render_path_traced()
+ * with a larger spp, so a frame of S samples can be rendered as consecutive
+ * slices (progressive rendering) whose images, each the mean of its own
+ * samples, average to the frame's estimate.  out_rgb receives the slice's
+ * mean; out_samples (H x W x spp x 3) its samples in order.  Other arguments,
+ * buffers and errors as in eagpt_render_path_traced();
+ * EAGPT_ERR_INVALID_ARGUMENT if first_sample < 0 or first_sample + spp >
+ * 2^24. */
+eagpt_status eagpt_render_path_traced_range(const eagpt_scene* scene, const eagpt_bvh* bvh,
+                                            const eagpt_camera* cam, const eagpt_params* params,
+                                            int32_t first_sample, int32_t spp, int32_t max_bounces,
+                                            int32_t rr_start_bounce, uint64_t seed, float* out_rgb, float* out_aux,
+                                            float* out_samples, int64_t* out_stats, void* workspace,
+                                            size_t workspace_bytes, eagpt_stream_t stream);
+
 
 /* ------------------------------------------------------------------------
  * Scene editing (the paper's edits: relight / toggle emitters, recolour,
@@ -285,7 +312,11 @@ eagpt_status eagpt_insert_surfels(eagpt_scene_mut* scene, int64_t capacity, cons
  * remaining work first (pixels x samples left x bounces): one sample per
  * request while it fits, the longest-admitted request always included, then
  * the rest of the queue in shortest-remaining-work order, so small requests
- * do not wait on large ones and no request starves.  Submitted renders are admitted before
+ * do not wait on large ones and no request starves.  Two waves are in
+ * flight, each on its own stream with its own queues: the next wave is
+ * planned and enqueued while the current one runs, and its first bounces
+ * overlap the current wave's last ones.  A request completes when the wave
+ * holding its last samples has finished.  Submitted renders are admitted before
  * the next wave, in submission order, when one of max_active request slots
  * and arena memory for the request's primary records and sums (64 bytes per
  * pixel) are free.  A request's image equals, bit for bit, what
@@ -299,8 +330,12 @@ eagpt_status eagpt_insert_surfels(eagpt_scene_mut* scene, int64_t capacity, cons
  * storage belong to the server until eagpt_server_destroy() returns; the
  * final scene is in the slot eagpt_server_scene() reports.
  * Memory: all device memory comes from the caller's arena (device, 256-byte
- * aligned, eagpt_server_arena_bytes() for a start); nothing is allocated on
- * the device.  The server creates one CUDA stream of its own.
+ * aligned, eagpt_server_arena_bytes() for a start: the second scene version,
+ * per in-flight wave 112 bytes per queue path, plus 64 bytes per admitted
+ * pixel); nothing is allocated on the device.  At creation the server makes
+ * two CUDA streams and a few events of its own and allocates two small
+ * pinned host buffers (request tables and queue counters of the two waves).
+ * An edit is done once the device has applied it.
  * Failure handling: a request past its timeout (timeout_s > 0) ends as
  * TIMED_OUT; eagpt_server_wait() takes its own timeout and returns
  * EAGPT_ERR_TIMEOUT; a CUDA error fails the running requests.
@@ -371,12 +406,16 @@ eagpt_status eagpt_server_destroy(eagpt_server server);
  * into the library; every GPU that loads the library holds that array until
  * the process exits.  The call itself allocates nothing.
  *  - Size limit: a render whose smallest workspace (one sample per pass,
- *    eagpt_render_workspace_min_bytes()) exceeds the scratch is rejected with
- *    EAGPT_ERR_INVALID_ARGUMENT and a message naming both sizes.  Larger
+ *    eagpt_render_workspace_min_bytes(), of kind 2 with emitter sampling)
+ *    exceeds the scratch is rejected with EAGPT_ERR_INVALID_ARGUMENT and a
+ *    message naming both sizes.  Larger
  *    renders fit in fewer samples per pass; results do not depend on it.
  *  - Set-up: the first call on each device looks up the scratch's device
  *    address (cudaGetSymbolAddress, with that device current) and caches it;
- *    make that first call before any stream capture begins.
+ *    make that first call before any stream capture begins.  The cached
+ *    address is that of the device's context at the first call: a process
+ *    that resets the device (cudaDeviceReset) must not call this entry point
+ *    on that device afterwards.
  *  - Sharing: all calls on a device share the one scratch array, which keeps
  *    the last call's contents (the render zeroes what it needs zeroed).  Calls
  *    whose work overlaps on the GPU (different streams, or different host

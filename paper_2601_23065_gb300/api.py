@@ -119,10 +119,13 @@ class Renderer:
 
     def path_traced(self, scene: DeviceScene, bvh: BVH, cam: HostCamera, spp: int, max_bounces: int,
                     rr_start: int = 2, seed: int = 0, prm: Optional[capi.Params] = None, want_aux=False,
-                    want_samples=False, want_stats=False, out: Optional[torch.Tensor] = None, stream=None):
+                    want_samples=False, want_stats=False, out: Optional[torch.Tensor] = None, stream=None,
+                    first_sample: int = 0):
         """Eq. 8 render; returns dict(rgb (H,W,3)[, aux (H,W,12)][, samples (H,W,spp,3)][, stats]).
         With ``prm.flags`` containing capi.FLAG_EMITTER_SAMPLING the path
-        tracer samples emitters at every reflection (MIS)."""
+        tracer samples emitters at every reflection (MIS).  ``first_sample``
+        > 0 renders samples first_sample .. first_sample + spp - 1 of each
+        pixel (a slice of a longer frame, same paths as in the full render)."""
         c = camera(cam)
         prm = prm or bvh.params
         ws = self._workspace(c, spp, 2 if prm.flags & capi.FLAG_EMITTER_SAMPLING else 1)
@@ -132,10 +135,16 @@ class Renderer:
         smp = torch.empty((H, W, spp, 3), dtype=torch.float32, device=self.device) if want_samples else None
         st = torch.zeros(16, dtype=torch.int64, device=self.device) if want_stats else None
         sc = scene.c()
-        capi.check(capi.lib().eagpt_render_path_traced(
-            ctypes.byref(sc), ctypes.byref(bvh.c()), ctypes.byref(c), ctypes.byref(prm), int(spp), int(max_bounces),
-            int(rr_start), ctypes.c_uint64(int(seed)), _ptr(rgb), _ptr(aux), _ptr(smp), _ptr(st), _ptr(ws),
-            ws.numel(), _stream(stream)))
+        if first_sample:
+            capi.check(capi.lib().eagpt_render_path_traced_range(
+                ctypes.byref(sc), ctypes.byref(bvh.c()), ctypes.byref(c), ctypes.byref(prm), int(first_sample),
+                int(spp), int(max_bounces), int(rr_start), ctypes.c_uint64(int(seed)), _ptr(rgb), _ptr(aux),
+                _ptr(smp), _ptr(st), _ptr(ws), ws.numel(), _stream(stream)))
+        else:
+            capi.check(capi.lib().eagpt_render_path_traced(
+                ctypes.byref(sc), ctypes.byref(bvh.c()), ctypes.byref(c), ctypes.byref(prm), int(spp),
+                int(max_bounces), int(rr_start), ctypes.c_uint64(int(seed)), _ptr(rgb), _ptr(aux), _ptr(smp),
+                _ptr(st), _ptr(ws), ws.numel(), _stream(stream)))
         r = {"rgb": rgb}
         if want_aux:
             r["aux"] = aux
@@ -144,6 +153,13 @@ class Renderer:
         if want_stats:
             r["stats"] = st
         return r
+
+    def segments(self, stream=None):
+        """(primary, secondary) segments traced by this renderer's last render
+        (synchronises the stream)."""
+        out = (ctypes.c_int64 * 2)()
+        capi.check(capi.lib().eagpt_render_segments(_ptr(self.ws), ctypes.cast(out, ctypes.c_void_p), _stream(stream)))
+        return int(out[0]), int(out[1])
 
     def single_bounce(self, scene: DeviceScene, bvh: BVH, cam: HostCamera, spp: int, seed: int = 0,
                       prm: Optional[capi.Params] = None, want_aux=False, want_samples=False, want_cache=False,

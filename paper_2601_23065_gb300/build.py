@@ -52,7 +52,7 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
     """Compile and link; returns the library path.  Skips when the sources and
     flags are unchanged since the last build.  Extra nvcc flags may also come
     from the EAGPT_NVCC_FLAGS environment variable (space-separated), e.g.
-    tuning macros such as -DEAGPT_LEAF_MAX=2."""
+    e.g. -DNDEBUG."""
     env_flags = tuple(os.environ.get("EAGPT_NVCC_FLAGS", "").split())
     extra_flags = tuple(extra_flags) + env_flags
     os.makedirs(OUT_DIR, exist_ok=True)

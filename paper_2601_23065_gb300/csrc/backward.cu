@@ -24,14 +24,8 @@ namespace eagpt {
 
 EAGPT_DEFINE_ERROR_READER(take_errors_backward)
 
-#ifndef EAGPT_BWD_KBUF
-#define EAGPT_BWD_KBUF 12
-#endif
-#ifndef EAGPT_BWD_MIN_BLOCKS
-#define EAGPT_BWD_MIN_BLOCKS 5
-#endif
-constexpr int kKb = EAGPT_BWD_KBUF;             // k-buffer of the adjoint's traversals
-constexpr int kBwdMinBlocks = EAGPT_BWD_MIN_BLOCKS;  // resident blocks per SM of the secondary adjoint
+constexpr int kKb = 12;           // k-buffer of the adjoint's traversals
+constexpr int kBwdMinBlocks = 5;  // resident blocks per SM of the secondary adjoint
 
 struct __align__(16) PrimRecB {
   float4 a, b, c;  // same layout as the forward's primary record
@@ -215,16 +209,12 @@ __device__ __forceinline__ float3 cosine_direction_adjoint(float3 n, float u0, f
   return l0 * g1 + l1 * g2 + l2 * dw;
 }
 
-// kCached: the forward stored each sample's secondary R and T (sample-major,
-// written by the single-bounce render from the same bit-identical blend), so
-// the values pass is read instead of traced; T < 1 exactly when the segment
-// blended a hit (alpha >= alpha_min > 0).
-template <bool kCached>
+// Re-tracing form (no forward sample cache): the secondary segment is traced
+// once for its blended R and T, then again for the adjoint.
 __global__ void __launch_bounds__(kBlock, kBwdMinBlocks) k_bwd_secondary(BvhView bvh, Consts C, eagpt_camera cam, eagpt_scene sc,
                                                           eagpt_scene_grad gr, const PrimRecB* __restrict__ prim,
                                                           const float* __restrict__ dL, int spp, uint64_t seed,
-                                                          int64_t npix, int s0, int batch, float4* per_sample,
-                                                          const float4* __restrict__ sb_cache) {
+                                                          int64_t npix, int s0, int batch, float4* per_sample) {
   __shared__ uint32_t s_stack[kStackSize * kBlock];
   const int64_t t = blockIdx.x * (int64_t)kBlock + threadIdx.x;
   if (t >= npix * (int64_t)batch) return;
@@ -244,14 +234,7 @@ __global__ void __launch_bounds__(kBlock, kBwdMinBlocks) k_bwd_secondary(BvhView
     TraceCounters cnt{0, 0, 0, 0, 0};
     // the secondary segment enters the pixel only through its R (Eq. 6)
     RBlendVisitor v1(bvh.shade, C, 0);
-    if (kCached) {
-      const float4 c = sb_cache[(int64_t)sample * npix + pixel];
-      v1.R = make_float3(c.x, c.y, c.z);
-      v1.T = c.w;
-      v1.n_hits = c.w < 1.f ? 1u : 0u;
-    } else {
-      trace_segment<kKb, false>(bvh, C, O2, w2, 0.f, s_stack + threadIdx.x, kBlock, v1, cnt);
-    }
+    trace_segment<kKb, false>(bvh, C, O2, w2, s_stack + threadIdx.x, kBlock, v1, cnt);
     const float invS = 1.f / (float)spp;
     const float3 g = make_float3(dL[3 * pixel], dL[3 * pixel + 1], dL[3 * pixel + 2]);
     const float3 P1 = make_float3(p.c.x, p.c.y, p.c.z);
@@ -272,7 +255,7 @@ __global__ void __launch_bounds__(kBlock, kBwdMinBlocks) k_bwd_secondary(BvhView
       av.V.T = v1.T;
       init_blend(av.run);
       av.dO = av.dw = make_float3(0.f, 0.f, 0.f);
-      trace_segment<kKb, false>(bvh, C, O2, w2, 0.f, s_stack + threadIdx.x, kBlock, av, cnt);
+      trace_segment<kKb, false>(bvh, C, O2, w2, s_stack + threadIdx.x, kBlock, av, cnt);
       // O2 = O + D~1 w + offset N~1 ; w2 = basis(N~1) l
       const float gDn = dot3(av.dO, w);
       const float3 gNn = C.bounce_offset * av.dO + cosine_direction_adjoint(Nn, u.x, u.y, av.dw);
@@ -285,15 +268,16 @@ __global__ void __launch_bounds__(kBlock, kBwdMinBlocks) k_bwd_secondary(BvhView
   per_sample[2 * t + 1] = outB;
 }
 
-// The cached adjoint of the secondary segments as a persistent kernel with
-// per-lane refill (as the forward bounce kernel): a lane whose sample is done
-// takes the next one, and traversal runs in chunks of kBwdSteps node or leaf
-// steps, so lanes of a warp do not idle while one traces a long segment.
-// Per sample it computes what k_bwd_secondary<true> computes, in the same
-// order of blended hits.
-#ifndef EAGPT_BWD_REFILL
-#define EAGPT_BWD_REFILL 1
-#endif
+// The cached adjoint of the secondary segments: the forward stored each
+// sample's secondary R and T (sample-major, written by the single-bounce
+// render from the same bit-identical blend), so the values pass is read
+// instead of traced (T < 1 exactly when the segment blended a hit, alpha >=
+// alpha_min > 0).  Persistent with per-lane refill, as the forward bounce
+// kernel: a lane whose sample is done takes the next one, and traversal runs
+// in chunks of kBwdSteps node or leaf steps, so lanes of a warp do not idle
+// while one traces a long segment.  Per sample it computes what
+// k_bwd_secondary computes after its values trace, in the same order of
+// blended hits.
 constexpr int kBwdSteps = 64;
 
 __global__ void __launch_bounds__(kBlock, kBwdMinBlocks) k_bwd_secondary_r(BvhView bvh, Consts C, eagpt_camera cam, eagpt_scene sc,
@@ -351,8 +335,7 @@ __global__ void __launch_bounds__(kBlock, kBwdMinBlocks) k_bwd_secondary_r(BvhVi
               av.V.T = c.w;
               init_blend(av.run);
               av.dO = av.dw = make_float3(0.f, 0.f, 0.f);
-              ray_begin(rt, O2, w2);
-              round_begin(rt, bvh);
+              ray_begin(rt, O2, w2, bvh);
               active = true;
             }
           }
@@ -386,7 +369,7 @@ __global__ void __launch_bounds__(kBlock, kBwdMinBlocks) k_bwd_secondary_r(BvhVi
         per_sample[2 * t + 1] = make_float4(gP1.x, gP1.y, gP1.z, 0.f);
         active = false;
       } else {
-        round_begin(rt, bvh);
+        round_next(rt, bvh);
       }
     }
   }
@@ -425,7 +408,7 @@ __global__ void __launch_bounds__(kBlock) k_bwd_primary(BvhView bvh, Consts C, e
   camera_ray(cam, (uint32_t)i, O, w);
   TraceCounters cnt{0, 0, 0, 0, 0};
   RawVisitor v1(bvh.shade, C, w, 0);
-  trace_segment<kKb, false>(bvh, C, O, w, 0.f, s_stack + threadIdx.x, kBlock, v1, cnt);
+  trace_segment<kKb, false>(bvh, C, O, w, s_stack + threadIdx.x, kBlock, v1, cnt);
   const Blend& V = v1.blend.b;
   AdjointVisitor av;
   av.shade = bvh.shade;
@@ -458,7 +441,7 @@ __global__ void __launch_bounds__(kBlock) k_bwd_primary(BvhView bvh, Consts C, e
     av.gP = f3(b);
     av.gR = make_float3(0.f, 0.f, 0.f);
   }
-  trace_segment<kKb, false>(bvh, C, O, w, 0.f, s_stack + threadIdx.x, kBlock, av, cnt);
+  trace_segment<kKb, false>(bvh, C, O, w, s_stack + threadIdx.x, kBlock, av, cnt);
 }
 
 // --------------------------------------------------------------------------
@@ -516,26 +499,18 @@ cudaError_t launch_backward(const BvhView& bvh, const Consts& C, const eagpt_cam
   if (e != cudaSuccess) return e;
   for (int s0 = 0; s0 < spp; s0 += batch) {
     const int n = spp - s0 < batch ? spp - s0 : batch;
-    if (sb_cache && EAGPT_BWD_REFILL) {
-      static int grid = 0;
-      if (!grid) {
-        int per_sm = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bwd_secondary_r, kBlock, 0);
-        grid = (per_sm > 0 ? per_sm : 1) * device_sms();
-      }
+    if (sb_cache) {
       uint32_t* counter = (uint32_t*)(base + L.counter);
-      cudaMemsetAsync(counter, 0, sizeof(uint32_t), st);
+      e = cudaMemsetAsync(counter, 0, sizeof(uint32_t), st);
+      if (e != cudaSuccess) return e;
       EAGPT_LAUNCH(st, "k_bwd_secondary",
-                   k_bwd_secondary_r<<<grid, kBlock, 0, st>>>(bvh, C, cam, sc, gr, prim, dL, spp, seed, npix, s0, n, per,
-                                                              sb_cache, counter));
-    } else if (sb_cache)
+                   k_bwd_secondary_r<<<persistent_grid((const void*)k_bwd_secondary_r), kBlock, 0, st>>>(
+                       bvh, C, cam, sc, gr, prim, dL, spp, seed, npix, s0, n, per, sb_cache, counter));
+    } else {
       EAGPT_LAUNCH(st, "k_bwd_secondary",
-                   k_bwd_secondary<true><<<nb(npix * n), kBlock, 0, st>>>(bvh, C, cam, sc, gr, prim, dL, spp, seed, npix,
-                                                                          s0, n, per, sb_cache));
-    else
-      EAGPT_LAUNCH(st, "k_bwd_secondary",
-                   k_bwd_secondary<false><<<nb(npix * n), kBlock, 0, st>>>(bvh, C, cam, sc, gr, prim, dL, spp, seed,
-                                                                           npix, s0, n, per, nullptr));
+                   k_bwd_secondary<<<nb(npix * n), kBlock, 0, st>>>(bvh, C, cam, sc, gr, prim, dL, spp, seed, npix, s0,
+                                                                    n, per));
+    }
     EAGPT_LAUNCH(st, "k_bwd_reduce", k_bwd_reduce<<<nb(npix), kBlock, 0, st>>>(npix, n, s0 == 0, per, acc));
   }
   EAGPT_LAUNCH(st, "k_bwd_primary",
@@ -558,7 +533,7 @@ __global__ void __launch_bounds__(kBlock) k_radiance_bwd(BvhView bvh, Consts C, 
   camera_ray(cam, (uint32_t)i, O, w);
   TraceCounters cnt{0, 0, 0, 0, 0};
   RBlendVisitor v1(bvh.shade, C, 0);
-  trace_segment<kKb, false>(bvh, C, O, w, 0.f, s_stack + threadIdx.x, kBlock, v1, cnt);
+  trace_segment<kKb, false>(bvh, C, O, w, s_stack + threadIdx.x, kBlock, v1, cnt);
   if (v1.n_hits == 0) return;
   AdjointVisitorT<true> av;
   av.shade = bvh.shade;
@@ -576,7 +551,7 @@ __global__ void __launch_bounds__(kBlock) k_radiance_bwd(BvhView bvh, Consts C, 
   av.gN = av.gP = make_float3(0.f, 0.f, 0.f);
   av.gR = make_float3(dL[3 * i], dL[3 * i + 1], dL[3 * i + 2]);
   av.gD = av.gA = 0.f;
-  trace_segment<kKb, false>(bvh, C, O, w, 0.f, s_stack + threadIdx.x, kBlock, av, cnt);
+  trace_segment<kKb, false>(bvh, C, O, w, s_stack + threadIdx.x, kBlock, av, cnt);
 }
 
 cudaError_t launch_radiance_backward(const BvhView& bvh, const Consts& C, const eagpt_camera& cam,

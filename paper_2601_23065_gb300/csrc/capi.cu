@@ -96,8 +96,6 @@ BvhView make_view(const eagpt_bvh& b) {
     v.trace = (const TraceRec*)(base + L.trace);
     v.shade = (const ShadeRec*)(base + L.shade);
     v.nodes = (const Node4*)(base + L.nodes);
-    v.nodes8 = (const Node8*)(base + L.nodes);
-    v.nodes4q = (const Node4q*)(base + L.nodes);
     v.root = 0;  // node 0: Karras root, or the single node of a small scene
     v.bounds_bits = (const uint32_t*)(base + L.header);
     v.hdr = (const BvhHeader*)(base + L.header);
@@ -194,13 +192,15 @@ static eagpt_status render_common(const eagpt_scene* scene, const eagpt_bvh* bvh
                                   const eagpt_params* params, int kind, int32_t spp, int32_t max_bounces,
                                   int32_t rr_start, uint64_t seed, float* out_rgb, float* out_aux, float* out_samples,
                                   int64_t* out_stats, void* ws, size_t ws_bytes, eagpt_stream_t stream,
-                                  float* out_li = nullptr, float4* sb_cache = nullptr) {
+                                  float* out_li = nullptr, float4* sb_cache = nullptr, int32_t first_sample = 0) {
   eagpt_status s;
   if ((s = check_scene(scene)) != EAGPT_OK) return s;
   if ((s = check_params(params)) != EAGPT_OK) return s;
   if ((s = check_camera(cam)) != EAGPT_OK) return s;
   if ((s = check_bvh(bvh, scene, params)) != EAGPT_OK) return s;
   if (spp <= 0 || spp > (1 << 24)) return fail(EAGPT_ERR_INVALID_ARGUMENT, "spp must be in [1, 2^24]%s");
+  if (first_sample < 0 || (int64_t)first_sample + spp > (int64_t)1 << 24)
+    return fail(EAGPT_ERR_INVALID_ARGUMENT, "first_sample must be >= 0 with first_sample + spp <= 2^24%s");
   if (kind == 1 && (max_bounces < 0 || max_bounces > 60))
     return fail(EAGPT_ERR_INVALID_ARGUMENT, "max_bounces must be in [0, 60]%s");
   if (!out_rgb) return fail(EAGPT_ERR_INVALID_ARGUMENT, "out_rgb is NULL%s");
@@ -217,6 +217,7 @@ static eagpt_status render_common(const eagpt_scene* scene, const eagpt_bvh* bvh
   a.kind = kind == 0 && out_li ? 2 : kind;
   a.out_li = out_li;
   a.spp = spp;
+  a.s_first = first_sample;
   a.max_bounces = kind == 0 ? 1 : max_bounces;
   a.rr_start = kind == 0 ? (1 << 30) : rr_start;
   a.seed = seed;
@@ -270,6 +271,24 @@ eagpt_status eagpt_render_path_traced(const eagpt_scene* scene, const eagpt_bvh*
                                       size_t workspace_bytes, eagpt_stream_t stream) {
   return render_common(scene, bvh, cam, params, 1, spp, max_bounces, rr_start_bounce, seed, out_rgb, out_aux,
                        out_samples, out_stats, workspace, workspace_bytes, stream);
+}
+
+eagpt_status eagpt_render_segments(const void* workspace, int64_t* out_segments, eagpt_stream_t stream) {
+  if (!workspace || !aligned(workspace, 256) || !out_segments)
+    return fail(EAGPT_ERR_INVALID_ARGUMENT, "workspace (256-byte aligned) and out_segments are required%s");
+  const cudaError_t e = render_summary(workspace, out_segments, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "segment summary read");
+  return EAGPT_OK;
+}
+
+eagpt_status eagpt_render_path_traced_range(const eagpt_scene* scene, const eagpt_bvh* bvh,
+                                            const eagpt_camera* cam, const eagpt_params* params,
+                                            int32_t first_sample, int32_t spp, int32_t max_bounces,
+                                            int32_t rr_start_bounce, uint64_t seed, float* out_rgb, float* out_aux,
+                                            float* out_samples, int64_t* out_stats, void* workspace,
+                                            size_t workspace_bytes, eagpt_stream_t stream) {
+  return render_common(scene, bvh, cam, params, 1, spp, max_bounces, rr_start_bounce, seed, out_rgb, out_aux,
+                       out_samples, out_stats, workspace, workspace_bytes, stream, nullptr, nullptr, first_sample);
 }
 
 size_t eagpt_render_backward_workspace_bytes(const eagpt_camera* cam, int32_t spp) {
@@ -329,7 +348,6 @@ eagpt_status eagpt_render_single_bounce_cached(const eagpt_scene* scene, const e
                                                const eagpt_camera* cam, const eagpt_params* params, int32_t spp,
                                                uint64_t seed, float* out_rgb, float* sample_cache, void* ws,
                                                size_t ws_bytes, eagpt_stream_t stream) {
-  if (!render_has_refill()) return fail(EAGPT_ERR_NOT_SUPPORTED, "the sample cache needs the refill bounce kernel%s");
   if (!sample_cache || !aligned(sample_cache, 16))
     return fail(EAGPT_ERR_INVALID_ARGUMENT, "sample_cache must be non-NULL and 16-byte aligned%s");
   return render_common(scene, bvh, cam, params, 0, spp, 1, 0, seed, out_rgb, nullptr, nullptr, nullptr, ws, ws_bytes,

@@ -12,18 +12,9 @@ namespace eagpt {
 // ---------------------------------------------------------------------------
 // Sizes and encodings
 // ---------------------------------------------------------------------------
-#ifndef EAGPT_LEAF_MAX
-#define EAGPT_LEAF_MAX 1
-#endif
-constexpr int kLeafMax = EAGPT_LEAF_MAX;  // surfels per BVH leaf (1..4)
-#ifndef EAGPT_STACK
-#define EAGPT_STACK 48
-#endif
-constexpr int kStackSize = EAGPT_STACK;  // traversal stack entries per ray
-#ifndef EAGPT_MIN_BLOCKS
-#define EAGPT_MIN_BLOCKS 6
-#endif
-constexpr int kMinBlocks = EAGPT_MIN_BLOCKS;  // resident trace blocks per SM the compiler must allow
+constexpr int kLeafMax = 1;  // surfels per BVH leaf
+constexpr int kStackSize = 48;  // traversal stack entries per ray (shared memory)
+constexpr int kMinBlocks = 6;  // resident trace blocks per SM the compiler must allow
 constexpr int kBlock = 128;          // threads per block of the trace kernels
 constexpr uint32_t kLeafBit = 0x80000000u;
 constexpr int kLeafCountShift = 29;  // leaf: bit31 | (count-1) << 29 | start
@@ -65,43 +56,6 @@ struct __align__(128) Node4 {
   uint4 child;
   uint4 pad;
 };
-
-// Quantised BVH4 node, 64 B (four 16-byte loads): per axis the children's
-// bounds as 8-bit multiples q of a power of two 2^e above the node's origin,
-// decoded as fma(q, 2^e, origin), rounded outward and checked against that
-// exact decode when built.
-//   u0 = (origin.x, origin.y, origin.z, exps)  exps bytes 0..2: biased e per axis
-//   u1 = child links 0..3
-//   u2 = (qlo.x, qlo.y, qlo.z, 0), byte k of a word = child k
-//   u3 = (qhi.x, qhi.y, qhi.z, 0)
-struct __align__(64) Node4q {
-  uint4 u0, u1, u2, u3;
-};
-
-// BVH8 node, 96 B (six 16-byte loads): eight child links and eight child
-// boxes quantised to 8 bits per bound relative to the node's box.
-//   u0 = (origin.x, origin.y, origin.z, exps)  exps bytes 0..2: biased
-//        exponents e of the per-axis quantum 2^(e - 127)
-//   u1, u2 = child links 0..3, 4..7
-//   u3 = qlo.x[0..7], qlo.y[0..7]; u4 = qlo.z[0..7], qhi.x[0..7];
-//   u5 = qhi.y[0..7], qhi.z[0..7]   (bytes)
-// A child box decodes as origin + q * quantum (fused multiply-add); the
-// build rounds lower bounds down and upper bounds up, checked against this
-// exact decode, so decoded boxes contain the true ones.
-struct __align__(16) Node8 {
-  uint4 u0, u1, u2, u3, u4, u5;
-};
-
-#ifndef EAGPT_BVH8
-#define EAGPT_BVH8 0
-#endif
-constexpr bool kBvh8 = EAGPT_BVH8 != 0;
-// quantised 64-byte BVH4 nodes instead of 128-byte ones
-#ifndef EAGPT_QNODE4
-#define EAGPT_QNODE4 0
-#endif
-constexpr bool kQ4 = EAGPT_QNODE4 != 0 && !kBvh8;
-constexpr int kBvhWidth = kBvh8 ? 8 : 4;
 
 constexpr int kMaxCollapseLevels = 96;  // BVH levels built top-down
 
@@ -176,9 +130,7 @@ inline BvhLayout bvh_layout(int64_t n) {
 struct BvhView {
   const TraceRec* trace;
   const ShadeRec* shade;
-  const Node4* nodes;    // BVH4 nodes (kBvh8 == false)
-  const Node8* nodes8;   // BVH8 nodes (kBvh8 == true), same storage
-  const Node4q* nodes4q; // quantised BVH4 nodes (kQ4 == true), same storage
+  const Node4* nodes;    // BVH4 nodes
   uint32_t root;  // node index, or an encoded leaf when n <= kLeafMax
   int64_t n;
   const uint32_t* bounds_bits;  // scene centroid bounds (BvhHeader), ordered-int encoded

@@ -29,6 +29,7 @@ struct RenderArgs {
   eagpt_camera cam;
   int kind;         // 0 single bounce, 1 path tracing, 2 single bounce with incident radiance (out_li)
   int spp, max_bounces, rr_start;
+  int s_first;      // samples s_first .. s_first + spp - 1 of each pixel are rendered
   uint64_t seed;
   float* out_rgb;
   float* out_aux;
@@ -41,7 +42,7 @@ struct RenderArgs {
 };
 
 struct RenderLayout {
-  size_t prim, acc, slots, q0, q1, counters, e0, e1, sk0, sk1, sv0, sv1, shist, total;
+  size_t summary, prim, acc, slots, q0, q1, counters, e0, e1, total;
   int64_t npix, batch_paths;
   int batch_spp;
 };
@@ -50,7 +51,7 @@ struct RenderLayout {
 RenderLayout render_layout(int64_t npix, int spp, int batch_spp, bool mis = false);
 int choose_batch_spp(int64_t npix, int spp, size_t ws_bytes, bool mis = false);
 cudaError_t launch_render(const RenderArgs& a, cudaStream_t st, int* launches);
-bool render_has_refill();  // the bounce kernel is the per-lane refill form
+cudaError_t render_summary(const void* ws, int64_t* out, cudaStream_t st);
 cudaError_t launch_trace_rays(const BvhView& bvh, const Consts& C, int mode, const float* rays, int64_t n_rays,
                               float* out_rec, int32_t* out_hits, int max_hits, int32_t* out_nhits, cudaStream_t st);
 
@@ -110,6 +111,9 @@ eagpt_status apply_edit_core(eagpt_scene_mut* scene, eagpt_bvh* bvh, const eagpt
 
 // number of SMs of the current device (cached per device)
 int device_sms();
+// blocks of a persistent launch of a kBlock-thread kernel on the current
+// device (resident blocks per SM x SMs; cached per kernel and device)
+int persistent_grid(const void* kernel);
 
 // profiler.cu: every kernel launch goes through a LaunchScope (counts the
 // launch; with profiling on, records CUDA events around it on its stream)

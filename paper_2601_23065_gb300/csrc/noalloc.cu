@@ -30,7 +30,9 @@ void* g_scratch_ptr[64] = {nullptr};
 }  // namespace
 
 // Device address of the scratch on the current device, looked up once per
-// device (with that device current) and cached.
+// device (with that device current) and cached.  The address belongs to the
+// device's context as it was at that first call; a device reset invalidates
+// it (documented in the header).
 static cudaError_t scratch_address(void** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -61,8 +63,10 @@ eagpt_status eagpt_render_path_traced_noalloc(const eagpt_scene* scene, const ea
                                               float* out_rgb, eagpt_stream_t stream) {
   if (!cam || cam->width <= 0 || cam->height <= 0 || spp <= 0)
     return set_error(EAGPT_ERR_INVALID_ARGUMENT, "camera size and spp must be positive");
-  // smallest workspace the render accepts: one sample per pass
-  const size_t need = eagpt_render_workspace_min_bytes(cam, spp, 1);
+  // smallest workspace the render accepts: one sample per pass (emitter
+  // sampling needs two more ray queues)
+  const int kind = params && (params->flags & EAGPT_FLAG_EMITTER_SAMPLING) ? 2 : 1;
+  const size_t need = eagpt_render_workspace_min_bytes(cam, spp, kind);
   if (need > kNoAllocScratchBytes) {
     char buf[256];
     std::snprintf(buf, sizeof(buf),

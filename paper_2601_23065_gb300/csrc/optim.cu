@@ -128,7 +128,7 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_shade_adjoint(BvhView bv
   camera_ray(cam, (uint32_t)i, O, w);
   ShadeAdjointVisitor v{C, g, grad, 1.f};
   TraceCounters cnt{0, 0, 0, 0, 0};
-  trace_segment<16, false>(bvh, C, O, w, 0.f, s_stack + threadIdx.x, kBlock, v, cnt);
+  trace_segment<16, false>(bvh, C, O, w, s_stack + threadIdx.x, kBlock, v, cnt);
 }
 
 struct AdamArgs {

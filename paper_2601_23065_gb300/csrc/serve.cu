@@ -7,6 +7,14 @@
 // samples into its own pixels in sample order.  Requests submitted while a
 // wave runs are admitted before the next wave when a request slot and arena
 // memory are free, so their paths share the device with the running ones.
+// Two waves are in flight, each on its own stream with its own ray queues,
+// per-sample values and request table: the host plans and enqueues wave
+// n + 1 while wave n runs, so wave n + 1's first bounces fill the GPU while
+// wave n's last, short bounces drain, and the host learns of a wave's end
+// from a CUDA event.  Only the accumulation is ordered across the streams (a
+// request's running sums take its waves in order), and a request's primary
+// records are made visible to both streams when it is admitted.  A request is
+// done when the wave that holds its last samples has finished.
 // A path's arithmetic and its random numbers depend only on its request
 // (seed, pixel, sample, bounce), and every pixel adds its samples in order,
 // so a request's image is bitwise the same alone and in any mix.
@@ -42,10 +50,7 @@ EAGPT_DEFINE_ERROR_READER(take_errors_serve)
 constexpr int kSrvMaxActive = 64;
 constexpr int kSrvMaxBounces = 60;
 constexpr int kSrvCounterWords = 2 * (kSrvMaxBounces + 2) + 8;
-#ifndef EAGPT_SERVE_KBUF
-#define EAGPT_SERVE_KBUF 12
-#endif
-constexpr int kSrvK = EAGPT_SERVE_KBUF;
+constexpr int kSrvK = 12;  // k-buffer of the traversal rounds
 
 struct __align__(16) ReqDev {
   eagpt_camera cam;
@@ -124,8 +129,7 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_srv_bounce(BvhView v0, B
           qi = idx;
           rq = __float_as_uint(q_in[qi].c.w);
           const BvhView& bvh = reqs[rq].version ? v1 : v0;
-          ray_begin(rt, f3(q_in[qi].a), f3(q_in[qi].b));
-          round_begin(rt, bvh);
+          ray_begin(rt, f3(q_in[qi].a), f3(q_in[qi].b), bvh);
           vis.shade = bvh.shade;
           vis.reset();
           active = true;
@@ -152,7 +156,7 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_srv_bounce(BvhView v0, B
                 make_float4(contrib.x, contrib.y, contrib.z, 0.f);
           active = false;
         } else {
-          round_begin(rt, bvh);
+          round_next(rt, bvh);
         }
       }
     }
@@ -268,6 +272,7 @@ struct Req {
   int s_next = 0;
   size_t off = 0, bytes = 0;
   int32_t rebuilt = 0;
+  int inflight = 0;  // waves in flight that hold samples of this request
 };
 
 }  // namespace
@@ -280,12 +285,38 @@ struct Server {
   int current = 0;
   int users[2] = {0, 0};  // running renders per version
   char* base = nullptr;
-  cudaStream_t stream = nullptr;
-  Ray* q[2] = {nullptr, nullptr};
-  float4* slots = nullptr;  // per-sample values of one wave, queue_cap of them
-  uint32_t* counters = nullptr;
-  ReqDev* table = nullptr;
+  // per wave slot: stream, two ray queues, per-sample values (queue_cap of
+  // them), queue counters
+  cudaStream_t streams[2] = {nullptr, nullptr};
+  Ray* q[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+  float4* slots[2] = {nullptr, nullptr};
+  uint32_t* counters[2] = {nullptr, nullptr};
   int64_t queue_cap = 0;
+  cudaEvent_t ev_ref = nullptr;   // time origin of the busy-time account
+  cudaEvent_t ev_sync = nullptr;  // cross-stream ordering (admission, edits)
+  cudaEvent_t ev_acc[2] = {nullptr, nullptr};
+  float last_done_ms = 0.f;
+  // the two waves in flight: device request tables, their pinned host
+  // sources, pinned copies of the wave's queue counters, start and end events
+  struct Wave {
+    bool busy = false;
+    std::vector<uint64_t> ids;   // requests in the wave
+    std::vector<char> last;      // the wave holds the request's last samples
+    int64_t paths = 0, pixels = 0;
+    int max_b = 0;
+  };
+  ReqDev* table_d[2] = {nullptr, nullptr};
+  ReqDev* table_h[2] = {nullptr, nullptr};
+  uint32_t* cnt_h[2] = {nullptr, nullptr};
+  cudaEvent_t ev_start[2] = {nullptr, nullptr}, ev_done[2] = {nullptr, nullptr};
+  // makes the other stream wait for what `from` has enqueued so far
+  cudaError_t join_other(int from) {
+    cudaError_t e = cudaEventRecord(ev_sync, streams[from]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(streams[from ^ 1], ev_sync, 0);
+    return e;
+  }
+  Wave wv[2];
+  int next_slot = 0, oldest = 0, in_flight = 0;
   Arena arena;
   std::mutex mu;
   std::condition_variable cv_work, cv_done;
@@ -302,7 +333,11 @@ struct Server {
   bool admit_locked(Req& r);
   void finish_locked(Req& r, int32_t state);
   bool apply_edit_locked(Req& r, std::unique_lock<std::mutex>& lk);
-  void wave(std::unique_lock<std::mutex>& lk);
+  bool plannable_locked() const;
+  void release_cancelled_locked(Req& r);
+  void enqueue_wave(std::unique_lock<std::mutex>& lk);
+  void complete_oldest(std::unique_lock<std::mutex>& lk);
+  void fail_all_locked(cudaError_t e);
 };
 
 static size_t scene_bytes(int64_t n) { return align256((size_t)(n > 0 ? n : 1) * 19 * sizeof(float)); }
@@ -326,7 +361,8 @@ bool Server::admit_locked(Req& r) {
   active.push_back(r.id);
   // primary records of the request on its scene version
   PrimRec* prim = (PrimRec*)(base + off);
-  launch_primary_records(bvh_view(bvh[current]), make_consts(params), r.rr.cam, 1, npix, prim, stream);
+  launch_primary_records(bvh_view(bvh[current]), make_consts(params), r.rr.cam, 1, npix, prim, streams[next_slot]);
+  join_other(next_slot);  // the request's later waves may run on the other stream
   stats.admitted += 1;
   return true;
 }
@@ -347,8 +383,9 @@ void Server::finish_locked(Req& r, int32_t state) {
 bool Server::apply_edit_locked(Req& r, std::unique_lock<std::mutex>& lk) {
   const int target = 1 - current;
   if (users[target] > 0) return false;  // the other version is still rendering
-  (void)lk;
   const int64_t n = scene[current].n;
+  // the edit runs on the next wave's stream; the other stream waits for it
+  cudaStream_t st = streams[next_slot];
   // copy the current version into the target slot, then edit the copy
   const float* src[7] = {scene[current].pos, scene[current].quat, scene[current].scale, scene[current].opacity,
                          scene[current].albedo, scene[current].radiance, scene[current].emissive};
@@ -357,10 +394,10 @@ bool Server::apply_edit_locked(Req& r, std::unique_lock<std::mutex>& lk) {
   const int width[7] = {3, 4, 2, 1, 3, 3, 1};
   cudaError_t e = cudaSuccess;
   for (int k = 0; k < 7 && e == cudaSuccess; ++k)
-    e = cudaMemcpyAsync(dst[k], src[k], (size_t)n * width[k] * sizeof(float), cudaMemcpyDeviceToDevice, stream);
+    e = cudaMemcpyAsync(dst[k], src[k], (size_t)n * width[k] * sizeof(float), cudaMemcpyDeviceToDevice, st);
   if (e == cudaSuccess && n > 0)
     e = cudaMemcpyAsync(bvh[target].storage, bvh[current].storage, bvh_layout(n).total, cudaMemcpyDeviceToDevice,
-                        stream);
+                        st);
   if (e != cudaSuccess) {
     error = cudaGetErrorString(e);
     finish_locked(r, EAGPT_REQ_FAILED);
@@ -372,10 +409,21 @@ bool Server::apply_edit_locked(Req& r, std::unique_lock<std::mutex>& lk) {
   bvh[target] = bvh[current];
   bvh[target].storage = storage;
   bvh[target].bytes = sbytes;
-  const eagpt_status st =
-      apply_edit_core(&scene[target], &bvh[target], &params, &r.edit, cfg.rebuild_ratio, &r.rebuilt, stream);
-  if (st != EAGPT_OK) {
+  const eagpt_status est =
+      apply_edit_core(&scene[target], &bvh[target], &params, &r.edit, cfg.rebuild_ratio, &r.rebuilt, st);
+  if (est != EAGPT_OK || join_other(next_slot) != cudaSuccess) {
     error = "edit failed";
+    finish_locked(r, EAGPT_REQ_FAILED);
+    return true;
+  }
+  // the edit is done when the device has applied it (callers may read the
+  // edited scene, e.g. to select surfels for the next edit); the other
+  // stream's wave keeps the GPU busy meanwhile
+  lk.unlock();
+  const cudaError_t se = cudaStreamSynchronize(st);
+  lk.lock();
+  if (se != cudaSuccess) {
+    error = cudaGetErrorString(se);
     finish_locked(r, EAGPT_REQ_FAILED);
     return true;
   }
@@ -436,19 +484,54 @@ static std::vector<int> plan_wave(const std::vector<const Req*>& act, int64_t qu
   return batch;
 }
 
-void Server::wave(std::unique_lock<std::mutex>& lk) {
-  std::vector<ReqDev> tab;
-  std::vector<uint64_t> in_wave;
-  tab.reserve(active.size());
-  int64_t paths = 0, pixels = 0;
-  int maxB = 0;
+// A running request the caller cancelled keeps its memory until no wave in
+// flight holds its samples (a later admission may reuse the memory on the
+// other stream).
+void Server::release_cancelled_locked(Req& r) {
+  if (r.inflight > 0 || std::find(active.begin(), active.end(), r.id) == active.end()) return;
+  r.state = EAGPT_REQ_RUNNING;
+  finish_locked(r, EAGPT_REQ_CANCELLED);
+}
+
+bool Server::plannable_locked() const {
+  for (uint64_t id : active) {
+    const Req& r = reqs.at(id);
+    if (r.state == EAGPT_REQ_RUNNING && r.s_next < r.rr.spp) return true;
+  }
+  return false;
+}
+
+void Server::fail_all_locked(cudaError_t e) {
+  error = cudaGetErrorString(e);
+  std::vector<uint64_t> ids = active;
+  for (uint64_t id : ids) finish_locked(reqs[id], EAGPT_REQ_FAILED);
+}
+
+// Plans the next wave from the requests' sample counters, enqueues it on the
+// stream and returns without waiting for it (lock held on entry and exit).
+void Server::enqueue_wave(std::unique_lock<std::mutex>& lk) {
+  const int slot = next_slot;
+  if (wv[slot].busy) complete_oldest(lk);  // its table slot is still in use
+  if (!plannable_locked()) return;
+  Wave& W = wv[slot];
+  W.ids.clear();
+  W.last.clear();
   std::vector<const Req*> act;
-  for (uint64_t id : active) act.push_back(&reqs[id]);
+  std::vector<uint64_t> act_ids;
+  for (uint64_t id : active) {
+    const Req& r = reqs[id];
+    if (r.state == EAGPT_REQ_RUNNING && r.s_next < r.rr.spp) {
+      act.push_back(&r);
+      act_ids.push_back(id);
+    }
+  }
   const std::vector<int> plan = plan_wave(act, queue_cap);
-  for (size_t k = 0; k < active.size(); ++k) {
+  int64_t paths = 0, pixels = 0;
+  int maxB = 0, nreq = 0;
+  ReqDev* tab = table_h[slot];
+  for (size_t k = 0; k < act.size(); ++k) {
     if (plan[k] == 0) continue;
-    Req& r = reqs[active[k]];
-    in_wave.push_back(r.id);
+    Req& r = reqs[act_ids[k]];
     ReqDev d{};
     d.cam = r.rr.cam;
     d.seed = r.rr.seed;
@@ -457,7 +540,7 @@ void Server::wave(std::unique_lock<std::mutex>& lk) {
     d.pix_off = pixels;
     d.prim = (PrimRec*)(base + r.off);
     d.acc = (float4*)(base + r.off + align256((size_t)r.npix * sizeof(PrimRec)));
-    d.slots = slots + paths;
+    d.slots = slots[slot] + paths;
     d.out_rgb = r.rr.out_rgb;
     d.spp = r.rr.spp;
     d.max_bounces = r.rr.max_bounces;
@@ -470,55 +553,103 @@ void Server::wave(std::unique_lock<std::mutex>& lk) {
     paths += r.npix * d.batch;
     pixels += r.npix;
     maxB = std::max(maxB, r.rr.max_bounces);
-    tab.push_back(d);
+    tab[nreq++] = d;
+    W.ids.push_back(r.id);
+    W.last.push_back((char)d.last);
+    r.s_next += d.batch;  // the next plan continues after this wave's samples
+    r.inflight += 1;
   }
-  const int nreq = (int)tab.size();
+  if (nreq == 0) return;
+  W.paths = paths;
+  W.pixels = pixels;
+  W.max_b = maxB;
+  W.busy = true;
+  next_slot ^= 1;
+  in_flight += 1;
   const BvhView v0 = bvh_view(bvh[0]), v1 = bvh_view(bvh[1]);
   const Consts C = make_consts(params);
+  ReqDev* table = table_d[slot];
+  cudaStream_t stream = streams[slot];
+  uint32_t* cnt = counters[slot];
+  Ray* const* qs = q[slot];
+  const bool chain = in_flight > 1;  // the previous wave (other stream) may still accumulate
   lk.unlock();
-  cudaError_t e = cudaMemcpyAsync(table, tab.data(), tab.size() * sizeof(ReqDev), cudaMemcpyHostToDevice, stream);
-  if (e == cudaSuccess) e = cudaMemsetAsync(counters, 0, kSrvCounterWords * sizeof(uint32_t), stream);
-  static int grid = 0;
-  if (!grid) {
-    int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_srv_bounce, kBlock, 0);
-    grid = std::max(1, per_sm) * device_sms();
-  }
+  cudaError_t e = cudaEventRecord(ev_start[slot], stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(table, tab, (size_t)nreq * sizeof(ReqDev), cudaMemcpyHostToDevice, stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(cnt, 0, kSrvCounterWords * sizeof(uint32_t), stream);
+  const int grid = persistent_grid((const void*)k_srv_bounce);
   if (e == cudaSuccess) {
     EAGPT_LAUNCH(stream, "k_srv_generate",
                  k_srv_generate<<<(unsigned)((paths + kBlock - 1) / kBlock), kBlock, 0, stream>>>(table, nreq, paths, C,
-                                                                                                  q[0], counters));
+                                                                                                  qs[0], cnt));
     for (int k = 1; k <= maxB; ++k)
       EAGPT_LAUNCH(stream, "k_srv_bounce",
-                   k_srv_bounce<<<grid, kBlock, 0, stream>>>(v0, v1, table, C, k, q[(k - 1) & 1], q[k & 1], counters));
-    EAGPT_LAUNCH(stream, "k_srv_accumulate",
-                 k_srv_accumulate<<<(unsigned)((pixels + kBlock - 1) / kBlock), kBlock, 0, stream>>>(table, nreq,
-                                                                                                    pixels, C));
-    e = cudaGetLastError();
+                   k_srv_bounce<<<grid, kBlock, 0, stream>>>(v0, v1, table, C, k, qs[(k - 1) & 1], qs[k & 1], cnt));
+    // a request's running sums take its waves in order
+    if (chain) e = cudaStreamWaitEvent(stream, ev_acc[slot ^ 1], 0);
+    if (e == cudaSuccess)
+      EAGPT_LAUNCH(stream, "k_srv_accumulate",
+                   k_srv_accumulate<<<(unsigned)((pixels + kBlock - 1) / kBlock), kBlock, 0, stream>>>(table, nreq,
+                                                                                                      pixels, C));
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaEventRecord(ev_acc[slot], stream);
   }
-  std::vector<uint32_t> cnt(kSrvCounterWords, 0);
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(cnt.data(), counters, kSrvCounterWords * sizeof(uint32_t), cudaMemcpyDeviceToHost, stream);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    e = cudaMemcpyAsync(cnt_h[slot], cnt, kSrvCounterWords * sizeof(uint32_t), cudaMemcpyDeviceToHost, stream);
+  if (e == cudaSuccess) e = cudaEventRecord(ev_done[slot], stream);
   lk.lock();
-  stats.waves += 1;
   if (e != cudaSuccess) {
-    error = cudaGetErrorString(e);
-    std::vector<uint64_t> ids = active;
-    for (uint64_t id : ids) finish_locked(reqs[id], EAGPT_REQ_FAILED);
+    W.busy = false;
+    in_flight -= 1;
+    fail_all_locked(e);
+  }
+}
+
+// Waits (lock released) for the oldest wave in flight, then books it: its
+// segments, and the requests whose last samples it held are done.
+void Server::complete_oldest(std::unique_lock<std::mutex>& lk) {
+  if (in_flight == 0) return;
+  const int slot = oldest;
+  lk.unlock();
+  cudaError_t e = cudaEventSynchronize(ev_done[slot]);
+  float t_start = 0.f, t_done = 0.f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&t_start, ev_ref, ev_start[slot]);
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&t_done, ev_ref, ev_done[slot]);
+  lk.lock();
+  Wave& W = wv[slot];
+  W.busy = false;
+  oldest ^= 1;
+  in_flight -= 1;
+  stats.waves += 1;
+  for (uint64_t id : W.ids) {
+    auto it = reqs.find(id);
+    if (it != reqs.end()) it->second.inflight -= 1;
+  }
+  if (e != cudaSuccess) {
+    fail_all_locked(e);
     return;
   }
-  int64_t segs = pixels;
-  for (int k = 1; k <= maxB; ++k) segs += cnt[2 * k];
+  // GPU time of the waves, overlapping waves counted once
+  stats.busy_s += std::max(0.f, t_done - std::max(t_start, last_done_ms)) * 1e-3;
+  last_done_ms = std::max(last_done_ms, t_done);
+  const uint32_t* cnt = cnt_h[slot];
+  int64_t segs = W.pixels;
+  for (int k = 1; k <= W.max_b; ++k) segs += cnt[2 * k];
   stats.segments += segs;
-  stats.paths += paths;
+  stats.paths += W.paths;
   const double t = now_s();
-  for (size_t k = 0; k < in_wave.size(); ++k) reqs[in_wave[k]].s_next += tab[k].batch;
-  std::vector<uint64_t> ids = active;
-  for (uint64_t id : ids) {
-    Req& r = reqs[id];
-    if (r.state == EAGPT_REQ_RUNNING && r.s_next >= r.rr.spp) finish_locked(r, EAGPT_REQ_DONE);
-    else if (r.state == EAGPT_REQ_RUNNING && r.deadline > 0 && t > r.deadline) finish_locked(r, EAGPT_REQ_TIMED_OUT);
+  for (size_t k = 0; k < W.ids.size(); ++k) {
+    auto it = reqs.find(W.ids[k]);
+    if (it == reqs.end()) continue;
+    Req& r = it->second;
+    if (r.state == EAGPT_REQ_CANCELLED) {
+      release_cancelled_locked(r);
+      continue;
+    }
+    if (r.state != EAGPT_REQ_RUNNING) continue;
+    if (W.last[k]) finish_locked(r, EAGPT_REQ_DONE);
+    else if (r.deadline > 0 && t > r.deadline) finish_locked(r, EAGPT_REQ_TIMED_OUT);
   }
 }
 
@@ -539,11 +670,7 @@ void Server::run() {
     // running requests cancelled by the caller
     std::vector<uint64_t> ids = active;
     for (uint64_t id : ids)
-      if (reqs[id].state == EAGPT_REQ_CANCELLED) {
-        Req& r = reqs[id];
-        r.state = EAGPT_REQ_RUNNING;
-        finish_locked(r, EAGPT_REQ_CANCELLED);
-      }
+      if (reqs[id].state == EAGPT_REQ_CANCELLED) release_cancelled_locked(reqs[id]);
     // admission in submission order
     while (!pending.empty()) {
       Req& r = reqs[pending.front()];
@@ -556,6 +683,14 @@ void Server::run() {
       if (!done) break;
       pending.pop_front();
     }
+    if (plannable_locked()) {
+      enqueue_wave(lk);
+      continue;
+    }
+    if (in_flight > 0) {
+      complete_oldest(lk);
+      continue;
+    }
     if (active.empty()) {
       if (stop && pending.empty()) break;
       if (stop) {
@@ -564,12 +699,8 @@ void Server::run() {
         pending.clear();
         break;
       }
-      cv_work.wait_for(lk, std::chrono::milliseconds(5));
-      continue;
     }
-    const double t0 = now_s();
-    wave(lk);
-    stats.busy_s += now_s() - t0;
+    cv_work.wait_for(lk, std::chrono::milliseconds(5));
   }
 }
 
@@ -581,16 +712,40 @@ struct eagpt_server_t {
   Server s;
 };
 
+static void release_host(Server& S) {
+  for (int k = 0; k < 2; ++k) {
+    if (S.table_h[k]) cudaFreeHost(S.table_h[k]);
+    if (S.cnt_h[k]) cudaFreeHost(S.cnt_h[k]);
+    if (S.ev_start[k]) cudaEventDestroy(S.ev_start[k]);
+    if (S.ev_done[k]) cudaEventDestroy(S.ev_done[k]);
+    if (S.ev_acc[k]) cudaEventDestroy(S.ev_acc[k]);
+    if (S.streams[k]) cudaStreamDestroy(S.streams[k]);
+    S.table_h[k] = nullptr;
+    S.cnt_h[k] = nullptr;
+    S.ev_start[k] = S.ev_done[k] = S.ev_acc[k] = nullptr;
+    S.streams[k] = nullptr;
+  }
+  if (S.ev_ref) cudaEventDestroy(S.ev_ref);
+  if (S.ev_sync) cudaEventDestroy(S.ev_sync);
+  S.ev_ref = S.ev_sync = nullptr;
+}
+
+// Arena bytes the server keeps for itself: the second scene version and its
+// BVH, and per wave slot two ray queues, the per-sample values, the counters
+// and the request table.
+static size_t fixed_bytes(int64_t n, int64_t queue_paths) {
+  return scene_bytes(n) + align256(bvh_layout(n).total) +
+         2 * (2 * align256((size_t)queue_paths * sizeof(Ray)) + align256((size_t)queue_paths * sizeof(float4)) +
+              align256(kSrvCounterWords * 4) + align256(kSrvMaxActive * sizeof(ReqDev)));
+}
+
 extern "C" {
 
 size_t eagpt_server_arena_bytes(int64_t n, int64_t queue_paths) {
   if (n < 0 || queue_paths <= 0) return 0;
-  // second scene version + its BVH, two ray queues, the wave's per-sample
-  // values, counters, request table, and primary records and sums for as
-  // many pixels as the queue holds paths
-  return scene_bytes(n) + align256(bvh_layout(n).total) + 2 * align256((size_t)queue_paths * sizeof(Ray)) +
-         align256((size_t)queue_paths * sizeof(float4)) + align256(kSrvCounterWords * 4) +
-         align256(kSrvMaxActive * sizeof(ReqDev)) + (size_t)queue_paths * (sizeof(float4) + sizeof(PrimRec));
+  // the server's own buffers, and primary records and sums for as many
+  // pixels as the queue holds paths
+  return fixed_bytes(n, queue_paths) + (size_t)queue_paths * (sizeof(float4) + sizeof(PrimRec));
 }
 
 eagpt_status eagpt_server_create(const eagpt_scene_mut* scene, const eagpt_bvh* bvh, const eagpt_params* params,
@@ -606,10 +761,7 @@ eagpt_status eagpt_server_create(const eagpt_scene_mut* scene, const eagpt_bvh* 
   if (bvh->scene_version != scene->version || bvh->n != scene->n)
     return set_error(EAGPT_ERR_STALE_BVH, "bvh does not match the scene");
   const int64_t n = scene->n;
-  const size_t fixed = scene_bytes(n) + align256(bvh_layout(n).total) +
-                       2 * align256((size_t)cfg->queue_paths * sizeof(Ray)) +
-                       align256((size_t)cfg->queue_paths * sizeof(float4)) + align256(kSrvCounterWords * 4) +
-                       align256(kSrvMaxActive * sizeof(ReqDev));
+  const size_t fixed = fixed_bytes(n, cfg->queue_paths);
   if (cfg->arena_bytes < fixed + 4096)
     return set_error(EAGPT_ERR_OUT_OF_MEMORY, "arena too small for the second scene version and the queues");
   eagpt_server_t* h = new eagpt_server_t();
@@ -639,15 +791,30 @@ eagpt_status eagpt_server_create(const eagpt_scene_mut* scene, const eagpt_bvh* 
   S.bvh[1] = *bvh;
   S.bvh[1].bytes = bvh_layout(n).total;
   S.bvh[1].storage = S.base + take(S.bvh[1].bytes);
-  S.q[0] = (Ray*)(S.base + take((size_t)cfg->queue_paths * sizeof(Ray)));
-  S.q[1] = (Ray*)(S.base + take((size_t)cfg->queue_paths * sizeof(Ray)));
-  S.slots = (float4*)(S.base + take((size_t)cfg->queue_paths * sizeof(float4)));
-  S.counters = (uint32_t*)(S.base + take(kSrvCounterWords * 4));
-  S.table = (ReqDev*)(S.base + take(kSrvMaxActive * sizeof(ReqDev)));
+  for (int k = 0; k < 2; ++k) {
+    S.q[k][0] = (Ray*)(S.base + take((size_t)cfg->queue_paths * sizeof(Ray)));
+    S.q[k][1] = (Ray*)(S.base + take((size_t)cfg->queue_paths * sizeof(Ray)));
+    S.slots[k] = (float4*)(S.base + take((size_t)cfg->queue_paths * sizeof(float4)));
+    S.counters[k] = (uint32_t*)(S.base + take(kSrvCounterWords * 4));
+    S.table_d[k] = (ReqDev*)(S.base + take(kSrvMaxActive * sizeof(ReqDev)));
+  }
   S.queue_cap = cfg->queue_paths;
   S.arena.init(o, cfg->arena_bytes - o);
-  cudaError_t e = cudaStreamCreateWithFlags(&S.stream, cudaStreamNonBlocking);
+  // set-up (not per wave): the two streams, the pinned host sides of the
+  // two request tables and counter copies, the events
+  cudaError_t e = cudaEventCreate(&S.ev_ref);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&S.ev_sync, cudaEventDisableTiming);
+  for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+    e = cudaStreamCreateWithFlags(&S.streams[k], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaHostAlloc((void**)&S.table_h[k], kSrvMaxActive * sizeof(ReqDev), cudaHostAllocDefault);
+    if (e == cudaSuccess) e = cudaHostAlloc((void**)&S.cnt_h[k], kSrvCounterWords * sizeof(uint32_t), cudaHostAllocDefault);
+    if (e == cudaSuccess) e = cudaEventCreate(&S.ev_start[k]);
+    if (e == cudaSuccess) e = cudaEventCreate(&S.ev_done[k]);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&S.ev_acc[k], cudaEventDisableTiming);
+  }
+  if (e == cudaSuccess) e = cudaEventRecord(S.ev_ref, S.streams[0]);
   if (e != cudaSuccess) {
+    release_host(S);
     delete h;
     return set_error(EAGPT_ERR_CUDA, cudaGetErrorString(e));
   }
@@ -780,8 +947,9 @@ eagpt_status eagpt_server_destroy(eagpt_server h) {
     h->s.cv_work.notify_all();
   }
   if (h->s.worker.joinable()) h->s.worker.join();
-  cudaStreamSynchronize(h->s.stream);
-  cudaStreamDestroy(h->s.stream);
+  cudaStreamSynchronize(h->s.streams[0]);
+  cudaStreamSynchronize(h->s.streams[1]);
+  release_host(h->s);
   delete h;
   return EAGPT_OK;
 }

@@ -379,6 +379,25 @@ class Workload:
     max_bounces: int
     rr_start: int
     seed: int = 0
+    # factor the generator applied to the scale law log-U[0.005, 0.05] m
+    # (rooms with denser walls than the medium room get smaller surfels)
+    scale_factor: float = 1.0
+
+
+def _box_wall_area(lo, hi) -> float:
+    return sum(_face_area(np.asarray(lo, np.float64), np.asarray(hi, np.float64), ax) for ax, _s in _FACES)
+
+
+def _layout_wall_area() -> float:
+    """Open wall area of the three-room layout: 94 + 70 + 94 m^2 minus two
+    1 x 2 m doors."""
+    full = _box_wall_area([-2.5, -2.0, -1.5], [2.5, 2.0, 1.5])
+    middle = full - 2 * 12.0  # its x-faces belong to its neighbours
+    return 2 * full + middle - 2 * 2.0
+
+
+def workload_scale_factor(n: int, wall_area: float) -> float:
+    return scale_factor(int(round(n * WALL_FRACTION)), wall_area)
 
 
 def tiny_room(n: int = 4096) -> SurfelScene:
@@ -422,15 +441,18 @@ def workload(name: str) -> Workload:
         return Workload("medium room 200k surfels 512x512 64spp 4 bounces RR>=2", medium_room,
                         horizontal_camera(512, 512), spp=64, max_bounces=4, rr_start=2)
     if name == "diff":
+        f = workload_scale_factor(1_000_000, _box_wall_area([-2.5, -2.0, -1.5], [2.5, 2.0, 1.5]))
         return Workload("single bounce fwd+bwd 1M surfels 800x800 16spp", diff_room,
-                        horizontal_camera(800, 800), spp=16, max_bounces=1, rr_start=2)
+                        horizontal_camera(800, 800), spp=16, max_bounces=1, rr_start=2, scale_factor=f)
     if name == "serving":
+        f = workload_scale_factor(3_000_000, _box_wall_area([-5.0, -4.0, -1.5], [5.0, 4.0, 1.5]))
         return Workload("serving room 3M surfels", serving_room,
-                        horizontal_camera(512, 512), spp=16, max_bounces=3, rr_start=2)
+                        horizontal_camera(512, 512), spp=16, max_bounces=3, rr_start=2, scale_factor=f)
     if name == "large":
+        f = workload_scale_factor(6_000_000, _layout_wall_area())
         return Workload("large three-room 6M surfels 1920x1080 1024spp 5 bounces RR>=2",
                         large_layout, horizontal_camera(1920, 1080), spp=1024, max_bounces=5,
-                        rr_start=2)
+                        rr_start=2, scale_factor=f)
     raise KeyError(name)
 
 
