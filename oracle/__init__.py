@@ -82,11 +82,11 @@ def _load():
             lib.ora_render.argtypes = [P(_Scene), P(_Camera), P(_Params), i32, i32, i32, i32, u64, P(i32), i64,
                                        P(d), P(d), P(u32), P(i64), i32]
             lib.ora_single_bounce_grad.argtypes = [P(_Scene), P(_Camera), P(_Params), i32, u64, P(i32), i64,
-                                                   P(d), P(d), P(u32), i32]
+                                                   P(d), P(d), P(u32), i32, i32]
             lib.ora_light_pdf.argtypes = [P(_Scene), P(_Params), P(d), P(d), P(d)]
             lib.ora_light_pdf.restype = i32
             lib.ora_radiance_grad.argtypes = [P(_Scene), P(_Camera), P(_Params), P(i32), i64, P(d), P(d), P(u32),
-                                              i32]
+                                              i32, i32]
             for f in ("ora_trace_segment", "ora_trace_rays", "ora_primary", "ora_render",
                       "ora_single_bounce_grad", "ora_radiance_grad"):
                 getattr(lib, f).restype = ctypes.c_int
@@ -240,8 +240,9 @@ def render(scene, camera, pixels, kind, spp, max_bounces=1, rr_start=2, seed=0, 
     return {"rgb": rgb, "samples": samples, "sample_flags": sflags, "segments": segs}
 
 
-def single_bounce_grad(scene, camera, pixels, dL_drgb, spp, seed=0, params=None, n_threads=None):
-    """Returns (grad (n,16), pixel flags)."""
+def single_bounce_grad(scene, camera, pixels, dL_drgb, spp, seed=0, params=None, n_threads=None, run=0):
+    """Returns (grad (n,16), pixel flags).  run > 0: conditioning run r (rays
+    and sigma g perturbed at FP32 scale)."""
     lib = _load()
     sc = _oscene(scene)
     pixels = np.ascontiguousarray(pixels, np.int32)
@@ -253,14 +254,15 @@ def single_bounce_grad(scene, camera, pixels, dL_drgb, spp, seed=0, params=None,
     rc = lib.ora_single_bounce_grad(ctypes.byref(sc._c), ctypes.byref(cam), ctypes.byref(prm), int(spp),
                                     ctypes.c_uint64(int(seed)), _ptr(pixels, ctypes.c_int32), pixels.size,
                                     _ptr(dL, ctypes.c_double), _ptr(grad, ctypes.c_double),
-                                    _ptr(fl, ctypes.c_uint32), n_threads or default_threads())
+                                    _ptr(fl, ctypes.c_uint32), n_threads or default_threads(), int(run))
     if rc:
         raise RuntimeError("oracle grad failed")
     return grad, fl
 
 
-def radiance_grad(scene, camera, pixels, dL_drgb, params=None, n_threads=None):
-    """Gradient of sum(dL_drgb * R_primary) (0-bounce render); returns (grad (n,16), flags)."""
+def radiance_grad(scene, camera, pixels, dL_drgb, params=None, n_threads=None, run=0):
+    """Gradient of sum(dL_drgb * R_primary) (0-bounce render); returns (grad (n,16), flags).
+    run > 0: conditioning run r (rays and sigma g perturbed at FP32 scale)."""
     lib = _load()
     sc = _oscene(scene)
     pixels = np.ascontiguousarray(pixels, np.int32)
@@ -271,7 +273,8 @@ def radiance_grad(scene, camera, pixels, dL_drgb, params=None, n_threads=None):
     cam = _cam(camera)
     rc = lib.ora_radiance_grad(ctypes.byref(sc._c), ctypes.byref(cam), ctypes.byref(prm),
                                _ptr(pixels, ctypes.c_int32), pixels.size, _ptr(dL, ctypes.c_double),
-                               _ptr(grad, ctypes.c_double), _ptr(fl, ctypes.c_uint32), n_threads or default_threads())
+                               _ptr(grad, ctypes.c_double), _ptr(fl, ctypes.c_uint32), n_threads or default_threads(),
+                               int(run))
     if rc:
         raise RuntimeError("oracle radiance grad failed")
     return grad, fl

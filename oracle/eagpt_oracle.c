@@ -473,6 +473,9 @@ typedef struct {
   int32_t* hit_idx;
 } rays_ctx;
 
+static void jitter_ray(double O[3], double w[3], uint64_t seed, int64_t pix, int32_t s, int32_t k, int32_t run,
+                       double mag);
+
 static int rays_item(job* jb, int64_t i, hitbuf* b) {
   rays_ctx* c = (rays_ctx*)jb->ctx;
   const double* r = &c->rays[6 * i];
@@ -480,9 +483,38 @@ static int rays_item(job* jb, int64_t i, hitbuf* b) {
   if (segment(&jb->W, r, r + 3, 0.0, c->mode, 0.0, 0.0, b, &g)) return -1;
   write_rec(&g, &c->out_rec[12 * i]);
   if (c->out_nhits) c->out_nhits[i] = g.n_hits;
-  if (c->out_flags) c->out_flags[i] = g.flags;
   if (c->hit_idx)
     for (int32_t k = 0; k < c->max_hits; ++k) c->hit_idx[i * c->max_hits + k] = k < b->n ? (int32_t)b->h[k].idx : -1;
+  /* a single segment is ill-conditioned in FP32 when re-tracing it with the
+   * ray perturbed at FP32 rounding scale (and every sigma g by +-4 ulps), as
+   * the render's conditioning runs do for whole samples, changes its blended
+   * surfel list or moves a blended value by more than cond_tol: R, P, E and A
+   * relative to the value, N~ by cond_tol / 5 absolute (the comparison's
+   * 2e-5 on a unit vector, with the same margin), D~ relative */
+  const ora_params* prm = jb->W.prm;
+  if (prm->fp32_eps > 0 && prm->cond_tol > 0 && g.n_hits > 0) {
+    const uint64_t sig = hits_signature(b);
+    for (int run = 1; run <= 2 && !(g.flags & ORA_FLAG_COND); ++run) {
+      world Wj = jb->W;
+      Wj.ajit = (uint32_t)run;
+      double Oj[3] = {r[0], r[1], r[2]}, wj[3] = {r[3], r[4], r[5]};
+      jitter_ray(Oj, wj, 0x9E3779B97F4A7C15ull, i, -2, 0, run, 2.0 * prm->fp32_eps);
+      ora_segment gj;
+      if (segment(&Wj, Oj, wj, 0.0, c->mode, 0.0, 0.0, b, &gj)) return -1;
+      int ill = hits_signature(b) != sig;
+      const double tol = prm->cond_tol;
+      for (int k = 0; k < 3 && !ill; ++k) {
+        ill |= fabs(gj.R[k] - g.R[k]) > tol * fabs(g.R[k]);
+        ill |= fabs(gj.P[k] - g.P[k]) > tol * fabs(g.P[k]);
+        ill |= fabs(gj.Nn[k] - g.Nn[k]) > tol / 5.0;
+      }
+      ill |= fabs(gj.E - g.E) > tol * fabs(g.E);
+      ill |= fabs(gj.A - g.A) > tol * fabs(g.A);
+      ill |= fabs(gj.Dn - g.Dn) > tol * fabs(g.Dn);
+      if (ill) g.flags |= ORA_FLAG_COND;
+    }
+  }
+  if (c->out_flags) c->out_flags[i] = g.flags;
   return 0;
 }
 
@@ -867,8 +899,8 @@ static int render_item(job* jb, int64_t i, hitbuf* b) {
   double* dev = NULL;
   double* mag = NULL;
   if (n_runs) {
-    dev = (double*)calloc((size_t)c->spp, sizeof(double));
-    mag = (double*)calloc((size_t)c->spp, sizeof(double));
+    dev = (double*)calloc((size_t)c->spp * 3, sizeof(double));
+    mag = (double*)calloc((size_t)c->spp * 3, sizeof(double));
     if (!dev || !mag) {
       free(dev);
       free(mag);
@@ -913,27 +945,30 @@ static int render_item(job* jb, int64_t i, hitbuf* b) {
       }
       for (int k = 0; k < 3; ++k) {
         double d = fabs(cj[k] - contrib[k]);
-        if (d > dev[s]) dev[s] = d;
+        if (d > dev[3 * s + k]) dev[3 * s + k] = d;
       }
       /* a discrete outcome along the path (a blended surfel, a bounce) that
        * FP32-scale perturbations change makes the sample ill-conditioned even
        * when this run's value happens to agree */
-      if (sigr != sig0) dev[s] = INFINITY;
+      if (sigr != sig0) dev[3 * s] = INFINITY;
     }
     for (int k = 0; k < 3; ++k) acc[k] += contrib[k];
-    if (mag) mag[s] = amax3(contrib);
+    if (mag)
+      for (int k = 0; k < 3; ++k) mag[3 * s + k] = fabs(contrib[k]);
     if (c->out_samples)
       for (int k = 0; k < 3; ++k) c->out_samples[(i * c->spp + s) * 3 + k] = contrib[k];
     if (c->out_sample_flags) c->out_sample_flags[i * c->spp + s] = sflags;
   }
   for (int k = 0; k < 3; ++k) c->out_rgb[3 * i + k] = c->spp > 0 ? acc[k] / c->spp : 0.0;
   if (n_runs && c->out_sample_flags) {
-    /* a sample is ill-conditioned when FP32-scale perturbations move it by
-     * more than cond_tol of its own value (radiance is non-negative, so a
+    /* a sample is ill-conditioned when FP32-scale perturbations move any of
+     * its channels by more than cond_tol of that channel's value (the
+     * comparison's tolerance is per channel; radiance is non-negative, so a
      * mean of unflagged samples keeps that relative bound) or change a
      * discrete outcome along its path */
     for (int32_t s = 0; s < c->spp; ++s)
-      if (dev[s] > prm->cond_tol * mag[s]) c->out_sample_flags[i * c->spp + s] |= ORA_FLAG_COND;
+      for (int k = 0; k < 3; ++k)
+        if (dev[3 * s + k] > prm->cond_tol * mag[3 * s + k]) c->out_sample_flags[i * c->spp + s] |= ORA_FLAG_COND;
   }
   free(dev);
   free(mag);
@@ -1142,6 +1177,7 @@ typedef struct {
   gradbuf* per_thread;
   int32_t n_threads;
   int32_t radiance_only; /* 0-bounce render: I = R_1 for every pixel */
+  int32_t run;           /* > 0: a conditioning run (rays and sigma g perturbed at FP32 scale, as in ora_render) */
 } grad_ctx;
 
 static int grad_pixel(const world* W, grad_ctx* c, int64_t i, hitbuf* b1, hitbuf* b2, gradbuf* gb) {
@@ -1150,6 +1186,10 @@ static int grad_pixel(const world* W, grad_ctx* c, int64_t i, hitbuf* b1, hitbuf
   const double* gI = &c->dL[3 * i];
   double O[3], w[3];
   primary_ray(c->cam, pix, O, w);
+  if (c->run > 0) {
+    double Oj[3] = {O[0], O[1], O[2]};
+    jitter_ray(Oj, w, c->seed, pix, -1, 0, c->run, 2.0 * prm->fp32_eps);
+  }
   ora_segment g1;
   if (segment(W, O, w, 0.0, 0, 0.0, ERR_C * prm->fp32_eps, b1, &g1)) return -1;
   uint32_t flags = g1.flags;
@@ -1177,6 +1217,7 @@ static int grad_pixel(const world* W, grad_ctx* c, int64_t i, hitbuf* b1, hitbuf
     cosine_local(u[0], u[1], l);
     ora_cosine_direction(g1.Nn, u[0], u[1], w2);
     for (int k = 0; k < 3; ++k) O2[k] = X[k] + prm->bounce_offset * g1.Nn[k];
+    if (c->run > 0) jitter_ray(O2, w2, c->seed, pix, s, 1, c->run, 2.0 * eps);
     const double eO2 = ERR_C * eps * amax3(O2);
     ora_segment g2;
     if (segment(W, O2, w2, 0.0, 0, eO2, ERR_C * eps, b2, &g2)) return -1;
@@ -1227,27 +1268,28 @@ static void* gworker(void* arg) {
 
 static int grad_common(const ora_scene* sc, const ora_camera* cam, const ora_params* prm, int32_t spp,
                        uint64_t seed, const int32_t* pixels, int64_t n_pix, const double* dL_drgb, double* grad,
-                       uint32_t* out_flags, int32_t n_threads, int32_t radiance_only);
+                       uint32_t* out_flags, int32_t n_threads, int32_t radiance_only, int32_t run);
 
 int ora_single_bounce_grad(const ora_scene* sc, const ora_camera* cam, const ora_params* prm, int32_t spp,
                            uint64_t seed, const int32_t* pixels, int64_t n_pix, const double* dL_drgb,
-                           double* grad, uint32_t* out_flags, int32_t n_threads) {
-  return grad_common(sc, cam, prm, spp, seed, pixels, n_pix, dL_drgb, grad, out_flags, n_threads, 0);
+                           double* grad, uint32_t* out_flags, int32_t n_threads, int32_t run) {
+  return grad_common(sc, cam, prm, spp, seed, pixels, n_pix, dL_drgb, grad, out_flags, n_threads, 0, run);
 }
 
 int ora_radiance_grad(const ora_scene* sc, const ora_camera* cam, const ora_params* prm, const int32_t* pixels,
-                      int64_t n_pix, const double* dL_drgb, double* grad, uint32_t* out_flags, int32_t n_threads) {
-  return grad_common(sc, cam, prm, 1, 0, pixels, n_pix, dL_drgb, grad, out_flags, n_threads, 1);
+                      int64_t n_pix, const double* dL_drgb, double* grad, uint32_t* out_flags, int32_t n_threads,
+                      int32_t run) {
+  return grad_common(sc, cam, prm, 1, 0, pixels, n_pix, dL_drgb, grad, out_flags, n_threads, 1, run);
 }
 
 static int grad_common(const ora_scene* sc, const ora_camera* cam, const ora_params* prm, int32_t spp,
                        uint64_t seed, const int32_t* pixels, int64_t n_pix, const double* dL_drgb, double* grad,
-                       uint32_t* out_flags, int32_t n_threads, int32_t radiance_only) {
+                       uint32_t* out_flags, int32_t n_threads, int32_t radiance_only, int32_t run) {
   if (n_threads < 1) n_threads = 1;
   if (n_threads > 256) n_threads = 256;
   surfel64* s = load_surfels(sc);
   if (!s) return -1;
-  world W = {s, sc->n, prm};
+  world W = {s, sc->n, prm, (uint32_t)(run > 0 ? run : 0)};
   gradbuf* per = (gradbuf*)calloc((size_t)n_threads, sizeof(gradbuf));
   gthread* th = (gthread*)calloc((size_t)n_threads, sizeof(gthread));
   pthread_t* pt = (pthread_t*)calloc((size_t)n_threads, sizeof(pthread_t));
@@ -1258,7 +1300,7 @@ static int grad_common(const ora_scene* sc, const ora_camera* cam, const ora_par
     free(pt);
     return -1;
   }
-  grad_ctx c = {sc, cam, spp, seed, pixels, dL_drgb, out_flags, per, n_threads, radiance_only};
+  grad_ctx c = {sc, cam, spp, seed, pixels, dL_drgb, out_flags, per, n_threads, radiance_only, run};
   int started = 0;
   for (int t = 0; t < n_threads; ++t) {
     th[t].W = &W;

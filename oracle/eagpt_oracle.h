@@ -40,8 +40,10 @@ typedef struct {
   int32_t emitters_reflect; /* 1: general rendering equation (test-only)    */
   double fp32_eps;       /* unit roundoff used by the near-boundary flags;
                             0 disables flagging                              */
-  double cond_tol;       /* flag a sample whose estimated FP32 relative error
-                            exceeds cond_tol (ORA_FLAG_COND); 0 disables     */
+  double cond_tol;       /* flag a sample (a traced segment) whose estimated
+                            FP32 relative error in any channel (any blended
+                            value) exceeds cond_tol (ORA_FLAG_COND); 0
+                            disables                                         */
   int32_t mis;           /* 1: path tracing with emitter sampling and
                             multiple importance sampling (see ora_render)   */
 } ora_params;
@@ -130,18 +132,24 @@ int ora_render(const ora_scene* sc, const ora_camera* cam, const ora_params* prm
  *   [0..2] centre p, [3..6] quaternion q (raw), [7..8] scales, [9] opacity,
  *   [10..12] albedo, [13..15] radiance.  (The emissive term enters only
  *   through threshold tests, so its derivative is zero almost everywhere.)
- * out_flags (nullable): per pixel OR of sample flags. */
+ * out_flags (nullable): per pixel OR of sample flags.
+ * run: 0 for the gradient; r > 0 for conditioning run r, which evaluates the
+ * same gradient with the primary direction, every secondary ray and every
+ * sigma g perturbed at FP32 rounding scale (the perturbations of ora_render's
+ * conditioning runs): how far an entry moves under them estimates how well
+ * an FP32 evaluation can resolve it. */
 int ora_single_bounce_grad(const ora_scene* sc, const ora_camera* cam, const ora_params* prm,
                            int32_t spp, uint64_t seed, const int32_t* pixels, int64_t n_pix,
                            const double* dL_drgb, double* grad, uint32_t* out_flags,
-                           int32_t n_threads);
+                           int32_t n_threads, int32_t run);
 
 /* Gradient of L = sum dL_drgb . I for the 0-bounce (radiance) render, whose
  * pixel value is the primary segment's blended radiance R (the radiant scene
  * of Sec. 3.2; light baking, Eq. 10).  Same layout and accumulation as
  * ora_single_bounce_grad. */
 int ora_radiance_grad(const ora_scene* sc, const ora_camera* cam, const ora_params* prm, const int32_t* pixels,
-                      int64_t n_pix, const double* dL_drgb, double* grad, uint32_t* out_flags, int32_t n_threads);
+                      int64_t n_pix, const double* dL_drgb, double* grad, uint32_t* out_flags, int32_t n_threads,
+                      int32_t run);
 
 #ifdef __cplusplus
 }

@@ -120,7 +120,9 @@ def test_refit_and_rebuild_match_oracle(api):
         ref = O.render(host, cam, np.arange(24 * 16, dtype=np.int32), "pt", 4, max_bounces=2, rr_start=2, seed=1,
                        want_samples=True)
         ok, st = compare_samples(g.cpu().numpy().reshape(-1, 4, 3), ref["samples"], ref["sample_flags"])
-        assert ok.mean() > 0.99, st
+        print(st)
+        assert st["lit_compared"] >= 20, st
+        assert ok.all(), st
         if step == 0:
             # scattering a random tenth of the surfels breaks the spatial order
             # the tree was built for; the refit's surface-area sum grows past

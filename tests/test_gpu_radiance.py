@@ -8,6 +8,7 @@ import numpy as np
 import pytest
 
 import oracle as O
+from parity_utils import grad_errors, oracle_grad_with_conditioning
 from paper_2601_23065_gb300 import scenes as S
 from parity_utils import radiance_close
 
@@ -80,14 +81,17 @@ def _compare_grad(api, scene, cam, pixels, wseed, tol=1e-3):
     dL = torch.from_numpy(w.reshape(cam.height, cam.width, 3).astype(np.float32)).cuda()
     g = api.radiance_backward(ds, bvh, cam, dL)
     api.sync_status()
-    ref, _ = O.radiance_grad(scene, cam, np.asarray(pixels, np.int32), w[pixels])
-    errs = {}
+    ref, _, ref_dev = oracle_grad_with_conditioning(O.radiance_grad, scene, cam, np.asarray(pixels, np.int32),
+                                                    w[pixels])
+    errs, worst, ill = {}, {}, {}
     for k, (a, b) in GROUPS.items():
         gg = g[k].cpu().numpy().astype(np.float64).reshape(scene.n, -1)
         rr = ref[:, a:b]
-        nrm = np.linalg.norm(rr)
-        errs[k] = float(np.linalg.norm(gg - rr) / nrm) if nrm > 0 else float(np.linalg.norm(gg))
-    print("relative gradient error per group:", errs, "pixels zeroed:", int(bad.sum()))
+        errs[k], ok, worst[k], ill[k] = grad_errors(gg, rr, tol, ref_dev[:, a:b])
+        assert ok.all(), (k, "entries over the per-entry bound:", int((~ok).sum()), "worst ratio", worst[k],
+                          np.argwhere(~ok)[:5])
+    print("relative gradient error per group:", errs, "worst entry / its bound:", worst,
+          "ill-conditioned entries:", ill, "pixels zeroed:", int(bad.sum()))
     for k, e in errs.items():
         assert e <= tol, (k, errs)
     # the 0-bounce image does not depend on the albedo

@@ -138,3 +138,36 @@ def test_small_requests_do_not_wait_on_a_large_one(api):
     assert srv.stats()["waves"] >= 21
     srv.close()
     api.sync_status()
+
+
+def test_cancel_a_running_request(api):
+    """A render cancelled while its waves are in flight ends as cancelled; its
+    memory is released only after those waves, so renders admitted after it
+    (which may reuse that memory on the other wave stream) stay exact."""
+    import time
+
+    import torch
+    sc = S.tiny_room(4096)
+    ds = api.DeviceScene.from_host(sc)
+    bvh = api.BVH(ds)
+    srv = api.Server(ds, bvh, queue_paths=100_000, max_active=2)
+    big_cam = S.look_at_camera(256, 256, 90.0, (0.0, 0.0, 0.0), (1, 0, 0), (0, 0, 1))
+    big, _ = srv.submit_render(big_cam, 128, 5, rr_start=2, seed=5)
+    t0 = time.time()
+    while srv.poll(big)["state"] != "running" and time.time() - t0 < 60:
+        time.sleep(1e-3)
+    srv.cancel(big)
+    after = []
+    for k in range(3):
+        cam = S.look_at_camera(48, 40, 90.0, (0.0, 0.05 * k, 0.0), (0, 1, 0), (0, 0, 1))
+        after.append((srv.submit_render(cam, 6, 3, rr_start=2, seed=30 + k), cam, 30 + k))
+    assert srv.wait(big, 120.0)["state"] == "cancelled"
+    for (rid, out), cam, seed in after:
+        assert srv.wait(rid, 120.0)["state"] == "done"
+        torch.cuda.synchronize()
+        ref = api.Renderer().path_traced(ds, bvh, cam, 6, 3, rr_start=2, seed=seed)["rgb"]
+        assert torch.equal(out, ref)
+    st = srv.stats()
+    assert st["completed"] == 3 and st["failed"] >= 1
+    srv.close()
+    api.sync_status()

@@ -409,6 +409,14 @@ def test_adjoint_matches_central_differences_small_scene():
     grad, n_ok = _fd_check(sc, cam, 4, 5, wts, todo)
     assert n_ok > 0.9 * len(todo)
     assert np.abs(grad[:, 0:10]).max() > 0  # geometry gradients are non-trivial
+    # conditioning runs: the same gradient at rays perturbed at FP32 scale,
+    # close to it (the scene is well conditioned) but not identical
+    pix = np.arange(cam.width * cam.height, dtype=np.int32)
+    g1, _ = O.single_bounce_grad(sc, cam, pix, wts, 4, seed=5, params=O.Params(fp32_eps=0.0))
+    assert np.array_equal(g1, grad)
+    gj, _ = O.single_bounce_grad(sc, cam, pix, wts, 4, seed=5, run=1)
+    assert not np.array_equal(gj, grad)
+    assert np.abs(gj - grad).max() <= 1e-4 * np.abs(grad).max()
 
 
 def test_adjoint_bounce_dependence():
