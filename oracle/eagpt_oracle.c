@@ -32,6 +32,10 @@
 
 #define ERR_C 3.0   /* FP32 roundings assumed per estimated quantity */
 #define FLAG_K 4.0  /* slack applied to the estimates at each decision */
+/* Conditioning runs per sample: the largest deviation over these runs
+ * estimates how far FP32 rounding can move the sample (two runs missed
+ * samples that four catch). */
+#define ORA_COND_RUNS 4
 #define ORA_PI 3.14159265358979323846
 
 /* ------------------------------------------------------------------------ */
@@ -895,7 +899,7 @@ static int render_item(job* jb, int64_t i, hitbuf* b) {
   double acc[3] = {0, 0, 0};
   /* conditioning runs: the whole sample (primary direction included) is
    * re-evaluated with every ray perturbed at FP32 scale */
-  const int n_runs = (prm->cond_tol > 0 && eps > 0) ? 2 : 0;
+  const int n_runs = (prm->cond_tol > 0 && eps > 0) ? ORA_COND_RUNS : 0;
   double* dev = NULL;
   double* mag = NULL;
   if (n_runs) {
@@ -907,10 +911,10 @@ static int render_item(job* jb, int64_t i, hitbuf* b) {
       return -1;
     }
   }
-  ora_segment gj[2];
-  double wj[2][3];
-  uint64_t sigj[2];
-  job jr[2];
+  ora_segment gj[ORA_COND_RUNS];
+  double wj[ORA_COND_RUNS][3];
+  uint64_t sigj[ORA_COND_RUNS];
+  job jr[ORA_COND_RUNS];
   for (int r = 0; r < n_runs; ++r) {
     jr[r] = *jb;
     jr[r].W.ajit = (uint32_t)(r + 1);

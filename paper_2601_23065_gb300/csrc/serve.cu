@@ -99,9 +99,12 @@ __global__ void __launch_bounds__(kBlock) k_srv_generate(const ReqDev* __restric
 // One bounce of every queued path of every admitted request, with the
 // per-lane refill of the single-request bounce kernel: a lane whose segment
 // is finished takes the next queued ray at once; traversal runs in chunks of
-// kSrvSteps node/leaf steps.  Each ray traces the BVH version of its request.
+// kSrvSteps node/leaf steps.  Each ray traces the BVH version of its request;
+// kMixed is false when every request of the wave uses version 0's view (the
+// common case), which spares the per-ray choice between the two views.
 constexpr int kSrvSteps = 64;
 
+template <bool kMixed>
 __global__ void __launch_bounds__(kBlock, kMinBlocks) k_srv_bounce(BvhView v0, BvhView v1,
                                                                    const ReqDev* __restrict__ reqs, Consts C, int k,
                                                                    const Ray* __restrict__ q_in, Ray* q_out,
@@ -128,7 +131,7 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_srv_bounce(BvhView v0, B
         if (idx < count) {
           qi = idx;
           rq = __float_as_uint(q_in[qi].c.w);
-          const BvhView& bvh = reqs[rq].version ? v1 : v0;
+          const BvhView& bvh = (kMixed && reqs[rq].version) ? v1 : v0;
           ray_begin(rt, f3(q_in[qi].a), f3(q_in[qi].b), bvh);
           vis.shade = bvh.shade;
           vis.reset();
@@ -143,7 +146,7 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_srv_bounce(BvhView v0, B
     Ray nr;
     if (active) {
       const ReqDev& R = reqs[rq];
-      const BvhView& bvh = R.version ? v1 : v0;
+      const BvhView& bvh = (kMixed && R.version) ? v1 : v0;
       if (round_steps<kSrvK, false>(rt, bvh, C, s_stack + threadIdx.x, kBlock, kSrvSteps, cnt)) {
         if (round_blend<kSrvK, false>(rt, bvh, C, vis, cnt)) {
           const SegRec s = finish(vis.get());
@@ -567,6 +570,10 @@ void Server::enqueue_wave(std::unique_lock<std::mutex>& lk) {
   next_slot ^= 1;
   in_flight += 1;
   const BvhView v0 = bvh_view(bvh[0]), v1 = bvh_view(bvh[1]);
+  // one BVH version for the whole wave (the usual case) or a per-ray choice
+  bool mixed = false;
+  for (int k = 1; k < nreq; ++k) mixed |= tab[k].version != tab[0].version;
+  const BvhView only = tab[0].version ? v1 : v0;
   const Consts C = make_consts(params);
   ReqDev* table = table_d[slot];
   cudaStream_t stream = streams[slot];
@@ -578,14 +585,22 @@ void Server::enqueue_wave(std::unique_lock<std::mutex>& lk) {
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(table, tab, (size_t)nreq * sizeof(ReqDev), cudaMemcpyHostToDevice, stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(cnt, 0, kSrvCounterWords * sizeof(uint32_t), stream);
-  const int grid = persistent_grid((const void*)k_srv_bounce);
+  const int grid = persistent_grid((const void*)k_srv_bounce<false>);
+  const int grid_mixed = persistent_grid((const void*)k_srv_bounce<true>);
   if (e == cudaSuccess) {
     EAGPT_LAUNCH(stream, "k_srv_generate",
                  k_srv_generate<<<(unsigned)((paths + kBlock - 1) / kBlock), kBlock, 0, stream>>>(table, nreq, paths, C,
                                                                                                   qs[0], cnt));
-    for (int k = 1; k <= maxB; ++k)
-      EAGPT_LAUNCH(stream, "k_srv_bounce",
-                   k_srv_bounce<<<grid, kBlock, 0, stream>>>(v0, v1, table, C, k, qs[(k - 1) & 1], qs[k & 1], cnt));
+    for (int k = 1; k <= maxB; ++k) {
+      if (mixed)
+        EAGPT_LAUNCH(stream, "k_srv_bounce",
+                     k_srv_bounce<true><<<grid_mixed, kBlock, 0, stream>>>(v0, v1, table, C, k, qs[(k - 1) & 1],
+                                                                           qs[k & 1], cnt));
+      else
+        EAGPT_LAUNCH(stream, "k_srv_bounce",
+                     k_srv_bounce<false><<<grid, kBlock, 0, stream>>>(only, only, table, C, k, qs[(k - 1) & 1],
+                                                                      qs[k & 1], cnt));
+    }
     // a request's running sums take its waves in order
     if (chain) e = cudaStreamWaitEvent(stream, ev_acc[slot ^ 1], 0);
     if (e == cudaSuccess)

@@ -61,11 +61,12 @@ GRAD_TOL = 1e-3  # gradient tolerance (per group and per entry)
 
 def oracle_grad_with_conditioning(fn, *args, **kw):
     """The oracle's gradient (fn = O.single_bounce_grad or O.radiance_grad)
-    and, per entry, how far its two conditioning runs (rays and sigma g
-    perturbed at FP32 rounding scale) move it: (grad, pixel flags, dev)."""
+    and, per entry, how far its four conditioning runs (rays and sigma g
+    perturbed at FP32 rounding scale, as the render's) move it:
+    (grad, pixel flags, dev)."""
     g, fl = fn(*args, **kw)
     dev = np.zeros_like(g)
-    for run in (1, 2):
+    for run in (1, 2, 3, 4):
         gj, _ = fn(*args, run=run, **kw)
         dev = np.maximum(dev, np.abs(gj - g))
     return g, fl, dev
