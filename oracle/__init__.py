@@ -77,10 +77,10 @@ def _load():
             lib.ora_cosine_direction.argtypes = [P(d), d, d, P(d)]
             lib.ora_trace_segment.argtypes = [P(_Scene), P(_Params), P(d), P(d), d, i32, P(_Segment), P(i32), i32]
             lib.ora_trace_rays.argtypes = [P(_Scene), P(_Params), P(d), i64, i32, P(d), P(i32), P(u32), P(i32),
-                                           i32, i32]
+                                           i32, P(d), i32]
             lib.ora_primary.argtypes = [P(_Scene), P(_Camera), P(_Params), i32, P(i32), i64, P(d), P(u32), i32]
             lib.ora_render.argtypes = [P(_Scene), P(_Camera), P(_Params), i32, i32, i32, i32, u64, P(i32), i64,
-                                       P(d), P(d), P(u32), P(i64), i32]
+                                       P(d), P(d), P(u32), P(i64), P(d), i32]
             lib.ora_single_bounce_grad.argtypes = [P(_Scene), P(_Camera), P(_Params), i32, u64, P(i32), i64,
                                                    P(d), P(d), P(u32), i32, i32]
             lib.ora_light_pdf.argtypes = [P(_Scene), P(_Params), P(d), P(d), P(d)]
@@ -181,8 +181,11 @@ def trace_segment(scene, O, w, t_lo=0.0, mode=0, params=None, max_hits=64):
     return out, hits[:min(seg.n_hits, max_hits)]
 
 
-def trace_rays(scene, rays, mode=0, params=None, max_hits=64, n_threads=None):
-    """rays (m, 6) origin+direction -> (rec (m,12), n_hits, flags, hit_idx (m,max_hits))."""
+def trace_rays(scene, rays, mode=0, params=None, max_hits=64, n_threads=None, want_dev=False):
+    """rays (m, 6) origin+direction -> (rec (m,12), n_hits, flags, hit_idx
+    (m,max_hits)) and, with want_dev, dev (m,12): per record column the
+    largest change over the conditioning re-traces (+inf where a re-trace
+    changes the blended surfel list)."""
     lib = _load()
     sc = _oscene(scene)
     rays = np.ascontiguousarray(rays, np.float64).reshape(-1, 6)
@@ -191,12 +194,16 @@ def trace_rays(scene, rays, mode=0, params=None, max_hits=64, n_threads=None):
     nh = np.zeros(m, np.int32)
     fl = np.zeros(m, np.uint32)
     hi = np.full((m, max_hits), -1, np.int32)
+    dev = np.zeros((m, 12)) if want_dev else None
     prm = (params or Params())._c()
     rc = lib.ora_trace_rays(ctypes.byref(sc._c), ctypes.byref(prm), _ptr(rays, ctypes.c_double), m, int(mode),
                             _ptr(rec, ctypes.c_double), _ptr(nh, ctypes.c_int32), _ptr(fl, ctypes.c_uint32),
-                            _ptr(hi, ctypes.c_int32), max_hits, n_threads or default_threads())
+                            _ptr(hi, ctypes.c_int32), max_hits, _ptr(dev, ctypes.c_double),
+                            n_threads or default_threads())
     if rc:
         raise RuntimeError("oracle trace_rays failed")
+    if want_dev:
+        return rec, nh, fl, hi, dev
     return rec, nh, fl, hi
 
 
@@ -217,15 +224,19 @@ def primary(scene, camera, pixels, mode=0, params=None, n_threads=None):
 
 
 def render(scene, camera, pixels, kind, spp, max_bounces=1, rr_start=2, seed=0, params=None,
-           want_samples=False, n_threads=None):
+           want_samples=False, n_threads=None, want_dev=False):
     """kind 'single' (Eq. 6) or 'pt' (Eq. 8).  Returns dict with rgb (m,3),
-    samples (m,spp,3), sample_flags (m,spp), segments (m,)."""
+    samples (m,spp,3), sample_flags (m,spp), segments (m,) and, with
+    want_dev, sample_dev (m,spp,3): per sample and channel the largest change
+    over the conditioning runs (+inf where a run changes a discrete outcome
+    along the path)."""
     lib = _load()
     sc = _oscene(scene)
     pixels = np.ascontiguousarray(pixels, np.int32)
     m = pixels.size
     rgb = np.zeros((m, 3))
     samples = np.zeros((m, spp, 3)) if want_samples else None
+    dev = np.zeros((m, spp, 3)) if want_dev else None
     sflags = np.zeros((m, spp), np.uint32)
     segs = np.zeros(m, np.int64)
     prm = (params or Params())._c()
@@ -234,10 +245,13 @@ def render(scene, camera, pixels, kind, spp, max_bounces=1, rr_start=2, seed=0, 
     rc = lib.ora_render(ctypes.byref(sc._c), ctypes.byref(cam), ctypes.byref(prm), k, int(spp), int(max_bounces),
                         int(rr_start), ctypes.c_uint64(int(seed)), _ptr(pixels, ctypes.c_int32), m,
                         _ptr(rgb, ctypes.c_double), _ptr(samples, ctypes.c_double), _ptr(sflags, ctypes.c_uint32),
-                        _ptr(segs, ctypes.c_int64), n_threads or default_threads())
+                        _ptr(segs, ctypes.c_int64), _ptr(dev, ctypes.c_double), n_threads or default_threads())
     if rc:
         raise RuntimeError("oracle render failed")
-    return {"rgb": rgb, "samples": samples, "sample_flags": sflags, "segments": segs}
+    out = {"rgb": rgb, "samples": samples, "sample_flags": sflags, "segments": segs}
+    if want_dev:
+        out["sample_dev"] = dev
+    return out
 
 
 def single_bounce_grad(scene, camera, pixels, dL_drgb, spp, seed=0, params=None, n_threads=None, run=0):

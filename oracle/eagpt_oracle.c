@@ -475,6 +475,7 @@ typedef struct {
   int32_t* out_nhits;
   uint32_t* out_flags;
   int32_t* hit_idx;
+  double* out_dev;
 } rays_ctx;
 
 static void jitter_ray(double O[3], double w[3], uint64_t seed, int64_t pix, int32_t s, int32_t k, int32_t run,
@@ -496,9 +497,16 @@ static int rays_item(job* jb, int64_t i, hitbuf* b) {
    * relative to the value, N~ by cond_tol / 5 absolute (the comparison's
    * 2e-5 on a unit vector, with the same margin), D~ relative */
   const ora_params* prm = jb->W.prm;
+  double* dv = c->out_dev ? &c->out_dev[12 * i] : NULL;
+  if (dv)
+    for (int k = 0; k < 12; ++k) dv[k] = 0.0;
   if (prm->fp32_eps > 0 && prm->cond_tol > 0 && g.n_hits > 0) {
     const uint64_t sig = hits_signature(b);
-    for (int run = 1; run <= 2 && !(g.flags & ORA_FLAG_COND); ++run) {
+    double rec0[12];
+    write_rec(&g, rec0);
+    /* with out_dev both runs are taken, so the spread covers both; the flag
+     * is the same either way */
+    for (int run = 1; run <= 2 && (dv || !(g.flags & ORA_FLAG_COND)); ++run) {
       world Wj = jb->W;
       Wj.ajit = (uint32_t)run;
       double Oj[3] = {r[0], r[1], r[2]}, wj[3] = {r[3], r[4], r[5]};
@@ -516,6 +524,17 @@ static int rays_item(job* jb, int64_t i, hitbuf* b) {
       ill |= fabs(gj.A - g.A) > tol * fabs(g.A);
       ill |= fabs(gj.Dn - g.Dn) > tol * fabs(g.Dn);
       if (ill) g.flags |= ORA_FLAG_COND;
+      if (dv) {
+        /* per record column, the largest change over the runs; +inf on
+         * every column when a run changes the blended surfel list */
+        const int discrete = hits_signature(b) != sig;
+        double recj[12];
+        write_rec(&gj, recj);
+        for (int k = 0; k < 12; ++k) {
+          const double d = discrete ? INFINITY : fabs(recj[k] - rec0[k]);
+          if (d > dv[k]) dv[k] = d;
+        }
+      }
     }
   }
   if (c->out_flags) c->out_flags[i] = g.flags;
@@ -524,11 +543,12 @@ static int rays_item(job* jb, int64_t i, hitbuf* b) {
 
 int ora_trace_rays(const ora_scene* sc, const ora_params* prm, const double* rays, int64_t n_rays,
                    int32_t mode, double* out_rec, int32_t* out_nhits, uint32_t* out_flags, int32_t* hit_idx,
-                   int32_t max_hits, int32_t n_threads) {
+                   int32_t max_hits, double* out_dev, int32_t n_threads) {
   surfel64* s = load_surfels(sc);
   if (!s) return -1;
-  rays_ctx c = {rays, mode, max_hits, out_rec, out_nhits, out_flags, hit_idx};
+  rays_ctx c = {rays, mode, max_hits, out_rec, out_nhits, out_flags, hit_idx, out_dev};
   job jb;
+  memset(&jb, 0, sizeof(jb)); /* W.ajit = 0: the exact evaluation, no perturbation */
   jb.W.s = s;
   jb.W.n = sc->n;
   jb.W.prm = prm;
@@ -568,6 +588,7 @@ int ora_primary(const ora_scene* sc, const ora_camera* cam, const ora_params* pr
   if (!s) return -1;
   prim_ctx c = {cam, mode, pixels, out_rec, out_flags};
   job jb;
+  memset(&jb, 0, sizeof(jb)); /* W.ajit = 0: the exact evaluation, no perturbation */
   jb.W.s = s;
   jb.W.n = sc->n;
   jb.W.prm = prm;
@@ -719,6 +740,7 @@ typedef struct {
   uint32_t* out_sample_flags;
   int64_t* out_segments;
   const emitters* em; /* emitter sampling (path tracing with mis), else NULL */
+  double* out_sample_dev;
 } render_ctx;
 
 /* Perturbs a ray at FP32 rounding scale for the conditioning estimate:
@@ -964,6 +986,13 @@ static int render_item(job* jb, int64_t i, hitbuf* b) {
     if (c->out_sample_flags) c->out_sample_flags[i * c->spp + s] = sflags;
   }
   for (int k = 0; k < 3; ++k) c->out_rgb[3 * i + k] = c->spp > 0 ? acc[k] / c->spp : 0.0;
+  if (c->out_sample_dev)
+    for (int32_t s = 0; s < c->spp; ++s) {
+      /* a discrete change is reported on every channel */
+      const int discrete = n_runs && isinf(dev[3 * s]);
+      for (int k = 0; k < 3; ++k)
+        c->out_sample_dev[(i * c->spp + s) * 3 + k] = !n_runs ? 0.0 : discrete ? INFINITY : dev[3 * s + k];
+    }
   if (n_runs && c->out_sample_flags) {
     /* a sample is ill-conditioned when FP32-scale perturbations move any of
      * its channels by more than cond_tol of that channel's value (the
@@ -983,12 +1012,13 @@ static int render_item(job* jb, int64_t i, hitbuf* b) {
 int ora_render(const ora_scene* sc, const ora_camera* cam, const ora_params* prm, int32_t kind, int32_t spp,
                int32_t max_bounces, int32_t rr_start, uint64_t seed, const int32_t* pixels, int64_t n_pix,
                double* out_rgb, double* out_samples, uint32_t* out_sample_flags, int64_t* out_segments,
-               int32_t n_threads) {
+               double* out_sample_dev, int32_t n_threads) {
   surfel64* s = load_surfels(sc);
   if (!s) return -1;
   render_ctx c = {cam, kind, spp, max_bounces, rr_start, seed, pixels, out_rgb, out_samples, out_sample_flags,
-                  out_segments, NULL};
+                  out_segments, NULL, out_sample_dev};
   job jb;
+  memset(&jb, 0, sizeof(jb)); /* W.ajit = 0: the exact evaluation, no perturbation */
   jb.W.s = s;
   jb.W.n = sc->n;
   jb.W.prm = prm;

@@ -93,10 +93,15 @@ int ora_trace_segment(const ora_scene* sc, const ora_params* prm, const double O
 /* Batch of rays (origin 3, direction 3 per ray; direction unit length)
  * traced with t_lo = 0.
  * out_rec: 12 doubles per ray (Nn3, Dn, R3, E, P3, A); out_nhits; out_flags;
- * hit_idx: max_hits int32 per ray (-1 padded). */
+ * hit_idx: max_hits int32 per ray (-1 padded).
+ * out_dev (nullable): 12 doubles per ray, per record column the largest
+ *         change over the two conditioning re-traces (ray perturbed at FP32
+ *         rounding scale, every sigma g by +-4 ulps; 0 when prm->fp32_eps or
+ *         prm->cond_tol is 0 or the ray hits nothing); +inf on every column
+ *         when a re-trace changes the blended surfel list. */
 int ora_trace_rays(const ora_scene* sc, const ora_params* prm, const double* rays, int64_t n_rays,
                    int32_t mode, double* out_rec, int32_t* out_nhits, uint32_t* out_flags,
-                   int32_t* hit_idx, int32_t max_hits, int32_t n_threads);
+                   int32_t* hit_idx, int32_t max_hits, double* out_dev, int32_t n_threads);
 
 /* Emitter sampling (path tracing with mis = 1): the solid-angle density at
  * origin O of sampling direction w by the emitter-sampling strategy, summed
@@ -120,11 +125,18 @@ int ora_primary(const ora_scene* sc, const ora_camera* cam, const ora_params* pr
  * out_samples (nullable): spp*3 doubles per pixel, per-sample contributions.
  * out_sample_flags (nullable): spp flags per pixel (OR over the sample's
  *         segments, including the primary segment).
- * out_segments (nullable): segments traced per pixel (primary counted once). */
+ * out_segments (nullable): segments traced per pixel (primary counted once).
+ * out_sample_dev (nullable): spp*3 doubles per pixel, per sample and channel
+ *         the largest change of the contribution over the conditioning runs
+ *         (every ray and sigma g perturbed at FP32 rounding scale; 0 when
+ *         prm->fp32_eps or prm->cond_tol is 0); +inf on every channel when a
+ *         run changes a discrete outcome along the path (a blended surfel, a
+ *         bounce, a roulette decision). */
 int ora_render(const ora_scene* sc, const ora_camera* cam, const ora_params* prm, int32_t kind,
                int32_t spp, int32_t max_bounces, int32_t rr_start, uint64_t seed,
                const int32_t* pixels, int64_t n_pix, double* out_rgb, double* out_samples,
-               uint32_t* out_sample_flags, int64_t* out_segments, int32_t n_threads);
+               uint32_t* out_sample_flags, int64_t* out_segments, double* out_sample_dev,
+               int32_t n_threads);
 
 /* Gradient of L = sum_p sum_c dL_drgb[p][c] * I[p][c] for the single-bounce
  * render of the listed pixels, with respect to every surfel parameter.
