@@ -22,21 +22,37 @@ def radiance_close(gpu, ref, rel=REL_TOL, floor_frac=FLOOR_FRAC, mean_ref=None):
     return ok.all(axis=-1)
 
 
-def compare_samples(gpu_samples, ref_samples, sample_flags, rel=REL_TOL, primary_emitter=None):
+COND_DEV_K = 8.0  # ill-conditioned samples, entries and segments: bound + 8 x the conditioning spread
+
+
+def compare_samples(gpu_samples, ref_samples, sample_flags, rel=REL_TOL, primary_emitter=None, sample_dev=None):
     """Sample by sample, on every sample the oracle did not flag as near a
     discrete decision or ill-conditioned in FP32:
     |L_gpu - L_ref| <= rel * max(|L_ref|, 1e-3 * mean |L_ref|) per channel.
+    With sample_dev (per sample and channel, how far the oracle's
+    conditioning runs move the sample; +inf where they change a discrete
+    outcome), a sample flagged only as ill-conditioned whose spread is finite
+    is compared too, held to |L_gpu - L_ref| <= bound + 8 dev per channel.
     Returns (ok (pixels, spp): True where compared and within the bound or
-    not compared, stats).  stats counts the compared samples, the lit ones
-    (radiance > 0) and, with primary_emitter (per pixel: the pixel sees an
+    not compared, stats).  stats counts the samples compared at the bound and
+    the ill-conditioned ones compared at bound + 8 dev, the lit ones (radiance
+    > 0) of each and, with primary_emitter (per pixel: the pixel sees an
     emitter directly), the lit ones whose light came through a bounce."""
     g = np.asarray(gpu_samples, np.float64)
     r = np.asarray(ref_samples, np.float64)
-    keep = np.asarray(sample_flags) == 0
+    flags = np.asarray(sample_flags)
+    keep = flags == 0
     mean_ref = float(np.mean(np.abs(r)))
     floor = FLOOR_FRAC * mean_ref
-    within = (np.abs(g - r) <= rel * np.maximum(np.abs(r), floor)).all(axis=-1)
-    ok = within | ~keep
+    bound = rel * np.maximum(np.abs(r), floor)
+    within = (np.abs(g - r) <= bound).all(axis=-1)
+    cond = np.zeros(keep.shape, bool)
+    within_c = np.zeros(keep.shape, bool)
+    if sample_dev is not None:
+        d = np.asarray(sample_dev, np.float64)
+        cond = (flags == O.FLAGS["cond"]) & np.isfinite(d).all(axis=-1)
+        within_c = (np.abs(g - r) <= bound + COND_DEV_K * np.where(np.isfinite(d), d, 0.0)).all(axis=-1)
+    ok = np.where(keep, within, np.where(cond, within_c, True))
     err = np.abs(g - r) / np.maximum(np.abs(r), floor + 1e-30)
     err_k = err[keep].max(axis=-1) if keep.any() else np.zeros(0)
     lit = np.abs(r).max(axis=-1) > 0
@@ -46,13 +62,18 @@ def compare_samples(gpu_samples, ref_samples, sample_flags, rel=REL_TOL, primary
              "max_rel": float(err_k.max()) if err_k.size else 0.0,
              "p999_rel": float(np.quantile(err_k, 0.999)) if err_k.size else 0.0,
              "mean_rel": float(err_k.mean()) if err_k.size else 0.0}
+    if sample_dev is not None:
+        stats["cond_compared"] = int(cond.sum())
+        stats["lit_cond_compared"] = int((lit & cond).sum())
     if primary_emitter is not None:
         bounced = lit & ~np.asarray(primary_emitter, bool)[:, None]
         stats["lit_bounced_compared"] = int((bounced & keep).sum())
+        if sample_dev is not None:
+            stats["lit_bounced_cond_compared"] = int((bounced & cond).sum())
     if stats["fail"]:
         bad = np.argwhere(~ok)[:4]
         stats["worst"] = [{"pixel_row": int(i), "sample": int(j), "gpu": g[i, j].tolist(), "ref": r[i, j].tolist(),
-                           "rel": float(err[i, j].max())} for i, j in bad]
+                           "rel": float(err[i, j].max()), "flags": int(flags[i, j])} for i, j in bad]
     return ok, stats
 
 
@@ -96,7 +117,7 @@ def grad_errors(g_gpu, g_ref, tol=GRAD_TOL, dev=None):
     if dev is not None:
         d = np.asarray(dev, np.float64)
         ill = d > 0.25 * bound
-        ok = np.where(ill, err <= bound + 8.0 * d, err <= bound)
+        ok = np.where(ill, err <= bound + COND_DEV_K * d, err <= bound)
     else:
         ok = err <= bound
     well = ~ill
@@ -157,12 +178,14 @@ def lit_pixels(scene, cam, n_pick, n_cand, seed=7, n_threads=None):
     """n_pick pixels, from n_cand random candidates (seeded), whose primary
     vertex (a non-emitter hit in the oracle's primary records) has the
     largest unoccluded form factor to the emitters, sum_i A_i cos_x cos_i /
-    (pi r^2): the pixels whose paths reach an emitter most often.  The choice
-    uses the oracle's records only."""
+    (pi r^2): the pixels whose paths reach an emitter most often.  Pixels
+    whose primary segment the oracle flags (a decision every sample of the
+    pixel shares) come last.  The choice uses the oracle's records only."""
     rng = np.random.default_rng(seed)
     npix = cam.width * cam.height
     cand = rng.choice(npix, min(n_cand, npix), replace=False).astype(np.int32)
     X, N, emit, hit = primary_vertices(scene, cam, cand, n_threads)
+    _rec, pfl = O.primary(scene, cam, cand, mode=1, n_threads=n_threads)
     _em, P, nE, area = emitter_frames(scene)
     F = np.full(cand.size, -1.0)
     ok = hit & ~emit
@@ -175,7 +198,7 @@ def lit_pixels(scene, cam, n_pick, n_cand, seed=7, n_threads=None):
         cx = np.clip((dn * N[b, None, :]).sum(-1), 0.0, None)
         ce = np.abs((dn * nE[None]).sum(-1))
         F[b] = (area[None] * cx * ce / (np.pi * r2)).sum(-1)
-    order = np.argsort(-F, kind="stable")
+    order = np.lexsort((-F, pfl != 0))
     return np.sort(cand[order[:n_pick]])
 
 
