@@ -48,6 +48,9 @@ def parse():
                     choices=["tiny", "medium", "diff", "large", "serving", "stage1", "bake", "mis"])
     ap.add_argument("--views", type=int, default=8, help="stage1/bake: training views")
     ap.add_argument("--requests", type=int, default=16, help="serving: requests in the stream")
+    ap.add_argument("--stream", default="mixed", choices=["mixed", "small"],
+                    help="serving: the mixed stream (256x256..1920x1080, 16/64/256 spp) or small requests only "
+                         "(256x256, 16 spp)")
     ap.add_argument("--spp", type=int, default=None, help="override samples per pixel (of the frame)")
     ap.add_argument("--slice-spp", type=int, default=None,
                     help="samples per step (default: 64 for the large render, the whole frame otherwise)")
@@ -298,7 +301,10 @@ def run_serving(args):
     torch.cuda.set_device(dev)
     host = S.serving_room()
     wl = S.workload("serving")
-    reqs = S.serving_requests(host, args.requests, seed=13)
+    if args.stream == "small":
+        reqs = S.serving_requests(host, args.requests, seed=13, spp_choices=[16], res_choices=[(256, 256)])
+    else:
+        reqs = S.serving_requests(host, args.requests, seed=13)
     n_render = sum(1 for r in reqs if r["type"] == "render")
     samples = sum(r["camera"].width * r["camera"].height * r["spp"] for r in reqs if r["type"] == "render")
     queue_paths = 1 << 27
@@ -402,7 +408,7 @@ def run_serving(args):
             "unit": "pixel samples/s", "n_gpus": 1, "steps": 1, "warmup": args.warmup, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "serving room 3M surfels, seeded request stream", "scale_factor": wl.scale_factor,
-                       "requests": len(reqs), "renders": n_render, "pixel_samples": samples,
+                       "stream": args.stream, "requests": len(reqs), "renders": n_render, "pixel_samples": samples,
                        "queue_paths": queue_paths, "max_active": 16},
             "plain": plain, "closed_loop": closed, "speedup_vs_plain": closed["throughput"] / plain["throughput"],
             "poisson": results}

@@ -443,33 +443,34 @@ bool Server::apply_edit_locked(Req& r, std::unique_lock<std::mutex>& lk) {
   return true;
 }
 
-// Samples of each active render in the next wave.  The queue is filled
-// shortest remaining work first (pixels x samples left x bounces), which keeps
-// small requests from waiting on large ones: one sample per request first,
-// in that order while it fits but with the longest-admitted request ahead of
-// all, so that it always progresses and no request starves; then the rest of
-// the queue in shortest-remaining-work order.  The batches only change which
-// wave a sample is traced in: every image still sums its samples in sample
-// order.
-static std::vector<int> plan_wave(const std::vector<const Req*>& act, int64_t queue_cap) {
-  const size_t n = act.size();
-  std::vector<size_t> order(n);
-  for (size_t k = 0; k < n; ++k) order[k] = k;
+// Samples of each active render in the next wave.  Requests still rendering
+// the previous scene version (admitted before an edit) come first, so that a
+// wave holds both versions only when the older one's remaining work no longer
+// fills it: two BVHs in one wave share the caches, and the plain order of a
+// request stream (the renders before an edit, then the edit) renders one
+// version at a time.  Within a version the queue is filled shortest
+// remaining work first (pixels x samples left x bounces), which keeps small
+// requests from waiting on large ones: one sample per request first, in that
+// order while it fits but with the longest-admitted request ahead of all, so
+// that it always progresses and no request starves; then the rest of the
+// queue in shortest-remaining-work order.  The batches only change which wave
+// a sample is traced in: every image still sums its samples in sample order.
+static void plan_group(const std::vector<const Req*>& act, const std::vector<size_t>& group, int64_t& left,
+                       std::vector<int>& batch) {
+  const size_t n = group.size();
+  if (!n) return;
+  std::vector<size_t> order = group;
   auto work = [&](size_t k) {
     const Req& r = *act[k];
     return (double)r.npix * (double)(r.rr.spp - r.s_next) * (double)std::max(1, r.rr.max_bounces);
   };
   std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) { return work(a) < work(b); });
   std::vector<size_t> first = order;
-  size_t oldest = 0;
-  for (size_t k = 1; k < n; ++k)
+  size_t oldest = group[0];
+  for (size_t k : group)
     if (act[k]->t_admit < act[oldest]->t_admit) oldest = k;
-  if (n) {
-    first.erase(std::find(first.begin(), first.end(), oldest));
-    first.insert(first.begin(), oldest);
-  }
-  std::vector<int> batch(n, 0);
-  int64_t left = queue_cap;
+  first.erase(std::find(first.begin(), first.end(), oldest));
+  first.insert(first.begin(), oldest);
   for (size_t k : first) {
     const Req& r = *act[k];
     if (r.s_next < r.rr.spp && r.npix <= left) {
@@ -483,6 +484,17 @@ static std::vector<int> plan_wave(const std::vector<const Req*>& act, int64_t qu
     const int64_t more = std::min<int64_t>(r.rr.spp - r.s_next - batch[k], left / std::max<int64_t>(1, r.npix));
     batch[k] += (int)more;
     left -= more * r.npix;
+  }
+}
+
+static std::vector<int> plan_wave(const std::vector<const Req*>& act, int64_t queue_cap, int current) {
+  std::vector<int> batch(act.size(), 0);
+  int64_t left = queue_cap;
+  for (int older = 1; older >= 0; --older) {
+    std::vector<size_t> group;
+    for (size_t k = 0; k < act.size(); ++k)
+      if ((act[k]->version != current) == (older == 1)) group.push_back(k);
+    plan_group(act, group, left, batch);
   }
   return batch;
 }
@@ -528,7 +540,7 @@ void Server::enqueue_wave(std::unique_lock<std::mutex>& lk) {
       act_ids.push_back(id);
     }
   }
-  const std::vector<int> plan = plan_wave(act, queue_cap);
+  const std::vector<int> plan = plan_wave(act, queue_cap, current);
   int64_t paths = 0, pixels = 0;
   int maxB = 0, nreq = 0;
   ReqDev* tab = table_h[slot];
