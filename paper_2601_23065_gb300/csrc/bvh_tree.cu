@@ -6,6 +6,8 @@
 //                 are broken by position, so the tree is always complete.
 //                 Records children, parents and the surfel range of every
 //                 internal node.
+//   k_treelets    rebuilds every maximal subtree of at most 32 surfels with
+//                 the surface area heuristic (sweep over sorted centres)
 //   k_refit       bottom-up boxes of the binary tree (visit counters: the
 //                 second child to arrive computes the parent), and the sum of
 //                 node surface areas (the refit-quality measure).
@@ -71,15 +73,167 @@ __global__ void k_hierarchy(const uint32_t* __restrict__ keys, int64_t n, uint32
   if (i == 0) inode_parent[0] = 0xFFFFFFFFu;
 }
 
+__device__ __forceinline__ float box_area(float4 lo, float4 hi) {
+  const float dx = fmaxf(hi.x - lo.x, 0.f), dy = fmaxf(hi.y - lo.y, 0.f), dz = fmaxf(hi.z - lo.z, 0.f);
+  return 2.f * (dx * dy + dy * dz + dz * dx);
+}
+
+// Treelet restructuring.  The radix tree orders surfels along the Morton
+// curve of their centres, which at the bottom of the tree groups thin surfels
+// of different sizes and orientations by where their centres fall.  Every
+// maximal subtree of at most kTreelet surfels is rebuilt top-down with the
+// surface area heuristic (SAH) over their boxes: at each node the centres are
+// sorted along each axis and every split point is scored by
+// area(left) x |left| + area(right) x |right|; the cheapest one is taken.
+// The subtree keeps its root and its internal node slots; only child links,
+// parents and subtree sizes change, and the records keep their positions, so
+// treelets rebuild independently.  A node's surfel range is then read only
+// for its size (one surfel per leaf).
+constexpr int kTreelet = 32;
+static_assert(kLeafMax == 1, "restructured nodes keep only the size of their surfel range");
+
+__device__ __forceinline__ float centre_on(const float4& lo, const float4& hi, int axis) {
+  return axis == 0 ? lo.x + hi.x : axis == 1 ? lo.y + hi.y : lo.z + hi.z;  // twice the centre
+}
+
+__global__ void k_treelets(int64_t n, const float4* __restrict__ plo, const float4* __restrict__ phi,
+                           int32_t* child_bin, int2* irange, uint32_t* leaf_parent, uint32_t* inode_parent) {
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n - 1; r += (int64_t)gridDim.x * blockDim.x) {
+    const int2 rr = irange[r];
+    const int m = rr.y - rr.x + 1;
+    if (m < 3 || m > kTreelet) continue;  // two surfels have one topology
+    const uint32_t p = inode_parent[r];
+    if (p != 0xFFFFFFFFu) {
+      const int2 pr = irange[p];
+      if (pr.y - pr.x + 1 <= kTreelet) continue;  // not a maximal subtree
+    }
+    // the subtree's internal slots (root first) and surfel positions
+    int32_t ids[kTreelet];
+    uint32_t pos[kTreelet];
+    int32_t stk[kTreelet + 1];
+    int nid = 0, np = 0, sp = 0;
+    bool ok = true;
+    stk[sp++] = (int32_t)r;
+    while (sp > 0 && ok) {
+      const int32_t c = stk[--sp];
+      if (c < 0) {
+        if (np < kTreelet) pos[np++] = (uint32_t)~c;
+        else ok = false;
+        continue;
+      }
+      if (nid >= kTreelet - 1 || sp + 2 > kTreelet + 1) {
+        ok = false;
+        continue;
+      }
+      ids[nid++] = c;
+      stk[sp++] = child_bin[2 * (int64_t)c + 1];
+      stk[sp++] = child_bin[2 * (int64_t)c];
+    }
+    if (!ok || np != m || nid != m - 1) {
+      raise_error(kErrBadIndex);
+      continue;
+    }
+    float4 lo[kTreelet], hi[kTreelet];
+    for (int k = 0; k < m; ++k) {
+      lo[k] = plo[pos[k]];
+      hi[k] = phi[pos[k]];
+    }
+    uint8_t item[kTreelet];
+    for (int k = 0; k < m; ++k) item[k] = (uint8_t)k;
+    // pending nodes: (first item, item count, slot)
+    uint8_t t_first[kTreelet], t_count[kTreelet];
+    int32_t t_id[kTreelet];
+    int nt = 0, next_slot = 1;
+    t_first[0] = 0;
+    t_count[0] = (uint8_t)m;
+    t_id[0] = (int32_t)r;
+    nt = 1;
+    while (nt > 0) {
+      --nt;
+      const int s = t_first[nt], k = t_count[nt];
+      const int32_t id = t_id[nt];
+      float best = __int_as_float(0x7f800000);
+      int best_axis = 0, best_split = k / 2;
+      uint8_t tmp[kTreelet];
+      float sfx[kTreelet];
+      for (int axis = 0; axis < 3; ++axis) {
+        for (int j = 0; j < k; ++j) tmp[j] = item[s + j];
+        // insertion sort by centre, ties by item index (deterministic)
+        for (int j = 1; j < k; ++j) {
+          const uint8_t v = tmp[j];
+          const float key = centre_on(lo[v], hi[v], axis);
+          int q = j - 1;
+          while (q >= 0) {
+            const float kq = centre_on(lo[tmp[q]], hi[tmp[q]], axis);
+            if (kq < key || (kq == key && tmp[q] < v)) break;
+            tmp[q + 1] = tmp[q];
+            --q;
+          }
+          tmp[q + 1] = v;
+        }
+        // areas of the suffixes tmp[j..k)
+        float4 bl = lo[tmp[k - 1]], bh = hi[tmp[k - 1]];
+        for (int j = k - 1; j >= 1; --j) {
+          const uint8_t v = tmp[j];
+          bl = make_float4(fminf(bl.x, lo[v].x), fminf(bl.y, lo[v].y), fminf(bl.z, lo[v].z), 0.f);
+          bh = make_float4(fmaxf(bh.x, hi[v].x), fmaxf(bh.y, hi[v].y), fmaxf(bh.z, hi[v].z), 0.f);
+          sfx[j] = box_area(bl, bh);
+        }
+        float4 al = lo[tmp[0]], ah = hi[tmp[0]];
+        for (int j = 1; j < k; ++j) {
+          const float cost = box_area(al, ah) * (float)j + sfx[j] * (float)(k - j);
+          if (cost < best) {
+            best = cost;
+            best_axis = axis;
+            best_split = j;
+          }
+          const uint8_t v = tmp[j];
+          al = make_float4(fminf(al.x, lo[v].x), fminf(al.y, lo[v].y), fminf(al.z, lo[v].z), 0.f);
+          ah = make_float4(fmaxf(ah.x, hi[v].x), fmaxf(ah.y, hi[v].y), fmaxf(ah.z, hi[v].z), 0.f);
+        }
+      }
+      // order the node's items along the chosen axis
+      for (int j = 1; j < k; ++j) {
+        const uint8_t v = item[s + j];
+        const float key = centre_on(lo[v], hi[v], best_axis);
+        int q = j - 1;
+        while (q >= 0) {
+          const float kq = centre_on(lo[item[s + q]], hi[item[s + q]], best_axis);
+          if (kq < key || (kq == key && item[s + q] < v)) break;
+          item[s + q + 1] = item[s + q];
+          --q;
+        }
+        item[s + q + 1] = v;
+      }
+      for (int side = 0; side < 2; ++side) {
+        const int cs = side == 0 ? s : s + best_split;
+        const int ck = side == 0 ? best_split : k - best_split;
+        int32_t code;
+        if (ck == 1) {
+          const uint32_t leaf = pos[item[cs]];
+          code = ~(int32_t)leaf;
+          leaf_parent[leaf] = (uint32_t)id;
+        } else {
+          const int32_t cid = ids[next_slot++];
+          code = cid;
+          inode_parent[cid] = (uint32_t)id;
+          irange[cid] = make_int2(rr.x, rr.x + ck - 1);  // the size is what is read
+          t_first[nt] = (uint8_t)cs;
+          t_count[nt] = (uint8_t)ck;
+          t_id[nt] = cid;
+          ++nt;
+        }
+        child_bin[2 * (int64_t)id + side] = code;
+      }
+    }
+  }
+}
+
 __global__ void k_clear_u32(uint32_t* p, int64_t n) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i < n) p[i] = 0u;
 }
 
-__device__ __forceinline__ float box_area(float4 lo, float4 hi) {
-  const float dx = fmaxf(hi.x - lo.x, 0.f), dy = fmaxf(hi.y - lo.y, 0.f), dz = fmaxf(hi.z - lo.z, 0.f);
-  return 2.f * (dx * dy + dy * dz + dz * dx);
-}
 
 __global__ void k_refit(int64_t n, const float4* __restrict__ plo, const float4* __restrict__ phi, float4* ilo,
                         float4* ihi, const uint32_t* __restrict__ leaf_parent,
@@ -308,6 +462,11 @@ cudaError_t launch_tree(const uint32_t* sorted_keys, char* base, const BvhLayout
                k_hierarchy<<<blocks_for(n - 1, 256), 256, 0, st>>>(
                    sorted_keys, n, (uint32_t*)(base + L.leaf_parent), (uint32_t*)(base + L.inode_parent),
                    (int32_t*)(base + L.child_bin), (int2*)(base + L.irange)));
+  EAGPT_LAUNCH(st, "k_treelets",
+               k_treelets<<<blocks_for(n - 1, 128), 128, 0, st>>>(
+                   n, (const float4*)(base + L.prim_lo), (const float4*)(base + L.prim_hi),
+                   (int32_t*)(base + L.child_bin), (int2*)(base + L.irange), (uint32_t*)(base + L.leaf_parent),
+                   (uint32_t*)(base + L.inode_parent)));
   launch_binary_refit(base, L, st);
   int2* fr[2] = {(int2*)(base + L.front0), (int2*)(base + L.front1)};
   EAGPT_LAUNCH(st, "k_collapse_init", k_collapse_init<<<1, 128, 0, st>>>(levels, fr[0]));
