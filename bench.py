@@ -150,7 +150,8 @@ class ClockSampler:
 # --------------------------------------------------------------------------
 # the sources that define the bounce kernel (its traffic summary is valid
 # while these are unchanged)
-BOUNCE_SOURCES = ("render.cu", "trace.cuh", "wave.cuh", "common.cuh")
+# the bounce kernel's sources and the BVH builder's (the tree shapes its traffic)
+BOUNCE_SOURCES = ("render.cu", "trace.cuh", "wave.cuh", "common.cuh", "bvh.cu", "bvh_tree.cu")
 
 
 def source_digest() -> str:

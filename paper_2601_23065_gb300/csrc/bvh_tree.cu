@@ -92,12 +92,10 @@ __device__ __forceinline__ float box_area(float4 lo, float4 hi) {
 constexpr int kTreelet = 32;
 static_assert(kLeafMax == 1, "restructured nodes keep only the size of their surfel range");
 
-__device__ __forceinline__ float centre_on(const float4& lo, const float4& hi, int axis) {
-  return axis == 0 ? lo.x + hi.x : axis == 1 ? lo.y + hi.y : lo.z + hi.z;  // twice the centre
-}
-
-__global__ void k_treelets(int64_t n, const float4* __restrict__ plo, const float4* __restrict__ phi,
-                           int32_t* child_bin, int2* irange, uint32_t* leaf_parent, uint32_t* inode_parent) {
+// Roots of the treelets: internal nodes of 3..kTreelet surfels whose parent
+// holds more (or the root), appended to a list.
+__global__ void k_treelet_roots(int64_t n, const int2* __restrict__ irange, const uint32_t* __restrict__ inode_parent,
+                                uint32_t* roots, uint32_t* count) {
   for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n - 1; r += (int64_t)gridDim.x * blockDim.x) {
     const int2 rr = irange[r];
     const int m = rr.y - rr.x + 1;
@@ -107,9 +105,40 @@ __global__ void k_treelets(int64_t n, const float4* __restrict__ plo, const floa
       const int2 pr = irange[p];
       if (pr.y - pr.x + 1 <= kTreelet) continue;  // not a maximal subtree
     }
+    roots[atomicAdd(count, 1u)] = (uint32_t)r;
+  }
+}
+
+// One warp per block, one treelet per lane; each lane's working set lives in
+// shared memory, laid out [field][slot][lane] so that the lanes of a warp
+// touch consecutive words.  Each axis's centre order is found once per
+// treelet (rank by comparison, ties by slot); a split keeps the three orders
+// of both children by stable partition, so a node costs O(size) per axis.
+// Each treelet's result depends only on the treelet, not on the lane or the
+// order of the root list.
+constexpr int kTreeletLanes = 32;
+
+__global__ void __launch_bounds__(kTreeletLanes) k_treelets(const uint32_t* __restrict__ roots,
+                                                            const uint32_t* __restrict__ count,
+                                                            const float4* __restrict__ plo,
+                                                            const float4* __restrict__ phi, int32_t* child_bin,
+                                                            int2* irange, uint32_t* leaf_parent,
+                                                            uint32_t* inode_parent) {
+  __shared__ float s_c[3][kTreelet][kTreeletLanes];  // box centres
+  __shared__ float s_e[3][kTreelet][kTreeletLanes];  // box half extents
+  __shared__ uint8_t s_ord[3][kTreelet][kTreeletLanes];
+  __shared__ uint8_t s_tmp[kTreelet][kTreeletLanes];
+  __shared__ uint8_t s_left[kTreelet][kTreeletLanes];
+  __shared__ float s_sfx[kTreelet][kTreeletLanes];
+  __shared__ uint32_t s_pos[kTreelet][kTreeletLanes];
+  __shared__ int32_t s_ids[kTreelet][kTreeletLanes];
+  const int ln = threadIdx.x;
+  const uint32_t nroots = *count;
+  for (uint32_t q = blockIdx.x * kTreeletLanes + ln; q < nroots; q += gridDim.x * kTreeletLanes) {
+    const uint32_t r = roots[q];
+    const int2 rr = irange[r];
+    const int m = rr.y - rr.x + 1;
     // the subtree's internal slots (root first) and surfel positions
-    int32_t ids[kTreelet];
-    uint32_t pos[kTreelet];
     int32_t stk[kTreelet + 1];
     int nid = 0, np = 0, sp = 0;
     bool ok = true;
@@ -117,7 +146,7 @@ __global__ void k_treelets(int64_t n, const float4* __restrict__ plo, const floa
     while (sp > 0 && ok) {
       const int32_t c = stk[--sp];
       if (c < 0) {
-        if (np < kTreelet) pos[np++] = (uint32_t)~c;
+        if (np < kTreelet) s_pos[np++][ln] = (uint32_t)~c;
         else ok = false;
         continue;
       }
@@ -125,7 +154,7 @@ __global__ void k_treelets(int64_t n, const float4* __restrict__ plo, const floa
         ok = false;
         continue;
       }
-      ids[nid++] = c;
+      s_ids[nid++][ln] = c;
       stk[sp++] = child_bin[2 * (int64_t)c + 1];
       stk[sp++] = child_bin[2 * (int64_t)c];
     }
@@ -133,88 +162,95 @@ __global__ void k_treelets(int64_t n, const float4* __restrict__ plo, const floa
       raise_error(kErrBadIndex);
       continue;
     }
-    float4 lo[kTreelet], hi[kTreelet];
     for (int k = 0; k < m; ++k) {
-      lo[k] = plo[pos[k]];
-      hi[k] = phi[pos[k]];
+      const float4 lo = plo[s_pos[k][ln]], hi = phi[s_pos[k][ln]];
+      s_c[0][k][ln] = 0.5f * (lo.x + hi.x);
+      s_c[1][k][ln] = 0.5f * (lo.y + hi.y);
+      s_c[2][k][ln] = 0.5f * (lo.z + hi.z);
+      // half extents (the heuristic needs the areas only approximately)
+      s_e[0][k][ln] = fmaxf(s_c[0][k][ln] - lo.x, hi.x - s_c[0][k][ln]);
+      s_e[1][k][ln] = fmaxf(s_c[1][k][ln] - lo.y, hi.y - s_c[1][k][ln]);
+      s_e[2][k][ln] = fmaxf(s_c[2][k][ln] - lo.z, hi.z - s_c[2][k][ln]);
     }
-    uint8_t item[kTreelet];
-    for (int k = 0; k < m; ++k) item[k] = (uint8_t)k;
-    // pending nodes: (first item, item count, slot)
+    for (int a = 0; a < 3; ++a)
+      for (int i = 0; i < m; ++i) {
+        const float ci = s_c[a][i][ln];
+        int rank = 0;
+        for (int j = 0; j < m; ++j) {
+          const float cj = s_c[a][j][ln];
+          rank += (cj < ci || (cj == ci && j < i)) ? 1 : 0;
+        }
+        s_ord[a][rank][ln] = (uint8_t)i;
+      }
+    // pending nodes: (first, count, slot); every node's items occupy
+    // [first, first + count) of all three orders
     uint8_t t_first[kTreelet], t_count[kTreelet];
     int32_t t_id[kTreelet];
-    int nt = 0, next_slot = 1;
+    int nt = 1, next_slot = 1;
     t_first[0] = 0;
     t_count[0] = (uint8_t)m;
     t_id[0] = (int32_t)r;
-    nt = 1;
     while (nt > 0) {
       --nt;
       const int s = t_first[nt], k = t_count[nt];
       const int32_t id = t_id[nt];
       float best = __int_as_float(0x7f800000);
       int best_axis = 0, best_split = k / 2;
-      uint8_t tmp[kTreelet];
-      float sfx[kTreelet];
-      for (int axis = 0; axis < 3; ++axis) {
-        for (int j = 0; j < k; ++j) tmp[j] = item[s + j];
-        // insertion sort by centre, ties by item index (deterministic)
-        for (int j = 1; j < k; ++j) {
-          const uint8_t v = tmp[j];
-          const float key = centre_on(lo[v], hi[v], axis);
-          int q = j - 1;
-          while (q >= 0) {
-            const float kq = centre_on(lo[tmp[q]], hi[tmp[q]], axis);
-            if (kq < key || (kq == key && tmp[q] < v)) break;
-            tmp[q + 1] = tmp[q];
-            --q;
-          }
-          tmp[q + 1] = v;
-        }
-        // areas of the suffixes tmp[j..k)
-        float4 bl = lo[tmp[k - 1]], bh = hi[tmp[k - 1]];
+      for (int a = 0; a < 3; ++a) {
+        // areas of the suffixes [j, k) of this axis's order
+        float lx = 3e38f, ly = 3e38f, lz = 3e38f, hx = -3e38f, hy = -3e38f, hz = -3e38f;
         for (int j = k - 1; j >= 1; --j) {
-          const uint8_t v = tmp[j];
-          bl = make_float4(fminf(bl.x, lo[v].x), fminf(bl.y, lo[v].y), fminf(bl.z, lo[v].z), 0.f);
-          bh = make_float4(fmaxf(bh.x, hi[v].x), fmaxf(bh.y, hi[v].y), fmaxf(bh.z, hi[v].z), 0.f);
-          sfx[j] = box_area(bl, bh);
+          const int v = s_ord[a][s + j][ln];
+          lx = fminf(lx, s_c[0][v][ln] - s_e[0][v][ln]);
+          ly = fminf(ly, s_c[1][v][ln] - s_e[1][v][ln]);
+          lz = fminf(lz, s_c[2][v][ln] - s_e[2][v][ln]);
+          hx = fmaxf(hx, s_c[0][v][ln] + s_e[0][v][ln]);
+          hy = fmaxf(hy, s_c[1][v][ln] + s_e[1][v][ln]);
+          hz = fmaxf(hz, s_c[2][v][ln] + s_e[2][v][ln]);
+          s_sfx[j][ln] = box_area(make_float4(lx, ly, lz, 0.f), make_float4(hx, hy, hz, 0.f));
         }
-        float4 al = lo[tmp[0]], ah = hi[tmp[0]];
+        lx = ly = lz = 3e38f;
+        hx = hy = hz = -3e38f;
         for (int j = 1; j < k; ++j) {
-          const float cost = box_area(al, ah) * (float)j + sfx[j] * (float)(k - j);
+          const int v = s_ord[a][s + j - 1][ln];
+          lx = fminf(lx, s_c[0][v][ln] - s_e[0][v][ln]);
+          ly = fminf(ly, s_c[1][v][ln] - s_e[1][v][ln]);
+          lz = fminf(lz, s_c[2][v][ln] - s_e[2][v][ln]);
+          hx = fmaxf(hx, s_c[0][v][ln] + s_e[0][v][ln]);
+          hy = fmaxf(hy, s_c[1][v][ln] + s_e[1][v][ln]);
+          hz = fmaxf(hz, s_c[2][v][ln] + s_e[2][v][ln]);
+          const float cost = box_area(make_float4(lx, ly, lz, 0.f), make_float4(hx, hy, hz, 0.f)) * (float)j +
+                             s_sfx[j][ln] * (float)(k - j);
           if (cost < best) {
             best = cost;
-            best_axis = axis;
+            best_axis = a;
             best_split = j;
           }
-          const uint8_t v = tmp[j];
-          al = make_float4(fminf(al.x, lo[v].x), fminf(al.y, lo[v].y), fminf(al.z, lo[v].z), 0.f);
-          ah = make_float4(fmaxf(ah.x, hi[v].x), fmaxf(ah.y, hi[v].y), fmaxf(ah.z, hi[v].z), 0.f);
         }
       }
-      // order the node's items along the chosen axis
-      for (int j = 1; j < k; ++j) {
-        const uint8_t v = item[s + j];
-        const float key = centre_on(lo[v], hi[v], best_axis);
-        int q = j - 1;
-        while (q >= 0) {
-          const float kq = centre_on(lo[item[s + q]], hi[item[s + q]], best_axis);
-          if (kq < key || (kq == key && item[s + q] < v)) break;
-          item[s + q + 1] = item[s + q];
-          --q;
+      // the left child's items: the first best_split of the chosen order;
+      // the two other orders are partitioned stably
+      for (int j = 0; j < k; ++j) s_left[s_ord[best_axis][s + j][ln]][ln] = (uint8_t)(j < best_split);
+      for (int a = 0; a < 3; ++a) {
+        if (a == best_axis) continue;
+        int nl = 0, nr = best_split;
+        for (int j = 0; j < k; ++j) {
+          const uint8_t v = s_ord[a][s + j][ln];
+          if (s_left[v][ln]) s_tmp[nl++][ln] = v;
+          else s_tmp[nr++][ln] = v;
         }
-        item[s + q + 1] = v;
+        for (int j = 0; j < k; ++j) s_ord[a][s + j][ln] = s_tmp[j][ln];
       }
       for (int side = 0; side < 2; ++side) {
         const int cs = side == 0 ? s : s + best_split;
         const int ck = side == 0 ? best_split : k - best_split;
         int32_t code;
         if (ck == 1) {
-          const uint32_t leaf = pos[item[cs]];
+          const uint32_t leaf = s_pos[s_ord[best_axis][cs][ln]][ln];
           code = ~(int32_t)leaf;
           leaf_parent[leaf] = (uint32_t)id;
         } else {
-          const int32_t cid = ids[next_slot++];
+          const int32_t cid = s_ids[next_slot++][ln];
           code = cid;
           inode_parent[cid] = (uint32_t)id;
           irange[cid] = make_int2(rr.x, rr.x + ck - 1);  // the size is what is read
@@ -462,9 +498,17 @@ cudaError_t launch_tree(const uint32_t* sorted_keys, char* base, const BvhLayout
                k_hierarchy<<<blocks_for(n - 1, 256), 256, 0, st>>>(
                    sorted_keys, n, (uint32_t*)(base + L.leaf_parent), (uint32_t*)(base + L.inode_parent),
                    (int32_t*)(base + L.child_bin), (int2*)(base + L.irange)));
+  // treelet roots go to the refit's visit counters (cleared before the refit),
+  // their count to the collapse's level counters (cleared before the collapse)
+  uint32_t* roots = (uint32_t*)(base + L.visit);
+  cudaError_t me = cudaMemsetAsync(levels, 0, sizeof(uint32_t), st);
+  if (me != cudaSuccess) return me;
+  EAGPT_LAUNCH(st, "k_treelet_roots",
+               k_treelet_roots<<<blocks_for(n - 1, 256), 256, 0, st>>>(
+                   n, (const int2*)(base + L.irange), (const uint32_t*)(base + L.inode_parent), roots, levels));
   EAGPT_LAUNCH(st, "k_treelets",
-               k_treelets<<<blocks_for(n - 1, 128), 128, 0, st>>>(
-                   n, (const float4*)(base + L.prim_lo), (const float4*)(base + L.prim_hi),
+               k_treelets<<<(unsigned)(8 * device_sms()), kTreeletLanes, 0, st>>>(
+                   roots, levels, (const float4*)(base + L.prim_lo), (const float4*)(base + L.prim_hi),
                    (int32_t*)(base + L.child_bin), (int2*)(base + L.irange), (uint32_t*)(base + L.leaf_parent),
                    (uint32_t*)(base + L.inode_parent)));
   launch_binary_refit(base, L, st);
