@@ -308,11 +308,14 @@ eagpt_status eagpt_insert_surfels(eagpt_scene_mut* scene, int64_t capacity, cons
  * A host thread runs waves: each wave takes the next samples of the admitted
  * renders, puts all their paths into one shared wavefront queue of
  * queue_paths paths (rays carry a request id) and runs the path-tracing
- * kernels once over it (continuous batching).  The queue is filled shortest
- * remaining work first (pixels x samples left x bounces): one sample per
- * request while it fits, the longest-admitted request always included, then
- * the rest of the queue in shortest-remaining-work order, so small requests
- * do not wait on large ones and no request starves.  Two waves are in
+ * kernels once over it (continuous batching).  Requests still rendering the
+ * previous scene version (admitted before an edit) are planned first, so a
+ * wave holds two versions only when the older one's remaining work does not
+ * fill it.  Within a version the queue is filled shortest remaining work first
+ * (pixels x samples left x bounces): one sample per request while it fits,
+ * the longest-admitted request always included, then the rest of the queue in
+ * shortest-remaining-work order, so small requests do not wait on large ones
+ * and no request starves.  Two waves are in
  * flight, each on its own stream with its own queues: the next wave is
  * planned and enqueued while the current one runs, and its first bounces
  * overlap the current wave's last ones.  A request completes when the wave
