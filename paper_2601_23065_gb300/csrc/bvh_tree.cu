@@ -6,7 +6,7 @@
 //                 are broken by position, so the tree is always complete.
 //                 Records children, parents and the surfel range of every
 //                 internal node.
-//   k_treelets    rebuilds every maximal subtree of at most 32 surfels with
+//   k_treelets    rebuilds every maximal subtree of at most 256 surfels with
 //                 the surface area heuristic (sweep over sorted centres)
 //   k_refit       bottom-up boxes of the binary tree (visit counters: the
 //                 second child to arrive computes the parent), and the sum of
@@ -89,8 +89,14 @@ __device__ __forceinline__ float box_area(float4 lo, float4 hi) {
 // parents and subtree sizes change, and the records keep their positions, so
 // treelets rebuild independently.  A node's surfel range is then read only
 // for its size (one surfel per leaf).
-constexpr int kTreelet = 32;
+//
+// A radix-tree subtree rooted at r covers the positions [f, l], and its
+// internal nodes are the slots [f, l] except the end of the range that r is
+// not (r is f or l): the slots and surfels of a treelet follow from its range.
+constexpr int kTreelet = 256;
+constexpr int kTreeletWarps = 4;  // one treelet per warp, four warps per block
 static_assert(kLeafMax == 1, "restructured nodes keep only the size of their surfel range");
+static_assert(kTreelet <= 256, "a treelet's surfels are indexed by bytes");
 
 // Roots of the treelets: internal nodes of 3..kTreelet surfels whose parent
 // holds more (or the root), appended to a list.
@@ -109,159 +115,205 @@ __global__ void k_treelet_roots(int64_t n, const int2* __restrict__ irange, cons
   }
 }
 
-// One warp per block, one treelet per lane; each lane's working set lives in
-// shared memory, laid out [field][slot][lane] so that the lanes of a warp
-// touch consecutive words.  Each axis's centre order is found once per
-// treelet (rank by comparison, ties by slot); a split keeps the three orders
-// of both children by stable partition, so a node costs O(size) per axis.
-// Each treelet's result depends only on the treelet, not on the lane or the
-// order of the root list.
-constexpr int kTreeletLanes = 32;
+struct Box6 {
+  float lx, ly, lz, hx, hy, hz;
+};
+__device__ __forceinline__ Box6 box_empty() { return {3e38f, 3e38f, 3e38f, -3e38f, -3e38f, -3e38f}; }
+__device__ __forceinline__ void box_grow(Box6& b, const Box6& o) {
+  b.lx = fminf(b.lx, o.lx);
+  b.ly = fminf(b.ly, o.ly);
+  b.lz = fminf(b.lz, o.lz);
+  b.hx = fmaxf(b.hx, o.hx);
+  b.hy = fmaxf(b.hy, o.hy);
+  b.hz = fmaxf(b.hz, o.hz);
+}
+__device__ __forceinline__ Box6 box_shfl_down(const Box6& b, int o) {
+  return {__shfl_down_sync(0xffffffffu, b.lx, o), __shfl_down_sync(0xffffffffu, b.ly, o),
+          __shfl_down_sync(0xffffffffu, b.lz, o), __shfl_down_sync(0xffffffffu, b.hx, o),
+          __shfl_down_sync(0xffffffffu, b.hy, o), __shfl_down_sync(0xffffffffu, b.hz, o)};
+}
+__device__ __forceinline__ Box6 box_shfl_up(const Box6& b, int o) {
+  return {__shfl_up_sync(0xffffffffu, b.lx, o), __shfl_up_sync(0xffffffffu, b.ly, o),
+          __shfl_up_sync(0xffffffffu, b.lz, o), __shfl_up_sync(0xffffffffu, b.hx, o),
+          __shfl_up_sync(0xffffffffu, b.hy, o), __shfl_up_sync(0xffffffffu, b.hz, o)};
+}
+__device__ __forceinline__ float box6_area(const Box6& b) {
+  return box_area(make_float4(b.lx, b.ly, b.lz, 0.f), make_float4(b.hx, b.hy, b.hz, 0.f));
+}
 
-__global__ void __launch_bounds__(kTreeletLanes) k_treelets(const uint32_t* __restrict__ roots,
-                                                            const uint32_t* __restrict__ count,
-                                                            const float4* __restrict__ plo,
-                                                            const float4* __restrict__ phi, int32_t* child_bin,
-                                                            int2* irange, uint32_t* leaf_parent,
-                                                            uint32_t* inode_parent) {
-  __shared__ float s_c[3][kTreelet][kTreeletLanes];  // box centres
-  __shared__ float s_e[3][kTreelet][kTreeletLanes];  // box half extents
-  __shared__ uint8_t s_ord[3][kTreelet][kTreeletLanes];
-  __shared__ uint8_t s_tmp[kTreelet][kTreeletLanes];
-  __shared__ uint8_t s_left[kTreelet][kTreeletLanes];
-  __shared__ float s_sfx[kTreelet][kTreeletLanes];
-  __shared__ uint32_t s_pos[kTreelet][kTreeletLanes];
-  __shared__ int32_t s_ids[kTreelet][kTreeletLanes];
-  const int ln = threadIdx.x;
+// One warp's working set: box centres and half extents (the heuristic needs
+// the areas only approximately), the three centre orders of the pending
+// nodes, and the pending nodes themselves.
+struct TreeletWork {
+  float c[3][kTreelet];
+  float e[3][kTreelet];
+  float sfx[kTreelet];
+  uint8_t ord[3][kTreelet];
+  uint8_t tmp[kTreelet];
+  uint8_t left[kTreelet];
+  uint16_t t_first[kTreelet], t_count[kTreelet];
+  int32_t t_id[kTreelet];
+};
+
+__device__ __forceinline__ Box6 item_box(const TreeletWork& W, int v) {
+  return {W.c[0][v] - W.e[0][v], W.c[1][v] - W.e[1][v], W.c[2][v] - W.e[2][v],
+          W.c[0][v] + W.e[0][v], W.c[1][v] + W.e[1][v], W.c[2][v] + W.e[2][v]};
+}
+
+__global__ void __launch_bounds__(32 * kTreeletWarps) k_treelets(const uint32_t* __restrict__ roots,
+                                                                 const uint32_t* __restrict__ count,
+                                                                 const float4* __restrict__ plo,
+                                                                 const float4* __restrict__ phi, int32_t* child_bin,
+                                                                 int2* irange, uint32_t* leaf_parent,
+                                                                 uint32_t* inode_parent) {
+  __shared__ TreeletWork s_work[kTreeletWarps];
+  TreeletWork& W = s_work[threadIdx.x >> 5];
+  const int lane = threadIdx.x & 31;
+  const uint32_t lt = (1u << lane) - 1u;
   const uint32_t nroots = *count;
-  for (uint32_t q = blockIdx.x * kTreeletLanes + ln; q < nroots; q += gridDim.x * kTreeletLanes) {
-    const uint32_t r = roots[q];
+  const uint32_t warps = gridDim.x * kTreeletWarps;
+  for (uint32_t q = blockIdx.x * kTreeletWarps + (threadIdx.x >> 5); q < nroots; q += warps) {
+    const int32_t r = (int32_t)roots[q];
     const int2 rr = irange[r];
-    const int m = rr.y - rr.x + 1;
-    // the subtree's internal slots (root first) and surfel positions
-    int32_t stk[kTreelet + 1];
-    int nid = 0, np = 0, sp = 0;
-    bool ok = true;
-    stk[sp++] = (int32_t)r;
-    while (sp > 0 && ok) {
-      const int32_t c = stk[--sp];
-      if (c < 0) {
-        if (np < kTreelet) s_pos[np++][ln] = (uint32_t)~c;
-        else ok = false;
-        continue;
-      }
-      if (nid >= kTreelet - 1 || sp + 2 > kTreelet + 1) {
-        ok = false;
-        continue;
-      }
-      s_ids[nid++][ln] = c;
-      stk[sp++] = child_bin[2 * (int64_t)c + 1];
-      stk[sp++] = child_bin[2 * (int64_t)c];
+    const int f = rr.x, m = rr.y - rr.x + 1;
+    const int excl = r == f ? rr.y : f;  // the range's slot that is not this subtree's
+    for (int i = lane; i < m; i += 32) {
+      const float4 lo = plo[f + i], hi = phi[f + i];
+      const float cx = 0.5f * (lo.x + hi.x), cy = 0.5f * (lo.y + hi.y), cz = 0.5f * (lo.z + hi.z);
+      W.c[0][i] = cx;
+      W.c[1][i] = cy;
+      W.c[2][i] = cz;
+      W.e[0][i] = fmaxf(cx - lo.x, hi.x - cx);
+      W.e[1][i] = fmaxf(cy - lo.y, hi.y - cy);
+      W.e[2][i] = fmaxf(cz - lo.z, hi.z - cz);
     }
-    if (!ok || np != m || nid != m - 1) {
-      raise_error(kErrBadIndex);
-      continue;
-    }
-    for (int k = 0; k < m; ++k) {
-      const float4 lo = plo[s_pos[k][ln]], hi = phi[s_pos[k][ln]];
-      s_c[0][k][ln] = 0.5f * (lo.x + hi.x);
-      s_c[1][k][ln] = 0.5f * (lo.y + hi.y);
-      s_c[2][k][ln] = 0.5f * (lo.z + hi.z);
-      // half extents (the heuristic needs the areas only approximately)
-      s_e[0][k][ln] = fmaxf(s_c[0][k][ln] - lo.x, hi.x - s_c[0][k][ln]);
-      s_e[1][k][ln] = fmaxf(s_c[1][k][ln] - lo.y, hi.y - s_c[1][k][ln]);
-      s_e[2][k][ln] = fmaxf(s_c[2][k][ln] - lo.z, hi.z - s_c[2][k][ln]);
-    }
+    __syncwarp();
+    // each axis's centre order: rank by comparison, ties by index
     for (int a = 0; a < 3; ++a)
-      for (int i = 0; i < m; ++i) {
-        const float ci = s_c[a][i][ln];
+      for (int i = lane; i < m; i += 32) {
+        const float ci = W.c[a][i];
         int rank = 0;
         for (int j = 0; j < m; ++j) {
-          const float cj = s_c[a][j][ln];
+          const float cj = W.c[a][j];
           rank += (cj < ci || (cj == ci && j < i)) ? 1 : 0;
         }
-        s_ord[a][rank][ln] = (uint8_t)i;
+        W.ord[a][rank] = (uint8_t)i;
       }
-    // pending nodes: (first, count, slot); every node's items occupy
-    // [first, first + count) of all three orders
-    uint8_t t_first[kTreelet], t_count[kTreelet];
-    int32_t t_id[kTreelet];
-    int nt = 1, next_slot = 1;
-    t_first[0] = 0;
-    t_count[0] = (uint8_t)m;
-    t_id[0] = (int32_t)r;
+    if (lane == 0) {
+      W.t_first[0] = 0;
+      W.t_count[0] = (uint16_t)m;
+      W.t_id[0] = r;
+    }
+    __syncwarp();
+    int nt = 1, next = f;
     while (nt > 0) {
       --nt;
-      const int s = t_first[nt], k = t_count[nt];
-      const int32_t id = t_id[nt];
+      const int s = W.t_first[nt], k = W.t_count[nt];
+      const int32_t id = W.t_id[nt];
+      __syncwarp();
+      // every split point of every axis: lane L scores the positions of its
+      // chunk [L cs, (L + 1) cs), the boxes of the other chunks by warp scans
+      const int cs = (k + 31) >> 5;
+      const int b0 = min(k, lane * cs), b1 = min(k, b0 + cs);
       float best = __int_as_float(0x7f800000);
-      int best_axis = 0, best_split = k / 2;
+      int best_axis = 0, best_split = k >> 1;
       for (int a = 0; a < 3; ++a) {
-        // areas of the suffixes [j, k) of this axis's order
-        float lx = 3e38f, ly = 3e38f, lz = 3e38f, hx = -3e38f, hy = -3e38f, hz = -3e38f;
-        for (int j = k - 1; j >= 1; --j) {
-          const int v = s_ord[a][s + j][ln];
-          lx = fminf(lx, s_c[0][v][ln] - s_e[0][v][ln]);
-          ly = fminf(ly, s_c[1][v][ln] - s_e[1][v][ln]);
-          lz = fminf(lz, s_c[2][v][ln] - s_e[2][v][ln]);
-          hx = fmaxf(hx, s_c[0][v][ln] + s_e[0][v][ln]);
-          hy = fmaxf(hy, s_c[1][v][ln] + s_e[1][v][ln]);
-          hz = fmaxf(hz, s_c[2][v][ln] + s_e[2][v][ln]);
-          s_sfx[j][ln] = box_area(make_float4(lx, ly, lz, 0.f), make_float4(hx, hy, hz, 0.f));
+        Box6 agg = box_empty();
+        for (int j = b0; j < b1; ++j) box_grow(agg, item_box(W, W.ord[a][s + j]));
+        // boxes of the chunks after and before this lane's
+        Box6 suf = agg, pre = agg;
+        for (int o = 1; o < 32; o <<= 1) {
+          const Box6 d = box_shfl_down(suf, o);
+          if (lane + o < 32) box_grow(suf, d);
+          const Box6 u = box_shfl_up(pre, o);
+          if (lane >= o) box_grow(pre, u);
         }
-        lx = ly = lz = 3e38f;
-        hx = hy = hz = -3e38f;
-        for (int j = 1; j < k; ++j) {
-          const int v = s_ord[a][s + j - 1][ln];
-          lx = fminf(lx, s_c[0][v][ln] - s_e[0][v][ln]);
-          ly = fminf(ly, s_c[1][v][ln] - s_e[1][v][ln]);
-          lz = fminf(lz, s_c[2][v][ln] - s_e[2][v][ln]);
-          hx = fmaxf(hx, s_c[0][v][ln] + s_e[0][v][ln]);
-          hy = fmaxf(hy, s_c[1][v][ln] + s_e[1][v][ln]);
-          hz = fmaxf(hz, s_c[2][v][ln] + s_e[2][v][ln]);
-          const float cost = box_area(make_float4(lx, ly, lz, 0.f), make_float4(hx, hy, hz, 0.f)) * (float)j +
-                             s_sfx[j][ln] * (float)(k - j);
-          if (cost < best) {
-            best = cost;
-            best_axis = a;
-            best_split = j;
+        Box6 after = box_shfl_down(suf, 1), before = box_shfl_up(pre, 1);
+        if (lane == 31) after = box_empty();
+        if (lane == 0) before = box_empty();
+        Box6 run = after;
+        for (int j = b1 - 1; j >= b0; --j) {
+          box_grow(run, item_box(W, W.ord[a][s + j]));
+          W.sfx[j] = box6_area(run);  // the items [j, k)
+        }
+        run = before;
+        float lbest = __int_as_float(0x7f800000);
+        int lsplit = k;
+        for (int j = b0; j < b1; ++j) {
+          if (j >= 1) {
+            const float cost = box6_area(run) * (float)j + W.sfx[j] * (float)(k - j);
+            if (cost < lbest) {
+              lbest = cost;
+              lsplit = j;
+            }
+          }
+          box_grow(run, item_box(W, W.ord[a][s + j]));
+        }
+        // the warp's cheapest split of this axis (ties: the lower position)
+        for (int o = 16; o > 0; o >>= 1) {
+          const float oc = __shfl_xor_sync(0xffffffffu, lbest, o);
+          const int os = __shfl_xor_sync(0xffffffffu, lsplit, o);
+          if (oc < lbest || (oc == lbest && os < lsplit)) {
+            lbest = oc;
+            lsplit = os;
           }
         }
+        if (lbest < best) {
+          best = lbest;
+          best_axis = a;
+          best_split = lsplit;
+        }
       }
-      // the left child's items: the first best_split of the chosen order;
-      // the two other orders are partitioned stably
-      for (int j = 0; j < k; ++j) s_left[s_ord[best_axis][s + j][ln]][ln] = (uint8_t)(j < best_split);
+      __syncwarp();
+      // the left child's items: the first best_split of the chosen order; the
+      // two other orders are partitioned stably
+      for (int j = lane; j < k; j += 32) W.left[W.ord[best_axis][s + j]] = (uint8_t)(j < best_split);
+      __syncwarp();
       for (int a = 0; a < 3; ++a) {
         if (a == best_axis) continue;
         int nl = 0, nr = best_split;
-        for (int j = 0; j < k; ++j) {
-          const uint8_t v = s_ord[a][s + j][ln];
-          if (s_left[v][ln]) s_tmp[nl++][ln] = v;
-          else s_tmp[nr++][ln] = v;
+        for (int b = 0; b < k; b += 32) {
+          const int j = b + lane;
+          const bool valid = j < k;
+          const uint8_t v = valid ? W.ord[a][s + j] : 0;
+          const bool isl = valid && W.left[v];
+          const uint32_t ml = __ballot_sync(0xffffffffu, isl);
+          const uint32_t mr = __ballot_sync(0xffffffffu, valid && !isl);
+          if (isl) W.tmp[nl + __popc(ml & lt)] = v;
+          else if (valid) W.tmp[nr + __popc(mr & lt)] = v;
+          nl += __popc(ml);
+          nr += __popc(mr);
         }
-        for (int j = 0; j < k; ++j) s_ord[a][s + j][ln] = s_tmp[j][ln];
+        __syncwarp();
+        for (int j = lane; j < k; j += 32) W.ord[a][s + j] = W.tmp[j];
+        __syncwarp();
       }
       for (int side = 0; side < 2; ++side) {
-        const int cs = side == 0 ? s : s + best_split;
+        const int cfirst = side == 0 ? s : s + best_split;
         const int ck = side == 0 ? best_split : k - best_split;
         int32_t code;
         if (ck == 1) {
-          const uint32_t leaf = s_pos[s_ord[best_axis][cs][ln]][ln];
-          code = ~(int32_t)leaf;
-          leaf_parent[leaf] = (uint32_t)id;
+          const int32_t leaf = f + W.ord[best_axis][cfirst];
+          code = ~leaf;
+          if (lane == 0) leaf_parent[leaf] = (uint32_t)id;
         } else {
-          const int32_t cid = s_ids[next_slot++][ln];
+          while (next == r || next == excl) ++next;
+          const int32_t cid = next++;
           code = cid;
-          inode_parent[cid] = (uint32_t)id;
-          irange[cid] = make_int2(rr.x, rr.x + ck - 1);  // the size is what is read
-          t_first[nt] = (uint8_t)cs;
-          t_count[nt] = (uint8_t)ck;
-          t_id[nt] = cid;
+          if (lane == 0) {
+            inode_parent[cid] = (uint32_t)id;
+            irange[cid] = make_int2(f, f + ck - 1);  // the size is what is read
+            W.t_first[nt] = (uint16_t)cfirst;
+            W.t_count[nt] = (uint16_t)ck;
+            W.t_id[nt] = cid;
+          }
           ++nt;
         }
-        child_bin[2 * (int64_t)id + side] = code;
+        if (lane == 0) child_bin[2 * (int64_t)id + side] = code;
       }
+      __syncwarp();
     }
+    if (next > rr.y + 1) raise_error(kErrBadIndex);  // more slots than the range holds
   }
 }
 
@@ -279,7 +331,13 @@ __global__ void k_refit(int64_t n, const float4* __restrict__ plo, const float4*
   if (j >= n) return;
   uint32_t node = leaf_parent[j];
   float area = 0.f;
-  while (node != 0xFFFFFFFFu) {
+  // a path to the root has fewer than n internal nodes: more means the parent
+  // links hold a cycle, recorded as a device error rather than followed
+  for (int64_t steps = 0; node != 0xFFFFFFFFu; ++steps) {
+    if (steps >= n) {
+      raise_error(kErrBadIndex);
+      break;
+    }
     __threadfence();
     if (atomicAdd(&visit[node], 1u) == 0u) break;  // first arrival: the sibling finishes
     __threadfence();
@@ -507,7 +565,7 @@ cudaError_t launch_tree(const uint32_t* sorted_keys, char* base, const BvhLayout
                k_treelet_roots<<<blocks_for(n - 1, 256), 256, 0, st>>>(
                    n, (const int2*)(base + L.irange), (const uint32_t*)(base + L.inode_parent), roots, levels));
   EAGPT_LAUNCH(st, "k_treelets",
-               k_treelets<<<(unsigned)(8 * device_sms()), kTreeletLanes, 0, st>>>(
+               k_treelets<<<(unsigned)(4 * device_sms()), 32 * kTreeletWarps, 0, st>>>(
                    roots, levels, (const float4*)(base + L.prim_lo), (const float4*)(base + L.prim_hi),
                    (int32_t*)(base + L.child_bin), (int2*)(base + L.irange), (uint32_t*)(base + L.leaf_parent),
                    (uint32_t*)(base + L.inode_parent)));
