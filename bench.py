@@ -48,6 +48,7 @@ def parse():
                     choices=["tiny", "medium", "diff", "large", "serving", "stage1", "bake", "mis"])
     ap.add_argument("--views", type=int, default=8, help="stage1/bake: training views")
     ap.add_argument("--requests", type=int, default=16, help="serving: requests in the stream")
+    ap.add_argument("--queue-log2", type=int, default=27, help="serving: log2 of the paths one wave holds")
     ap.add_argument("--stream", default="mixed", choices=["mixed", "small"],
                     help="serving: the mixed stream (256x256..1920x1080, 16/64/256 spp) or small requests only "
                          "(256x256, 16 spp)")
@@ -308,7 +309,7 @@ def run_serving(args):
         reqs = S.serving_requests(host, args.requests, seed=13)
     n_render = sum(1 for r in reqs if r["type"] == "render")
     samples = sum(r["camera"].width * r["camera"].height * r["spp"] for r in reqs if r["type"] == "render")
-    queue_paths = 1 << 27
+    queue_paths = 1 << args.queue_log2
 
     def resolve_edit(ds, r):
         idx = torch.from_numpy(r["idx"]).to(dev) if "idx" in r else api.select(ds, "sphere", r["sphere"])

@@ -153,6 +153,7 @@ struct TreeletWork {
   uint8_t left[kTreelet];
   uint16_t t_first[kTreelet], t_count[kTreelet];
   int32_t t_id[kTreelet];
+  uint8_t t_axis[kTreelet];  // an order that is valid over the node's range (the parent's split axis)
 };
 
 __device__ __forceinline__ Box6 item_box(const TreeletWork& W, int v) {
@@ -203,6 +204,7 @@ __global__ void __launch_bounds__(32 * kTreeletWarps) k_treelets(const uint32_t*
       W.t_first[0] = 0;
       W.t_count[0] = (uint16_t)m;
       W.t_id[0] = r;
+      W.t_axis[0] = 0;
     }
     __syncwarp();
     int nt = 1, next = f;
@@ -210,14 +212,17 @@ __global__ void __launch_bounds__(32 * kTreeletWarps) k_treelets(const uint32_t*
       --nt;
       const int s = W.t_first[nt], k = W.t_count[nt];
       const int32_t id = W.t_id[nt];
+      const int valid_axis = W.t_axis[nt];
       __syncwarp();
       // every split point of every axis: lane L scores the positions of its
       // chunk [L cs, (L + 1) cs), the boxes of the other chunks by warp scans
       const int cs = (k + 31) >> 5;
       const int b0 = min(k, lane * cs), b1 = min(k, b0 + cs);
       float best = __int_as_float(0x7f800000);
-      int best_axis = 0, best_split = k >> 1;
-      for (int a = 0; a < 3; ++a) {
+      // two surfels have one split, read from the order valid over the range
+      // (a node of three or more surfels has all three orders valid)
+      int best_axis = valid_axis, best_split = k >> 1;
+      for (int a = 0; a < (k > 2 ? 3 : 0); ++a) {
         Box6 agg = box_empty();
         for (int j = b0; j < b1; ++j) box_grow(agg, item_box(W, W.ord[a][s + j]));
         // boxes of the chunks after and before this lane's
@@ -266,10 +271,13 @@ __global__ void __launch_bounds__(32 * kTreeletWarps) k_treelets(const uint32_t*
       }
       __syncwarp();
       // the left child's items: the first best_split of the chosen order; the
-      // two other orders are partitioned stably
-      for (int j = lane; j < k; j += 32) W.left[W.ord[best_axis][s + j]] = (uint8_t)(j < best_split);
+      // two other orders are partitioned stably (only a child of three or
+      // more surfels is split by order again)
+      const bool reorder = best_split > 2 || k - best_split > 2;
+      if (reorder)
+        for (int j = lane; j < k; j += 32) W.left[W.ord[best_axis][s + j]] = (uint8_t)(j < best_split);
       __syncwarp();
-      for (int a = 0; a < 3; ++a) {
+      for (int a = 0; a < (reorder ? 3 : 0); ++a) {
         if (a == best_axis) continue;
         int nl = 0, nr = best_split;
         for (int b = 0; b < k; b += 32) {
@@ -306,6 +314,7 @@ __global__ void __launch_bounds__(32 * kTreeletWarps) k_treelets(const uint32_t*
             W.t_first[nt] = (uint16_t)cfirst;
             W.t_count[nt] = (uint16_t)ck;
             W.t_id[nt] = cid;
+            W.t_axis[nt] = (uint8_t)best_axis;
           }
           ++nt;
         }
@@ -565,7 +574,7 @@ cudaError_t launch_tree(const uint32_t* sorted_keys, char* base, const BvhLayout
                k_treelet_roots<<<blocks_for(n - 1, 256), 256, 0, st>>>(
                    n, (const int2*)(base + L.irange), (const uint32_t*)(base + L.inode_parent), roots, levels));
   EAGPT_LAUNCH(st, "k_treelets",
-               k_treelets<<<(unsigned)(4 * device_sms()), 32 * kTreeletWarps, 0, st>>>(
+               k_treelets<<<(unsigned)(5 * device_sms()), 32 * kTreeletWarps, 0, st>>>(
                    roots, levels, (const float4*)(base + L.prim_lo), (const float4*)(base + L.prim_hi),
                    (int32_t*)(base + L.child_bin), (int2*)(base + L.irange), (uint32_t*)(base + L.leaf_parent),
                    (uint32_t*)(base + L.inode_parent)));
