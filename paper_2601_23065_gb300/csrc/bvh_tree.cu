@@ -177,10 +177,16 @@ __global__ void __launch_bounds__(32 * kTreeletWarps) k_treelets(const uint32_t*
     const int32_t r = (int32_t)roots[q];
     const int2 rr = irange[r];
     const int f = rr.x, m = rr.y - rr.x + 1;
+    if (m < 3 || m > kTreelet || (r != f && r != rr.y)) {
+      raise_error(kErrBadIndex);
+      continue;
+    }
     const int excl = r == f ? rr.y : f;  // the range's slot that is not this subtree's
     for (int i = lane; i < m; i += 32) {
       const float4 lo = plo[f + i], hi = phi[f + i];
-      const float cx = 0.5f * (lo.x + hi.x), cy = 0.5f * (lo.y + hi.y), cz = 0.5f * (lo.z + hi.z);
+      // a NaN centre sorts last (the orders stay permutations)
+      const float cx0 = 0.5f * (lo.x + hi.x), cy0 = 0.5f * (lo.y + hi.y), cz0 = 0.5f * (lo.z + hi.z);
+      const float cx = cx0 == cx0 ? cx0 : 3e38f, cy = cy0 == cy0 ? cy0 : 3e38f, cz = cz0 == cz0 ? cz0 : 3e38f;
       W.c[0][i] = cx;
       W.c[1][i] = cy;
       W.c[2][i] = cz;
