@@ -120,8 +120,9 @@ void eagpt_default_params(eagpt_params* out);
 
 /* ------------------------------------------------------------------------
  * Acceleration structure: a software LBVH over the support bounds of the
- * surfels (the paper uses a hardware BVH, Sec. 4.2; any BVH that returns
- * every hit gives the same image).  Storage is one caller-owned device
+ * surfels, whose subtrees of at most 256 surfels are rebuilt with the surface
+ * area heuristic, collapsed to a 4-wide BVH (the paper uses a hardware BVH,
+ * Sec. 4.2; any BVH that returns every hit gives the same image).  Storage is one caller-owned device
  * buffer of eagpt_bvh_bytes(n) bytes, 256-byte aligned.  The handle is a
  * plain host struct filled by eagpt_build_bvh().
  * ------------------------------------------------------------------------ */
