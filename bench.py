@@ -195,6 +195,26 @@ def cpu_sample_spp(wl) -> int:
     return min(wl.spp, 2 if wl.scene_fn.__name__ == "large_layout" else 16)
 
 
+def host_cpu() -> str:
+    """The host CPU's model name and the cores this process may run on."""
+    model = ""
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                key = line.split(":")[0].strip().lower()
+                if key in ("model name", "cpu model", "hardware") and ":" in line:
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    import platform
+    try:
+        n = len(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
+        n = os.cpu_count() or 0
+    return f"{model or platform.machine()}, {n} cores available"
+
+
 def cpu_baseline(wl, scene, seconds: float):
     """The FP64 oracle on a bounded pixel sample of the same workload."""
     import numpy as np
@@ -220,7 +240,7 @@ def cpu_baseline(wl, scene, seconds: float):
         if total_t >= seconds or m >= 4096:
             break
         m = int(min(4096, max(m * 2, m * seconds / max(dt, 1e-3) / 2)))
-    return {"value": total_segs / total_t, "unit": METRIC, "cores": n_threads, "kind": "oracle",
+    return {"value": total_segs / total_t, "unit": METRIC, "cores": n_threads, "kind": "oracle", "cpu": host_cpu(),
             "sample": f"{total_pix} random pixels x {spp} spp (the frame's first samples) of the same workload "
                       f"({total_segs} segments in {total_t:.1f} s, brute force over {scene.n} surfels, FP64)"}
 
@@ -278,7 +298,8 @@ def run_reference(args, rank, world):
             "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": wl.name, "scale_factor": wl.scale_factor},
-            "cpu_baseline": {"value": v, "unit": METRIC, "cores": n_threads, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": v, "unit": METRIC, "cores": n_threads, "kind": "oracle", "cpu": host_cpu(),
+                             "sample": sample},
             "e2e": {"value": v, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -487,7 +508,7 @@ def fit_cpu_baseline(scene, cam, field, spp, seconds):
         m = int(min(4096, max(m * 2, m * seconds / max(dt, 1e-3) / 2)))
     per_iter = total_t / total_pix * npix
     what = f"single bounce {spp} spp + full FP64 adjoint" if field == 0 else "0-bounce + FP64 adjoint"
-    return {"value": 1.0 / per_iter, "unit": "iterations/s", "cores": n_threads, "kind": "oracle",
+    return {"value": 1.0 / per_iter, "unit": "iterations/s", "cores": n_threads, "kind": "oracle", "cpu": host_cpu(),
             "sample": f"{total_pix} random pixels of one {cam.width}x{cam.height} view ({what}, brute force "
                       f"over {scene.n} surfels) in {total_t:.1f} s, scaled to the full view"}
 
