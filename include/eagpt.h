@@ -330,7 +330,8 @@ eagpt_status eagpt_insert_surfels(eagpt_scene_mut* scene, int64_t capacity, cons
  * scene before the edit, later ones see the edit.  Two scene+BVH versions
  * are kept (the caller's and one in the arena): an edit copies the current
  * version into the other slot once no running render uses it, edits and
- * refits the copy and makes it current.  The caller's scene arrays and BVH
+ * refits the copy on a stream of its own (the waves in flight keep running;
+ * later waves wait for the edit) and makes it current.  The caller's scene arrays and BVH
  * storage belong to the server until eagpt_server_destroy() returns; the
  * final scene is in the slot eagpt_server_scene() reports.
  * Memory: all device memory comes from the caller's arena (device, 256-byte

@@ -22,8 +22,9 @@
 // Edits are applied in submission order: renders submitted before an edit see
 // the old scene, later ones the new.  The server keeps two scene+BVH
 // versions: an edit copies the current version into the other slot (once no
-// running request uses it), edits and refits the copy and makes it current,
-// while requests admitted earlier finish on the old version.
+// running request uses it), edits and refits the copy on a stream of its own
+// beside the waves in flight, and makes it current, while requests admitted
+// earlier finish on the old version.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -296,7 +297,9 @@ struct Server {
   uint32_t* counters[2] = {nullptr, nullptr};
   int64_t queue_cap = 0;
   cudaEvent_t ev_ref = nullptr;   // time origin of the busy-time account
-  cudaEvent_t ev_sync = nullptr;  // cross-stream ordering (admission, edits)
+  cudaEvent_t ev_sync = nullptr;  // cross-stream ordering (admission)
+  cudaStream_t edit_stream = nullptr;  // edits: their own stream, waited for by both wave streams
+  cudaEvent_t ev_edit = nullptr;
   cudaEvent_t ev_acc[2] = {nullptr, nullptr};
   float last_done_ms = 0.f;
   // the two waves in flight: device request tables, their pinned host
@@ -387,8 +390,10 @@ bool Server::apply_edit_locked(Req& r, std::unique_lock<std::mutex>& lk) {
   const int target = 1 - current;
   if (users[target] > 0) return false;  // the other version is still rendering
   const int64_t n = scene[current].n;
-  // the edit runs on the next wave's stream; the other stream waits for it
-  cudaStream_t st = streams[next_slot];
+  // the edit runs on its own stream, beside the waves in flight (none of
+  // them reads the target slot, which has no users); both wave streams wait
+  // for it before their next work
+  cudaStream_t st = edit_stream;
   // copy the current version into the target slot, then edit the copy
   const float* src[7] = {scene[current].pos, scene[current].quat, scene[current].scale, scene[current].opacity,
                          scene[current].albedo, scene[current].radiance, scene[current].emissive};
@@ -414,14 +419,16 @@ bool Server::apply_edit_locked(Req& r, std::unique_lock<std::mutex>& lk) {
   bvh[target].bytes = sbytes;
   const eagpt_status est =
       apply_edit_core(&scene[target], &bvh[target], &params, &r.edit, cfg.rebuild_ratio, &r.rebuilt, st);
-  if (est != EAGPT_OK || join_other(next_slot) != cudaSuccess) {
+  cudaError_t je = est == EAGPT_OK ? cudaEventRecord(ev_edit, st) : cudaErrorUnknown;
+  for (int k = 0; k < 2 && je == cudaSuccess; ++k) je = cudaStreamWaitEvent(streams[k], ev_edit, 0);
+  if (est != EAGPT_OK || je != cudaSuccess) {
     error = "edit failed";
     finish_locked(r, EAGPT_REQ_FAILED);
     return true;
   }
   // the edit is done when the device has applied it (callers may read the
-  // edited scene, e.g. to select surfels for the next edit); the other
-  // stream's wave keeps the GPU busy meanwhile
+  // edited scene, e.g. to select surfels for the next edit); the waves in
+  // flight keep the GPU busy meanwhile
   lk.unlock();
   const cudaError_t se = cudaStreamSynchronize(st);
   lk.lock();
@@ -754,7 +761,10 @@ static void release_host(Server& S) {
   }
   if (S.ev_ref) cudaEventDestroy(S.ev_ref);
   if (S.ev_sync) cudaEventDestroy(S.ev_sync);
-  S.ev_ref = S.ev_sync = nullptr;
+  if (S.ev_edit) cudaEventDestroy(S.ev_edit);
+  if (S.edit_stream) cudaStreamDestroy(S.edit_stream);
+  S.ev_ref = S.ev_sync = S.ev_edit = nullptr;
+  S.edit_stream = nullptr;
 }
 
 // Arena bytes the server keeps for itself: the second scene version and its
@@ -831,6 +841,8 @@ eagpt_status eagpt_server_create(const eagpt_scene_mut* scene, const eagpt_bvh* 
   // two request tables and counter copies, the events
   cudaError_t e = cudaEventCreate(&S.ev_ref);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&S.ev_sync, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&S.ev_edit, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&S.edit_stream, cudaStreamNonBlocking);
   for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
     e = cudaStreamCreateWithFlags(&S.streams[k], cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaHostAlloc((void**)&S.table_h[k], kSrvMaxActive * sizeof(ReqDev), cudaHostAllocDefault);
