@@ -81,13 +81,15 @@ def _load():
             lib.ora_primary.argtypes = [P(_Scene), P(_Camera), P(_Params), i32, P(i32), i64, P(d), P(u32), i32]
             lib.ora_render.argtypes = [P(_Scene), P(_Camera), P(_Params), i32, i32, i32, i32, u64, P(i32), i64,
                                        P(d), P(d), P(u32), P(i64), P(d), i32]
+            lib.ora_render_lod.argtypes = [P(_Scene), P(_Scene), i32, P(_Camera), P(_Params), i32, i32, i32, u64,
+                                           P(i32), i64, P(d), P(d), P(u32), P(i64), P(d), i32]
             lib.ora_single_bounce_grad.argtypes = [P(_Scene), P(_Camera), P(_Params), i32, u64, P(i32), i64,
                                                    P(d), P(d), P(u32), i32, i32]
             lib.ora_light_pdf.argtypes = [P(_Scene), P(_Params), P(d), P(d), P(d)]
             lib.ora_light_pdf.restype = i32
             lib.ora_radiance_grad.argtypes = [P(_Scene), P(_Camera), P(_Params), P(i32), i64, P(d), P(d), P(u32),
                                               i32, i32]
-            for f in ("ora_trace_segment", "ora_trace_rays", "ora_primary", "ora_render",
+            for f in ("ora_trace_segment", "ora_trace_rays", "ora_primary", "ora_render", "ora_render_lod",
                       "ora_single_bounce_grad", "ora_radiance_grad"):
                 getattr(lib, f).restype = ctypes.c_int
             _lib = lib
@@ -248,6 +250,36 @@ def render(scene, camera, pixels, kind, spp, max_bounces=1, rr_start=2, seed=0, 
                         _ptr(segs, ctypes.c_int64), _ptr(dev, ctypes.c_double), n_threads or default_threads())
     if rc:
         raise RuntimeError("oracle render failed")
+    out = {"rgb": rgb, "samples": samples, "sample_flags": sflags, "segments": segs}
+    if want_dev:
+        out["sample_dev"] = dev
+    return out
+
+
+def render_lod(scene, lod_scene, lod_from, camera, pixels, spp, max_bounces=1, rr_start=2, seed=0, params=None,
+               want_samples=False, n_threads=None, want_dev=False):
+    """Path tracing (Eq. 8) whose bounce segments k >= lod_from trace
+    ``lod_scene`` (the primary and earlier bounces trace ``scene``).  Returns
+    the dict of ``render``."""
+    lib = _load()
+    sc = _oscene(scene)
+    lsc = _oscene(lod_scene)
+    pixels = np.ascontiguousarray(pixels, np.int32)
+    m = pixels.size
+    rgb = np.zeros((m, 3))
+    samples = np.zeros((m, spp, 3)) if want_samples else None
+    dev = np.zeros((m, spp, 3)) if want_dev else None
+    sflags = np.zeros((m, spp), np.uint32)
+    segs = np.zeros(m, np.int64)
+    prm = (params or Params())._c()
+    cam = _cam(camera)
+    rc = lib.ora_render_lod(ctypes.byref(sc._c), ctypes.byref(lsc._c), int(lod_from), ctypes.byref(cam),
+                            ctypes.byref(prm), int(spp), int(max_bounces), int(rr_start), ctypes.c_uint64(int(seed)),
+                            _ptr(pixels, ctypes.c_int32), m, _ptr(rgb, ctypes.c_double),
+                            _ptr(samples, ctypes.c_double), _ptr(sflags, ctypes.c_uint32),
+                            _ptr(segs, ctypes.c_int64), _ptr(dev, ctypes.c_double), n_threads or default_threads())
+    if rc:
+        raise RuntimeError("oracle level-of-detail render failed")
     out = {"rgb": rgb, "samples": samples, "sample_flags": sflags, "segments": segs}
     if want_dev:
         out["sample_dev"] = dev

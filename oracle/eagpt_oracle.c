@@ -213,6 +213,11 @@ typedef struct {
   const ora_params* prm;
   uint32_t ajit; /* conditioning run r > 0: every sigma g is perturbed by a
                     reproducible relative +-4 FP32 ulps (its FP32 rounding) */
+  /* level of detail: bounce segments k >= lod_from trace these surfels
+   * instead (NULL: no level of detail) */
+  const surfel64* s_lod;
+  int64_t n_lod;
+  int32_t lod_from;
 } world;
 
 /* splitmix64 finaliser (Steele, Lea, Flood: "Fast splittable pseudorandom
@@ -860,8 +865,15 @@ static int path_sample(job* jb, const render_ctx* c, hitbuf* b, int64_t pix, int
     }
     if (run > 0) jitter_ray(O2, w2, c->seed, pix, s, k, run, 2.0 * eps);
     ora_segment g2;
+    /* the surfels this bounce segment traces: the merged ones from bounce
+     * lod_from on */
+    world Wk = jb->W;
+    if (Wk.s_lod && k >= Wk.lod_from) {
+      Wk.s = Wk.s_lod;
+      Wk.n = Wk.n_lod;
+    }
     /* margins at this segment's own FP32 rounding scale */
-    if (segment(&jb->W, O2, w2, 0.0, seg_mode, ERR_C * eps * amax3(O2), ERR_C * eps, b, &g2)) return -1;
+    if (segment(&Wk, O2, w2, 0.0, seg_mode, ERR_C * eps * amax3(O2), ERR_C * eps, b, &g2)) return -1;
     *psig = mix64(*psig ^ hits_signature(b));
     ++*segments;
     *sflags |= g2.flags;
@@ -1037,6 +1049,38 @@ int ora_render(const ora_scene* sc, const ora_camera* cam, const ora_params* prm
   }
   int rc = run_job(&jb, n_threads);
   free_emitters(&em);
+  free(s);
+  return rc;
+}
+
+int ora_render_lod(const ora_scene* sc, const ora_scene* lod_sc, int32_t lod_from, const ora_camera* cam,
+                   const ora_params* prm, int32_t spp, int32_t max_bounces, int32_t rr_start, uint64_t seed,
+                   const int32_t* pixels, int64_t n_pix, double* out_rgb, double* out_samples,
+                   uint32_t* out_sample_flags, int64_t* out_segments, double* out_sample_dev,
+                   int32_t n_threads) {
+  if (prm->mis || !lod_sc || lod_from < 1) return -1;
+  surfel64* s = load_surfels(sc);
+  surfel64* sl = load_surfels(lod_sc);
+  if (!s || !sl) {
+    free(s);
+    free(sl);
+    return -1;
+  }
+  render_ctx c = {cam, 1, spp, max_bounces, rr_start, seed, pixels, out_rgb, out_samples, out_sample_flags,
+                  out_segments, NULL, out_sample_dev};
+  job jb;
+  memset(&jb, 0, sizeof(jb));
+  jb.W.s = s;
+  jb.W.n = sc->n;
+  jb.W.prm = prm;
+  jb.W.s_lod = sl;
+  jb.W.n_lod = lod_sc->n;
+  jb.W.lod_from = lod_from;
+  jb.fn = render_item;
+  jb.n_items = n_pix;
+  jb.ctx = &c;
+  int rc = run_job(&jb, n_threads);
+  free(sl);
   free(s);
   return rc;
 }

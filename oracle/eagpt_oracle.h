@@ -138,6 +138,18 @@ int ora_render(const ora_scene* sc, const ora_camera* cam, const ora_params* prm
                uint32_t* out_sample_flags, int64_t* out_segments, double* out_sample_dev,
                int32_t n_threads);
 
+/* Path tracing (kind 1, Eq. 8) with a level of detail: the primary segment
+ * and the bounce segments k < lod_from trace sc, the bounce segments
+ * k >= lod_from (k = 1 is the segment after the first reflection) trace
+ * lod_sc (the merged surfels of the level-of-detail reading).  Everything
+ * else as in ora_render; emitter sampling (prm->mis) is not supported
+ * (returns -1). */
+int ora_render_lod(const ora_scene* sc, const ora_scene* lod_sc, int32_t lod_from, const ora_camera* cam,
+                   const ora_params* prm, int32_t spp, int32_t max_bounces, int32_t rr_start, uint64_t seed,
+                   const int32_t* pixels, int64_t n_pix, double* out_rgb, double* out_samples,
+                   uint32_t* out_sample_flags, int64_t* out_segments, double* out_sample_dev,
+                   int32_t n_threads);
+
 /* Gradient of L = sum_p sum_c dL_drgb[p][c] * I[p][c] for the single-bounce
  * render of the listed pixels, with respect to every surfel parameter.
  * grad: 16 doubles per surfel, accumulated (+=):
