@@ -45,7 +45,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--workload", default="large",
-                    choices=["tiny", "medium", "diff", "large", "serving", "stage1", "bake", "mis"])
+                    choices=["tiny", "medium", "diff", "large", "serving", "stage1", "bake", "mis", "lod"])
     ap.add_argument("--views", type=int, default=8, help="stage1/bake: training views")
     ap.add_argument("--requests", type=int, default=16, help="serving: requests in the stream")
     ap.add_argument("--queue-log2", type=int, default=27, help="serving: log2 of the paths one wave holds")
@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--adjoint-retrace", action="store_true",
                     help="diff: the adjoint re-traces every secondary segment instead of reading the forward's cache")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--lod-cell", type=float, default=0.05, help="lod: grid cell edge of the surfel groups (m)")
+    ap.add_argument("--lod-from", type=int, default=2, help="lod: first bounce that traces the merged surfels")
     return ap.parse_args()
 
 
@@ -992,8 +994,133 @@ def run_render(args, rank, world, local):
         torch.distributed.destroy_process_group()
 
 
+# grid corner that puts the walls of the large layout in mid-cell (5 and 2.5 cm cells)
+LOD_ORIGIN = (-7.6125, -2.1125, -1.6125)
+
+
+def run_lod(args):
+    """Level of detail on the large final render: plain steps and merged
+    steps (the bounce segments from --lod-from on trace the merged surfels)
+    timed in the same process on the same 64-sample slices; each merged step
+    also rebuilds the merged surfels and their BVH.  The images of the first
+    slice are compared after the timed spans."""
+    import numpy as np
+    import torch
+
+    from paper_2601_23065_gb300 import api, build
+    from paper_2601_23065_gb300 import capi
+    from paper_2601_23065_gb300 import scenes as S
+
+    build.build()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    wl = S.workload("large")
+    frame_spp = args.spp or wl.spp
+    slice_spp = min(args.slice_spp or 64, frame_spp)
+    slices = frame_slices(frame_spp, slice_spp)
+    host_scene = wl.scene_fn()
+    cam = wl.camera
+    ds = api.DeviceScene.from_host(host_scene, device=dev)
+    r = api.Renderer(device=dev)
+    stream = torch.cuda.current_stream(dev)
+    L = capi.lib()
+    img = torch.empty((cam.height, cam.width, 3), dtype=torch.float32, device=dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    state = {}
+
+    def plain_step(k):
+        first, n = slices[k % len(slices)]
+        bvh = api.BVH(ds, stream=stream)
+        r.path_traced(ds, bvh, cam, n, wl.max_bounces, rr_start=wl.rr_start, seed=0, stream=stream,
+                      first_sample=first, out=img)
+
+    def lod_step(k):
+        first, n = slices[k % len(slices)]
+        bvh = api.BVH(ds, stream=stream)
+        lod = api.LevelOfDetail(ds, LOD_ORIGIN, args.lod_cell, stream=stream)
+        state["lod_n"] = lod.scene.n
+        r.path_traced_lod(ds, bvh, lod, args.lod_from, cam, n, wl.max_bounces, rr_start=wl.rr_start, seed=0,
+                          stream=stream, first_sample=first, out=img)
+
+    def timed(step):
+        for k in range(args.warmup):
+            step(k)
+        torch.cuda.synchronize(dev)
+        times, segs = [], 0
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            step(k)
+            b.record(stream)
+            b.synchronize()
+            times.append(a.elapsed_time(b))
+            p, q = r.segments(stream)
+            segs += p + q
+        return sum(times) / 1e3, segs, sum(times) / len(times)
+
+    clocks = ClockSampler(0)
+    clocks.start()
+    launches0 = L.eagpt_launch_count()
+    t_plain, s_plain, ms_plain = timed(plain_step)
+    t_lod, s_lod, ms_lod = timed(lod_step)
+    launches = L.eagpt_launch_count() - launches0
+    clk = clocks.stop()
+    api.sync_status()
+    # merge alone (preprocess of the merged scene: groups, sort, moments)
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    merged = api.build_lod(ds, LOD_ORIGIN, args.lod_cell, stream=stream)
+    b.record(stream)
+    b.synchronize()
+    merge_ms = a.elapsed_time(b)
+    # work per secondary segment (counting variant, first slice) and images
+    first0, n0 = slices[0]
+    bvh = api.BVH(ds, stream=stream)
+    lod = api.LevelOfDetail(ds, LOD_ORIGIN, args.lod_cell, stream=stream)
+    full = r.path_traced(ds, bvh, cam, n0, wl.max_bounces, rr_start=wl.rr_start, seed=0, first_sample=first0,
+                         want_stats=True)
+    cf, fimg = full["stats"].cpu().numpy().copy(), full["rgb"].cpu().numpy().astype(np.float64)
+    co = r.path_traced_lod(ds, bvh, lod, args.lod_from, cam, n0, wl.max_bounces, rr_start=wl.rr_start, seed=0,
+                           first_sample=first0, want_stats=True)
+    cl, limg = co["stats"].cpu().numpy().copy(), co["rgb"].cpu().numpy().astype(np.float64)
+    api.sync_status()
+
+    def per(c):
+        sec = max(1, int(c[1]))
+        return {"nodes": int(c[4]) / sec, "tests": int(c[5]) / sec, "blended": int(c[3]) / sec,
+                "secondary_segments": int(c[1])}
+
+    value = s_lod / t_lod
+    line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_lod, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"large final render with level of detail: {wl.name}; bounce segments k >= "
+                                   f"{args.lod_from} trace the surfels merged over {args.lod_cell} m cells",
+                       "surfels": host_scene.n, "merged_surfels": int(state.get("lod_n", merged.n)),
+                       "scale_factor": wl.scale_factor, "lod_cell_m": args.lod_cell, "lod_from": args.lod_from,
+                       "lod_origin": LOD_ORIGIN, "spp_per_step": slice_spp, "frame_spp": frame_spp,
+                       "step": "LBVH build + merge + merged LBVH build + render of one 64-sample slice",
+                       "l2": "flushed between steps (512 MB write)"},
+            "plain": {"value": s_plain / t_plain, "ms_per_step": ms_plain,
+                      "step": "LBVH build + render of the same slices"},
+            "speedup": (s_lod / t_lod) / (s_plain / t_plain),
+            "merge_ms": merge_ms,
+            "per_secondary_segment": {"plain": per(cf), "lod": per(cl)},
+            "image_first_slice": {"mean_plain": float(fimg.mean()), "mean_lod": float(limg.mean()),
+                                  "mean_rel_diff": float(abs(limg.mean() - fimg.mean()) / fimg.mean()),
+                                  "rel_rmse": float(np.sqrt(np.mean((limg - fimg) ** 2)) / fimg.mean())},
+            "gpu_launches": int(launches), "clocks": clk}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
+    if args.workload == "lod" and args.impl == "native":
+        run_lod(args)
+        return
     rank, world, local = dist_env()
     if args.workload == "serving":
         run_serving(args)

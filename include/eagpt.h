@@ -224,6 +224,64 @@ eagpt_status eagpt_render_path_traced_range(const eagpt_scene* scene, const eagp
                                             float* out_samples, int64_t* out_stats, void* workspace,
                                             size_t workspace_bytes, eagpt_stream_t stream);
 
+/* ------------------------------------------------------------------------
+ * Level of detail.  The paper names a level-of-detail hierarchy over the
+ * reconstruction as the way to fewer ray-Gaussian intersections per ray
+ * (limitations and the hit-count discussion: fewer Gaussians, fewer hits
+ * per ray, a faster render) and gives no algorithm.  This library's reading:
+ *
+ * eagpt_build_lod(): merges the surfels of `scene` group by group.  A
+ *   surfel's group is (the cell of a uniform grid with corner `origin` (host,
+ *   3 floats) and edge `cell_size` holding its centre p, the coordinate axis
+ *   its normal is closest to, e > tau_E).  Cell coordinates
+ *   floor((p - origin) * (1 / cell_size)) are taken in FP32 (each operation
+ *   rounded to nearest) and clamped to [0, 2^20 - 1]; the axis is the largest
+ *   |component| (lowest axis on a tie) of (2(xz + wy), 2(yz - wx),
+ *   (ww + zz) - (xx + yy)) from the raw quaternion (w, x, y, z), products
+ *   and sums rounded to FP32 in that order.  Each group becomes one surfel by
+ *   moment matching, with weights w_i = sigma_i s_u,i s_v,i (all-zero
+ *   weights: unit weights and sigma 0) and W = sum w_i:
+ *     p = weighted mean centre; n = normalised weighted sum of the normals
+ *     turned to the group axis' positive side; the union's second moment
+ *     sum w_i (d_i d_i^T + s_u,i^2 t_u,i t_u,i^T + s_v,i^2 t_v,i t_v,i^T) / W
+ *     about p, projected on the plane of n, gives t_u (principal axis),
+ *     t_v = n x t_u and s_u^2, s_v^2 (its variances along them);
+ *     sigma = W / (s_u s_v), the group's footprint (may exceed 1: alpha is
+ *     still clamped at alpha_max); rho, r, e = weighted means.
+ *   Merged surfels are written in ascending group key (cell x << 43 |
+ *   cell y << 23 | cell z << 3 | axis << 1 | emitter) to out's device arrays
+ *   (capacity out->n >= scene->n surfels, else EAGPT_ERR_OUT_OF_MEMORY);
+ *   out_keys (device, nullable, 8-byte aligned) receives the keys.  The
+ *   group count is written to *out_count (host): the call synchronises
+ *   `stream` once to read it.  out->n and out->version are not modified.
+ *   workspace: device, eagpt_lod_workspace_bytes(scene->n) bytes, 256-byte
+ *   aligned.  Positions must be finite and scales positive.
+ *   EAGPT_ERR_INVALID_ARGUMENT for a non-finite origin or a cell_size that
+ *   is not positive and finite (with a finite inverse).
+ *
+ * eagpt_render_path_traced_lod(): eagpt_render_path_traced_range() (Eq. 8)
+ *   in which the bounce segments k >= lod_from_bounce (k = 1 is the segment
+ *   after the first reflection) trace lod_scene through lod_bvh (built by
+ *   eagpt_build_bvh() over the first *out_count merged surfels); the primary
+ *   segment and the bounce segments k < lod_from_bounce trace scene.  With
+ *   lod_from_bounce > max_bounces the image is the plain render's, bit for
+ *   bit.  EAGPT_ERR_NOT_SUPPORTED with EAGPT_FLAG_EMITTER_SAMPLING;
+ *   EAGPT_ERR_INVALID_ARGUMENT if lod_from_bounce < 1; lod_bvh is checked
+ *   against lod_scene as bvh against scene.  Other arguments, buffers and
+ *   errors as in eagpt_render_path_traced_range().
+ * ------------------------------------------------------------------------ */
+size_t eagpt_lod_workspace_bytes(int64_t n);
+eagpt_status eagpt_build_lod(const eagpt_scene* scene, const eagpt_params* params, const float origin[3],
+                             float cell_size, eagpt_scene_mut* out, uint64_t* out_keys, int64_t* out_count,
+                             void* workspace, size_t workspace_bytes, eagpt_stream_t stream);
+eagpt_status eagpt_render_path_traced_lod(const eagpt_scene* scene, const eagpt_bvh* bvh,
+                                          const eagpt_scene* lod_scene, const eagpt_bvh* lod_bvh,
+                                          int32_t lod_from_bounce, const eagpt_camera* cam,
+                                          const eagpt_params* params, int32_t first_sample, int32_t spp,
+                                          int32_t max_bounces, int32_t rr_start_bounce, uint64_t seed,
+                                          float* out_rgb, float* out_aux, float* out_samples, int64_t* out_stats,
+                                          void* workspace, size_t workspace_bytes, eagpt_stream_t stream);
+
 
 /* ------------------------------------------------------------------------
  * Scene editing (the paper's edits: relight / toggle emitters, recolour,

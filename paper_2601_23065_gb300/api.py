@@ -154,6 +154,31 @@ class Renderer:
             r["stats"] = st
         return r
 
+    def path_traced_lod(self, scene: DeviceScene, bvh: BVH, lod: "LevelOfDetail", lod_from: int, cam: HostCamera,
+                        spp: int, max_bounces: int, rr_start: int = 2, seed: int = 0,
+                        prm: Optional[capi.Params] = None, want_samples=False, want_stats=False,
+                        out: Optional[torch.Tensor] = None, stream=None, first_sample: int = 0):
+        """Eq. 8 render whose bounce segments k >= lod_from trace the merged
+        surfels of ``lod``; returns dict(rgb[, samples][, stats])."""
+        c = camera(cam)
+        prm = prm or bvh.params
+        ws = self._workspace(c, spp, 1)
+        H, W = cam.height, cam.width
+        rgb = out if out is not None else torch.empty((H, W, 3), dtype=torch.float32, device=self.device)
+        smp = torch.empty((H, W, spp, 3), dtype=torch.float32, device=self.device) if want_samples else None
+        st = torch.zeros(16, dtype=torch.int64, device=self.device) if want_stats else None
+        capi.check(capi.lib().eagpt_render_path_traced_lod(
+            ctypes.byref(scene.c()), ctypes.byref(bvh.c()), ctypes.byref(lod.scene.c()), ctypes.byref(lod.bvh.c()),
+            int(lod_from), ctypes.byref(c), ctypes.byref(prm), int(first_sample), int(spp), int(max_bounces),
+            int(rr_start), ctypes.c_uint64(int(seed)), _ptr(rgb), None, _ptr(smp), _ptr(st), _ptr(ws), ws.numel(),
+            _stream(stream)))
+        r = {"rgb": rgb}
+        if want_samples:
+            r["samples"] = smp
+        if want_stats:
+            r["stats"] = st
+        return r
+
     def segments(self, stream=None):
         """(primary, secondary) segments traced by this renderer's last render
         (synchronises the stream)."""
@@ -196,6 +221,46 @@ class Renderer:
         if want_samples:
             r["samples"] = smp
         return r
+
+
+def build_lod(scene: DeviceScene, origin, cell_size: float, prm: Optional[capi.Params] = None, stream=None,
+              want_keys=False):
+    """Merged surfels of the level of detail (eagpt_build_lod): returns
+    (DeviceScene of the merged surfels[, keys int64 tensor]).  Synchronises
+    the stream once (the group count is read back)."""
+    prm = prm or params()
+    dev = scene.t["pos"].device
+    n = scene.n
+    out = {k: torch.empty((n, SHAPES[k]) if SHAPES[k] > 1 else (n,), dtype=torch.float32, device=dev)
+           for k in FIELDS}
+    keys = torch.empty(n, dtype=torch.int64, device=dev) if want_keys else None
+    ws = torch.empty(max(capi.lib().eagpt_lod_workspace_bytes(n), 256), dtype=torch.uint8, device=dev)
+    o = DeviceScene(out).c()
+    org = (capi.c_f * 3)(*[float(v) for v in origin])
+    count = capi.c_i64(0)
+    capi.check(capi.lib().eagpt_build_lod(ctypes.byref(scene.c()), ctypes.byref(prm), org, float(cell_size),
+                                          ctypes.byref(o), _ptr(keys), ctypes.byref(count), _ptr(ws), ws.numel(),
+                                          _stream(stream)))
+    m = int(count.value)
+    merged = DeviceScene({k: v[:m].contiguous() for k, v in out.items()})
+    return (merged, keys[:m]) if want_keys else merged
+
+
+class LevelOfDetail:
+    """Merged surfels (build_lod) and their BVH, for path_traced_lod."""
+
+    def __init__(self, scene: DeviceScene, origin, cell_size: float, prm: Optional[capi.Params] = None,
+                 stream=None):
+        self.origin, self.cell_size = tuple(float(v) for v in origin), float(cell_size)
+        self.scene = build_lod(scene, origin, cell_size, prm, stream)
+        self.bvh = BVH(self.scene, prm, stream)
+
+    @classmethod
+    def of(cls, scene: DeviceScene, bvh: BVH) -> "LevelOfDetail":
+        """A level of detail made of a given scene and its BVH."""
+        lod = cls.__new__(cls)
+        lod.origin, lod.cell_size, lod.scene, lod.bvh = None, None, scene, bvh
+        return lod
 
 
 def trace_rays(scene: DeviceScene, bvh: BVH, rays: torch.Tensor, mode: int = 0, max_hits: int = 0,

@@ -118,6 +118,10 @@ SIGNATURES = {
     "eagpt_render_segments": (c_i32, [c_vp, c_vp, c_vp]),
     "eagpt_render_path_traced_range": (c_i32, [P(Scene), P(Bvh), P(Camera), P(Params), c_i32, c_i32, c_i32, c_i32,
                                                c_u64, c_vp, c_vp, c_vp, c_vp, c_vp, c_sz, c_vp]),
+    "eagpt_lod_workspace_bytes": (c_sz, [c_i64]),
+    "eagpt_build_lod": (c_i32, [P(Scene), P(Params), P(c_f), c_f, P(Scene), c_vp, P(c_i64), c_vp, c_sz, c_vp]),
+    "eagpt_render_path_traced_lod": (c_i32, [P(Scene), P(Bvh), P(Scene), P(Bvh), c_i32, P(Camera), P(Params), c_i32,
+                                             c_i32, c_i32, c_i32, c_u64, c_vp, c_vp, c_vp, c_vp, c_vp, c_sz, c_vp]),
     "eagpt_trace_rays": (c_i32, [P(Scene), P(Bvh), P(Params), c_i32, c_vp, c_i64, c_vp, c_vp, c_i32, c_vp, c_vp]),
     "eagpt_select_scratch_bytes": (c_sz, [c_i64]),
     "eagpt_select": (c_i32, [P(Scene), c_i32, P(c_f), c_vp, c_i64, c_vp, c_vp, c_sz, c_vp]),

@@ -192,7 +192,8 @@ static eagpt_status render_common(const eagpt_scene* scene, const eagpt_bvh* bvh
                                   const eagpt_params* params, int kind, int32_t spp, int32_t max_bounces,
                                   int32_t rr_start, uint64_t seed, float* out_rgb, float* out_aux, float* out_samples,
                                   int64_t* out_stats, void* ws, size_t ws_bytes, eagpt_stream_t stream,
-                                  float* out_li = nullptr, float4* sb_cache = nullptr, int32_t first_sample = 0) {
+                                  float* out_li = nullptr, float4* sb_cache = nullptr, int32_t first_sample = 0,
+                                  const eagpt_bvh* lod_bvh = nullptr, int32_t lod_from = 0) {
   eagpt_status s;
   if ((s = check_scene(scene)) != EAGPT_OK) return s;
   if ((s = check_params(params)) != EAGPT_OK) return s;
@@ -228,6 +229,10 @@ static eagpt_status render_common(const eagpt_scene* scene, const eagpt_bvh* bvh
   a.ws = ws;
   a.ws_bytes = ws_bytes;
   a.sb_cache = sb_cache;
+  if (lod_bvh) {
+    a.bvh_lod = make_view(*lod_bvh);
+    a.lod_from = lod_from;
+  }
   cudaError_t e = launch_render(a, (cudaStream_t)stream, nullptr);
   if (e != cudaSuccess) return cuda_fail(e, "render launch");
   return EAGPT_OK;
@@ -289,6 +294,60 @@ eagpt_status eagpt_render_path_traced_range(const eagpt_scene* scene, const eagp
                                             size_t workspace_bytes, eagpt_stream_t stream) {
   return render_common(scene, bvh, cam, params, 1, spp, max_bounces, rr_start_bounce, seed, out_rgb, out_aux,
                        out_samples, out_stats, workspace, workspace_bytes, stream, nullptr, nullptr, first_sample);
+}
+
+eagpt_status eagpt_render_path_traced_lod(const eagpt_scene* scene, const eagpt_bvh* bvh,
+                                          const eagpt_scene* lod_scene, const eagpt_bvh* lod_bvh,
+                                          int32_t lod_from_bounce, const eagpt_camera* cam,
+                                          const eagpt_params* params, int32_t first_sample, int32_t spp,
+                                          int32_t max_bounces, int32_t rr_start_bounce, uint64_t seed,
+                                          float* out_rgb, float* out_aux, float* out_samples, int64_t* out_stats,
+                                          void* workspace, size_t workspace_bytes, eagpt_stream_t stream) {
+  eagpt_status s;
+  if ((s = check_params(params)) != EAGPT_OK) return s;
+  if (params->flags & EAGPT_FLAG_EMITTER_SAMPLING)
+    return fail(EAGPT_ERR_NOT_SUPPORTED, "the level-of-detail render has no emitter sampling%s");
+  if (lod_from_bounce < 1) return fail(EAGPT_ERR_INVALID_ARGUMENT, "lod_from_bounce must be >= 1%s");
+  if ((s = check_scene(lod_scene)) != EAGPT_OK) return s;
+  if ((s = check_bvh(lod_bvh, lod_scene, params)) != EAGPT_OK) return s;
+  return render_common(scene, bvh, cam, params, 1, spp, max_bounces, rr_start_bounce, seed, out_rgb, out_aux,
+                       out_samples, out_stats, workspace, workspace_bytes, stream, nullptr, nullptr, first_sample,
+                       lod_bvh, lod_from_bounce);
+}
+
+size_t eagpt_lod_workspace_bytes(int64_t n) { return n < 0 ? 0 : lod_workspace_bytes(n); }
+
+eagpt_status eagpt_build_lod(const eagpt_scene* scene, const eagpt_params* params, const float origin[3],
+                             float cell_size, eagpt_scene_mut* out, uint64_t* out_keys, int64_t* out_count,
+                             void* workspace, size_t workspace_bytes, eagpt_stream_t stream) {
+  eagpt_status s;
+  if ((s = check_scene(scene)) != EAGPT_OK) return s;
+  if ((s = check_params(params)) != EAGPT_OK) return s;
+  if (!origin || !out_count || !out) return fail(EAGPT_ERR_INVALID_ARGUMENT, "origin, out and out_count are required%s");
+  for (int k = 0; k < 3; ++k)
+    if (!std::isfinite(origin[k])) return fail(EAGPT_ERR_INVALID_ARGUMENT, "origin must be finite%s");
+  const float inv_h = 1.0f / cell_size;
+  if (!(cell_size > 0.f) || !std::isfinite(cell_size) || !std::isfinite(inv_h))
+    return fail(EAGPT_ERR_INVALID_ARGUMENT, "cell_size must be positive and finite with a finite inverse%s");
+  if (out->n < scene->n)
+    return fail(EAGPT_ERR_OUT_OF_MEMORY, "out holds fewer surfels than the scene (capacity %s%lld)", "",
+                (long long)out->n);
+  if (scene->n > 0) {
+    float* optrs[7] = {out->pos, out->quat, out->scale, out->opacity, out->albedo, out->radiance, out->emissive};
+    for (int i = 0; i < 7; ++i)
+      if (!optrs[i] || !aligned(optrs[i], 4))
+        return fail(EAGPT_ERR_INVALID_ARGUMENT, "out arrays must be non-NULL and 4-byte aligned%s");
+    if (out_keys && !aligned(out_keys, 8)) return fail(EAGPT_ERR_INVALID_ARGUMENT, "out_keys must be 8-byte aligned%s");
+    if (!workspace || !aligned(workspace, 256))
+      return fail(EAGPT_ERR_INVALID_ARGUMENT, "workspace must be non-NULL and 256-byte aligned%s");
+    if (workspace_bytes < lod_workspace_bytes(scene->n))
+      return fail(EAGPT_ERR_OUT_OF_MEMORY, "workspace too small: need %s%lld bytes", "",
+                  (long long)lod_workspace_bytes(scene->n));
+  }
+  const cudaError_t e =
+      launch_lod(*scene, origin, inv_h, params->tau_E, *out, out_keys, workspace, out_count, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "level-of-detail merge");
+  return EAGPT_OK;
 }
 
 size_t eagpt_render_backward_workspace_bytes(const eagpt_camera* cam, int32_t spp) {

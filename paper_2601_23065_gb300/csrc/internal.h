@@ -39,6 +39,10 @@ struct RenderArgs {
   void* ws;
   size_t ws_bytes;
   float4* sb_cache;  // single bounce: per-sample secondary (R, T), sample-major, or NULL
+  // level of detail (path tracing without emitter sampling): bounce segments
+  // k >= lod_from trace bvh_lod; lod_from = 0 (the default) turns it off
+  BvhView bvh_lod;
+  int lod_from;
 };
 
 struct RenderLayout {
@@ -88,6 +92,13 @@ uint32_t take_errors_tree();
 uint32_t take_errors_edit();
 uint32_t take_errors_serve();
 uint32_t take_errors_optim();
+
+// lod.cu: merged surfels of the level of detail (group keys, sort, merge);
+// reads the group count back to *out_count (synchronises the stream)
+size_t lod_workspace_bytes(int64_t n);
+cudaError_t launch_lod(const eagpt_scene& sc, const float origin[3], float inv_h, float tau_E,
+                       const eagpt_scene_mut& out, uint64_t* out_keys, void* ws, int64_t* out_count,
+                       cudaStream_t st);
 
 // edit.cu
 cudaError_t launch_select(const eagpt_scene& sc, int shape, const float* v, int32_t* out, int64_t capacity,

@@ -631,7 +631,10 @@ static cudaError_t render_impl(const RenderArgs& a, cudaStream_t st, int* launch
                                                                         sa, q[(k - 1) & 1], q[k & 1], counters, slots,
                                                                         a.out_stats, a.sb_cache));
       } else {
-        EAGPT_LAUNCH(st, "k_bounce", k_bounce_r<kCount, false><<<bounce_grid, kBlock, 0, st>>>(a.bvh, a.C, a.kind, k, B, a.rr_start, a.seed, npix,
+        // with a level of detail, bounce segments k >= lod_from trace the
+        // merged surfels
+        const BvhView& bk = a.lod_from > 0 && k >= a.lod_from ? a.bvh_lod : a.bvh;
+        EAGPT_LAUNCH(st, "k_bounce", k_bounce_r<kCount, false><<<bounce_grid, kBlock, 0, st>>>(bk, a.C, a.kind, k, B, a.rr_start, a.seed, npix,
                                                                   sa, q[(k - 1) & 1], q[k & 1], counters, slots,
                                                                   a.out_stats, nullptr));
       }

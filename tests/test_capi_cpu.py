@@ -115,3 +115,60 @@ def test_sample_cache_argument_checks(lib):
     assert bwd(ctypes.byref(sc), ctypes.byref(bvh), ctypes.byref(cam), ctypes.byref(p), 4, 0, rgb, None,
                ctypes.byref(g), ws, 1 << 20, None) == 1
     assert b"sample_cache" in lib.eagpt_last_error()
+
+
+def test_level_of_detail_argument_checks(lib):
+    """The level-of-detail entry points: workspace size, the checks made
+    before any launch (grid, capacity, emitter sampling, lod_from, stale
+    merged BVH), and an empty scene, which merges to nothing without a
+    launch."""
+    from paper_2601_23065_gb300 import capi
+    assert lib.eagpt_lod_workspace_bytes(1000) >= 1000 * 4 * 7
+    assert lib.eagpt_lod_workspace_bytes(-1) == 0
+    p = capi.default_params()
+    sc = capi.Scene()
+    out = capi.Scene()
+    org = (ctypes.c_float * 3)(0.0, 0.0, 0.0)
+    cnt = ctypes.c_int64(-1)
+    ws = ctypes.c_void_p(256)
+    build = lib.eagpt_build_lod
+    for h in (0.0, -1.0, float("inf"), float("nan"), 1e-45):
+        assert build(ctypes.byref(sc), ctypes.byref(p), org, h, ctypes.byref(out), None, ctypes.byref(cnt), ws,
+                     1 << 20, None) == 1
+        assert b"cell_size" in lib.eagpt_last_error()
+    bad = (ctypes.c_float * 3)(0.0, float("inf"), 0.0)
+    assert build(ctypes.byref(sc), ctypes.byref(p), bad, 0.1, ctypes.byref(out), None, ctypes.byref(cnt), ws,
+                 1 << 20, None) == 1
+    assert build(ctypes.byref(sc), ctypes.byref(p), org, 0.1, ctypes.byref(out), None, None, ws, 1 << 20, None) == 1
+    assert build(ctypes.byref(sc), ctypes.byref(p), org, 0.1, ctypes.byref(out), None, ctypes.byref(cnt), ws,
+                 1 << 20, None) == 0
+    assert cnt.value == 0
+    buf = (ctypes.c_float * 64)()
+    addr = ctypes.addressof(buf)
+    for k in ("pos", "quat", "scale", "opacity", "albedo", "radiance", "emissive"):
+        setattr(sc, k, addr)
+    sc.n, out.n = 5, 4
+    assert build(ctypes.byref(sc), ctypes.byref(p), org, 0.1, ctypes.byref(out), None, ctypes.byref(cnt), ws,
+                 1 << 20, None) == 2
+    assert b"capacity" in lib.eagpt_last_error()
+    # render
+    sc.n = 0
+    sc.version = 3
+    lsc = capi.Scene()
+    lsc.version = 7
+    bvh, lbvh = capi.Bvh(), capi.Bvh()
+    bvh.n, bvh.scene_version, bvh.support_sigma = 0, 3, 3.0
+    lbvh.n, lbvh.scene_version, lbvh.support_sigma = 0, 6, 3.0
+    cam = capi.Camera(8, 8, 4.0, 4.0, 4.0, 4.0)
+    rgb = ctypes.c_void_p(256)
+    render = lib.eagpt_render_path_traced_lod
+
+    def call(prm, lod_from):
+        return render(ctypes.byref(sc), ctypes.byref(bvh), ctypes.byref(lsc), ctypes.byref(lbvh), lod_from,
+                      ctypes.byref(cam), ctypes.byref(prm), 0, 4, 3, 2, 0, rgb, None, None, None, ws, 1 << 20, None)
+
+    mis = capi.default_params()
+    mis.flags = capi.FLAG_EMITTER_SAMPLING
+    assert call(mis, 2) == 6
+    assert call(p, 0) == 1 and b"lod_from" in lib.eagpt_last_error()
+    assert call(p, 2) == 4  # the merged BVH was built for another version of the merged scene
