@@ -59,8 +59,10 @@ def parse():
     ap.add_argument("--adjoint-retrace", action="store_true",
                     help="diff: the adjoint re-traces every secondary segment instead of reading the forward's cache")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--lod-cell", type=float, default=0.05, help="lod: grid cell edge of the surfel groups (m)")
-    ap.add_argument("--lod-from", type=int, default=2, help="lod: first bounce that traces the merged surfels")
+    ap.add_argument("--lod-cell", default="0.05",
+                    help="lod: grid cell edge of the surfel groups (m); a comma-separated list sweeps")
+    ap.add_argument("--lod-from", default="2",
+                    help="lod: first bounce that traces the merged surfels; a comma-separated list sweeps")
     return ap.parse_args()
 
 
@@ -1000,10 +1002,15 @@ LOD_ORIGIN = (-7.6125, -2.1125, -1.6125)
 
 def run_lod(args):
     """Level of detail on the large final render: plain steps and merged
-    steps (the bounce segments from --lod-from on trace the merged surfels)
+    steps (the bounce segments from lod_from on trace the merged surfels)
     timed in the same process on the same 64-sample slices; each merged step
-    also rebuilds the merged surfels and their BVH.  The images of the first
-    slice are compared after the timed spans."""
+    also rebuilds the merged surfels and their BVH.  --lod-cell and
+    --lod-from take comma-separated lists: the first pair is the line's
+    value, every pair is reported under "sweep".  Accuracy is read after the
+    timed spans on the first slice: the image mean, and the RMS difference of
+    32x32-pixel block means (relative to the image mean) against the plain
+    render, beside the same figure for two plain renders of different seeds
+    (the Monte Carlo noise floor of that comparison)."""
     import numpy as np
     import torch
 
@@ -1026,7 +1033,9 @@ def run_lod(args):
     L = capi.lib()
     img = torch.empty((cam.height, cam.width, 3), dtype=torch.float32, device=dev)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-    state = {}
+    cells = [float(v) for v in str(args.lod_cell).split(",")]
+    froms = [int(v) for v in str(args.lod_from).split(",")]
+    pairs = [(h, f) for h in cells for f in froms]
 
     def plain_step(k):
         first, n = slices[k % len(slices)]
@@ -1034,13 +1043,14 @@ def run_lod(args):
         r.path_traced(ds, bvh, cam, n, wl.max_bounces, rr_start=wl.rr_start, seed=0, stream=stream,
                       first_sample=first, out=img)
 
-    def lod_step(k):
-        first, n = slices[k % len(slices)]
-        bvh = api.BVH(ds, stream=stream)
-        lod = api.LevelOfDetail(ds, LOD_ORIGIN, args.lod_cell, stream=stream)
-        state["lod_n"] = lod.scene.n
-        r.path_traced_lod(ds, bvh, lod, args.lod_from, cam, n, wl.max_bounces, rr_start=wl.rr_start, seed=0,
-                          stream=stream, first_sample=first, out=img)
+    def lod_step(h, f):
+        def step(k):
+            first, n = slices[k % len(slices)]
+            bvh = api.BVH(ds, stream=stream)
+            lod = api.LevelOfDetail(ds, LOD_ORIGIN, h, stream=stream)
+            r.path_traced_lod(ds, bvh, lod, f, cam, n, wl.max_bounces, rr_start=wl.rr_start, seed=0,
+                              stream=stream, first_sample=first, out=img)
+        return step
 
     def timed(step):
         for k in range(args.warmup):
@@ -1058,61 +1068,76 @@ def run_lod(args):
             times.append(a.elapsed_time(b))
             p, q = r.segments(stream)
             segs += p + q
-        return sum(times) / 1e3, segs, sum(times) / len(times)
-
-    clocks = ClockSampler(0)
-    clocks.start()
-    launches0 = L.eagpt_launch_count()
-    t_plain, s_plain, ms_plain = timed(plain_step)
-    t_lod, s_lod, ms_lod = timed(lod_step)
-    launches = L.eagpt_launch_count() - launches0
-    clk = clocks.stop()
-    api.sync_status()
-    # merge alone (preprocess of the merged scene: groups, sort, moments)
-    a = torch.cuda.Event(enable_timing=True)
-    b = torch.cuda.Event(enable_timing=True)
-    a.record(stream)
-    merged = api.build_lod(ds, LOD_ORIGIN, args.lod_cell, stream=stream)
-    b.record(stream)
-    b.synchronize()
-    merge_ms = a.elapsed_time(b)
-    # work per secondary segment (counting variant, first slice) and images
-    first0, n0 = slices[0]
-    bvh = api.BVH(ds, stream=stream)
-    lod = api.LevelOfDetail(ds, LOD_ORIGIN, args.lod_cell, stream=stream)
-    full = r.path_traced(ds, bvh, cam, n0, wl.max_bounces, rr_start=wl.rr_start, seed=0, first_sample=first0,
-                         want_stats=True)
-    cf, fimg = full["stats"].cpu().numpy().copy(), full["rgb"].cpu().numpy().astype(np.float64)
-    co = r.path_traced_lod(ds, bvh, lod, args.lod_from, cam, n0, wl.max_bounces, rr_start=wl.rr_start, seed=0,
-                           first_sample=first0, want_stats=True)
-    cl, limg = co["stats"].cpu().numpy().copy(), co["rgb"].cpu().numpy().astype(np.float64)
-    api.sync_status()
+        return segs / (sum(times) / 1e3), sum(times) / len(times)
 
     def per(c):
         sec = max(1, int(c[1]))
         return {"nodes": int(c[4]) / sec, "tests": int(c[5]) / sec, "blended": int(c[3]) / sec,
                 "secondary_segments": int(c[1])}
 
-    value = s_lod / t_lod
-    line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": 1, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms_lod, "higher_is_better": True, "scaling": "weak",
+    def blocks(x, b=32):
+        H, W = (x.shape[0] // b) * b, (x.shape[1] // b) * b
+        return x[:H, :W].reshape(H // b, b, W // b, b, 3).mean((1, 3))
+
+    first0, n0 = slices[0]
+
+    def first_slice(render, seed=0):
+        out = render(seed)
+        api.sync_status()
+        return out["stats"].cpu().numpy().copy(), out["rgb"].cpu().numpy().astype(np.float64)
+
+    clocks = ClockSampler(0)
+    clocks.start()
+    launches0 = L.eagpt_launch_count()
+    v_plain, ms_plain = timed(plain_step)
+    timed_pairs = [timed(lod_step(h, f)) for h, f in pairs]
+    launches = L.eagpt_launch_count() - launches0
+    clk = clocks.stop()
+    api.sync_status()
+
+    bvh = api.BVH(ds, stream=stream)
+    cf, fimg = first_slice(lambda sd: r.path_traced(ds, bvh, cam, n0, wl.max_bounces, rr_start=wl.rr_start, seed=sd,
+                                                    first_sample=first0, want_stats=True))
+    _, fimg2 = first_slice(lambda sd: r.path_traced(ds, bvh, cam, n0, wl.max_bounces, rr_start=wl.rr_start, seed=sd,
+                                                    first_sample=first0, want_stats=True), seed=1)
+    mean_f = float(fimg.mean())
+    noise = float(np.sqrt(np.mean((blocks(fimg2) - blocks(fimg)) ** 2)) / mean_f)
+    sweep = []
+    for (h, f), (v, ms) in zip(pairs, timed_pairs):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        lod = api.LevelOfDetail(ds, LOD_ORIGIN, h, stream=stream)
+        b.record(stream)
+        b.synchronize()
+        build_ms = a.elapsed_time(b)
+        cl, limg = first_slice(lambda sd: r.path_traced_lod(ds, bvh, lod, f, cam, n0, wl.max_bounces,
+                                                            rr_start=wl.rr_start, seed=sd, first_sample=first0,
+                                                            want_stats=True))
+        sweep.append({"lod_cell_m": h, "lod_from": f, "merged_surfels": lod.scene.n, "value": v, "ms_per_step": ms,
+                      "speedup": v / v_plain, "merge_and_bvh_ms": build_ms,
+                      "per_secondary_segment": per(cl),
+                      "image_mean_rel_diff": float((limg.mean() - mean_f) / mean_f),
+                      "block_rel_rmse": float(np.sqrt(np.mean((blocks(limg) - blocks(fimg)) ** 2)) / mean_f)})
+    head = sweep[0]
+    line = {"metric": METRIC, "value": head["value"], "unit": METRIC, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"large final render with level of detail: {wl.name}; bounce segments k >= "
-                                   f"{args.lod_from} trace the surfels merged over {args.lod_cell} m cells",
-                       "surfels": host_scene.n, "merged_surfels": int(state.get("lod_n", merged.n)),
-                       "scale_factor": wl.scale_factor, "lod_cell_m": args.lod_cell, "lod_from": args.lod_from,
-                       "lod_origin": LOD_ORIGIN, "spp_per_step": slice_spp, "frame_spp": frame_spp,
+                                   f"{head['lod_from']} trace the surfels merged over {head['lod_cell_m']} m cells",
+                       "surfels": host_scene.n, "merged_surfels": head["merged_surfels"],
+                       "scale_factor": wl.scale_factor, "lod_cell_m": head["lod_cell_m"],
+                       "lod_from": head["lod_from"], "lod_origin": LOD_ORIGIN, "spp_per_step": slice_spp,
+                       "frame_spp": frame_spp,
                        "step": "LBVH build + merge + merged LBVH build + render of one 64-sample slice",
                        "l2": "flushed between steps (512 MB write)"},
-            "plain": {"value": s_plain / t_plain, "ms_per_step": ms_plain,
-                      "step": "LBVH build + render of the same slices"},
-            "speedup": (s_lod / t_lod) / (s_plain / t_plain),
-            "merge_ms": merge_ms,
-            "per_secondary_segment": {"plain": per(cf), "lod": per(cl)},
-            "image_first_slice": {"mean_plain": float(fimg.mean()), "mean_lod": float(limg.mean()),
-                                  "mean_rel_diff": float(abs(limg.mean() - fimg.mean()) / fimg.mean()),
-                                  "rel_rmse": float(np.sqrt(np.mean((limg - fimg) ** 2)) / fimg.mean())},
-            "gpu_launches": int(launches), "clocks": clk}
+            "plain": {"value": v_plain, "ms_per_step": ms_plain, "step": "LBVH build + render of the same slices",
+                      "per_secondary_segment": per(cf)},
+            "speedup": head["speedup"],
+            "accuracy": {"what": "first 64-sample slice: image mean and RMS of 32x32 block-mean differences against "
+                                 "the plain render, relative to the plain image mean",
+                         "plain_mean": mean_f, "noise_floor_block_rel_rmse": noise},
+            "sweep": sweep, "gpu_launches": int(launches), "clocks": clk}
     print(json.dumps(line), flush=True)
 
 
