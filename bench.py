@@ -271,7 +271,8 @@ def run_reference(args, rank, world):
                 "e2e": {"value": c["value"], "unit": c["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(line), flush=True)
         return
-    wl = S.workload(args.workload)
+    lod = args.workload == "lod"
+    wl = S.workload("large" if lod else args.workload)
     if args.spp:
         wl.spp = args.spp
     scene = wl.scene_fn()
@@ -280,12 +281,24 @@ def run_reference(args, rank, world):
     spp = cpu_sample_spp(wl)
     npix = wl.camera.width * wl.camera.height
     rng = np.random.default_rng(321)
+    if lod:
+        # the oracle's own merge of the same groups (untimed set-up), then its
+        # level-of-detail render
+        from oracle import lod as OL
+        lod_cell = float(str(args.lod_cell).split(",")[0])
+        lod_from = int(str(args.lod_from).split(",")[0])
+        merged = O.OracleScene(OL.to_scene(OL.merge(scene, LOD_ORIGIN, lod_cell, with_members=False),
+                                           S.SurfelScene))
 
     def one(m):
         pix = rng.choice(npix, m, replace=False).astype(np.int32)
         t0 = time.perf_counter()
-        out = O.render(osc, wl.camera, pix, "pt", spp, max_bounces=wl.max_bounces, rr_start=wl.rr_start, seed=0,
-                       params=O.Params(fp32_eps=0.0), n_threads=n_threads)
+        if lod:
+            out = O.render_lod(osc, merged, lod_from, wl.camera, pix, spp, max_bounces=wl.max_bounces,
+                               rr_start=wl.rr_start, seed=0, params=O.Params(fp32_eps=0.0), n_threads=n_threads)
+        else:
+            out = O.render(osc, wl.camera, pix, "pt", spp, max_bounces=wl.max_bounces, rr_start=wl.rr_start,
+                           seed=0, params=O.Params(fp32_eps=0.0), n_threads=n_threads)
         return int(out["segments"].sum()), time.perf_counter() - t0
 
     for _ in range(max(0, args.warmup)):
@@ -301,7 +314,10 @@ def run_reference(args, rank, world):
     line = {"metric": METRIC, "value": v, "unit": METRIC, "impl": "reference", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": wl.name, "scale_factor": wl.scale_factor},
+            "config": ({"workload": wl.name, "scale_factor": wl.scale_factor} if not lod else
+                       {"workload": f"large final render with level of detail: {wl.name}; bounce segments k >= "
+                                    f"{lod_from} trace the surfels merged over {lod_cell} m cells",
+                        "scale_factor": wl.scale_factor, "lod_cell_m": lod_cell, "lod_from": lod_from}),
             "cpu_baseline": {"value": v, "unit": METRIC, "cores": n_threads, "kind": "oracle", "cpu": host_cpu(),
                              "sample": sample},
             "e2e": {"value": v, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}

@@ -137,10 +137,93 @@ def merge_group(p, tu, tv, n, scale, sigma, rho, r, e, axis):
     }
 
 
-def merge(scene, origin, cell_size, tau_E=0.1):
+def quat_from_frames(tu, tv, n):
+    """quat_from_frame for every row of (m, 3) frames (the same branch rule,
+    row by row)."""
+    R = np.stack([tu, tv, n], 2)  # R[g, :, j] = column j
+    r = lambda i, j: R[:, i, j]
+    tr = r(0, 0) + r(1, 1) + r(2, 2)
+    k = np.argmax(np.stack([tr, r(0, 0), r(1, 1), r(2, 2)], 1), 1)
+    q = np.zeros((len(tr), 4))
+    with np.errstate(invalid="ignore", divide="ignore"):
+        cand = []
+        s = 2.0 * np.sqrt(1.0 + tr)
+        cand.append([0.25 * s, (r(2, 1) - r(1, 2)) / s, (r(0, 2) - r(2, 0)) / s, (r(1, 0) - r(0, 1)) / s])
+        s = 2.0 * np.sqrt(1.0 + r(0, 0) - r(1, 1) - r(2, 2))
+        cand.append([(r(2, 1) - r(1, 2)) / s, 0.25 * s, (r(0, 1) + r(1, 0)) / s, (r(0, 2) + r(2, 0)) / s])
+        s = 2.0 * np.sqrt(1.0 + r(1, 1) - r(0, 0) - r(2, 2))
+        cand.append([(r(0, 2) - r(2, 0)) / s, (r(0, 1) + r(1, 0)) / s, 0.25 * s, (r(1, 2) + r(2, 1)) / s])
+        s = 2.0 * np.sqrt(1.0 + r(2, 2) - r(0, 0) - r(1, 1))
+        cand.append([(r(1, 0) - r(0, 1)) / s, (r(0, 2) + r(2, 0)) / s, (r(1, 2) + r(2, 1)) / s, 0.25 * s])
+    for b in range(4):
+        sel = k == b
+        q[sel] = np.stack(cand[b], 1)[sel]
+    return q
+
+
+def merge(scene, origin, cell_size, tau_E=0.1, with_members=True):
     """The merged scene of ``scene`` (a SurfelScene): dict of FP64 arrays in
     ascending key order, plus 'keys' (uint64), 'cov' (m, 3, 3), 'normal'
-    (m, 3), 'weight' (m,) and 'members' (list of index arrays, ascending)."""
+    (m, 3), 'weight' (m,) and, with_members, 'members' (list of index
+    arrays, ascending).  Every group at once: the sums of merge_group taken
+    per group with np.add.reduceat over the key-sorted surfels, the
+    projected moments decomposed by a batched np.linalg.eigh; the same
+    definition, step for step, as merge_group (a test holds the two equal)."""
+    keys, axis = group_keys(scene.pos, scene.quat, scene.emissive, origin, cell_size, tau_E)
+    order = np.argsort(keys, kind="stable")
+    ks = keys[order]
+    N = len(ks)
+    if N == 0:
+        res = {k: np.zeros((0, 3)) for k in ("pos", "albedo", "radiance", "normal")}
+        res.update(quat=np.zeros((0, 4)), scale=np.zeros((0, 2)), opacity=np.zeros(0), emissive=np.zeros(0),
+                   cov=np.zeros((0, 3, 3)), weight=np.zeros(0), keys=ks)
+        if with_members:
+            res["members"] = []
+        return res
+    starts = np.flatnonzero(np.concatenate([[True], ks[1:] != ks[:-1]]))
+    ends = np.append(starts[1:], N)
+    gid = np.repeat(np.arange(len(starts)), ends - starts)
+    f64 = lambda a: np.asarray(a, np.float64)[order]
+    p, sc, sg = f64(scene.pos), f64(scene.scale), f64(scene.opacity)
+    rho, r, e = f64(scene.albedo), f64(scene.radiance), f64(scene.emissive)
+    tu, tv, n = frames(np.asarray(scene.quat)[order])
+    ax = axis[order]
+    seg = lambda x: np.add.reduceat(x, starts, axis=0)
+    w = sg * sc[:, 0] * sc[:, 1]
+    W = seg(w)
+    zero = ~(W > 0.0)
+    w = np.where(zero[gid], 1.0, w)
+    W = seg(w)
+    pc = seg(w[:, None] * p) / W[:, None]
+    flip = np.where(n[np.arange(N), ax] < 0.0, -1.0, 1.0)
+    nsum = seg((w * flip)[:, None] * n)
+    nc = nsum / np.linalg.norm(nsum, axis=1, keepdims=True)
+    d = p - pc[gid]
+    outer = lambda a: a[:, :, None] * a[:, None, :]
+    M = seg(w[:, None, None] * (outer(d) + sc[:, 0, None, None] ** 2 * outer(tu) + sc[:, 1, None, None] ** 2 * outer(tv)))
+    M /= W[:, None, None]
+    P = np.eye(3)[None] - outer(nc)
+    S = P @ M @ P
+    lam, vec = np.linalg.eigh(S)
+    v = vec[:, :, 2]
+    tuc = v - nc * (v * nc).sum(1, keepdims=True)
+    tuc /= np.linalg.norm(tuc, axis=1, keepdims=True)
+    tvc = np.cross(nc, tuc)
+    su = np.sqrt(np.maximum(lam[:, 2], 0.0))
+    sv = np.sqrt(np.maximum(np.einsum("gi,gij,gj->g", tvc, M, tvc), 0.0))
+    sig = np.where(zero, 0.0, W / (su * sv))
+    res = {"pos": pc, "quat": quat_from_frames(tuc, tvc, nc), "scale": np.stack([su, sv], 1), "opacity": sig,
+           "albedo": seg(w[:, None] * rho) / W[:, None], "radiance": seg(w[:, None] * r) / W[:, None],
+           "emissive": seg(w * e) / W, "cov": su[:, None, None] ** 2 * outer(tuc) + sv[:, None, None] ** 2 * outer(tvc),
+           "normal": nc, "weight": W, "keys": ks[starts]}
+    if with_members:
+        res["members"] = [order[a:b] for a, b in zip(starts, ends)]
+    return res
+
+
+def merge_by_group(scene, origin, cell_size, tau_E=0.1):
+    """merge() computed one group at a time with merge_group (the plain
+    form; slow on large scenes)."""
     keys, axis = group_keys(scene.pos, scene.quat, scene.emissive, origin, cell_size, tau_E)
     order = np.argsort(keys, kind="stable")
     ks = keys[order]

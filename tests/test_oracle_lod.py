@@ -276,3 +276,36 @@ def test_lod_render_rejects_emitter_sampling():
     cam = S.horizontal_camera(4, 4)
     with pytest.raises(RuntimeError):
         O.render_lod(sc, sc, 1, cam, np.arange(4, dtype=np.int32), 1, max_bounces=2, params=O.Params(mis=True))
+
+
+def test_vectorised_merge_equals_group_by_group():
+    """merge() (all groups at once) equals merge_by_group() (merge_group one
+    group at a time) on the tiny room: keys, members and every merged value,
+    the Gaussian through its covariance (also as rebuilt from the merged
+    quaternion and scales; the in-plane axis of a round group is arbitrary)."""
+    sc = S.tiny_room(4096)
+    for h in (0.05, 0.2):
+        a = L.merge(sc, (-0.6125,) * 3, h)
+        b = L.merge_by_group(sc, (-0.6125,) * 3, h)
+        assert np.array_equal(a["keys"], b["keys"])
+        assert all(np.array_equal(x, y) for x, y in zip(a["members"], b["members"]))
+        for k in ("pos", "scale", "opacity", "albedo", "radiance", "emissive", "normal", "weight"):
+            np.testing.assert_allclose(a[k], b[k], rtol=1e-12, atol=1e-15, err_msg=k)
+        big = np.abs(b["cov"]).max((1, 2), keepdims=True)
+        assert (np.abs(a["cov"] - b["cov"]) <= 1e-12 * big).all()
+        assert (np.abs(cov_of(a["quat"], a["scale"]) - b["cov"]) <= 1e-12 * big).all()
+
+
+def test_quaternions_of_many_frames_row_by_row():
+    """quat_from_frames() equals quat_from_frame() row by row, on random
+    frames that take every one of its four branches."""
+    rng = np.random.default_rng(8)
+    q = rng.normal(size=(400, 4))
+    q[:100, 0] *= 20
+    q[100:200, 1] *= 20
+    q[200:300, 2] *= 20
+    q[300:, 3] *= 20
+    tu, tv, n = L.frames(q)
+    many = L.quat_from_frames(tu, tv, n)
+    one = np.array([L.quat_from_frame(a, b, c) for a, b, c in zip(tu, tv, n)])
+    assert np.array_equal(many, one)
