@@ -227,8 +227,9 @@ eagpt_status eagpt_render_path_traced_range(const eagpt_scene* scene, const eagp
 /* ------------------------------------------------------------------------
  * Level of detail.  The paper names a level-of-detail hierarchy over the
  * reconstruction as the way to fewer ray-Gaussian intersections per ray
- * (limitations and the hit-count discussion: fewer Gaussians, fewer hits
- * per ray, a faster render) and gives no algorithm.  This library's reading:
+ * (Sec. 5, conclusion, and Appendix D, path tracing: fewer Gaussians, fewer
+ * hits per ray, a faster render) and gives no algorithm.  This library's
+ * reading:
  *
  * eagpt_build_lod(): merges the surfels of `scene` group by group.  A
  *   surfel's group is (the cell of a uniform grid with corner `origin` (host,
@@ -287,7 +288,8 @@ eagpt_status eagpt_render_path_traced_lod(const eagpt_scene* scene, const eagpt_
 
 /* ------------------------------------------------------------------------
  * Scene editing (the paper's edits: relight / toggle emitters, recolour,
- * move selected Gaussians; teaser and Sec. 5, selection by boxes).
+ * move selected Gaussians; teaser and Sec. 4.3; selection by boxes,
+ * Appendix D).
  *
  * eagpt_select(): indices of the surfels whose centre p lies in a shape, in
  *   increasing index order.  shape 0: box, params = (lo3, hi3); shape 1:

@@ -609,7 +609,7 @@ int ora_primary(const ora_scene* sc, const ora_camera* cam, const ora_params* pr
 /* emitter sampling with multiple importance sampling (path tracing, mis = 1)
  *
  * The paper names emitter importance sampling with MIS as future work
- * (Sec. 6 and the appendix on sampling); this is one exact form of it.  The
+ * (Sec. 5 and Appendix D, on sampling); this is one exact form of it.  The
  * blended radiance of a segment is a sum of per-surfel terms, R = sum_i w_i
  * r~_i (Eq. 2, w_i = T_{i-1} alpha_i), and each emitter term of the
  * one-bounce integral is estimated by two strategies combined with the power

@@ -4,8 +4,9 @@ TEST INFRASTRUCTURE ONLY: imported by ``tests/`` alone.  It shares no code
 with the CUDA path.
 
 The paper names a level-of-detail hierarchy over the reconstruction as the
-way to cut the ray-Gaussian intersections per ray (limitations, the hit-count
-discussion: fewer Gaussians gave fewer intersections and a faster render), and
+way to cut the ray-Gaussian intersections per ray (Sec. 5, conclusion, and
+Appendix D, path tracing: fewer Gaussians gave fewer intersections and a faster
+render), and
 gives no algorithm.  The reading this library implements, written out here:
 
 * Groups.  A surfel belongs to the group (cell, axis, emitter) where cell is

@@ -1,5 +1,6 @@
-// Scene edits (teaser and Sec. 5 of the paper: relighting, recolouring,
-// moving selected Gaussians; box selection) applied in place on the device,
+// Scene edits (teaser and Sec. 4.3 of the paper: relighting, recolouring,
+// moving selected Gaussians; box selection, Appendix D) applied in place on
+// the device,
 // followed by an update of the affected BVH records and a refit.
 //
 //   k_select       surfels whose centre lies in a box or a sphere -> ordered

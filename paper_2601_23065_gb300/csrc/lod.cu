@@ -1,8 +1,8 @@
 // Level of detail: merged surfels for the deeper bounces.
 //
 // The paper names a level-of-detail hierarchy over the reconstruction as the
-// way to fewer ray-Gaussian intersections per ray (limitations and the
-// hit-count discussion: fewer Gaussians, fewer hits, a faster render) and
+// way to fewer ray-Gaussian intersections per ray (Sec. 5, conclusion, and
+// Appendix D, path tracing: fewer Gaussians, fewer hits, a faster render) and
 // gives no algorithm.  The library's reading: surfels are grouped by
 // (grid cell of the centre, the coordinate axis the normal is closest to,
 // emitter class e > tau_E) and every group becomes one surfel by moment
