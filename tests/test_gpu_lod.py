@@ -38,7 +38,7 @@ def eg():
     return api
 
 
-def _check_groups(gpu, ref, sel=None):
+def _check_groups(gpu, ref):
     """Merged surfels of the GPU (dict of numpy arrays) against the oracle's
     merge (dict from oracle.lod.merge or merge_group), row by row."""
     n = len(ref["pos"])
