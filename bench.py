@@ -1016,7 +1016,7 @@ def run_render(args, rank, world, local):
 LOD_ORIGIN = (-7.6125, -2.1125, -1.6125)
 
 
-def run_lod(args):
+def run_lod(args, local=0):
     """Level of detail on the large final render: plain steps and merged
     steps (the bounce segments from lod_from on trace the merged surfels)
     timed in the same process on the same 64-sample slices; each merged step
@@ -1035,7 +1035,7 @@ def run_lod(args):
     from paper_2601_23065_gb300 import scenes as S
 
     build.build()
-    dev = torch.device("cuda", 0)
+    dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
     wl = S.workload("large")
     frame_spp = args.spp or wl.spp
@@ -1102,7 +1102,7 @@ def run_lod(args):
         api.sync_status()
         return out["stats"].cpu().numpy().copy(), out["rgb"].cpu().numpy().astype(np.float64)
 
-    clocks = ClockSampler(0)
+    clocks = ClockSampler(local)
     clocks.start()
     launches0 = L.eagpt_launch_count()
     v_plain, ms_plain = timed(plain_step)
@@ -1159,10 +1159,11 @@ def run_lod(args):
 
 def main():
     args = parse()
-    if args.workload == "lod" and args.impl == "native":
-        run_lod(args)
-        return
     rank, world, local = dist_env()
+    if args.workload == "lod" and args.impl == "native":
+        if rank == 0:  # a one-GPU comparison; other ranks have nothing to do
+            run_lod(args, local)
+        return
     if args.workload == "serving":
         run_serving(args)
         return
