@@ -309,3 +309,37 @@ def test_quaternions_of_many_frames_row_by_row():
     many = L.quat_from_frames(tu, tv, n)
     one = np.array([L.quat_from_frame(a, b, c) for a, b, c in zip(tu, tv, n)])
     assert np.array_equal(many, one)
+
+
+def test_merged_gaussian_matches_sampled_union():
+    """Moment matching checked by sampling: points drawn from every member's
+    Gaussian (in its own plane, N(0, s_u^2) along t_u and N(0, s_v^2) along
+    t_v about p), the member chosen with probability w_i / W, have a mean and
+    an in-plane second moment that the merged surfel's centre and covariance
+    must match within the sampling error (5 coplanar surfels of random
+    rotation, scale and opacity, 2e6 points)."""
+    rng = np.random.default_rng(21)
+    m = 5
+    th = rng.uniform(0, math.pi, m)
+    pos = np.column_stack([rng.uniform(0.40, 0.46, m), rng.uniform(0.40, 0.46, m), np.full(m, 0.45)])
+    scale = np.exp(rng.uniform(math.log(0.003), math.log(0.02), (m, 2)))
+    sigma = rng.uniform(0.5, 1.0, m)
+    sc = scene_of(pos, [qz(t) for t in th], scale, sigma)
+    g = L.merge(sc, (0, 0, 0), 0.5)
+    assert len(g["keys"]) == 1
+    p = sc.pos.astype(np.float64)
+    s = sc.scale.astype(np.float64)
+    w = sc.opacity.astype(np.float64) * s[:, 0] * s[:, 1]
+    tu, tv, _ = L.frames(sc.quat)
+    N = 2_000_000
+    who = rng.choice(m, N, p=w / w.sum())
+    a = rng.standard_normal(N) * s[who, 0]
+    b = rng.standard_normal(N) * s[who, 1]
+    x = p[who] + a[:, None] * tu[who] + b[:, None] * tv[who]
+    mean = x.mean(0)
+    d = x - mean
+    C = d.T @ d / N
+    spread = math.sqrt(np.trace(C))
+    assert np.abs(g["pos"][0] - mean).max() < 5 * spread / math.sqrt(N)
+    np.testing.assert_allclose(g["cov"][0][:2, :2], C[:2, :2], atol=6 * np.abs(C).max() * math.sqrt(2 / N))
+    assert np.abs(g["cov"][0][2]).max() < 1e-15 and np.abs(C[2]).max() < 1e-15
