@@ -258,7 +258,8 @@ eagpt_status eagpt_render_path_traced_range(const eagpt_scene* scene, const eagp
  *   out's arrays must not overlap the scene's (the merge reads every
  *   surfel of a group after earlier groups are written).  The result is
  *   deterministic: each group's sums run over its surfels in ascending
- *   index order, with no atomics.
+ *   index order (no floating-point atomics).  Of `params` (validated as
+ *   for every call) only tau_E is used.  Every buffer is caller-owned.
  *   workspace: device, eagpt_lod_workspace_bytes(scene->n) bytes, 256-byte
  *   aligned.  Positions must be finite and scales positive.
  *   EAGPT_ERR_INVALID_ARGUMENT for a non-finite origin or a cell_size that
